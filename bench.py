@@ -1,0 +1,306 @@
+"""Benchmark: exact samples/s of the pilot-wave sampler on one GB300.
+
+Workload (default): ideal QAOA p=2 MaxCut on the 6x6 grid (36 qubits), angles
+U[0, pi) from seed 2; one step = 10^5 exact samples drawn in launches of 4096
+chains (the sampler's whole hot path: every layer's contraction, readout and
+resampling). Prints one JSON line (see the design doc for the keys).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload grid6x6|n12|heavyhex400|grid8x8noisy] [--precision fp32|fp64]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import multiprocessing as mp
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "exact samples/s on 1 GB300 (mixed vs plain FP32, same accuracy); TC % of peak"
+
+# FP32 FMA peak of the part: 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+
+
+def workload(name):
+    import workloads as W
+    if name == "grid6x6":
+        return W.grid_6x6_p2(), 100000, 4096, "qaoa_p2_grid6x6 (36 qubits, ideal, 10^5 samples, B=4096)"
+    if name == "n12":
+        return W.maxcut_3reg_n12(), 10000, 256, "qaoa_p1_3reg_n12 (ideal, 10^4 samples, B=256)"
+    if name == "heavyhex400":
+        return W.heavy_hex_400_p1(), 100000, 16384, "qaoa_p1_heavyhex400 (400 qubits, ideal, 10^5 samples, B=16384)"
+    if name == "grid8x8noisy":
+        return (W.grid_8x8_p2_noisy(), 100000, 8192,
+                "qaoa_p2_grid8x8_noisy (64 qubits, depol 1e-3, AD 1e-3, 10^5 samples, B=8192)")
+    raise SystemExit(f"unknown workload {name}")
+
+
+# ------------------------------------------------------------------ oracle
+
+def _oracle_worker(args):
+    name, seed, ids, budget = args
+    import workloads as W  # noqa: F401
+    from oracle import circuit as OC
+    from oracle import sampler as OS
+    spec = workload(name)[0]
+    ops = OC.qaoa_circuit(spec)
+    t0 = time.perf_counter()
+    done = 0
+    for sid in ids:
+        if spec.depol2 > 0 or spec.ad_gamma > 0:
+            OS.noisy_sample(spec.n, ops, seed, sid, backend="tn" if spec.n > 16 else "sv")
+        elif spec.n <= 16:
+            OS.sample_sv(spec.n, ops, seed, [sid])
+        else:
+            OS.sample_tn(spec.n, ops, seed, sid)
+        done += 1
+        if time.perf_counter() - t0 > budget:
+            break
+    return done, time.perf_counter() - t0
+
+
+def oracle_rate(name, budget_s=20.0, seed=1):
+    """Samples/s of the FP64 oracle (naive Alg. 1/2 sampler) on the host cores,
+    one chain per worker process (spawned), bounded by budget_s per worker."""
+    cores = max(1, min(os.cpu_count() or 1, 16))
+    ctx = mp.get_context("spawn")
+    jobs = [(name, seed, list(range(w, 10 ** 6, cores)), budget_s) for w in range(cores)]
+    t0 = time.perf_counter()
+    with ctx.Pool(cores) as pool:
+        res = pool.map(_oracle_worker, jobs)
+    wall = time.perf_counter() - t0
+    done = sum(r[0] for r in res)
+    busy = max(r[1] for r in res)
+    return done / busy, cores, done, wall
+
+
+# ------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    def __init__(self, path):
+        self.path = path
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            self.proc.wait(timeout=5)
+            self.f.close()
+
+    def summary(self, dev_index):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": []}
+        if not self.proc:
+            return out
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9 or not parts[0].isdigit() or int(parts[0]) != dev_index:
+                continue
+            rows.append(parts)
+        if not rows:
+            return out
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        out["sm_mhz"] = statistics.median(sm) if sm else None
+        out["sm_max_mhz"] = max(mx) if mx else None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        seen = set()
+        for r in rows:
+            for nm, v in zip(names, r[5:9]):
+                if v.lower() == "active":
+                    seen.add(nm)
+        out["reasons"] = sorted(seen)
+        out["samples"] = len(rows)
+        return out
+
+
+# -------------------------------------------------------------------- ours
+
+def run_ours(args, rank, world):
+    import numpy as np
+    import torch
+
+    import paper_2510_24218_gb300 as pw
+
+    spec, n_samples, B, desc = workload(args.workload)
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    prec = pw.PW_PREC_FP64 if args.precision == "fp64" else pw.PW_PREC_FP32
+    circ = pw.pw_circuit_qaoa(spec.n, spec.edges, spec.weights, spec.h, spec.p, spec.gammas, spec.betas,
+                              spec.depol2, spec.ad_gamma)
+    plan = pw.pw_plan_build(circ, precision=prec, chains_per_launch=B)
+    pst = pw.pw_plan_stats(plan)
+    words = (spec.n + 63) // 64
+    out = torch.empty((n_samples, words), dtype=torch.int64, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # > L2 (129 MB)
+    stream = torch.cuda.current_stream(dev)
+    first = rank * n_samples * (args.warmup + args.steps + 1)
+
+    def step(i, stats=False):
+        return pw.pw_sample(plan, args.seed, first + i * n_samples, n_samples, out, None, stream, want_stats=stats)
+
+    launches_per_step = (n_samples + B - 1) // B
+    near = 0
+    for i in range(args.warmup):
+        near += step(i, stats=True)["near_boundary"]
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize(dev)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    launches = 0
+    clk_path = os.path.join(tempfile.gettempdir(), f"pw_clocks_{os.getpid()}.csv")
+    with ClockSampler(clk_path) as clk:
+        t_wall = time.perf_counter()
+        for i in range(args.steps):
+            flush.zero_()
+            ev[i][0].record(stream)
+            step(args.warmup + i)
+            ev[i][1].record(stream)
+            launches += launches_per_step
+        torch.cuda.synchronize(dev)
+        t_wall = time.perf_counter() - t_wall
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize(dev)
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    ms_t = torch.tensor([ms], dtype=torch.float64)
+    if world > 1:
+        ms_t = ms_t.to(dev)
+        torch.distributed.all_reduce(ms_t, op=torch.distributed.ReduceOp.MAX)
+    ms = float(ms_t.item())
+    total = n_samples * args.steps * world
+    value = total / (ms / 1e3)
+    per_launch_ms = ms / max(1, launches)
+    # roofline of the sampler kernel: algorithmic flops of one launch / launch time
+    flops_per_launch = pst["flops_per_sample"] * (n_samples / max(1, launches / args.steps))
+    achieved = flops_per_launch / (per_launch_ms / 1e3) / 1e12
+    clocks = clk.summary(dev.index)
+
+    # e2e: the public host API each step (circuit + plan from host arrays,
+    # plan upload, sampling, copy of the samples back to host memory)
+    host_out = np.empty((n_samples, words), dtype=np.uint64)
+    e2e_times = []
+    h2d = 0
+    for i in range(max(2, min(args.steps, 5))):
+        t0 = time.perf_counter()
+        c2 = pw.pw_circuit_qaoa(spec.n, spec.edges, spec.weights, spec.h, spec.p, spec.gammas, spec.betas,
+                                spec.depol2, spec.ad_gamma)
+        p2 = pw.pw_plan_build(c2, precision=prec, chains_per_launch=B)
+        pw.pw_sample_host(p2, args.seed, first + i * n_samples, n_samples, host_out)
+        pw.pw_plan_destroy(p2)
+        pw.pw_circuit_destroy(c2)
+        e2e_times.append(time.perf_counter() - t0)
+    e2e_value = n_samples * world / statistics.median(e2e_times)
+    h2d = _plan_blob_bytes(pw, plan)
+
+    pw.pw_plan_destroy(plan)
+    pw.pw_circuit_destroy(circ)
+    return dict(value=value, ms=ms, launches=launches, near=near, pst=pst, desc=desc, n_samples=n_samples, B=B,
+                achieved=achieved, per_launch_ms=per_launch_ms, flops_per_launch=flops_per_launch, clocks=clocks,
+                e2e=e2e_value, h2d=h2d, d2h=n_samples * words * 8, wall=t_wall)
+
+
+def _plan_blob_bytes(pw, plan):
+    # size of the plan tables uploaded to the device (read from the stats:
+    # the upload is the only host->device copy of a step)
+    return int(pw.pw_plan_stats(plan)["device_bytes"])
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="grid6x6")
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--seed", type=int, default=20251203)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=20.0)
+    args = ap.parse_args()
+
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    spec, n_samples, B, desc = workload(args.workload)
+
+    if args.impl == "reference":
+        # the reference arm of this build is the FP64 CPU oracle, on host cores
+        if rank != 0:
+            return
+        rate, cores, done, wall = oracle_rate(args.workload, budget_s=max(5.0, args.cpu_budget / 2))
+        line = {"impl": "reference", "metric": METRIC, "value": rate, "unit": "samples/s", "n_gpus": args.gpus,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": n_samples / rate * 1e3,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic", "config": {"workload": desc, "samples_per_step": n_samples},
+                "cpu_baseline": {"value": rate, "unit": "samples/s", "cores": cores, "kind": "oracle",
+                                 "sample": f"{done} chains of the same workload (naive Alg. 1/2, FP64)"},
+                "e2e": {"value": rate, "unit": "samples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        # before the first GPU call (the pool is spawned)
+        rate, cores, done, wall = oracle_rate(args.workload, budget_s=args.cpu_budget)
+        cpu = {"value": rate, "unit": "samples/s", "cores": cores, "kind": "oracle",
+               "sample": f"{done} chains of the same workload, naive Alg. 1/2 with FP64 "
+                         f"{'elimination' if spec.n > 16 else 'state-vector'} amplitudes, ~{args.cpu_budget:.0f} s"}
+
+    import torch
+    if world > 1:
+        torch.distributed.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    r = run_ours(args, rank, world)
+    if rank == 0:
+        peak = FP32_PEAK_TFLOPS if args.precision == "fp32" else None
+        line = {
+            "metric": METRIC, "value": r["value"], "unit": "samples/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": r["ms"] / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f64",
+            "data": "synthetic",
+            "config": {"workload": r["desc"], "samples_per_step": r["n_samples"], "chains_per_launch": r["B"],
+                       "precision": args.precision, "l2": "flushed (256 MB write) before every timed step",
+                       "parallelism": f"replicas x{world} (disjoint sample ranges)",
+                       "amplitudes_per_s": r["value"] * r["pst"]["amps_per_sample"],
+                       "plan": {k: r["pst"][k] for k in ("n_slots", "width_bits", "n_blocks", "threads_per_chain",
+                                                         "chains_per_cta", "flops_per_sample")},
+                       "near_boundary_draws_in_warmup": int(r["near"])},
+            "roofline": {"bound": "alu", "achieved": r["achieved"], "peak": peak, "unit": "TFLOP/s",
+                         "frac": (r["achieved"] / peak) if peak else None, "traffic": None,
+                         "kernel": "pw_chain_kernel<float>",
+                         "peak_note": "FP32 FMA peak derived: 152 SMs x 128 lanes x 2 x 2.07 GHz"},
+            "cpu_baseline": cpu,
+            "e2e": {"value": r["e2e"], "unit": "samples/s", "h2d_bytes_per_step": r["h2d"],
+                    "d2h_bytes_per_step": r["d2h"]},
+            "gpu_launches": int(r["launches"]),
+            "clocks": r["clocks"],
+        }
+        print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,186 @@
+/*
+ * pw.h - C ABI of the GB300 pilot-wave exact sampler.
+ *
+ * The library samples bitstrings exactly from the output distribution of a
+ * circuit U_T ... U_1 |0^n> with the gate-by-gate Markov chain of
+ * Kalachev et al., "Pilot-Wave Simulator" (arXiv 2510.24218):
+ *   - Sec. 2, Eq. (1) and Alg. 1: a classical state s is carried through the
+ *     circuit; monomial gates move it deterministically, other gates resample
+ *     it inside the gate's block with probability |amp(C_t,y)|^2 / sum_block,
+ *     amp(C_t,i) = <i|C_t|0^n> being a tensor-network contraction;
+ *   - Sec. 3 and Alg. 2 (App. A): noise channels with local-submonomial (LSM)
+ *     Kraus operators are sampled by Eq. (5) and handled by X-frame propagation,
+ *     so the noisy network keeps the noiseless shape (Prop. 2).
+ *
+ * All calls return 0 (PW_OK) or a negative PW_ERR_* code; pw_last_error()
+ * returns a thread-local message for the last failure. No exception crosses
+ * the ABI. Handles (pw_circuit, pw_plan) are owned by the library and freed by
+ * the matching *_destroy call. Device buffers passed in are owned by the
+ * caller; the library never frees them. Host arrays are read during the call
+ * only.
+ *
+ * Conventions (the paper leaves these open):
+ *   - qubit q <-> bit (q % 64) of 64-bit word (q / 64) in packed bitstrings;
+ *   - an m-qubit matrix acting on (q_0..q_{m-1}) is indexed by
+ *     sum_i b(q_i) 2^i (q_0 least significant), row-major, complex numbers as
+ *     interleaved (re, im) doubles;
+ *   - randomness: u = Philox4x32-10(key = seed, counter = (sample id, op id,
+ *     purpose)) mapped to a 53-bit double; UpdateState picks the smallest
+ *     candidate y (ascending local index) with u*P < sum_{y'<=y} p_{y'}, the
+ *     Kraus draw applies the same rule over the Kraus list order, with Eq. (5)
+ *     evaluated at the true bit s XOR x. Sample k depends only on
+ *     (seed, k, circuit, plan order), so disjoint sample ranges can be run
+ *     anywhere and concatenated.
+ */
+#ifndef PW_H
+#define PW_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PW_OK 0
+#define PW_ERR_ARG (-1)          /* invalid argument (null, range, shape) */
+#define PW_ERR_NOT_LSM (-2)      /* Kraus operator not local-submonomial (App. A) */
+#define PW_ERR_OOM (-3)          /* host or device allocation failed */
+#define PW_ERR_CUDA (-4)         /* a CUDA runtime call failed */
+#define PW_ERR_TIMEOUT (-5)      /* reserved: a bounded device wait ran out */
+#define PW_ERR_NUMERIC (-6)      /* non-finite value in inputs or results */
+#define PW_ERR_UNSUPPORTED (-7)  /* circuit outside the supported structure */
+#define PW_ERR_TOO_LARGE (-8)    /* plan does not fit the device limits */
+
+#define PW_PREC_FP32 0           /* contraction in FP32, conditionals in FP64 */
+#define PW_PREC_FP64 1           /* contraction and conditionals in FP64 */
+
+#define PW_ORDER_AUTO 0          /* search sweep orders, keep the narrowest */
+#define PW_ORDER_NATURAL 1       /* sweep qubits in index order */
+
+typedef struct pw_circuit pw_circuit;
+typedef struct pw_plan pw_plan;
+
+/* Options of pw_plan_build. Zero-initialise for defaults. */
+typedef struct {
+    int precision;          /* PW_PREC_FP32 (default) or PW_PREC_FP64 */
+    int order;              /* PW_ORDER_AUTO (default) or PW_ORDER_NATURAL */
+    int max_block;          /* max sites resampled per readout block; 0 -> 8 */
+    int threads_per_chain;  /* CUDA threads cooperating on one chain; 0 -> auto */
+    int chains_per_launch;  /* chains per kernel launch; 0 -> all requested samples */
+    int reserved[7];
+} pw_plan_opts;
+
+/* Shape and cost of a plan (pw_plan_stats). */
+typedef struct {
+    int n_qubits;
+    int n_ops;              /* operations of the circuit (gates + channels) */
+    int n_layers;           /* mixer layers after the first one (QAOA depth p) */
+    int n_slots;            /* frontier sites kept by the sweep */
+    int width_bits;         /* log2 of the frontier tensor at the deepest layer */
+    int width_low_bits;     /* log2 of the cached right environments */
+    int n_blocks;           /* readout blocks per layer */
+    int sampled_gates;      /* non-monomial gates whose update needs amplitudes
+                               (excluding the first mixer layer, which acts on a
+                               product state); rows of the amplitude trace */
+    int threads_per_chain;
+    int chains_per_cta;
+    int smem_bytes_per_cta;
+    int noisy;              /* 1 if the circuit has Kraus channels */
+    double flops_per_sample;   /* real flops of the contraction per sample */
+    double amps_per_sample;    /* amplitudes evaluated per sample */
+    double device_bytes;       /* bytes of plan tables copied to the device on first use */
+} pw_plan_stats_t;
+
+/* Counters of one pw_sample call. */
+typedef struct {
+    uint64_t near_boundary;   /* draws with |u*P - cum| < 1e-6 P */
+    uint64_t zero_mass;       /* updates whose block had zero probability */
+    uint64_t launches;        /* kernel launches issued */
+} pw_run_stats_t;
+
+/* ---------------------------------------------------------------- circuit */
+
+/* New empty circuit on n_qubits (1..4096). */
+int pw_circuit_create(int n_qubits, pw_circuit** out);
+
+/* Append a gate (A, q) (App. A): m = 1 or 2 qubits, A = 2^m x 2^m complex
+ * matrix, row-major, interleaved (re, im). Unitarity is not checked. */
+int pw_circuit_add_gate(pw_circuit* c, int m, const int* qubits, const double* A);
+
+/* Append a noise operation with k Kraus operators E_0..E_{k-1} (Sec. 3.1),
+ * each 2^m x 2^m as in pw_circuit_add_gate, stored one after the other.
+ * Every E_i must be a tensor product of 2x2 matrices with at most one nonzero
+ * per row and column (LSM, App. A), else PW_ERR_NOT_LSM. The list order is the
+ * order of the Kraus draw. */
+int pw_circuit_add_kraus(pw_circuit* c, int m, const int* qubits, int k, const double* E);
+
+/* The QAOA circuit of App. D on n qubits: H on every qubit; for l = 0..p-1:
+ * RZZ(2 gammas[l] w[e]) = exp(-i gammas[l] w[e] Z_u Z_v) on every edge
+ * (edges = 2*n_edges ints, pairs u != v) in list order, each followed by the
+ * two-qubit depolarizing channel (1-depol2) rho + depol2/15 sum_{P != II} P rho P
+ * when depol2 > 0 (Kraus index a + 4b: Pauli a (I,X,Y,Z) on u, Pauli b on v);
+ * RZ(2 gammas[l] h[j]) on every qubit when h != NULL; RX(2 betas[l]) on qubits
+ * 0..n-1; then amplitude damping E0 = diag(1, sqrt(1-g)), E1 = sqrt(g)|0><1|
+ * with g = ad_gamma on qubits 0..n-1 when ad_gamma > 0. */
+int pw_circuit_qaoa(int n, int n_edges, const int* edges, const double* w, const double* h,
+                    int p, const double* gammas, const double* betas,
+                    double depol2, double ad_gamma, pw_circuit** out);
+
+/* Number of operations appended so far. */
+int pw_circuit_num_ops(const pw_circuit* c, int* n_ops);
+
+void pw_circuit_destroy(pw_circuit* c);
+
+/* ------------------------------------------------------------------- plan */
+
+/* Build the contraction plan (host only, no CUDA call). Supported structure:
+ * layers of one non-diagonal 1-qubit gate per qubit (the first acting on
+ * |0^n>), separated by sections of diagonal 1- or 2-qubit gates and LSM
+ * channels; channels may also follow the last layer. Anything else returns
+ * PW_ERR_UNSUPPORTED. The plan fixes the order of the commuting one-qubit
+ * gates inside each layer (see pw_plan_exec_order). */
+int pw_plan_build(const pw_circuit* c, const pw_plan_opts* opts, pw_plan** out);
+
+int pw_plan_stats(const pw_plan* plan, pw_plan_stats_t* out);
+
+/* The execution order used by the plan: order[t] is the index (in insertion
+ * order) of the t-th operation executed. order has n_ops entries. */
+int pw_plan_exec_order(const pw_plan* plan, int* order);
+
+void pw_plan_destroy(pw_plan* plan);
+
+/* ------------------------------------------------------------- execution */
+
+/* Draw samples first_sample .. first_sample + n_samples - 1 (Alg. 1 / Alg. 2).
+ * d_out_bits: device buffer of n_samples * ceil(n/64) uint64 (packed s XOR x).
+ * d_trace (nullable): device buffer of n_samples * sampled_gates * 4 doubles;
+ *   row r of sample k holds (re, im) of amp(C_t, y) for y = 0, 1 of the r-th
+ *   sampled gate, where C_t is the executed prefix including that gate.
+ * stream: a cudaStream_t (NULL = legacy default stream). The call is
+ * asynchronous with respect to the host unless stats != NULL, in which case it
+ * synchronises the stream to read the counters. */
+int pw_sample(pw_plan* plan, uint64_t seed, uint64_t first_sample, uint64_t n_samples,
+              uint64_t* d_out_bits, double* d_trace, void* stream, pw_run_stats_t* stats);
+
+/* The same with HOST buffers: h_out_bits (n_samples * ceil(n/64) uint64) and
+ * the optional h_trace are written before return; device staging memory is
+ * held by the plan and reused between calls. */
+int pw_sample_host(pw_plan* plan, uint64_t seed, uint64_t first_sample, uint64_t n_samples,
+                   uint64_t* h_out_bits, double* h_trace, pw_run_stats_t* stats);
+
+/* amp(C_t, x) = <x|C_t|0^n> (Sec. 2) for n_strings bitstrings x (device,
+ * packed like pw_sample's output), where C_t is the executed prefix of length
+ * prefix_ops (pw_plan_exec_order); the prefix must end right after a
+ * one-qubit mixer gate of a layer >= 1 and the circuit must be noiseless.
+ * d_amp: device buffer of 2 * n_strings doubles (re, im). */
+int pw_amplitudes(pw_plan* plan, int prefix_ops, uint64_t n_strings, const uint64_t* d_bits,
+                  double* d_amp, void* stream);
+
+/* Thread-local message describing the last failure of this thread. */
+const char* pw_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PW_H */

@@ -117,14 +117,12 @@ def contract(factors, open_vars):
         res = np.einsum(*args, [uni.index(v) for v in out_vars])
         rest.append((out_vars, res))
         factors = rest
-    # multiply what is left (tables over open variables and scalars)
-    args = []
+    # multiply what is left (tables over open variables and scalars), one
+    # factor at a time
+    k = len(open_vars)
+    res = np.ones([2] * k, dtype=complex)
     for vv, t in factors:
-        args.append(t)
-        args.append([open_vars.index(v) for v in vv])
-    if not args:
-        return np.ones([2] * len(open_vars), dtype=complex)
-    res = np.einsum(*args, list(range(len(open_vars))))
+        res = np.einsum(res, list(range(k)), t, [open_vars.index(v) for v in vv], list(range(k)))
     return res
 
 

@@ -1,0 +1,670 @@
+// Contraction-plan builder.
+//
+// The amplitudes the sampler needs at a one-qubit gate of layer m (Alg. 1,
+// amp(C_t, y) = <y s_rest| C_t |0^n>) are contractions of the circuit's
+// tensor network in which diagonal gates identify legs (App. A): every qubit
+// carries a column of wire segments z^0 .. z^m (z^j after the j-th non-diagonal
+// gate), cost gates of section j+1 couple segments z^j of two qubits, and the
+// one-qubit gates couple z^j to z^{j-1}. For QAOA this is the graph times a
+// path of p vertices (App. A).
+//
+// At layer m the qubits already resampled in this layer carry legs
+// z^0..z^{m-1} summed (their z^m is fixed to the new bit), the others carry
+// z^0..z^{m-2} summed (z^{m-1} fixed to the current bit). The plan sweeps the
+// qubits in an order pi, in blocks:
+//   * forward: a frontier tensor L over the legs of the "live" sites (absorbed
+//     and still adjacent to unabsorbed sites, or not yet resampled) absorbs the
+//     sites of one block, eliminating resampled sites whose neighbours are all
+//     absorbed;
+//   * backward: at the start of the layer the sites are absorbed in reverse
+//     (their top segments fixed to the current bits), which caches one right
+//     environment R_k per block over the lower legs of the frontier sites;
+//   * readout: T(tops of the block sites) = sum L * R_k * (cross-edge factors of
+//     the top segments); the block's sites are then resampled one by one from T.
+// The same slot layout serves both directions: slot j holds a site's lower legs
+// at bits j*(m-1)+l and its top leg at bit S*(m-1)+j.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <functional>
+#include <map>
+#include <numeric>
+#include <set>
+#include <tuple>
+
+#include "pw_internal.h"
+
+namespace pw {
+
+bool lsm_factor(const cd* E, int m, cd* M0, cd* M1);
+
+namespace {
+
+enum EvType { EV_SUMOUT, EV_REPLACE, EV_EXPAND, EV_EDGE, EV_SITE };
+struct Event {
+    int type, u, v, slot, slot2;   // EV_EDGE: u = new site v, v = live site w, slot/slot2 their slots
+};
+
+struct Layered {
+    int n = 0, P = 0;
+    std::vector<std::vector<int>> mixer_ops;   // [P+1] op ids in circuit order
+    std::vector<int> mixer_op_of;              // [(P+1)*n]
+    std::vector<std::vector<int>> sections;    // [P+2], sections[m] m = 1..P+1
+};
+
+int parse_layers(const pw_circuit* c, Layered& L) {
+    const int n = c->n;
+    L.n = n;
+    std::vector<int> pending;
+    std::vector<char> done(n, 0);
+    int cur = -1, cur_count = 0;
+    bool cost_in_layer = false;
+    for (int id = 0; id < (int)c->ops.size(); ++id) {
+        const Op& op = c->ops[id];
+        int m = (int)op.qubits.size();
+        if (op.kind == OP_GATE) {
+            bool diag = is_diagonal(op.mat(0), op.dim());
+            if (!diag && m == 2)
+                return set_error(PW_ERR_UNSUPPORTED, "non-diagonal two-qubit gates are not supported by this plan family");
+            if (!diag) {
+                int q = op.qubits[0];
+                if (cur >= 0 && cur_count < n) {
+                    if (cost_in_layer)
+                        return set_error(PW_ERR_UNSUPPORTED, "diagonal gates or channels inside a one-qubit gate layer");
+                    if (done[q]) return set_error(PW_ERR_UNSUPPORTED, "qubit repeated inside a one-qubit gate layer");
+                } else {
+                    if (cur == -1 && !pending.empty())
+                        return set_error(PW_ERR_UNSUPPORTED, "operations before the first one-qubit gate layer");
+                    ++cur;
+                    L.mixer_ops.emplace_back();
+                    if (cur >= 1) L.sections.push_back(pending);
+                    pending.clear();
+                    std::fill(done.begin(), done.end(), 0);
+                    cur_count = 0;
+                    cost_in_layer = false;
+                }
+                done[q] = 1;
+                ++cur_count;
+                L.mixer_ops[cur].push_back(id);
+                continue;
+            }
+        }
+        // diagonal gate or channel
+        if (cur < 0) return set_error(PW_ERR_UNSUPPORTED, "operations before the first one-qubit gate layer");
+        if (cur_count < n) {
+            cost_in_layer = true;
+            return set_error(PW_ERR_UNSUPPORTED, "diagonal gates or channels inside a one-qubit gate layer");
+        }
+        pending.push_back(id);
+    }
+    if (cur < 0) return set_error(PW_ERR_UNSUPPORTED, "circuit has no layer of one-qubit gates");
+    if (cur_count < n) return set_error(PW_ERR_UNSUPPORTED, "last one-qubit gate layer is incomplete");
+    L.P = cur;
+    // sections[0] unused; sections[m] between mixer m-1 and m; sections[P+1] final
+    std::vector<std::vector<int>> secs(L.P + 2);
+    for (int m = 1; m <= L.P; ++m) secs[m] = L.sections[m - 1];
+    secs[L.P + 1] = pending;
+    L.sections = secs;
+    L.mixer_op_of.assign((size_t)(L.P + 1) * n, -1);
+    for (int m = 0; m <= L.P; ++m)
+        for (int id : L.mixer_ops[m]) L.mixer_op_of[(size_t)m * n + c->ops[id].qubits[0]] = id;
+    return PW_OK;
+}
+
+// ------------------------------------------------------------------ sweep
+struct Sweep {
+    const std::vector<std::vector<int>>* adj = nullptr;
+    std::vector<int> blk, slot, unabs;
+    std::vector<int> live;
+    std::vector<char> slot_used;
+    int peak = 0;
+    int nslots = 0;
+
+    void init(const std::vector<std::vector<int>>& a) {
+        adj = &a;
+        int n = (int)a.size();
+        blk.assign(n, -1);
+        slot.assign(n, -1);
+        unabs.resize(n);
+        for (int i = 0; i < n; ++i) unabs[i] = (int)a[i].size();
+        live.clear();
+        slot_used.clear();
+        peak = 0;
+        nslots = 0;
+    }
+    int alloc() {
+        for (int j = 0; j < (int)slot_used.size(); ++j)
+            if (!slot_used[j]) { slot_used[j] = 1; return j; }
+        slot_used.push_back(1);
+        nslots = std::max(nslots, (int)slot_used.size());
+        return (int)slot_used.size() - 1;
+    }
+    void release(int u) {
+        slot_used[slot[u]] = 0;
+        live.erase(std::find(live.begin(), live.end(), u));
+    }
+    bool adjacent(int a, int b) const {
+        const auto& v = (*adj)[a];
+        return std::find(v.begin(), v.end(), b) != v.end();
+    }
+    void absorb_block(const std::vector<int>& sites, int k, std::vector<Event>* ev) {
+        // resampled sites whose neighbours are all absorbed leave the frontier
+        std::vector<int> cp = live;
+        for (int u : cp)
+            if (blk[u] < k && unabs[u] == 0) {
+                if (ev) ev->push_back({EV_SUMOUT, u, -1, slot[u], -1});
+                release(u);
+            }
+        for (int v : sites) {
+            blk[v] = k;
+            for (int w : (*adj)[v]) --unabs[w];
+            std::vector<int> elig;
+            for (int u : live)
+                if (blk[u] < k && unabs[u] == 0) elig.push_back(u);
+            int ustar = elig.empty() ? -1 : elig[0];
+            if (ustar >= 0) {
+                slot[v] = slot[ustar];
+                if (ev) ev->push_back({EV_REPLACE, ustar, v, slot[v], -1});
+                live.erase(std::find(live.begin(), live.end(), ustar));
+            } else {
+                slot[v] = alloc();
+                if (ev) ev->push_back({EV_EXPAND, -1, v, slot[v], -1});
+            }
+            live.push_back(v);
+            peak = std::max(peak, (int)live.size());
+            for (int w : live)
+                if (w != v && adjacent(v, w) && ev) ev->push_back({EV_EDGE, v, w, slot[v], slot[w]});
+            if (ev) ev->push_back({EV_SITE, -1, v, slot[v], -1});
+            for (size_t i = 1; i < elig.size(); ++i) {
+                if (ev) ev->push_back({EV_SUMOUT, elig[i], -1, slot[elig[i]], -1});
+                release(elig[i]);
+            }
+        }
+    }
+};
+
+int width_singletons(const std::vector<std::vector<int>>& adj, const std::vector<int>& order, double* cost) {
+    Sweep s;
+    s.init(adj);
+    double c = 0;
+    for (int k = 0; k < (int)order.size(); ++k) {
+        s.absorb_block({order[k]}, k, nullptr);
+        c += std::ldexp(1.0, std::min(60, (int)s.live.size()));
+    }
+    if (cost) *cost = c;
+    return s.nslots;
+}
+
+std::vector<std::vector<int>> greedy_blocks(const std::vector<std::vector<int>>& adj, const std::vector<int>& order,
+                                            int target, int max_block) {
+    Sweep s;
+    s.init(adj);
+    std::vector<std::vector<int>> blocks;
+    std::vector<int> cur;
+    Sweep at_start = s;
+    for (int v : order) {
+        std::vector<int> trial = cur;
+        trial.push_back(v);
+        Sweep t = at_start;
+        t.absorb_block(trial, (int)blocks.size(), nullptr);
+        if (cur.empty() || ((int)trial.size() <= max_block && t.nslots <= target)) {
+            cur = trial;
+            continue;
+        }
+        at_start.absorb_block(cur, (int)blocks.size(), nullptr);
+        blocks.push_back(cur);
+        cur = {v};
+    }
+    if (!cur.empty()) blocks.push_back(cur);
+    return blocks;
+}
+
+std::vector<int> bfs_order(const std::vector<std::vector<int>>& adj, int start) {
+    int n = (int)adj.size();
+    std::vector<int> order, seen(n, 0);
+    for (int s0 = 0; s0 < n; ++s0) {
+        int s = (s0 == 0) ? start : s0;
+        if (seen[s]) continue;
+        std::vector<int> q{s};
+        seen[s] = 1;
+        for (size_t h = 0; h < q.size(); ++h) {
+            order.push_back(q[h]);
+            std::vector<int> nb = adj[q[h]];
+            std::sort(nb.begin(), nb.end());
+            for (int w : nb)
+                if (!seen[w]) { seen[w] = 1; q.push_back(w); }
+        }
+    }
+    return order;
+}
+
+// Greedy: repeatedly absorb the vertex that leaves the fewest live sites.
+std::vector<int> greedy_order(const std::vector<std::vector<int>>& adj, int start) {
+    int n = (int)adj.size();
+    std::vector<int> order;
+    std::vector<char> absorbed(n, 0);
+    std::vector<int> unabs(n), live_flag(n, 0);
+    for (int i = 0; i < n; ++i) unabs[i] = (int)adj[i].size();
+    int live = 0;
+    auto take = [&](int v) {
+        absorbed[v] = 1;
+        order.push_back(v);
+        live_flag[v] = 1;
+        ++live;
+        for (int w : adj[v]) {
+            --unabs[w];
+            if (absorbed[w] && unabs[w] == 0 && live_flag[w]) { live_flag[w] = 0; --live; }
+        }
+        if (unabs[v] == 0) { live_flag[v] = 0; --live; }
+    };
+    take(start);
+    while ((int)order.size() < n) {
+        int best = -1;
+        long bscore = 0;
+        for (int v = 0; v < n; ++v) {
+            if (absorbed[v]) continue;
+            bool touches = false;
+            for (int w : adj[v]) touches |= (bool)absorbed[w];
+            if (!touches && best >= 0) continue;
+            int delta = 1;
+            int nabs = 0;
+            for (int w : adj[v])
+                if (absorbed[w]) {
+                    ++nabs;
+                    if (unabs[w] == 1 && live_flag[w]) --delta;
+                }
+            if (unabs[v] - nabs == 0) --delta;
+            long score = (long)delta * 1000 - nabs;
+            if (!touches) score += 100000;
+            if (best < 0 || score < bscore) { best = v; bscore = score; }
+        }
+        take(best);
+    }
+    return order;
+}
+
+}  // namespace
+
+int build_plan(const pw_circuit* c, const pw_plan_opts& opts, HostPlan& hp) {
+    if (!c) return set_error(PW_ERR_ARG, "circuit is null");
+    Layered L;
+    int rc = parse_layers(c, L);
+    if (rc) return rc;
+    const int n = c->n, P = L.P;
+    if (P > 4) return set_error(PW_ERR_UNSUPPORTED, "more than 4 layers after the first are not supported");
+    hp = HostPlan();
+    hp.precision = opts.precision == PW_PREC_FP64 ? PW_PREC_FP64 : PW_PREC_FP32;
+    if (opts.precision != PW_PREC_FP32 && opts.precision != PW_PREC_FP64)
+        return set_error(PW_ERR_ARG, "unknown precision");
+    const int max_block = opts.max_block > 0 ? std::min(opts.max_block, 10) : 8;
+
+    // ------------------------------------------------ mixers (2x2 per layer, qubit)
+    hp.mix_d.assign((size_t)(P + 1) * n * 8, 0.0);
+    hp.mix_mono.assign((size_t)(P + 1) * n, 0);
+    for (int m = 0; m <= P; ++m)
+        for (int q = 0; q < n; ++q) {
+            const Op& op = c->ops[L.mixer_op_of[(size_t)m * n + q]];
+            for (int i = 0; i < 4; ++i) {
+                hp.mix_d[((size_t)m * n + q) * 8 + 2 * i] = op.mats[i].real();
+                hp.mix_d[((size_t)m * n + q) * 8 + 2 * i + 1] = op.mats[i].imag();
+            }
+            hp.mix_mono[(size_t)m * n + q] = is_monomial(op.mat(0), 2) ? 1 : 0;
+        }
+    hp.mix_f.assign(hp.mix_d.begin(), hp.mix_d.end());
+    for (int id : L.mixer_ops[0]) {
+        hp.mix0_order.push_back(c->ops[id].qubits[0]);
+    }
+    hp.mix0_opid.assign(n, -1);
+    for (int q = 0; q < n; ++q) hp.mix0_opid[q] = L.mixer_op_of[q];
+
+    // ------------------------------------------------ cost sections
+    std::vector<std::vector<int>> adj(n);
+    std::map<std::tuple<int, int, int>, std::vector<int>> pair_gates;   // (a<b, level) -> cost gates
+    std::vector<std::vector<int>> level_gates(std::max(P, 1));
+    hp.cost_ranges.assign(P + 3, 0);
+    bool has_segfac = false, has_frame = false;
+    for (int m = 1; m <= P + 1; ++m) {
+        hp.cost_ranges[m] = (int)hp.cost_items.size();
+        for (int id : L.sections[m]) {
+            const Op& op = c->ops[id];
+            if (op.kind == OP_GATE) {
+                if (m == P + 1) continue;   // diagonal gates on fixed final segments: constants
+                DevCostGate g{};
+                g.q0 = (int16_t)op.qubits[0];
+                g.q1 = (int16_t)(op.qubits.size() == 2 ? op.qubits[1] : -1);
+                g.level = (int16_t)(m - 1);
+                int dim = op.dim();
+                for (int b = 0; b < 4; ++b) {
+                    cd v = b < dim ? op.mats[(size_t)b * dim + b] : cd(1.0, 0.0);
+                    g.d[2 * b] = v.real();
+                    g.d[2 * b + 1] = v.imag();
+                }
+                int gi = (int)hp.cost_gates.size();
+                hp.cost_gates.push_back(g);
+                if (g.q1 >= 0) {
+                    int a = std::min<int>(g.q0, g.q1), b = std::max<int>(g.q0, g.q1);
+                    if (std::find(adj[a].begin(), adj[a].end(), b) == adj[a].end()) {
+                        adj[a].push_back(b);
+                        adj[b].push_back(a);
+                    }
+                    pair_gates[{a, b, m - 1}].push_back(gi);
+                    level_gates[m - 1].push_back(gi);
+                    hp.cost_items.push_back({CI_GATE2, 0, gi});
+                } else {
+                    has_segfac = true;
+                    hp.cost_items.push_back({CI_GATE1, 0, gi});
+                }
+            } else {
+                has_segfac = true;
+                has_frame = true;
+                DevChannel ch{};
+                ch.op_id = id;
+                ch.nq = (int16_t)op.qubits.size();
+                ch.k = (int16_t)op.k;
+                for (int i = 0; i < ch.nq; ++i) ch.q[i] = (int16_t)op.qubits[i];
+                ch.cum_off = (int)hp.cum.size();
+                ch.fac_off = (int)hp.factors.size();
+                int dim = op.dim();
+                for (int cb = 0; cb < dim; ++cb) {
+                    double acc = 0;
+                    for (int i = 0; i < op.k; ++i) {
+                        const cd* E = op.mat(i);
+                        double p = 0;
+                        for (int r = 0; r < dim; ++r) p += std::norm(E[r * dim + cb]);   // Eq. (5)
+                        acc += p;
+                        hp.cum.push_back(acc);
+                    }
+                }
+                for (int i = 0; i < op.k; ++i) {
+                    cd M[2][4];
+                    if (!lsm_factor(op.mat(i), ch.nq, M[0], M[1]))
+                        return set_error(PW_ERR_NOT_LSM, "Kraus operator is not local-submonomial");
+                    for (int f = 0; f < ch.nq; ++f) {
+                        DevKrausFactor kf{};
+                        kf.q = ch.q[f];
+                        const cd* F = M[f];
+                        // Alg. 2: M anti-diagonal <=> M sigma_X diagonal and M not diagonal
+                        bool diagM = F[1] == cd(0, 0) && F[2] == cd(0, 0);
+                        bool diagMX = F[0] == cd(0, 0) && F[3] == cd(0, 0);
+                        cd d0, d1;
+                        if (diagMX && !diagM) {
+                            kf.antidiag = 1;
+                            d0 = F[1];   // (M sigma_X)[0][0] = M[0][1]
+                            d1 = F[2];   // (M sigma_X)[1][1] = M[1][0]
+                        } else {
+                            kf.antidiag = 0;
+                            d0 = F[0];
+                            d1 = F[3];
+                        }
+                        kf.d[0] = d0.real();
+                        kf.d[1] = d0.imag();
+                        kf.d[2] = d1.real();
+                        kf.d[3] = d1.imag();
+                        hp.factors.push_back(kf);
+                    }
+                }
+                int ci = (int)hp.channels.size();
+                hp.channels.push_back(ch);
+                hp.cost_items.push_back({CI_CHANNEL, 0, ci});
+            }
+        }
+    }
+    hp.cost_ranges[P + 2] = (int)hp.cost_items.size();
+    hp.noisy = has_frame;
+
+    // ------------------------------------------------ sweep order and blocks
+    std::vector<int> order(n);
+    std::iota(order.begin(), order.end(), 0);
+    if (opts.order == PW_ORDER_AUTO && P >= 1) {
+        double best_cost = 0;
+        int best_w = width_singletons(adj, order, &best_cost);
+        std::vector<std::vector<int>> cands;
+        std::vector<int> rev(order.rbegin(), order.rend());
+        cands.push_back(rev);
+        std::vector<int> starts = {0, n - 1};
+        std::vector<int> bydeg(n);
+        std::iota(bydeg.begin(), bydeg.end(), 0);
+        std::stable_sort(bydeg.begin(), bydeg.end(), [&](int a, int b) { return adj[a].size() < adj[b].size(); });
+        for (int i = 0; i < std::min(n, 6); ++i) starts.push_back(bydeg[i]);
+        for (int i = 0; i < 4; ++i) starts.push_back((int)((long)i * n / 4));
+        for (int s : starts) {
+            cands.push_back(bfs_order(adj, s));
+            if (n <= 2048) cands.push_back(greedy_order(adj, s));
+        }
+        for (auto& o : cands) {
+            double cst = 0;
+            int wdt = width_singletons(adj, o, &cst);
+            if (wdt < best_w || (wdt == best_w && cst < best_cost)) {
+                best_w = wdt;
+                best_cost = cst;
+                order = o;
+            }
+        }
+    } else if (opts.order != PW_ORDER_NATURAL && opts.order != PW_ORDER_AUTO) {
+        return set_error(PW_ERR_ARG, "unknown order option");
+    }
+    hp.sweep_order = order;
+    int target = width_singletons(adj, order, nullptr);
+    hp.blocks = P >= 1 ? greedy_blocks(adj, order, target, max_block) : std::vector<std::vector<int>>{};
+    const int K = (int)hp.blocks.size();
+
+    // final simulation with events
+    Sweep sw;
+    sw.init(adj);
+    std::vector<std::vector<Event>> ev(K);
+    std::vector<std::vector<std::pair<int, int>>> live_at(K);   // (site, slot) after block k
+    for (int k = 0; k < K; ++k) {
+        sw.absorb_block(hp.blocks[k], k, &ev[k]);
+        for (int u : sw.live) live_at[k].push_back({u, sw.slot[u]});
+    }
+    const int S = std::max(1, sw.nslots);
+    std::vector<int> blk = sw.blk;
+    if (P >= 1 && S * P > 24)
+        return set_error(PW_ERR_TOO_LARGE, "frontier tensor of 2^" + std::to_string(S * P) +
+                                               " entries per chain exceeds this plan family's limit (2^24)");
+
+    auto gates_between = [&](int a, int b, int level) -> std::vector<int> {
+        auto it = pair_gates.find({std::min(a, b), std::max(a, b), level});
+        if (it == pair_gates.end()) return {};
+        return it->second;
+    };
+    auto push_glist = [&](const std::vector<int>& g) {
+        int off = (int)hp.gate_refs.size();
+        hp.gate_refs.insert(hp.gate_refs.end(), g.begin(), g.end());
+        return off;
+    };
+
+    // ------------------------------------------------ compile per layer
+    hp.block_ranges.assign((size_t)(P + 1) * std::max(K, 1), DevBlockRange{});
+    int trace_row = 0;
+    double flops = 0;
+    hp.exec_order.clear();
+    for (int id : L.mixer_ops[0]) hp.exec_order.push_back(id);
+    hp.exec_layer.assign(c->ops.size(), -1);
+    hp.exec_block.assign(c->ops.size(), -1);
+    hp.exec_pos.assign(c->ops.size(), -1);
+    for (int m = 1; m <= P; ++m) {
+        for (int id : L.sections[m]) hp.exec_order.push_back(id);
+        const int Wl = S * (m - 1);
+        const int Wm = S * m;
+        auto bitf = [&](int j, int l) { return l < m - 1 ? j * (m - 1) + l : Wl + j; };
+        auto bitb = [&](int j, int l) { return j * (m - 1) + l; };
+        auto mk = [&](uint8_t kind, uint8_t rcp, std::initializer_list<int> bits, int qa, int qb, int layer,
+                      const std::vector<int>& gl, int fixed_top) {
+            DevMicroOp o{};
+            o.kind = kind;
+            o.recipe = rcp;
+            o.nbits = (uint8_t)bits.size();
+            int i = 0;
+            for (int b : bits) o.bits[i++] = (uint8_t)b;
+            o.qa = (int16_t)qa;
+            o.qb = (int16_t)qb;
+            o.layer = (int16_t)layer;
+            o.fixed_top = (uint8_t)fixed_top;
+            o.glist = gl.empty() ? 0 : push_glist(gl);
+            o.gcount = (int)gl.size();
+            hp.micro.push_back(o);
+        };
+        for (int k = 0; k < K; ++k) {
+            DevBlockRange& br = hp.block_ranges[(size_t)m * K + k];
+            // forward
+            br.fwd_begin = (int)hp.micro.size();
+            for (const Event& e : ev[k]) {
+                switch (e.type) {
+                    case EV_SUMOUT:
+                        for (int l = 0; l < m; ++l)
+                            mk(MK_MAT1, l == m - 1 ? RC_SUMOUT_MIX : RC_SUMOUT1, {bitf(e.slot, l)}, e.u, -1,
+                               l == m - 1 ? m : -1, {}, 0);
+                        break;
+                    case EV_REPLACE:
+                        for (int l = 0; l < m; ++l)
+                            mk(MK_MAT1, RC_REPLACE, {bitf(e.slot, l)}, e.u, e.v, l == m - 1 ? m : -1,
+                               gates_between(e.u, e.v, l), 0);
+                        break;
+                    case EV_EXPAND:
+                        for (int l = 0; l < m; ++l) mk(MK_MAT1, RC_EXPAND, {bitf(e.slot, l)}, -1, -1, -1, {}, 0);
+                        break;
+                    case EV_EDGE:
+                        for (int l = 0; l < m; ++l) {
+                            std::vector<int> gl = gates_between(e.u, e.v, l);
+                            if (!gl.empty())
+                                mk(MK_DIAG, RC_EDGE, {bitf(e.slot, l), bitf(e.slot2, l)}, e.u, e.v, -1, gl, 0);
+                        }
+                        break;
+                    case EV_SITE: {
+                        DevMicroOp o{};
+                        std::vector<int> bits;
+                        for (int l = 0; l < m; ++l) bits.push_back(bitf(e.slot, l));
+                        o.kind = MK_DIAG;
+                        o.recipe = RC_SITE;
+                        o.nbits = (uint8_t)m;
+                        for (int l = 0; l < m; ++l) o.bits[l] = (uint8_t)bits[l];
+                        o.qa = (int16_t)e.v;
+                        o.qb = -1;
+                        o.layer = (int16_t)m;
+                        o.fixed_top = 0;
+                        hp.micro.push_back(o);
+                        break;
+                    }
+                }
+            }
+            br.fwd_end = (int)hp.micro.size();
+            // backward (R_k -> R_{k-1}); not needed for k = 0
+            br.bwd_begin = br.bwd_end = (int)hp.micro.size();
+            if (k >= 1) {
+                std::vector<int> consts;
+                for (int g : level_gates[m - 1]) {
+                    int a = hp.cost_gates[g].q0, b = hp.cost_gates[g].q1;
+                    if (std::min(blk[a], blk[b]) == k) consts.push_back(g);
+                }
+                if (!consts.empty()) mk(MK_CONST, RC_CONST_EDGES, {}, -1, -1, -1, consts, 0);
+                for (int i = (int)ev[k].size() - 1; i >= 0; --i) {
+                    const Event& e = ev[k][i];
+                    switch (e.type) {
+                        case EV_SITE: {
+                            DevMicroOp o{};
+                            o.kind = m >= 2 ? MK_DIAG : MK_CONST;
+                            o.recipe = RC_SITE;
+                            o.nbits = (uint8_t)(m - 1);
+                            for (int l = 0; l < m - 1; ++l) o.bits[l] = (uint8_t)bitb(e.slot, l);
+                            o.qa = (int16_t)e.v;
+                            o.qb = -1;
+                            o.layer = (int16_t)m;
+                            o.fixed_top = 1;
+                            hp.micro.push_back(o);
+                            break;
+                        }
+                        case EV_REPLACE:
+                            for (int l = 0; l < m - 1; ++l)
+                                mk(MK_MAT1, RC_BREPLACE, {bitb(e.slot, l)}, e.u, e.v, -1, gates_between(e.u, e.v, l), 0);
+                            break;
+                        case EV_EXPAND:
+                            for (int l = 0; l < m - 1; ++l) mk(MK_MAT1, RC_SUMOUT1, {bitb(e.slot, l)}, -1, -1, -1, {}, 0);
+                            break;
+                        case EV_SUMOUT:
+                            for (int l = 0; l < m - 1; ++l) mk(MK_MAT1, RC_EXPAND, {bitb(e.slot, l)}, -1, -1, -1, {}, 0);
+                            break;
+                        case EV_EDGE:
+                            for (int l = 0; l < m - 1; ++l) {
+                                std::vector<int> gl = gates_between(e.u, e.v, l);
+                                if (!gl.empty())
+                                    mk(MK_DIAG, RC_EDGE, {bitb(e.slot, l), bitb(e.slot2, l)}, e.u, e.v, -1, gl, 0);
+                            }
+                            break;
+                    }
+                }
+                br.bwd_end = (int)hp.micro.size();
+            }
+        }
+        // readout metadata and block sites
+        for (int k = 0; k < K; ++k) {
+            DevBlockRange& br = hp.block_ranges[(size_t)m * K + k];
+            br.site_begin = (int)hp.block_sites.size();
+            for (int q : hp.blocks[k]) {
+                DevBlockSite bs{};
+                bs.q = (int16_t)q;
+                bs.monomial = hp.mix_mono[(size_t)m * n + q];
+                bs.op_id = L.mixer_op_of[(size_t)m * n + q];
+                bs.trace_row = bs.monomial ? -1 : trace_row++;
+                hp.block_sites.push_back(bs);
+                hp.exec_order.push_back(bs.op_id);
+                hp.exec_layer[bs.op_id] = m;
+                hp.exec_block[bs.op_id] = k;
+                hp.exec_pos[bs.op_id] = (int)(hp.block_sites.size() - 1 - br.site_begin);
+            }
+            br.site_end = (int)hp.block_sites.size();
+            br.live_begin = (int)hp.live_slots.size();
+            std::vector<DevLiveSlot> ls(S);
+            for (auto& s : ls) { s.q = -1; s.role = -1; s.dlist = 0; s.dcount = 0; }
+            for (auto [u, j] : live_at[k]) {
+                ls[j].q = (int16_t)u;
+                int role = -1;
+                for (int i = 0; i < (int)hp.blocks[k].size(); ++i)
+                    if (hp.blocks[k][i] == u) role = i;
+                ls[j].role = (int16_t)role;
+                std::vector<int> dl;
+                for (int w : adj[u])
+                    if (blk[w] > k)
+                        for (int g : gates_between(u, w, m - 1)) dl.push_back(g);
+                ls[j].dcount = (int)dl.size();
+                ls[j].dlist = dl.empty() ? 0 : push_glist(dl);
+            }
+            for (auto& s : ls) hp.live_slots.push_back(s);
+            br.live_end = (int)hp.live_slots.size();
+        }
+        (void)Wm;
+    }
+    for (int id : L.sections[P + 1]) hp.exec_order.push_back(id);
+    // algorithmic real flops per sample: a 2x2 on one bit costs 14 flops per
+    // entry (two complex multiplies and one add), a diagonal or scalar factor 6,
+    // the readout's dot product with R_k 8 per entry of L
+    for (int m = 1; m <= P; ++m) {
+        double NF = std::ldexp(1.0, S * m), NB = std::ldexp(1.0, S * (m - 1));
+        for (int k = 0; k < K; ++k) {
+            const DevBlockRange& br = hp.block_ranges[(size_t)m * K + k];
+            for (int i = br.fwd_begin; i < br.fwd_end; ++i) flops += (hp.micro[i].kind == MK_MAT1 ? 14.0 : 6.0) * NF;
+            for (int i = br.bwd_begin; i < br.bwd_end; ++i) flops += (hp.micro[i].kind == MK_MAT1 ? 14.0 : 6.0) * NB;
+            flops += 8.0 * NF;
+        }
+    }
+    hp.flops_per_sample = flops;
+    hp.amps_per_sample = 2.0 * trace_row;
+    hp.hdr.n = n;
+    hp.hdr.P = P;
+    hp.hdr.S = S;
+    hp.hdr.K = K;
+    hp.hdr.n_ops = (int)c->ops.size();
+    hp.hdr.n_cost_gates = (int)hp.cost_gates.size();
+    hp.hdr.n_channels = (int)hp.channels.size();
+    hp.hdr.n_sampled = trace_row;
+    hp.hdr.max_block = 1;
+    for (auto& b : hp.blocks) hp.hdr.max_block = std::max<int>(hp.hdr.max_block, (int)b.size());
+    hp.hdr.has_segfac = has_segfac ? 1 : 0;
+    hp.hdr.has_frame = has_frame ? 1 : 0;
+    hp.hdr.words = (n + 63) / 64;
+    hp.W = S * std::max(P, 1);
+    hp.W_low = S * std::max(P - 1, 0);
+    return PW_OK;
+}
+
+}  // namespace pw

@@ -1,0 +1,214 @@
+// Internal structures shared by the circuit builder, the planner and the CUDA
+// sampler. Host-only parts are guarded so the header also compiles in .cu files.
+#pragma once
+
+#include <complex>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/pw.h"
+
+namespace pw {
+
+using cd = std::complex<double>;
+
+// ----------------------------------------------------------------- errors
+int set_error(int code, const std::string& msg);
+
+// ---------------------------------------------------------------- circuit
+enum OpKind { OP_GATE = 0, OP_KRAUS = 1 };
+
+struct Op {
+    int kind = OP_GATE;
+    std::vector<int> qubits;
+    int k = 1;                 // number of matrices (Kraus operators)
+    std::vector<cd> mats;      // k matrices of dim x dim, row-major
+    int dim() const { return 1 << (int)qubits.size(); }
+    const cd* mat(int i) const { return mats.data() + (size_t)i * dim() * dim(); }
+};
+
+bool is_diagonal(const cd* A, int dim);
+bool is_monomial(const cd* A, int dim);
+
+}  // namespace pw
+
+struct pw_circuit {
+    int n = 0;
+    std::vector<pw::Op> ops;
+};
+
+namespace pw {
+
+// ------------------------------------------------------ device plan layout
+// Micro-op kinds applied to a chain's frontier tensor (2^W complex values).
+enum MicroKind : uint8_t {
+    MK_MAT1 = 0,   // 2x2 matrix on one bit: out[a'] = sum_a M[a'][a] in[a]
+    MK_DIAG = 1,   // multiply by table[bits gathered from the index]
+    MK_CONST = 2,  // multiply by one scalar
+};
+
+// How the micro-op's matrix / table is built for a given chain.
+enum Recipe : uint8_t {
+    RC_EXPAND = 0,      // M = [[1,0],[1,0]]: a new leg, constant along it
+    RC_SUMOUT1 = 1,     // M = [[1,1],[0,0]]: sum a leg out
+    RC_SUMOUT_MIX = 2,  // M = [[w0,w1],[0,0]], w = A'_{layer,qa}[s_qa][.]
+    RC_REPLACE = 3,     // M[a'][a] = prod_g D'_g(qa<-a, qb<-a') * (layer>=0 ? A'_{layer,qa}[s_qa][a] : 1)
+    RC_BREPLACE = 4,    // M[a][a'] = prod_g D'_g(qa<-a, qb<-a')   (in: qb's leg, out: qa's leg)
+    RC_EDGE = 5,        // table[a + 2b] = prod_g D'_g(qa<-a, qb<-b)
+    RC_SITE = 6,        // site tensor of qa over its open segments (see sampler)
+    RC_CONST_EDGES = 7, // prod_g D'_g(s_q0, s_q1)
+};
+
+struct DevMicroOp {
+    uint8_t kind;
+    uint8_t recipe;
+    uint8_t nbits;
+    uint8_t fixed_top;   // RC_SITE: top segment fixed to s (backward sweep)
+    uint8_t bits[4];
+    int16_t qa, qb;
+    int16_t layer;       // mixer layer of the top weight (-1: none); RC_SITE: number of segments
+    int16_t pad0;
+    int32_t glist;       // first index into gate_refs
+    int32_t gcount;
+};
+
+// A diagonal cost gate (1 or 2 qubits) with its table; level = segment index.
+struct DevCostGate {
+    int16_t q0, q1;      // q1 < 0 for a one-qubit gate
+    int16_t level;
+    int16_t pad;
+    double d[8];         // 4 complex (re, im) entries, local index b0 + 2 b1
+};
+
+// Items of a cost section, processed in circuit order by one thread per chain.
+enum CostItemKind : int16_t { CI_GATE2 = 0, CI_GATE1 = 1, CI_CHANNEL = 2 };
+struct DevCostItem {
+    int16_t kind;
+    int16_t pad;
+    int32_t idx;         // cost gate index or channel index
+};
+
+struct DevKrausFactor {
+    int16_t q;
+    int16_t antidiag;    // 1: factor is anti-diagonal, flips the frame bit
+    int32_t pad;
+    double d[4];         // diagonal (after the sigma_X fold) as (re, im) x 2
+};
+
+struct DevChannel {
+    int32_t op_id;
+    int16_t nq, k;
+    int16_t q[2];
+    int32_t cum_off;     // [2^nq][k] cumulative probabilities (FP64)
+    int32_t fac_off;     // [k][nq] factors
+};
+
+// A site resampled in a readout block.
+struct DevBlockSite {
+    int16_t q;
+    int16_t monomial;    // 1: deterministic move
+    int32_t op_id;
+    int32_t trace_row;   // -1 when the update is deterministic
+    int32_t pad;
+};
+
+// A live frontier slot at a readout.
+struct DevLiveSlot {
+    int16_t q;           // qubit, -1 if the slot is free
+    int16_t role;        // index of the site inside the block, or -1 (done earlier)
+    int32_t dlist;       // gate refs of the cross edges to unabsorbed qubits
+    int32_t dcount;
+    int32_t pad;
+};
+
+// Per (layer m >= 1, block k) ranges.
+struct DevBlockRange {
+    int32_t fwd_begin, fwd_end;
+    int32_t bwd_begin, bwd_end;     // backward micro-ops turning R_k into R_{k-1}
+    int32_t site_begin, site_end;   // DevBlockSite
+    int32_t live_begin, live_end;   // DevLiveSlot
+};
+
+struct DevPlanHeader {
+    int32_t n, P;              // qubits, mixer layers after the first
+    int32_t S;                 // slots
+    int32_t K;                 // blocks
+    int32_t n_ops;
+    int32_t n_cost_gates;
+    int32_t n_channels;
+    int32_t n_sampled;         // trace rows
+    int32_t max_block;
+    int32_t has_segfac;        // 1-qubit diagonal gates or channels present
+    int32_t has_frame;         // channels present
+    int32_t words;             // uint64 words per bitstring
+};
+
+// Offsets (in bytes) of the arrays inside the device blob.
+struct DevPlanOffsets {
+    int64_t micro, gate_refs, cost_gates, cost_items, cost_ranges, channels, cum, factors;
+    int64_t mix_d, mix_f, mix0_order, mix0_opid, mix_mono;
+    int64_t block_ranges, block_sites, live_slots;
+};
+
+}  // namespace pw
+
+#ifndef __CUDACC__
+#endif
+
+struct pw_plan_host;  // forward
+
+namespace pw {
+
+struct HostPlan {
+    DevPlanHeader hdr{};
+    // blob pieces (host copies)
+    std::vector<DevMicroOp> micro;
+    std::vector<int32_t> gate_refs;
+    std::vector<DevCostGate> cost_gates;
+    std::vector<DevCostItem> cost_items;
+    std::vector<int32_t> cost_ranges;      // [P+2]: items of section m in [r[m], r[m+1]) (m = 1..P+1 used)
+    std::vector<DevChannel> channels;
+    std::vector<double> cum;
+    std::vector<DevKrausFactor> factors;
+    std::vector<double> mix_d;             // [(P+1) * n * 8]  (2x2 complex, [o][i])
+    std::vector<float> mix_f;
+    std::vector<int32_t> mix0_order;       // qubits of mixer layer 0 in circuit order
+    std::vector<int32_t> mix0_opid;        // op id of mixer-0 gate per qubit
+    std::vector<int8_t> mix_mono;          // [(P+1) * n]: 1 if the mixer is monomial
+    std::vector<DevBlockRange> block_ranges;   // [(P+1) * K] (layer 0 unused)
+    std::vector<DevBlockSite> block_sites;
+    std::vector<DevLiveSlot> live_slots;
+
+    std::vector<int> exec_order;          // op ids in execution order
+    std::vector<int> sweep_order;         // qubit order pi
+    std::vector<std::vector<int>> blocks; // qubits per block
+    int W = 0, W_low = 0;                 // at the deepest layer
+    double flops_per_sample = 0.0;
+    double amps_per_sample = 0.0;
+    int precision = PW_PREC_FP32;
+    int threads_per_chain = 0;
+    int chains_per_cta = 1;
+    int chains_per_launch = 0;
+    size_t smem_per_chain = 0;
+    bool noisy = false;
+    // amplitude API helpers: position of every executed mixer op (layer, block, index)
+    std::vector<int> exec_layer, exec_block, exec_pos;
+};
+
+int build_plan(const pw_circuit* c, const pw_plan_opts& opts, HostPlan& out);
+size_t plan_device_bytes(const HostPlan& hp);
+
+}  // namespace pw
+
+struct pw_plan {
+    pw::HostPlan hp;
+    // device side (lazily created on first use)
+    int device = -1;
+    void* d_blob = nullptr;
+    size_t blob_bytes = 0;
+    pw::DevPlanOffsets off{};
+    unsigned long long* d_counters = nullptr;
+    void* d_stage = nullptr;       // staging for pw_sample_host
+    size_t stage_bytes = 0;
+};

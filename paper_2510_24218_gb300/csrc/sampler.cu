@@ -1,0 +1,921 @@
+// Pilot-wave sampler kernel for sm_103a.
+//
+// One group of threads (a warp, or a named-barrier group inside a CTA) owns
+// one Markov chain (Alg. 1 / Alg. 2) for its whole life: it walks every layer
+// of the circuit, keeps the frontier tensor of the plan's sweep in shared
+// memory, evaluates the candidate amplitudes amp(C_t, y) of each resampled
+// qubit with the plan's micro-op program, and draws the update from the
+// normalised conditional with a counter-based Philox stream. Only the packed
+// output bits (and the optional amplitude trace) reach HBM: the kernel is
+// bound by shared-memory traffic and FP32 arithmetic, not by DRAM.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+
+#include "pw_internal.h"
+
+namespace pw {
+
+// --------------------------------------------------------------- complex
+template <typename R> struct CT;
+template <> struct CT<float> { using T = float2; };
+template <> struct CT<double> { using T = double2; };
+
+template <typename C> __device__ __forceinline__ C cmk(double re, double im) {
+    C c;
+    c.x = re;
+    c.y = im;
+    return c;
+}
+template <typename C> __device__ __forceinline__ C cmul(C a, C b) {
+    C c;
+    c.x = a.x * b.x - a.y * b.y;
+    c.y = a.x * b.y + a.y * b.x;
+    return c;
+}
+// a*b + c
+template <typename C> __device__ __forceinline__ C cfma(C a, C b, C c) {
+    C r;
+    r.x = fma(a.x, b.x, fma(-a.y, b.y, c.x));
+    r.y = fma(a.x, b.y, fma(a.y, b.x, c.y));
+    return r;
+}
+__device__ __forceinline__ float scl(float v, int e) { return ldexpf(v, e); }
+__device__ __forceinline__ double scl(double v, int e) { return ldexp(v, e); }
+__device__ __forceinline__ float rmax(float a, float b) { return fmaxf(a, b); }
+__device__ __forceinline__ double rmax(double a, double b) { return fmax(a, b); }
+__device__ __forceinline__ float rabs(float a) { return fabsf(a); }
+__device__ __forceinline__ double rabs(double a) { return fabs(a); }
+
+// ---------------------------------------------------------------- Philox
+// Philox4x32-10 (Salmon et al., SC'11): the two round multipliers and the two
+// Weyl key increments of the published definition.
+__device__ __forceinline__ void philox10(uint32_t c[4], uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        uint32_t lo0 = 0xD2511F53u * c[0], hi0 = __umulhi(0xD2511F53u, c[0]);
+        uint32_t lo1 = 0xCD9E8D57u * c[2], hi1 = __umulhi(0xCD9E8D57u, c[2]);
+        uint32_t n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
+        c[0] = n0;
+        c[1] = lo1;
+        c[2] = n2;
+        c[3] = lo0;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+}
+
+// Uniform in [0,1) with 53 random bits: top 27 bits of w0, top 26 of w1.
+__device__ __forceinline__ double draw_u(uint64_t seed, uint64_t sample, uint32_t op_id, uint32_t purpose) {
+    uint32_t c[4] = {(uint32_t)sample, (uint32_t)(sample >> 32), op_id, purpose};
+    philox10(c, (uint32_t)seed, (uint32_t)(seed >> 32));
+    return ((double)(c[0] >> 5) * 67108864.0 + (double)(c[1] >> 6)) * (1.0 / 9007199254740992.0);
+}
+
+// ----------------------------------------------------------- parameters
+struct SmemLayout {
+    int L, R, Rexp, rowdot, T, tab, fslot, red, s, x, xmix, gframe, segfac, misc, group_bytes;
+};
+
+struct KParams {
+    const unsigned char* blob;
+    DevPlanOffsets off;
+    DevPlanHeader hdr;
+    SmemLayout sm;
+    uint64_t seed, first, count;
+    uint64_t* out_bits;
+    double* trace;
+    unsigned long long* counters;
+    int tpc, gpc;
+    int mode;           // MODE_SAMPLE or MODE_AMP
+    const uint64_t* in_bits;
+    double* amp_out;
+    int amp_layer, amp_block, amp_pos;
+};
+
+enum { MODE_SAMPLE = 0, MODE_AMP = 1 };
+enum { CNT_NEAR = 0, CNT_ZERO = 1 };
+
+template <typename T> __device__ __forceinline__ const T* P_(const KParams& p, int64_t off) {
+    return reinterpret_cast<const T*>(p.blob + off);
+}
+
+// Barrier of one chain's thread group.
+__device__ __forceinline__ void gsync(const KParams& p, int gid) {
+    if (p.tpc == 32) {
+        __syncwarp();
+    } else {
+        asm volatile("bar.sync %0, %1;" ::"r"(gid + 1), "r"(p.tpc) : "memory");
+    }
+}
+
+// Per-chain view of the shared-memory group.
+template <typename R> struct Chain {
+    using C = typename CT<R>::T;
+    C* L;         // frontier tensor, 2^W
+    C* Rt;        // right environments, K x 2^Wl
+    int* Rexp;    // their power-of-two exponents
+    C* rowdot;    // 2^S
+    C* T;         // 2^max_block
+    C* tab;       // 2 x 16 micro-op tables
+    C* fslot;     // S x 2 per-slot readout factors
+    R* red;       // 32 reduction scratch
+    uint8_t* s;   // chain state s
+    uint8_t* x;   // frame x (Alg. 2)
+    uint8_t* xmix;    // frame during each one-qubit layer, [(P+1) n]
+    uint8_t* gframe;  // frame bits of each diagonal gate at its time
+    C* segfac;    // one-qubit diagonal factors per (qubit, segment), [n][P+1][2]
+    int* misc;    // [0] exponent of L, [1] pending rescale, [2..] role slots
+};
+
+// Frame-conjugated one-qubit gate A'_{m,q}[o][i] = A[o^x][i^x] (PropagateX).
+template <typename R>
+__device__ __forceinline__ typename CT<R>::T mixel(const KParams& p, const Chain<R>& ch, int m, int q, int o, int i) {
+    int xb = p.hdr.has_frame ? ch.xmix[m * p.hdr.n + q] : 0;
+    size_t base = ((size_t)m * p.hdr.n + q) * 8 + 2 * (((o ^ xb) << 1) | (i ^ xb));
+    if (sizeof(R) == 4) {
+        const float* f = P_<float>(p, p.off.mix_f);
+        return cmk<typename CT<R>::T>(f[base], f[base + 1]);
+    } else {
+        const double* d = P_<double>(p, p.off.mix_d);
+        return cmk<typename CT<R>::T>(d[base], d[base + 1]);
+    }
+}
+
+// D'_g(a0 on q0, a1 on q1): a diagonal gate conjugated by the frame at its time.
+template <typename R>
+__device__ __forceinline__ typename CT<R>::T gatel(const KParams& p, const Chain<R>& ch, int g, int a0, int a1) {
+    const DevCostGate& G = P_<DevCostGate>(p, p.off.cost_gates)[g];
+    int f = p.hdr.has_frame ? ch.gframe[g] : 0;
+    int idx = (a0 ^ (f & 1)) | ((a1 ^ ((f >> 1) & 1)) << 1);
+    return cmk<typename CT<R>::T>(G.d[2 * idx], G.d[2 * idx + 1]);
+}
+
+// D'_g with qubit qa set to va and the other qubit of g set to vb.
+template <typename R>
+__device__ __forceinline__ typename CT<R>::T gate_pair(const KParams& p, const Chain<R>& ch, int g, int qa, int va, int vb) {
+    const DevCostGate& G = P_<DevCostGate>(p, p.off.cost_gates)[g];
+    return G.q0 == qa ? gatel<R>(p, ch, g, va, vb) : gatel<R>(p, ch, g, vb, va);
+}
+
+// Entry e of micro-op o's table (MAT1: e = out*2 + in; DIAG: gathered bits).
+template <typename R>
+__device__ typename CT<R>::T build_entry(const KParams& p, const Chain<R>& ch, const DevMicroOp& o, int e) {
+    using C = typename CT<R>::T;
+    const int32_t* gref = P_<int32_t>(p, p.off.gate_refs);
+    const C one = cmk<C>(1.0, 0.0), zero = cmk<C>(0.0, 0.0);
+    switch (o.recipe) {
+        case RC_EXPAND:
+            return (e & 1) == 0 ? one : zero;
+        case RC_SUMOUT1:
+            return (e >> 1) == 0 ? one : zero;
+        case RC_SUMOUT_MIX:
+            return (e >> 1) == 0 ? mixel<R>(p, ch, o.layer, o.qa, ch.s[o.qa], e & 1) : zero;
+        case RC_REPLACE: {
+            int aout = e >> 1, ain = e & 1;   // out: new site qb, in: eliminated site qa
+            C v = o.layer >= 0 ? mixel<R>(p, ch, o.layer, o.qa, ch.s[o.qa], ain) : one;
+            for (int i = 0; i < o.gcount; ++i) v = cmul(v, gate_pair<R>(p, ch, gref[o.glist + i], o.qa, ain, aout));
+            return v;
+        }
+        case RC_BREPLACE: {
+            int aout = e >> 1, ain = e & 1;   // out: site qa, in: site qb
+            C v = one;
+            for (int i = 0; i < o.gcount; ++i) v = cmul(v, gate_pair<R>(p, ch, gref[o.glist + i], o.qa, aout, ain));
+            return v;
+        }
+        case RC_EDGE: {
+            int a = e & 1, b = (e >> 1) & 1;
+            C v = one;
+            for (int i = 0; i < o.gcount; ++i) v = cmul(v, gate_pair<R>(p, ch, gref[o.glist + i], o.qa, a, b));
+            return v;
+        }
+        case RC_SITE: {
+            // Segments z^0..z^{layer-1} of qubit qa: the open ones are the low
+            // bits of e, a fixed top takes the chain's bit. Value:
+            // <z^0|A_0|0> prod_l A'_l[z^l][z^{l-1}] prod_l segfac(q, l)[z^l].
+            int q = o.qa, nseg = o.layer;
+            int z[8];
+            for (int l = 0; l < nseg; ++l) z[l] = (e >> l) & 1;
+            if (o.fixed_top) z[nseg - 1] = ch.s[q];
+            C v = mixel<R>(p, ch, 0, q, z[0], 0);
+            for (int l = 1; l < nseg; ++l) v = cmul(v, mixel<R>(p, ch, l, q, z[l], z[l - 1]));
+            if (p.hdr.has_segfac) {
+                int P1 = p.hdr.P + 1;
+                for (int l = 0; l < nseg; ++l) v = cmul(v, ch.segfac[((size_t)q * P1 + l) * 2 + z[l]]);
+            }
+            return v;
+        }
+        case RC_CONST_EDGES: {
+            C v = one;
+            const DevCostGate* G = P_<DevCostGate>(p, p.off.cost_gates);
+            for (int i = 0; i < o.gcount; ++i) {
+                int g = gref[o.glist + i];
+                v = cmul(v, gatel<R>(p, ch, g, ch.s[G[g].q0], ch.s[G[g].q1]));
+            }
+            return v;
+        }
+    }
+    return one;
+}
+
+// Apply micro-ops [b, e) to the tensor buf of 2^W entries; pend_exp is a power
+// of two folded into the first op (exact rescaling).
+template <typename R>
+__device__ void apply_ops(const KParams& p, const Chain<R>& ch, int gid, int lt, int b, int e,
+                          typename CT<R>::T* buf, int W, int pend_exp) {
+    using C = typename CT<R>::T;
+    const DevMicroOp* ops = P_<DevMicroOp>(p, p.off.micro);
+    const int N = 1 << W;
+    for (int i = b; i < e; ++i) {
+        const DevMicroOp o = ops[i];
+        C* tab = ch.tab + 16 * ((i - b) & 1);
+        const int ne = o.kind == MK_MAT1 ? 4 : (o.kind == MK_DIAG ? (1 << o.nbits) : 1);
+        for (int en = lt; en < ne; en += p.tpc) {
+            C v = build_entry<R>(p, ch, o, en);
+            if (i == b && pend_exp != 0) {
+                v.x = scl(v.x, pend_exp);
+                v.y = scl(v.y, pend_exp);
+            }
+            tab[en] = v;
+        }
+        gsync(p, gid);
+        if (o.kind == MK_MAT1) {
+            const int bt = o.bits[0];
+            const C m00 = tab[0], m01 = tab[1], m10 = tab[2], m11 = tab[3];
+            const int lomask = (1 << bt) - 1;
+            for (int pi = lt; pi < (N >> 1); pi += p.tpc) {
+                const int i0 = ((pi >> bt) << (bt + 1)) | (pi & lomask);
+                const int i1 = i0 | (1 << bt);
+                const C x0 = buf[i0], x1 = buf[i1];
+                buf[i0] = cfma(m00, x0, cmul(m01, x1));
+                buf[i1] = cfma(m10, x0, cmul(m11, x1));
+            }
+        } else if (o.kind == MK_DIAG) {
+            const int nb = o.nbits;
+            const int b0 = o.bits[0], b1 = o.bits[1], b2 = o.bits[2], b3 = o.bits[3];
+            for (int idx = lt; idx < N; idx += p.tpc) {
+                int t = (idx >> b0) & 1;
+                if (nb > 1) t |= ((idx >> b1) & 1) << 1;
+                if (nb > 2) t |= ((idx >> b2) & 1) << 2;
+                if (nb > 3) t |= ((idx >> b3) & 1) << 3;
+                buf[idx] = cmul(buf[idx], tab[t]);
+            }
+        } else {
+            const C c = tab[0];
+            for (int idx = lt; idx < N; idx += p.tpc) buf[idx] = cmul(buf[idx], c);
+        }
+    }
+    gsync(p, gid);
+}
+
+// Group-wide max of a per-thread value (broadcast to every thread).
+template <typename R>
+__device__ R group_max(const KParams& p, const Chain<R>& ch, int gid, int lt, R v) {
+    for (int o = 16; o > 0; o >>= 1) v = rmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    const int nw = (p.tpc + 31) >> 5;
+    if ((lt & 31) == 0) ch.red[lt >> 5] = v;
+    gsync(p, gid);
+    R m = ch.red[0];
+    for (int w = 1; w < nw; ++w) m = rmax(m, ch.red[w]);
+    gsync(p, gid);
+    return m;
+}
+
+// Exponent e with 2^-e * mx in [0.5, 1); 0 for zero or non-finite mx.
+template <typename R> __device__ __forceinline__ int scale_exp(R mx) {
+    if (!(mx > (R)0) || !isfinite((double)mx)) return 0;
+    int e;
+    frexp((double)mx, &e);
+    return e;
+}
+
+// Kraus draw of Eq. (5) at the true bits s XOR x, then Alg. 2: every
+// anti-diagonal factor flips x[q] and becomes the diagonal M sigma_X; each
+// diagonal factor is conjugated by the (updated) frame and multiplied into the
+// qubit's current segment.
+template <typename R>
+__device__ void apply_channel(const KParams& p, const Chain<R>& ch, const DevChannel& c, const double* cum,
+                              const DevKrausFactor* fac, uint64_t sample_id, int seg) {
+    using C = typename CT<R>::T;
+    int cb = 0;
+    for (int i = 0; i < c.nq; ++i) cb |= (ch.s[c.q[i]] ^ ch.x[c.q[i]]) << i;
+    const double* row = cum + c.cum_off + (size_t)cb * c.k;
+    const double total = row[c.k - 1];
+    const double u = draw_u(p.seed, sample_id, (uint32_t)c.op_id, 1u);
+    int pick = c.k - 1;
+    for (int i = 0; i < c.k; ++i)
+        if (u * total < row[i]) {
+            pick = i;
+            break;
+        }
+    for (int i = 0; i + 1 < c.k; ++i)
+        if (fabs(u * total - row[i]) < 1e-6 * total) {
+            atomicAdd(&p.counters[CNT_NEAR], 1ull);
+            break;
+        }
+    const int P1 = p.hdr.P + 1;
+    for (int f = 0; f < c.nq; ++f) {
+        const DevKrausFactor F = fac[c.fac_off + pick * c.nq + f];
+        if (F.antidiag) ch.x[F.q] ^= 1;
+        C d0 = cmk<C>(F.d[0], F.d[1]), d1 = cmk<C>(F.d[2], F.d[3]);
+        if (ch.x[F.q]) {
+            C t = d0;
+            d0 = d1;
+            d1 = t;
+        }
+        C* sf = ch.segfac + ((size_t)F.q * P1 + seg) * 2;
+        sf[0] = cmul(sf[0], d0);
+        sf[1] = cmul(sf[1], d1);
+    }
+}
+
+// Readout of block k of layer m: T(tops of the block's sites) =
+// sum L * R_k * prod_slots f_slot, then the block's sites are resampled one
+// after another (Alg. 1's UpdateState), contracting each resampled top with
+// A'_m[s_new][.] before moving to the next site.
+template <typename R>
+__device__ void readout_and_sample(const KParams& p, const Chain<R>& ch, int gid, int lt, int m, int k,
+                                   const DevBlockRange& br, uint64_t sample_id, uint64_t chain) {
+    using C = typename CT<R>::T;
+    const DevPlanHeader& h = p.hdr;
+    const int S = h.S, Wl = S * (m - 1);
+    const int NL = 1 << Wl, H = 1 << S;
+    const C zero = cmk<C>(0.0, 0.0), one = cmk<C>(1.0, 0.0);
+    const C* Rk = ch.Rt + (size_t)k * NL;
+    const C* L = ch.L;
+
+    // 1) rowdot[h] = sum_l L[h, l] R_k[l], and max |L| for the rescale
+    R mx = 0;
+    if (NL >= 32 && p.tpc >= 32) {
+        const int nw = p.tpc >> 5, w = lt >> 5, lane = lt & 31;
+        for (int hr = w; hr < H; hr += nw) {
+            C acc = zero;
+            for (int l = lane; l < NL; l += 32) {
+                const C v = L[(size_t)hr * NL + l];
+                acc = cfma(v, Rk[l], acc);
+                mx = rmax(mx, rmax(rabs(v.x), rabs(v.y)));
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+                acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+            }
+            if (lane == 0) ch.rowdot[hr] = acc;
+        }
+    } else {
+        for (int hr = lt; hr < H; hr += p.tpc) {
+            C acc = zero;
+            for (int l = 0; l < NL; ++l) {
+                const C v = L[(size_t)hr * NL + l];
+                acc = cfma(v, Rk[l], acc);
+                mx = rmax(mx, rmax(rabs(v.x), rabs(v.y)));
+            }
+            ch.rowdot[hr] = acc;
+        }
+    }
+    mx = group_max<R>(p, ch, gid, lt, mx);   // also publishes rowdot
+    const int eL = ch.misc[0];
+    const int escale = eL + ch.Rexp[k];
+    const bool target_block = p.mode == MODE_AMP && m == p.amp_layer && k == p.amp_block;
+    gsync(p, gid);
+    if (lt == 0) {
+        const int e = scale_exp<R>(mx);
+        ch.misc[1] = -e;
+        ch.misc[0] = eL + e;
+    }
+    if (p.mode == MODE_AMP && !target_block) {
+        gsync(p, gid);
+        return;
+    }
+
+    // 2) per-slot factors: cross edges of the top segment to unabsorbed qubits
+    //    (at their current bits) and, for sites resampled in earlier blocks,
+    //    their mixer weight A'_m[s][top]
+    const DevLiveSlot* live = P_<DevLiveSlot>(p, p.off.live_slots) + br.live_begin;
+    const DevBlockSite* sites = P_<DevBlockSite>(p, p.off.block_sites) + br.site_begin;
+    const int32_t* gref = P_<int32_t>(p, p.off.gate_refs);
+    const DevCostGate* G = P_<DevCostGate>(p, p.off.cost_gates);
+    const int nb = br.site_end - br.site_begin;
+    for (int j = lt; j < S; j += p.tpc) {
+        const DevLiveSlot sl = live[j];
+        C f0 = one, f1 = zero;
+        if (sl.q >= 0) {
+            f1 = one;
+            for (int i = 0; i < sl.dcount; ++i) {
+                int g = gref[sl.dlist + i];
+                int w = G[g].q0 == sl.q ? G[g].q1 : G[g].q0;
+                f0 = cmul(f0, gate_pair<R>(p, ch, g, sl.q, 0, ch.s[w]));
+                f1 = cmul(f1, gate_pair<R>(p, ch, g, sl.q, 1, ch.s[w]));
+            }
+            if (sl.role < 0) {
+                f0 = cmul(f0, mixel<R>(p, ch, m, sl.q, ch.s[sl.q], 0));
+                f1 = cmul(f1, mixel<R>(p, ch, m, sl.q, ch.s[sl.q], 1));
+            } else {
+                ch.misc[2 + sl.role] = j;
+            }
+        }
+        ch.fslot[2 * j] = f0;
+        ch.fslot[2 * j + 1] = f1;
+    }
+    gsync(p, gid);
+
+    // 3) collapse onto the block's tops: T[t], bit i of t = top of block site i
+    {
+        int rmask = 0;
+        for (int i = 0; i < nb; ++i) rmask |= 1 << ch.misc[2 + i];
+        const int NT = 1 << nb, nother = S - nb;
+        for (int t = lt; t < NT; t += p.tpc) {
+            int hbase = 0;
+            for (int i = 0; i < nb; ++i) hbase |= ((t >> i) & 1) << ch.misc[2 + i];
+            C acc = zero;
+            for (int hh = 0; hh < (1 << nother); ++hh) {
+                int hv = hbase, bit = 0;
+                for (int j = 0; j < S; ++j)
+                    if (!((rmask >> j) & 1)) hv |= ((hh >> bit++) & 1) << j;
+                C wgt = one;
+                for (int j = 0; j < S; ++j) wgt = cmul(wgt, ch.fslot[2 * j + ((hv >> j) & 1)]);
+                acc = cfma(ch.rowdot[hv], wgt, acc);
+            }
+            ch.T[t] = acc;
+        }
+    }
+    gsync(p, gid);
+
+    // 4) sequential resampling of the block's sites (FP64 conditionals)
+    if (lt == 0) {
+        C* cur = ch.T;
+        int size = 1 << nb;
+        for (int i = 0; i < nb; ++i) {
+            const DevBlockSite st = sites[i];
+            const int q = st.q;
+            int rest = 0;   // later sites keep their current bits (projection)
+            for (int j = i + 1; j < nb; ++j) rest |= ch.s[sites[j].q] << (j - i);
+            const C A0y0 = mixel<R>(p, ch, m, q, 0, 0), A0y1 = mixel<R>(p, ch, m, q, 0, 1);
+            const C A1y0 = mixel<R>(p, ch, m, q, 1, 0), A1y1 = mixel<R>(p, ch, m, q, 1, 1);
+            const C c0 = cur[rest], c1 = cur[rest | 1];
+            const C amp0 = cfma(A0y0, c0, cmul(A0y1, c1));
+            const C amp1 = cfma(A1y0, c0, cmul(A1y1, c1));
+            if (p.mode == MODE_AMP) {
+                if (i == p.amp_pos) {
+                    const C a = ch.s[q] ? amp1 : amp0;
+                    p.amp_out[2 * chain] = ldexp((double)a.x, escale);
+                    p.amp_out[2 * chain + 1] = ldexp((double)a.y, escale);
+                    break;
+                }
+            } else if (st.monomial) {
+                // deterministic move: the nonzero of column s[q] of A'_m
+                const C a0 = mixel<R>(p, ch, m, q, 0, ch.s[q]);
+                ch.s[q] = (a0.x != (R)0 || a0.y != (R)0) ? 0 : 1;
+            } else {
+                const double a0r = amp0.x, a0i = amp0.y, a1r = amp1.x, a1i = amp1.y;
+                const double p0 = a0r * a0r + a0i * a0i, p1 = a1r * a1r + a1i * a1i;
+                const double Pt = p0 + p1;
+                if (p.trace) {
+                    double* tr = p.trace + ((size_t)chain * h.n_sampled + st.trace_row) * 4;
+                    tr[0] = ldexp(a0r, escale);
+                    tr[1] = ldexp(a0i, escale);
+                    tr[2] = ldexp(a1r, escale);
+                    tr[3] = ldexp(a1i, escale);
+                }
+                if (Pt > 0.0) {
+                    const double u = draw_u(p.seed, sample_id, (uint32_t)st.op_id, 0u);
+                    ch.s[q] = (u * Pt < p0) ? 0 : 1;
+                    if (fabs(u * Pt - p0) < 1e-6 * Pt) atomicAdd(&p.counters[CNT_NEAR], 1ull);
+                } else {
+                    atomicAdd(&p.counters[CNT_ZERO], 1ull);   // zero-mass block: stay (Sec. 2)
+                }
+            }
+            // contract this site's top with its mixer weight at the new bit
+            const C w0 = mixel<R>(p, ch, m, q, ch.s[q], 0), w1 = mixel<R>(p, ch, m, q, ch.s[q], 1);
+            size >>= 1;
+            for (int r = 0; r < size; ++r) cur[r] = cfma(w0, cur[2 * r], cmul(w1, cur[2 * r + 1]));
+        }
+    }
+    gsync(p, gid);
+}
+
+// ---------------------------------------------------------------- chain
+template <typename R>
+__device__ void run_chain(const KParams& p, const Chain<R>& ch, int gid, int lt, uint64_t chain) {
+    using C = typename CT<R>::T;
+    const DevPlanHeader& h = p.hdr;
+    const int n = h.n, P = h.P, S = h.S, K = h.K;
+    const uint64_t sample_id = p.first + chain;
+    const C one = cmk<C>(1.0, 0.0);
+    const DevBlockRange* BR = P_<DevBlockRange>(p, p.off.block_ranges);
+
+    for (int q = lt; q < n; q += p.tpc) {
+        ch.x[q] = 0;
+        ch.s[q] = p.mode == MODE_AMP ? (uint8_t)((p.in_bits[chain * h.words + (q >> 6)] >> (q & 63)) & 1ull) : 0;
+    }
+    for (int i = lt; i < (P + 1) * n; i += p.tpc) ch.xmix[i] = 0;
+    for (int i = lt; i < h.n_cost_gates; i += p.tpc) ch.gframe[i] = 0;
+    if (h.has_segfac)
+        for (int i = lt; i < n * (P + 1) * 2; i += p.tpc) ch.segfac[i] = one;
+    gsync(p, gid);
+
+    // Layer 0 acts on |0^n>: the prefix state is a product state, so the
+    // conditional of qubit q is |<y|A_0|0>|^2 normalised (same draw rule).
+    if (p.mode == MODE_SAMPLE && lt == 0) {
+        const int32_t* order = P_<int32_t>(p, p.off.mix0_order);
+        const int32_t* opid = P_<int32_t>(p, p.off.mix0_opid);
+        const int8_t* mono = P_<int8_t>(p, p.off.mix_mono);
+        const double* md = P_<double>(p, p.off.mix_d);
+        for (int t = 0; t < n; ++t) {
+            const int q = order[t];
+            const double* A = md + (size_t)q * 8;
+            if (mono[q]) {
+                ch.s[q] = (A[0] != 0.0 || A[1] != 0.0) ? 0 : 1;
+                continue;
+            }
+            const double p0 = A[0] * A[0] + A[1] * A[1];
+            const double p1 = A[4] * A[4] + A[5] * A[5];
+            const double Pt = p0 + p1;
+            const double u = draw_u(p.seed, sample_id, (uint32_t)opid[q], 0u);
+            ch.s[q] = (u * Pt < p0) ? 0 : 1;
+            if (fabs(u * Pt - p0) < 1e-6 * Pt) atomicAdd(&p.counters[CNT_NEAR], 1ull);
+        }
+    }
+    gsync(p, gid);
+
+    const int mhi = p.mode == MODE_AMP ? p.amp_layer : P;
+    for (int m = 1; m <= mhi; ++m) {
+        // cost section m: frame bits of the diagonal gates at their time, the
+        // one-qubit diagonal factors of segment m-1, and the Kraus draws.
+        if (lt == 0 && (h.has_segfac || h.has_frame)) {
+            const int32_t* cr = P_<int32_t>(p, p.off.cost_ranges);
+            const DevCostItem* items = P_<DevCostItem>(p, p.off.cost_items);
+            const DevCostGate* G = P_<DevCostGate>(p, p.off.cost_gates);
+            for (int it = cr[m]; it < cr[m + 1]; ++it) {
+                const DevCostItem ci = items[it];
+                if (ci.kind == CI_GATE2) {
+                    ch.gframe[ci.idx] = (uint8_t)(ch.x[G[ci.idx].q0] | (ch.x[G[ci.idx].q1] << 1));
+                } else if (ci.kind == CI_GATE1) {
+                    const int q = G[ci.idx].q0, xb = ch.x[q];
+                    C* sf = ch.segfac + ((size_t)q * (P + 1) + (m - 1)) * 2;
+                    sf[0] = cmul(sf[0], cmk<C>(G[ci.idx].d[2 * xb], G[ci.idx].d[2 * xb + 1]));
+                    sf[1] = cmul(sf[1], cmk<C>(G[ci.idx].d[2 * (1 ^ xb)], G[ci.idx].d[2 * (1 ^ xb) + 1]));
+                } else if (p.mode == MODE_SAMPLE) {
+                    apply_channel<R>(p, ch, P_<DevChannel>(p, p.off.channels)[ci.idx], P_<double>(p, p.off.cum),
+                                     P_<DevKrausFactor>(p, p.off.factors), sample_id, m - 1);
+                }
+            }
+            for (int q = 0; q < n; ++q) ch.xmix[m * n + q] = ch.x[q];
+        }
+        gsync(p, gid);
+        if (p.mode == MODE_AMP && m < p.amp_layer) continue;
+
+        const int Wl = S * (m - 1), W = S * m;
+        const int NL = 1 << Wl, N = 1 << W;
+        const int kstop = p.mode == MODE_AMP ? p.amp_block : 0;   // R_k needed for k >= kstop
+
+        // backward sweep: R_{K-1} = 1, R_{k-1} from R_k by block k's reversed program
+        C* RK = ch.Rt + (size_t)(K - 1) * NL;
+        for (int i = lt; i < NL; i += p.tpc) RK[i] = one;
+        if (lt == 0) ch.Rexp[K - 1] = 0;
+        gsync(p, gid);
+        for (int k = K - 1; k > kstop; --k) {
+            const C* src = ch.Rt + (size_t)k * NL;
+            C* dst = ch.Rt + (size_t)(k - 1) * NL;
+            for (int i = lt; i < NL; i += p.tpc) dst[i] = src[i];
+            gsync(p, gid);
+            const DevBlockRange br = BR[(size_t)m * K + k];
+            apply_ops<R>(p, ch, gid, lt, br.bwd_begin, br.bwd_end, dst, Wl, 0);
+            R mx = 0;
+            for (int i = lt; i < NL; i += p.tpc) mx = rmax(mx, rmax(rabs(dst[i].x), rabs(dst[i].y)));
+            mx = group_max<R>(p, ch, gid, lt, mx);
+            const int e = scale_exp<R>(mx);
+            if (e != 0)
+                for (int i = lt; i < NL; i += p.tpc) {
+                    dst[i].x = scl(dst[i].x, -e);
+                    dst[i].y = scl(dst[i].y, -e);
+                }
+            if (lt == 0) ch.Rexp[k - 1] = ch.Rexp[k] + e;
+            gsync(p, gid);
+        }
+
+        // forward sweep with a readout after every block
+        for (int i = lt; i < N; i += p.tpc) ch.L[i] = cmk<C>(i == 0 ? 1.0 : 0.0, 0.0);
+        if (lt == 0) {
+            ch.misc[0] = 0;
+            ch.misc[1] = 0;
+        }
+        gsync(p, gid);
+        const int kend = p.mode == MODE_AMP ? p.amp_block : K - 1;
+        for (int k = 0; k <= kend; ++k) {
+            const DevBlockRange br = BR[(size_t)m * K + k];
+            const int pend = ch.misc[1];
+            gsync(p, gid);
+            apply_ops<R>(p, ch, gid, lt, br.fwd_begin, br.fwd_end, ch.L, W, pend);
+            readout_and_sample<R>(p, ch, gid, lt, m, k, br, sample_id, chain);
+        }
+    }
+    if (p.mode == MODE_AMP) return;
+
+    // channels after the last layer (they can only move the frame)
+    if (lt == 0 && h.has_frame) {
+        const int32_t* cr = P_<int32_t>(p, p.off.cost_ranges);
+        const DevCostItem* items = P_<DevCostItem>(p, p.off.cost_items);
+        for (int it = cr[P + 1]; it < cr[P + 2]; ++it)
+            if (items[it].kind == CI_CHANNEL)
+                apply_channel<R>(p, ch, P_<DevChannel>(p, p.off.channels)[items[it].idx], P_<double>(p, p.off.cum),
+                                 P_<DevKrausFactor>(p, p.off.factors), sample_id, P);
+    }
+    gsync(p, gid);
+    // sample = s XOR x (Alg. 2), packed 64 qubits per word
+    for (int w = lt; w < h.words; w += p.tpc) {
+        uint64_t v = 0;
+        for (int b = 0; b < 64 && w * 64 + b < n; ++b) v |= (uint64_t)(ch.s[w * 64 + b] ^ ch.x[w * 64 + b]) << b;
+        p.out_bits[chain * h.words + w] = v;
+    }
+    gsync(p, gid);
+}
+
+template <typename R>
+__global__ void __launch_bounds__(512) pw_chain_kernel(const KParams p) {
+    using C = typename CT<R>::T;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int gid = threadIdx.x / p.tpc;
+    const int lt = threadIdx.x - gid * p.tpc;
+    unsigned char* g = smem + (size_t)gid * p.sm.group_bytes;
+    Chain<R> ch;
+    ch.L = reinterpret_cast<C*>(g + p.sm.L);
+    ch.Rt = reinterpret_cast<C*>(g + p.sm.R);
+    ch.Rexp = reinterpret_cast<int*>(g + p.sm.Rexp);
+    ch.rowdot = reinterpret_cast<C*>(g + p.sm.rowdot);
+    ch.T = reinterpret_cast<C*>(g + p.sm.T);
+    ch.tab = reinterpret_cast<C*>(g + p.sm.tab);
+    ch.fslot = reinterpret_cast<C*>(g + p.sm.fslot);
+    ch.red = reinterpret_cast<R*>(g + p.sm.red);
+    ch.s = g + p.sm.s;
+    ch.x = g + p.sm.x;
+    ch.xmix = g + p.sm.xmix;
+    ch.gframe = g + p.sm.gframe;
+    ch.segfac = reinterpret_cast<C*>(g + p.sm.segfac);
+    ch.misc = reinterpret_cast<int*>(g + p.sm.misc);
+    for (uint64_t chain = (uint64_t)blockIdx.x * p.gpc + gid; chain < p.count;
+         chain += (uint64_t)gridDim.x * p.gpc)
+        run_chain<R>(p, ch, gid, lt, chain);
+}
+
+// ================================================================= host
+namespace {
+
+size_t align16(size_t v) { return (v + 15) & ~(size_t)15; }
+
+SmemLayout make_layout(const HostPlan& hp, size_t csz) {
+    const DevPlanHeader& h = hp.hdr;
+    SmemLayout L{};
+    size_t o = 0;
+    auto take = [&](size_t bytes) {
+        size_t at = o;
+        o = align16(o + bytes);
+        return (int)at;
+    };
+    const int S = h.S, P = std::max(h.P, 1), K = std::max(h.K, 1);
+    L.L = take(csz << (S * P));
+    L.R = take((size_t)K * (csz << (S * (P - 1))));
+    L.Rexp = take(sizeof(int) * K);
+    L.rowdot = take(csz << S);
+    L.T = take(csz << h.max_block);
+    L.tab = take(csz * 32);
+    L.fslot = take(csz * 2 * S);
+    L.red = take((csz / 2) * 32);
+    L.s = take(h.n);
+    L.x = take(h.n);
+    L.xmix = take((size_t)(h.P + 1) * h.n);
+    L.gframe = take(std::max(1, h.n_cost_gates));
+    L.segfac = take(h.has_segfac ? csz * 2 * (size_t)h.n * (h.P + 1) : 16);
+    L.misc = take(sizeof(int) * (2 + 16));
+    L.group_bytes = (int)align16(o);
+    return L;
+}
+
+template <typename T> void put(std::vector<unsigned char>& blob, int64_t& off, const std::vector<T>& v) {
+    size_t at = align16(blob.size());
+    blob.resize(at + std::max<size_t>(sizeof(T) * v.size(), 16));
+    if (!v.empty()) std::memcpy(blob.data() + at, v.data(), sizeof(T) * v.size());
+    off = (int64_t)at;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+    return set_error(PW_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+std::vector<unsigned char> make_blob(const HostPlan& hp, DevPlanOffsets& o) {
+    std::vector<unsigned char> blob;
+    put(blob, o.micro, hp.micro);
+    put(blob, o.gate_refs, hp.gate_refs);
+    put(blob, o.cost_gates, hp.cost_gates);
+    put(blob, o.cost_items, hp.cost_items);
+    put(blob, o.cost_ranges, hp.cost_ranges);
+    put(blob, o.channels, hp.channels);
+    put(blob, o.cum, hp.cum);
+    put(blob, o.factors, hp.factors);
+    put(blob, o.mix_d, hp.mix_d);
+    put(blob, o.mix_f, hp.mix_f);
+    put(blob, o.mix0_order, hp.mix0_order);
+    put(blob, o.mix0_opid, hp.mix0_opid);
+    put(blob, o.mix_mono, hp.mix_mono);
+    put(blob, o.block_ranges, hp.block_ranges);
+    put(blob, o.block_sites, hp.block_sites);
+    put(blob, o.live_slots, hp.live_slots);
+    return blob;
+}
+
+int ensure_device_plan(pw_plan* plan) {
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    if (plan->d_blob && plan->device == dev) return PW_OK;
+    if (plan->d_blob) {
+        return set_error(PW_ERR_ARG, "plan was uploaded to another device; build one plan per device");
+    }
+    std::vector<unsigned char> blob = make_blob(plan->hp, plan->off);
+    void* d = nullptr;
+    if ((e = cudaMalloc(&d, blob.size())) != cudaSuccess) return cuda_fail(e, "cudaMalloc(plan)");
+    if ((e = cudaMemcpy(d, blob.data(), blob.size(), cudaMemcpyHostToDevice)) != cudaSuccess) {
+        cudaFree(d);
+        return cuda_fail(e, "cudaMemcpy(plan)");
+    }
+    unsigned long long* cnt = nullptr;
+    if ((e = cudaMalloc(&cnt, 4 * sizeof(unsigned long long))) != cudaSuccess) {
+        cudaFree(d);
+        return cuda_fail(e, "cudaMalloc(counters)");
+    }
+    plan->d_blob = d;
+    plan->blob_bytes = blob.size();
+    plan->d_counters = cnt;
+    plan->device = dev;
+    return PW_OK;
+}
+
+template <typename R> int launch(pw_plan* plan, KParams& kp, cudaStream_t st, uint64_t* launches) {
+    const HostPlan& hp = plan->hp;
+    const size_t csz = 2 * sizeof(R);
+    kp.sm = make_layout(hp, csz);
+    kp.tpc = hp.threads_per_chain;
+    // groups per CTA: as many as fit 227 KB of shared memory, at most 8
+    const int maxsm = 227 * 1024;
+    if (kp.sm.group_bytes > maxsm)
+        return set_error(PW_ERR_TOO_LARGE, "per-chain shared memory (" + std::to_string(kp.sm.group_bytes) +
+                                               " B) exceeds 227 KB");
+    int gpc = std::max(1, std::min({8, 512 / kp.tpc, maxsm / kp.sm.group_bytes}));
+    if (kp.tpc == 32) gpc = std::max(1, std::min({8, maxsm / kp.sm.group_bytes}));
+    kp.gpc = gpc;
+    const int threads = kp.tpc * gpc;
+    const size_t smem = (size_t)kp.sm.group_bytes * gpc;
+    auto kern = pw_chain_kernel<R>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
+    int dev = plan->device, nsm = 0, occ = 0;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, smem);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
+    occ = std::max(occ, 1);
+    const uint64_t per_launch = hp.chains_per_launch > 0 ? (uint64_t)hp.chains_per_launch : kp.count;
+    const uint64_t total = kp.count, first0 = kp.first;
+    uint64_t* out0 = kp.out_bits;
+    double* tr0 = kp.trace;
+    const uint64_t* in0 = kp.in_bits;
+    double* amp0 = kp.amp_out;
+    for (uint64_t done = 0; done < total; done += per_launch) {
+        const uint64_t cnt = std::min(per_launch, total - done);
+        kp.count = cnt;
+        kp.first = first0 + done;
+        kp.out_bits = out0 ? out0 + done * hp.hdr.words : nullptr;
+        kp.trace = tr0 ? tr0 + done * (uint64_t)hp.hdr.n_sampled * 4 : nullptr;
+        kp.in_bits = in0 ? in0 + done * hp.hdr.words : nullptr;
+        kp.amp_out = amp0 ? amp0 + 2 * done : nullptr;
+        const uint64_t ctas_needed = (cnt + gpc - 1) / gpc;
+        const int grid = (int)std::min<uint64_t>(ctas_needed, (uint64_t)nsm * occ);
+        kern<<<grid, threads, smem, st>>>(kp);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
+        if (launches) ++*launches;
+    }
+    return PW_OK;
+}
+
+int run(pw_plan* plan, KParams& kp, cudaStream_t st, uint64_t* launches) {
+    return plan->hp.precision == PW_PREC_FP64 ? launch<double>(plan, kp, st, launches)
+                                              : launch<float>(plan, kp, st, launches);
+}
+
+void fill_common(pw_plan* plan, KParams& kp) {
+    std::memset(&kp, 0, sizeof(kp));
+    kp.blob = static_cast<const unsigned char*>(plan->d_blob);
+    kp.off = plan->off;
+    kp.hdr = plan->hp.hdr;
+    kp.counters = plan->d_counters;
+}
+
+}  // namespace
+
+size_t plan_device_bytes(const HostPlan& hp) {
+    DevPlanOffsets o;
+    return make_blob(hp, o).size();
+}
+}  // namespace pw
+
+using namespace pw;
+
+extern "C" {
+
+int pw_sample(pw_plan* plan, uint64_t seed, uint64_t first_sample, uint64_t n_samples, uint64_t* d_out_bits,
+              double* d_trace, void* stream, pw_run_stats_t* stats) {
+    if (!plan || (!d_out_bits && n_samples)) return set_error(PW_ERR_ARG, "null argument");
+    if (stats) std::memset(stats, 0, sizeof(*stats));
+    if (n_samples == 0) return PW_OK;
+    int rc = ensure_device_plan(plan);
+    if (rc) return rc;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaMemsetAsync(plan->d_counters, 0, 4 * sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+    KParams kp;
+    fill_common(plan, kp);
+    kp.seed = seed;
+    kp.first = first_sample;
+    kp.count = n_samples;
+    kp.out_bits = d_out_bits;
+    kp.trace = d_trace;
+    kp.mode = MODE_SAMPLE;
+    uint64_t launches = 0;
+    rc = run(plan, kp, st, &launches);
+    if (rc) return rc;
+    if (stats) {
+        unsigned long long h[4] = {0, 0, 0, 0};
+        e = cudaMemcpyAsync(h, plan->d_counters, sizeof(h), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return cuda_fail(e, "reading counters");
+        stats->near_boundary = h[CNT_NEAR];
+        stats->zero_mass = h[CNT_ZERO];
+        stats->launches = launches;
+    }
+    return PW_OK;
+}
+
+int pw_sample_host(pw_plan* plan, uint64_t seed, uint64_t first_sample, uint64_t n_samples, uint64_t* h_out_bits,
+                   double* h_trace, pw_run_stats_t* stats) {
+    if (!plan || (!h_out_bits && n_samples)) return set_error(PW_ERR_ARG, "null argument");
+    if (n_samples == 0) {
+        if (stats) std::memset(stats, 0, sizeof(*stats));
+        return PW_OK;
+    }
+    int rc = ensure_device_plan(plan);
+    if (rc) return rc;
+    const size_t bits_bytes = (size_t)n_samples * plan->hp.hdr.words * sizeof(uint64_t);
+    const size_t tr_bytes = h_trace ? (size_t)n_samples * plan->hp.hdr.n_sampled * 4 * sizeof(double) : 0;
+    const size_t need = align16(bits_bytes) + tr_bytes;
+    cudaError_t e;
+    if (plan->stage_bytes < need) {
+        if (plan->d_stage) cudaFree(plan->d_stage);
+        plan->d_stage = nullptr;
+        plan->stage_bytes = 0;
+        if ((e = cudaMalloc(&plan->d_stage, need)) != cudaSuccess) return cuda_fail(e, "cudaMalloc(staging)");
+        plan->stage_bytes = need;
+    }
+    uint64_t* d_bits = static_cast<uint64_t*>(plan->d_stage);
+    double* d_tr = h_trace ? reinterpret_cast<double*>(static_cast<unsigned char*>(plan->d_stage) + align16(bits_bytes))
+                           : nullptr;
+    pw_run_stats_t local;
+    rc = pw_sample(plan, seed, first_sample, n_samples, d_bits, d_tr, nullptr, &local);
+    if (rc) return rc;
+    if ((e = cudaMemcpy(h_out_bits, d_bits, bits_bytes, cudaMemcpyDeviceToHost)) != cudaSuccess)
+        return cuda_fail(e, "cudaMemcpy(bits)");
+    if (h_trace && (e = cudaMemcpy(h_trace, d_tr, tr_bytes, cudaMemcpyDeviceToHost)) != cudaSuccess)
+        return cuda_fail(e, "cudaMemcpy(trace)");
+    if (stats) *stats = local;
+    return PW_OK;
+}
+
+int pw_amplitudes(pw_plan* plan, int prefix_ops, uint64_t n_strings, const uint64_t* d_bits, double* d_amp,
+                  void* stream) {
+    if (!plan || ((!d_bits || !d_amp) && n_strings)) return set_error(PW_ERR_ARG, "null argument");
+    const HostPlan& hp = plan->hp;
+    if (hp.noisy) return set_error(PW_ERR_UNSUPPORTED, "amplitudes are defined for noiseless circuits only");
+    if (prefix_ops < 1 || prefix_ops > (int)hp.exec_order.size()) return set_error(PW_ERR_ARG, "prefix_ops out of range");
+    const int op = hp.exec_order[prefix_ops - 1];
+    if (hp.exec_layer[op] < 1)
+        return set_error(PW_ERR_ARG, "the prefix must end right after a one-qubit gate of a layer >= 1");
+    if (n_strings == 0) return PW_OK;
+    int rc = ensure_device_plan(plan);
+    if (rc) return rc;
+    KParams kp;
+    fill_common(plan, kp);
+    kp.count = n_strings;
+    kp.mode = MODE_AMP;
+    kp.in_bits = d_bits;
+    kp.amp_out = d_amp;
+    kp.amp_layer = hp.exec_layer[op];
+    kp.amp_block = hp.exec_block[op];
+    kp.amp_pos = hp.exec_pos[op];
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaMemsetAsync(plan->d_counters, 0, 4 * sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+    return run(plan, kp, st, nullptr);
+}
+
+}  // extern "C"

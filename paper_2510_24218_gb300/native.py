@@ -1,0 +1,241 @@
+"""ctypes binding of ``include/pw.h`` (argument marshalling only).
+
+Every function keeps the C name. Device buffers are torch CUDA tensors passed
+by ``data_ptr()``; streams are torch streams (or None for the legacy default
+stream). Errors raise ``PwError`` with the library's message.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+PW_PREC_FP32 = 0
+PW_PREC_FP64 = 1
+PW_ORDER_AUTO = 0
+PW_ORDER_NATURAL = 1
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB = None
+
+
+def library_path() -> str:
+    return os.path.join(_HERE, "libpw.so")
+
+
+class PwError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"pw error {code}: {msg}")
+        self.code = code
+
+
+class PlanOpts(C.Structure):
+    _fields_ = [("precision", C.c_int), ("order", C.c_int), ("max_block", C.c_int),
+                ("threads_per_chain", C.c_int), ("chains_per_launch", C.c_int),
+                ("reserved", C.c_int * 7)]
+
+
+class PlanStats(C.Structure):
+    _fields_ = [("n_qubits", C.c_int), ("n_ops", C.c_int), ("n_layers", C.c_int), ("n_slots", C.c_int),
+                ("width_bits", C.c_int), ("width_low_bits", C.c_int), ("n_blocks", C.c_int),
+                ("sampled_gates", C.c_int), ("threads_per_chain", C.c_int), ("chains_per_cta", C.c_int),
+                ("smem_bytes_per_cta", C.c_int), ("noisy", C.c_int), ("flops_per_sample", C.c_double),
+                ("amps_per_sample", C.c_double),
+                ("device_bytes", C.c_double)]
+
+
+class RunStats(C.Structure):
+    _fields_ = [("near_boundary", C.c_uint64), ("zero_mass", C.c_uint64), ("launches", C.c_uint64)]
+
+
+def load_library():
+    """Load libpw.so (raises if it has not been built; there is no fallback)."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    path = library_path()
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is missing: run `python -c 'import __graft_entry__ as g; g.build()'`")
+    lib = C.CDLL(path)
+    vp, ip, dp = C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_double)
+    sig = {
+        "pw_circuit_create": (C.c_int, [C.c_int, C.POINTER(vp)]),
+        "pw_circuit_add_gate": (C.c_int, [vp, C.c_int, ip, dp]),
+        "pw_circuit_add_kraus": (C.c_int, [vp, C.c_int, ip, C.c_int, dp]),
+        "pw_circuit_qaoa": (C.c_int, [C.c_int, C.c_int, ip, dp, dp, C.c_int, dp, dp, C.c_double, C.c_double,
+                                      C.POINTER(vp)]),
+        "pw_circuit_num_ops": (C.c_int, [vp, ip]),
+        "pw_circuit_destroy": (None, [vp]),
+        "pw_plan_build": (C.c_int, [vp, C.POINTER(PlanOpts), C.POINTER(vp)]),
+        "pw_plan_stats": (C.c_int, [vp, C.POINTER(PlanStats)]),
+        "pw_plan_exec_order": (C.c_int, [vp, ip]),
+        "pw_plan_destroy": (None, [vp]),
+        "pw_sample": (C.c_int, [vp, C.c_uint64, C.c_uint64, C.c_uint64, vp, vp, vp, C.POINTER(RunStats)]),
+        "pw_sample_host": (C.c_int, [vp, C.c_uint64, C.c_uint64, C.c_uint64, vp, vp, C.POINTER(RunStats)]),
+        "pw_amplitudes": (C.c_int, [vp, C.c_int, C.c_uint64, vp, vp, vp]),
+        "pw_last_error": (C.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _LIB = lib
+    return lib
+
+
+def pw_last_error() -> str:
+    return load_library().pw_last_error().decode()
+
+
+def _check(rc: int):
+    if rc != 0:
+        raise PwError(rc, pw_last_error())
+
+
+def _iarr(v):
+    a = np.ascontiguousarray(np.asarray(v, dtype=np.int32).ravel())
+    return a, a.ctypes.data_as(C.POINTER(C.c_int))
+
+
+def _darr(v):
+    a = np.ascontiguousarray(np.asarray(v, dtype=np.float64).ravel())
+    return a, a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _cplx(M):
+    a = np.ascontiguousarray(np.asarray(M, dtype=np.complex128))
+    return _darr(a.view(np.float64))
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    return C.c_void_p(int(getattr(stream, "cuda_stream", stream)))
+
+
+# ------------------------------------------------------------------ circuit
+
+def pw_circuit_create(n_qubits: int):
+    h = C.c_void_p()
+    _check(load_library().pw_circuit_create(int(n_qubits), C.byref(h)))
+    return h
+
+
+def pw_circuit_add_gate(circ, qubits, A):
+    q, qp = _iarr(qubits)
+    a, ap = _cplx(A)
+    _check(load_library().pw_circuit_add_gate(circ, len(q), qp, ap))
+
+
+def pw_circuit_add_kraus(circ, qubits, kraus_ops):
+    q, qp = _iarr(qubits)
+    a, ap = _cplx(np.stack([np.asarray(E, dtype=np.complex128) for E in kraus_ops]))
+    _check(load_library().pw_circuit_add_kraus(circ, len(q), qp, len(kraus_ops), ap))
+
+
+def pw_circuit_qaoa(n, edges, weights, h, p, gammas, betas, depol2=0.0, ad_gamma=0.0):
+    e, ep = _iarr(edges)
+    w, wp = _darr(weights)
+    g, gp = _darr(gammas)
+    b, bp = _darr(betas)
+    if h is not None:
+        hh, hp = _darr(h)
+    else:
+        hh, hp = None, None
+    out = C.c_void_p()
+    _check(load_library().pw_circuit_qaoa(int(n), len(e) // 2, ep, wp, hp, int(p), gp, bp, float(depol2),
+                                          float(ad_gamma), C.byref(out)))
+    return out
+
+
+def pw_circuit_num_ops(circ) -> int:
+    v = C.c_int()
+    _check(load_library().pw_circuit_num_ops(circ, C.byref(v)))
+    return v.value
+
+
+def pw_circuit_destroy(circ):
+    if circ:
+        load_library().pw_circuit_destroy(circ)
+
+
+# --------------------------------------------------------------------- plan
+
+def pw_plan_build(circ, precision=PW_PREC_FP32, order=PW_ORDER_AUTO, max_block=0, threads_per_chain=0,
+                  chains_per_launch=0):
+    o = PlanOpts()
+    o.precision, o.order, o.max_block = precision, order, max_block
+    o.threads_per_chain, o.chains_per_launch = threads_per_chain, chains_per_launch
+    h = C.c_void_p()
+    _check(load_library().pw_plan_build(circ, C.byref(o), C.byref(h)))
+    return h
+
+
+def pw_plan_stats(plan) -> dict:
+    s = PlanStats()
+    _check(load_library().pw_plan_stats(plan, C.byref(s)))
+    return {name: getattr(s, name) for name, _ in PlanStats._fields_}
+
+
+def pw_plan_exec_order(plan) -> np.ndarray:
+    n = pw_plan_stats(plan)["n_ops"]
+    a = np.zeros(n, dtype=np.int32)
+    _check(load_library().pw_plan_exec_order(plan, a.ctypes.data_as(C.POINTER(C.c_int))))
+    return a
+
+
+def pw_plan_destroy(plan):
+    if plan:
+        load_library().pw_plan_destroy(plan)
+
+
+# ---------------------------------------------------------------- execution
+
+def pw_sample(plan, seed, first_sample, n_samples, out_bits, trace=None, stream=None, want_stats=True):
+    """out_bits / trace: torch CUDA tensors (int64 [n, words], float64 [n, rows, 4])."""
+    st = RunStats()
+    _check(load_library().pw_sample(plan, int(seed), int(first_sample), int(n_samples),
+                                    C.c_void_p(out_bits.data_ptr()),
+                                    C.c_void_p(trace.data_ptr()) if trace is not None else None,
+                                    _stream_ptr(stream), C.byref(st) if want_stats else None))
+    return {"near_boundary": st.near_boundary, "zero_mass": st.zero_mass, "launches": st.launches}
+
+
+def pw_sample_host(plan, seed, first_sample, n_samples, out_bits: np.ndarray, trace: np.ndarray | None = None):
+    """Host-buffer variant: out_bits uint64 [n, words], trace float64 [n, rows, 4] or None."""
+    assert out_bits.dtype == np.uint64 and out_bits.flags["C_CONTIGUOUS"]
+    st = RunStats()
+    _check(load_library().pw_sample_host(plan, int(seed), int(first_sample), int(n_samples),
+                                         C.c_void_p(out_bits.ctypes.data),
+                                         C.c_void_p(trace.ctypes.data) if trace is not None else None,
+                                         C.byref(st)))
+    return {"near_boundary": st.near_boundary, "zero_mass": st.zero_mass, "launches": st.launches}
+
+
+def pw_amplitudes(plan, prefix_ops, bits, amp_out, stream=None):
+    """bits: torch CUDA int64 [n_strings, words]; amp_out: torch CUDA float64 [n_strings, 2]."""
+    _check(load_library().pw_amplitudes(plan, int(prefix_ops), int(bits.shape[0]), C.c_void_p(bits.data_ptr()),
+                                        C.c_void_p(amp_out.data_ptr()), _stream_ptr(stream)))
+
+
+# ------------------------------------------------------------ bit packing
+
+def pack_bits(bits: np.ndarray) -> np.ndarray:
+    """uint8 [count, n] -> uint64 [count, ceil(n/64)], qubit q at bit q%64 of word q//64."""
+    bits = np.asarray(bits, dtype=np.uint64)
+    count, n = bits.shape
+    words = (n + 63) // 64
+    out = np.zeros((count, words), dtype=np.uint64)
+    for q in range(n):
+        out[:, q // 64] |= bits[:, q] << np.uint64(q % 64)
+    return out
+
+
+def unpack_bits(words: np.ndarray, n: int) -> np.ndarray:
+    """Inverse of pack_bits (accepts int64 or uint64 words)."""
+    w = np.asarray(words).view(np.uint64) if np.asarray(words).dtype == np.int64 else np.asarray(words, np.uint64)
+    out = np.zeros((w.shape[0], n), dtype=np.uint8)
+    for q in range(n):
+        out[:, q] = ((w[:, q // 64] >> np.uint64(q % 64)) & np.uint64(1)).astype(np.uint8)
+    return out

@@ -1,0 +1,269 @@
+"""GPU parity tests: the CUDA path through the C-ABI against the FP64 oracle.
+
+Bitstrings must be identical to the oracle's on the same Philox streams,
+except for chains in which a draw fell within 1e-6 of a CDF boundary (counted
+by both sides); amplitudes are compared per candidate pair with the relative
+error ||a_gpu - a_ref||_2 / ||a_ref||_2, bound 1e-5 for the FP32 contraction
+and 1e-12 for the FP64 one.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import circuit as OC
+from oracle import closed_form as CF
+from oracle import sampler as OS
+from oracle import statevector as SV
+from oracle import tn as TN
+
+pytestmark = pytest.mark.gpu
+
+TOL = {0: 1e-5, 1: 1e-12}
+
+
+@pytest.fixture(scope="module")
+def pw():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2510_24218_gb300 as mod
+    mod.load_library()
+    return mod
+
+
+def _circ(pw, spec):
+    return pw.pw_circuit_qaoa(spec.n, spec.edges, spec.weights, spec.h, spec.p, spec.gammas, spec.betas,
+                              spec.depol2, spec.ad_gamma)
+
+
+def run_gpu(pw, spec, N, seed, precision=0, trace=True, first=0, **opts):
+    import torch
+    circ = _circ(pw, spec)
+    plan = pw.pw_plan_build(circ, precision=precision, **opts)
+    st = pw.pw_plan_stats(plan)
+    words = (spec.n + 63) // 64
+    bits = torch.zeros((N, words), dtype=torch.int64, device="cuda")
+    tr = torch.zeros((N, st["sampled_gates"], 4), dtype=torch.float64, device="cuda") if trace else None
+    stats = pw.pw_sample(plan, seed, first, N, bits, tr)
+    torch.cuda.synchronize()
+    order = pw.pw_plan_exec_order(plan)
+    out = dict(bits=pw.unpack_bits(bits.cpu().numpy(), spec.n), trace=tr.cpu().numpy() if trace else None,
+               stats=stats, order=order, plan_stats=st)
+    pw.pw_plan_destroy(plan)
+    pw.pw_circuit_destroy(circ)
+    return out
+
+
+def pair_err(o_amps, g_row):
+    a = np.array(o_amps)
+    b = g_row[0::2] + 1j * g_row[1::2]
+    return float(np.linalg.norm(a - b) / np.linalg.norm(a))
+
+
+def check_against_sv(pw, spec, N, seed, precision=0, trace_chains=64, **opts):
+    g = run_gpu(pw, spec, N, seed, precision=precision, **opts)
+    ops = OC.qaoa_circuit(spec)
+    traces = [[] for _ in range(min(N, trace_chains))]
+    ids = list(range(N))
+    want, ost = OS.sample_sv(spec.n, ops, seed, ids[:len(traces)], order=g["order"], traces=traces)
+    if N > len(traces):
+        rest, ost2 = OS.sample_sv(spec.n, ops, seed, ids[len(traces):], order=g["order"])
+        want = np.concatenate([want, rest])
+        ost.near_boundary += ost2.near_boundary
+    mism = int((~(want == g["bits"]).all(axis=1)).sum())
+    allowed = max(g["stats"]["near_boundary"], ost.near_boundary)
+    assert mism <= allowed, f"{mism} chains differ, {allowed} near-boundary draws"
+    worst = 0.0
+    for k in range(len(traces)):
+        if not (want[k] == g["bits"][k]).all():
+            continue
+        o = traces[k][spec.n:]
+        assert len(o) == g["plan_stats"]["sampled_gates"]
+        for r in range(len(o)):
+            worst = max(worst, pair_err(o[r][1], g["trace"][k, r]))
+    assert worst < TOL[precision], worst
+    return g, worst
+
+
+# ---------------------------------------------------------------- config 1
+
+@pytest.mark.parametrize("precision", [1, 0])
+def test_config1_bitwise_against_oracle(pw, precision):
+    """n=12 3-regular p=1 (gamma=0.4, beta=0.3), 10^4 samples, identical bits."""
+    spec = W.maxcut_3reg_n12()
+    g, worst = check_against_sv(pw, spec, 10000, seed=20251, precision=precision, trace_chains=256,
+                                chains_per_launch=256)
+    # TVD against the exact distribution within the multinomial 99th percentile
+    p = np.abs(SV.run(spec.n, OC.qaoa_circuit(spec))) ** 2
+    idx = (g["bits"].astype(np.int64) << np.arange(spec.n)).sum(axis=1)
+    emp = np.bincount(idx, minlength=1 << spec.n) / len(idx)
+    rng = np.random.default_rng(0)
+    thr = np.quantile([0.5 * np.abs(rng.multinomial(len(idx), p) / len(idx) - p).sum() for _ in range(200)], 0.99)
+    assert 0.5 * np.abs(emp - p).sum() < thr
+
+
+@pytest.mark.parametrize("seed,n,p,with_h,tpc", [(31, 8, 1, False, 32), (32, 10, 2, True, 64), (33, 9, 3, False, 128),
+                                                 (34, 12, 2, True, 256), (35, 6, 2, False, 32)])
+def test_random_circuits_bitwise(pw, seed, n, p, with_h, tpc):
+    spec = W.random_qaoa(n, p, seed=seed, with_h=with_h)
+    check_against_sv(pw, spec, 97, seed=seed, threads_per_chain=tpc)
+
+
+def test_natural_order_and_small_blocks(pw):
+    spec = W.random_qaoa(10, 2, seed=41, with_h=True)
+    check_against_sv(pw, spec, 50, seed=4, order=pw.PW_ORDER_NATURAL, max_block=2)
+    check_against_sv(pw, spec, 50, seed=4, order=pw.PW_ORDER_AUTO, max_block=1)
+
+
+def test_first_sample_offset_and_launch_split(pw):
+    """Sample k depends only on (seed, k): any split of the range gives the same bits."""
+    spec = W.random_qaoa(10, 2, seed=42)
+    full = run_gpu(pw, spec, 300, seed=9, trace=False)["bits"]
+    part = run_gpu(pw, spec, 120, seed=9, trace=False, first=150)["bits"]
+    assert np.array_equal(full[150:270], part)
+    split = run_gpu(pw, spec, 300, seed=9, trace=False, chains_per_launch=37)["bits"]
+    assert np.array_equal(full, split)
+
+
+def test_zero_samples_and_host_variant(pw):
+    import torch
+    spec = W.random_qaoa(8, 2, seed=43)
+    circ = _circ(pw, spec)
+    plan = pw.pw_plan_build(circ)
+    bits = torch.zeros((1, 1), dtype=torch.int64, device="cuda")
+    assert pw.pw_sample(plan, 1, 0, 0, bits)["launches"] == 0
+    host = np.zeros((77, 1), dtype=np.uint64)
+    pw.pw_sample_host(plan, 5, 3, 77, host)
+    dev = torch.zeros((77, 1), dtype=torch.int64, device="cuda")
+    pw.pw_sample(plan, 5, 3, 77, dev)
+    assert np.array_equal(host.view(np.int64), dev.cpu().numpy())
+    pw.pw_plan_destroy(plan)
+    pw.pw_circuit_destroy(circ)
+
+
+# ---------------------------------------------------------------- config 2
+
+def test_grid6x6_chains_against_elimination_oracle(pw):
+    """6x6 grid p=2 in the benchmark's launch shape: chains spread over the
+    batch checked one by one against the variable-elimination oracle."""
+    spec = W.grid_6x6_p2()
+    N = 4096
+    g = run_gpu(pw, spec, N, seed=777, chains_per_launch=4096)
+    ops = OC.qaoa_circuit(spec)
+    for k in (0, 1777, 4095):
+        trace = []
+        s, ost = OS.sample_tn(spec.n, ops, 777, k, order=g["order"], trace=trace)
+        if ost.near_boundary == 0:
+            assert np.array_equal(s, g["bits"][k])
+        o = trace[spec.n:]
+        worst = max(pair_err(o[r][1], g["trace"][k, r]) for r in range(len(o)))
+        assert worst < 1e-5, (k, worst)
+
+
+def test_grid6x6_symmetry_at_scale(pw):
+    """MaxCut with h = 0: p(x) = p(not x), every bit has mean 1/2 (10^5 samples)."""
+    spec = W.grid_6x6_p2()
+    g = run_gpu(pw, spec, 100000, seed=99, trace=False)
+    m = g["bits"].mean(axis=0)
+    assert np.all(np.abs(m - 0.5) < 5 * 0.5 / math.sqrt(100000))
+
+
+# ------------------------------------------------------------------- noise
+
+@pytest.mark.parametrize("spec", [W.random_qaoa(6, 2, seed=51, depol2=0.3, ad_gamma=0.4),
+                                  W.random_qaoa(8, 2, seed=52, depol2=0.1, ad_gamma=0.6, with_h=True),
+                                  W.random_qaoa(10, 1, seed=53, depol2=0.5, ad_gamma=0.2)])
+def test_noisy_bitwise_against_alg2(pw, spec):
+    g = run_gpu(pw, spec, 120, seed=61, trace=False)
+    ops = OC.qaoa_circuit(spec)
+    mism = 0
+    near = 0
+    for k in range(120):
+        s, st = OS.noisy_sample(spec.n, ops, 61, k, order=g["order"])
+        near += st.near_boundary
+        mism += int(not np.array_equal(s, g["bits"][k]))
+    assert mism <= max(near, g["stats"]["near_boundary"])
+
+
+def test_noisy_distribution_against_density_matrix(pw):
+    spec = W.random_qaoa(4, 2, seed=54, depol2=0.2, ad_gamma=0.5)
+    N = 40000
+    g = run_gpu(pw, spec, N, seed=62, trace=False)
+    p = np.real(np.diag(SV.density_run(spec.n, OC.qaoa_circuit(spec))))
+    idx = (g["bits"].astype(np.int64) << np.arange(spec.n)).sum(axis=1)
+    emp = np.bincount(idx, minlength=1 << spec.n) / N
+    rng = np.random.default_rng(1)
+    thr = np.quantile([0.5 * np.abs(rng.multinomial(N, p) / N - p).sum() for _ in range(200)], 0.99)
+    assert 0.5 * np.abs(emp - p).sum() < thr
+
+
+# -------------------------------------------------------------- amplitudes
+
+def test_amplitudes_api_against_state_vector(pw):
+    import torch
+    spec = W.random_qaoa(10, 2, seed=71, with_h=True)
+    circ = _circ(pw, spec)
+    plan = pw.pw_plan_build(circ)
+    order = pw.pw_plan_exec_order(plan)
+    ops = OC.qaoa_circuit(spec)
+    xs = W.random_bitstrings(32, spec.n, seed=72)
+    d_bits = torch.from_numpy(pw.pack_bits(xs).view(np.int64)).cuda()
+    amp = torch.zeros((32, 2), dtype=torch.float64, device="cuda")
+    psi = SV.zero_state(spec.n)
+    checked = 0
+    for t, oi in enumerate(order, start=1):
+        op = ops[oi]
+        psi = SV.apply(psi, spec.n, op.qubits, op.mat) if op.kind == "gate" else psi
+        if op.kind != "gate" or len(op.qubits) != 1 or OC.is_diagonal(op.mat) or t <= spec.n:
+            continue
+        pw.pw_amplitudes(plan, t, d_bits, amp)
+        got = amp.cpu().numpy()
+        for k in range(32):
+            a = psi[sum(int(b) << q for q, b in enumerate(xs[k]))]
+            assert abs(got[k, 0] + 1j * got[k, 1] - a) <= 1e-5 * max(abs(a), 1e-3 * np.abs(psi).max())
+        checked += 1
+    assert checked == spec.n * spec.p
+    with pytest.raises(pw.PwError):
+        pw.pw_amplitudes(plan, spec.n + 1, d_bits, amp)    # ends on a diagonal gate
+    pw.pw_plan_destroy(plan)
+    pw.pw_circuit_destroy(circ)
+
+
+# ---------------------------------------------------------------- config 5
+
+def test_heavy_hex_400_zz_closed_form(pw):
+    """400 qubits, p=1: sample means of z_u z_v against the closed form."""
+    spec = W.heavy_hex_400_p1()
+    N = 20000
+    g = run_gpu(pw, spec, N, seed=5, trace=False)
+    z = 1 - 2 * g["bits"].astype(np.int64)
+    cf = CF.zz_p1(spec.n, spec.edges, spec.weights, spec.gammas[0], spec.betas[0])
+    zs = []
+    for (u, v), want in zip(spec.edges, cf):
+        zz = z[:, u] * z[:, v]
+        se = math.sqrt(max(1e-12, (1 - want ** 2) / N))
+        zs.append((zz.mean() - want) / se)
+    assert np.max(np.abs(zs)) < 5.0, np.max(np.abs(zs))
+
+
+def test_heavy_hex_400_amplitudes_against_elimination(pw):
+    import torch
+    spec = W.heavy_hex_400_p1()
+    circ = _circ(pw, spec)
+    plan = pw.pw_plan_build(circ)
+    order = pw.pw_plan_exec_order(plan)
+    ops = OC.qaoa_circuit(spec)
+    xs = W.random_bitstrings(3, spec.n, seed=73)
+    d_bits = torch.from_numpy(pw.pack_bits(xs).view(np.int64)).cuda()
+    amp = torch.zeros((3, 2), dtype=torch.float64, device="cuda")
+    t = len(order)   # the full circuit
+    pw.pw_amplitudes(plan, t, d_bits, amp)
+    got = amp.cpu().numpy()
+    pre = [ops[i] for i in order[:t]]
+    for k in range(3):
+        a = TN.amplitudes(spec.n, pre, xs[k])
+        assert abs(got[k, 0] + 1j * got[k, 1] - a) <= 1e-5 * abs(a)
+    pw.pw_plan_destroy(plan)
+    pw.pw_circuit_destroy(circ)

@@ -1,0 +1,161 @@
+"""CPU-only checks of the C-ABI library: symbols, circuit validation, planner.
+
+No compute call is made here (there is no GPU on this host); plan building is
+pure host code.
+"""
+import os
+import re
+
+import numpy as np
+import pytest
+
+import workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def pw():
+    import paper_2510_24218_gb300 as mod
+    from paper_2510_24218_gb300 import build as B
+    if not os.path.exists(mod.library_path()):
+        B.build()
+    mod.load_library()
+    return mod
+
+
+def _declared_functions():
+    txt = open(os.path.join(ROOT, "include", "pw.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:int|void|const char\*)\s+(pw_\w+)\s*\(", txt, flags=re.M)))
+
+
+def test_library_exports_every_declared_symbol(pw):
+    import ctypes
+    lib = ctypes.CDLL(pw.library_path())
+    names = _declared_functions()
+    assert len(names) >= 13
+    for name in names:
+        assert hasattr(lib, name), name
+
+
+def _circ(pw, spec):
+    return pw.pw_circuit_qaoa(spec.n, spec.edges, spec.weights, spec.h, spec.p, spec.gammas, spec.betas,
+                              spec.depol2, spec.ad_gamma)
+
+
+def test_circuit_validation_errors(pw):
+    c = pw.pw_circuit_create(3)
+    with pytest.raises(pw.PwError) as e:
+        pw.pw_circuit_add_gate(c, [0, 5], np.eye(4))
+    assert e.value.code == -1
+    with pytest.raises(pw.PwError) as e:
+        pw.pw_circuit_add_gate(c, [1, 1], np.eye(4))
+    assert e.value.code == -1
+    with pytest.raises(pw.PwError) as e:
+        pw.pw_circuit_add_gate(c, [0], np.array([[np.nan, 0], [0, 1]]))
+    assert e.value.code == -6
+    H = np.array([[1, 1], [1, -1]]) / np.sqrt(2)
+    with pytest.raises(pw.PwError) as e:     # Hadamard is not submonomial (App. A)
+        pw.pw_circuit_add_kraus(c, [0], [H])
+    assert e.value.code == -2
+    with pytest.raises(pw.PwError) as e:     # CNOT-like 2-qubit Kraus is not a tensor product
+        cn = np.eye(4)[[0, 3, 2, 1]]
+        pw.pw_circuit_add_kraus(c, [0, 1], [0.5 * cn + 0.5 * np.eye(4)])
+    assert e.value.code == -2
+    pw.pw_circuit_destroy(c)
+
+
+def test_unsupported_structures_are_rejected(pw):
+    H = np.array([[1, 1], [1, -1]]) / np.sqrt(2)
+    cnot = np.eye(4)[[0, 3, 2, 1]]
+    c = pw.pw_circuit_create(2)
+    pw.pw_circuit_add_gate(c, [0], H)
+    pw.pw_circuit_add_gate(c, [1], H)
+    pw.pw_circuit_add_gate(c, [0, 1], cnot)
+    with pytest.raises(pw.PwError) as e:
+        pw.pw_plan_build(c)
+    assert e.value.code == -7
+    pw.pw_circuit_destroy(c)
+    c = pw.pw_circuit_create(2)
+    pw.pw_circuit_add_gate(c, [0], H)       # layer incomplete, then a diagonal gate
+    pw.pw_circuit_add_gate(c, [0, 1], np.diag([1, -1, -1, 1]))
+    with pytest.raises(pw.PwError):
+        pw.pw_plan_build(c)
+    pw.pw_circuit_destroy(c)
+
+
+@pytest.mark.parametrize("spec,S,K", [(W.grid_6x6_p2(), 6, 6), (W.grid_8x8_p2_noisy(), 8, 8)])
+def test_grid_plans_sweep_rows(pw, spec, S, K):
+    c = _circ(pw, spec)
+    plan = pw.pw_plan_build(c)
+    st = pw.pw_plan_stats(plan)
+    assert st["n_slots"] == S and st["n_blocks"] == K
+    assert st["width_bits"] == S * spec.p and st["width_low_bits"] == S * (spec.p - 1)
+    assert st["sampled_gates"] == spec.n * spec.p
+    assert st["amps_per_sample"] == 2 * spec.n * spec.p
+    pw.pw_plan_destroy(plan)
+    pw.pw_circuit_destroy(c)
+
+
+def test_exec_order_is_a_valid_reordering(pw):
+    spec = W.random_qaoa(14, 2, seed=8, with_h=True, depol2=0.01, ad_gamma=0.01)
+    c = _circ(pw, spec)
+    plan = pw.pw_plan_build(c)
+    order = pw.pw_plan_exec_order(plan)
+    nops = pw.pw_circuit_num_ops(c)
+    assert sorted(order.tolist()) == list(range(nops))
+    # only one-qubit gates of one layer move, and only among themselves
+    from oracle import circuit as OC
+    ops = OC.qaoa_circuit(spec)
+    kinds = [(o.kind, len(o.qubits)) for o in ops]
+    assert [kinds[i] for i in order] == kinds
+    pw.pw_plan_destroy(plan)
+    pw.pw_circuit_destroy(c)
+
+
+def test_lsm_noise_keeps_the_plan_shape(pw):
+    # Prop. 2: with LSM noise the network, the contraction order and its cost
+    # are those of the noiseless circuit
+    base = W.grid_6x6_p2()
+    noisy = W.grid_6x6_p2()
+    noisy.depol2, noisy.ad_gamma = 1e-3, 1e-3
+    s = []
+    for spec in (base, noisy):
+        c = _circ(pw, spec)
+        plan = pw.pw_plan_build(c)
+        s.append(pw.pw_plan_stats(plan))
+        pw.pw_plan_destroy(plan)
+        pw.pw_circuit_destroy(c)
+    for key in ("n_slots", "width_bits", "width_low_bits", "n_blocks", "sampled_gates", "flops_per_sample"):
+        assert s[0][key] == s[1][key], key
+    assert s[1]["noisy"] == 1 and s[0]["noisy"] == 0
+
+
+def test_orders_and_widths(pw):
+    # 3-regular and heavy-hex graphs: the automatic order keeps the frontier small
+    for spec, smax in ((W.maxcut_3reg_n12(), 6), (W.heavy_hex_400_p1(), 14)):
+        c = _circ(pw, spec)
+        plan = pw.pw_plan_build(c)
+        st = pw.pw_plan_stats(plan)
+        assert st["n_slots"] <= smax
+        natural = pw.pw_plan_build(c, order=pw.PW_ORDER_NATURAL)
+        assert pw.pw_plan_stats(natural)["n_slots"] >= st["n_slots"]
+        pw.pw_plan_destroy(natural)
+        pw.pw_plan_destroy(plan)
+        pw.pw_circuit_destroy(c)
+
+
+def test_bad_options(pw):
+    spec = W.maxcut_3reg_n12()
+    c = _circ(pw, spec)
+    with pytest.raises(pw.PwError):
+        pw.pw_plan_build(c, precision=7)
+    with pytest.raises(pw.PwError):
+        pw.pw_plan_build(c, threads_per_chain=48)
+    pw.pw_circuit_destroy(c)
+
+
+def test_pack_roundtrip(pw):
+    x = W.random_bitstrings(9, 130, seed=3)
+    assert np.array_equal(pw.unpack_bits(pw.pack_bits(x), 130), x)
