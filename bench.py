@@ -145,6 +145,8 @@ def run_ours(args, rank, world):
     import paper_2510_24218_gb300 as pw
 
     spec, n_samples, B, desc = workload(args.workload)
+    if args.samples:
+        n_samples = args.samples
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
     torch.cuda.set_device(dev)
     prec = pw.PW_PREC_FP64 if args.precision == "fp64" else pw.PW_PREC_FP32
@@ -240,6 +242,7 @@ def main():
     ap.add_argument("--seed", type=int, default=20251203)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
+    ap.add_argument("--samples", type=int, default=0, help="override samples per step (profiling)")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", 0))
