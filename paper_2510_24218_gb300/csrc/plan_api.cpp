@@ -6,6 +6,7 @@
 #include <new>
 
 #include "pw_internal.h"
+#include "smem_layout.h"
 
 using namespace pw;
 
@@ -13,13 +14,13 @@ namespace {
 
 int choose_threads(const HostPlan& hp, int requested) {
     if (requested > 0) {
-        if (requested % 32 || requested > 512 || (requested & (requested - 1)))
+        if (requested % 32 || requested > 256 || (requested & (requested - 1)))
             return -1;
         return requested;
     }
     long N = 1L << hp.W;
-    long t = N / 16;
-    t = std::max(32L, std::min(512L, t));
+    long t = N / 32;
+    t = std::max(32L, std::min(256L, t));
     long pw2 = 32;
     while (pw2 < t) pw2 <<= 1;
     return (int)pw2;
@@ -49,7 +50,7 @@ int pw_plan_build(const pw_circuit* c, const pw_plan_opts* opts, pw_plan** out) 
     int tpc = choose_threads(plan->hp, o.threads_per_chain);
     if (tpc < 0) {
         delete plan;
-        return set_error(PW_ERR_ARG, "threads_per_chain must be a power of two in 32..512");
+        return set_error(PW_ERR_ARG, "threads_per_chain must be a power of two in 32..256");
     }
     plan->hp.threads_per_chain = tpc;
     if (o.chains_per_launch < 0) {
@@ -78,19 +79,11 @@ int pw_plan_stats(const pw_plan* plan, pw_plan_stats_t* s) {
     s->flops_per_sample = hp.flops_per_sample;
     s->amps_per_sample = hp.amps_per_sample;
     s->device_bytes = (double)plan_device_bytes(hp);
-    // shared-memory estimate matching the kernel's layout
-    const size_t csz = hp.precision == PW_PREC_FP64 ? 16 : 8;
-    auto a16 = [](size_t v) { return (v + 15) & ~(size_t)15; };
-    const int S = hp.hdr.S, P = std::max(hp.hdr.P, 1), K = std::max(hp.hdr.K, 1);
-    size_t b = a16(csz << (S * P)) + a16((size_t)K * (csz << (S * (P - 1)))) + a16(4 * K) + a16(csz << S) +
-               a16(csz << hp.hdr.max_block) + a16(csz * 32) + a16(csz * 2 * S) + a16(csz / 2 * 32) + a16(hp.hdr.n) * 2 +
-               a16((size_t)(hp.hdr.P + 1) * hp.hdr.n) + a16(std::max(1, hp.hdr.n_cost_gates)) +
-               a16(hp.hdr.has_segfac ? csz * 2 * (size_t)hp.hdr.n * (hp.hdr.P + 1) : 16) + a16(4 * 18);
-    const size_t maxsm = 227 * 1024;
-    int gpc = (int)std::max<size_t>(1, std::min<size_t>({8, (size_t)(hp.threads_per_chain == 32 ? 8 : 512 / hp.threads_per_chain),
-                                                        maxsm / std::max<size_t>(b, 1)}));
+    // shared memory of the kernel's layout
+    const SmemLayout L = make_layout(hp, hp.precision == PW_PREC_FP64 ? 16 : 8);
+    const int gpc = groups_per_cta(hp.threads_per_chain, L.group_bytes);
     s->chains_per_cta = gpc;
-    s->smem_bytes_per_cta = (int)(b * gpc);
+    s->smem_bytes_per_cta = L.group_bytes * gpc;
     return PW_OK;
 }
 

@@ -283,6 +283,51 @@ std::vector<int> greedy_order(const std::vector<std::vector<int>>& adj, int star
     return order;
 }
 
+// Group consecutive micro-ops into fused passes: up to two 2x2 matrices on
+// distinct bits, followed by diagonal/scalar factors whose bits (together)
+// number at most 5. Returns the table entries of the range.
+int fuse_range(HostPlan& hp, int b, int e) {
+    int tab = 0;
+    int i = b;
+    while (i < e) {
+        DevFused f{};
+        f.op_begin = i;
+        while (i < e && hp.micro[i].kind == MK_MAT1 && f.nmat < 2 &&
+               (f.nmat == 0 || hp.micro[i].bits[0] != f.mbits[0])) {
+            f.mbits[f.nmat++] = hp.micro[i].bits[0];
+            ++i;
+        }
+        std::vector<int> db;
+        while (i < e && hp.micro[i].kind != MK_MAT1) {
+            const DevMicroOp& o = hp.micro[i];
+            std::vector<int> u = db;
+            for (int j = 0; j < o.nbits; ++j)
+                if (std::find(u.begin(), u.end(), (int)o.bits[j]) == u.end()) u.push_back(o.bits[j]);
+            if (u.size() > 5) break;
+            db = u;
+            ++i;
+        }
+        f.op_end = i;
+        f.ndiag = (uint8_t)db.size();
+        for (size_t j = 0; j < db.size(); ++j) f.dbits[j] = (uint8_t)db[j];
+        for (int m = 0; m < 2; ++m) {
+            f.mpos[m] = -1;
+            if (m < f.nmat)
+                for (size_t j = 0; j < db.size(); ++j)
+                    if (db[j] == f.mbits[m]) f.mpos[m] = (int8_t)j;
+        }
+        for (int k = f.op_begin + f.nmat; k < f.op_end; ++k) {
+            DevMicroOp& o = hp.micro[k];
+            for (int j = 0; j < o.nbits; ++j)
+                o.fpos[j] = (uint8_t)(std::find(db.begin(), db.end(), (int)o.bits[j]) - db.begin());
+        }
+        f.tab_off = tab;
+        tab += 4 * f.nmat + (1 << f.ndiag);
+        hp.fused.push_back(f);
+    }
+    return tab;
+}
+
 }  // namespace
 
 int build_plan(const pw_circuit* c, const pw_plan_opts& opts, HostPlan& hp) {
@@ -338,6 +383,8 @@ int build_plan(const pw_circuit* c, const pw_plan_opts& opts, HostPlan& hp) {
                     cd v = b < dim ? op.mats[(size_t)b * dim + b] : cd(1.0, 0.0);
                     g.d[2 * b] = v.real();
                     g.d[2 * b + 1] = v.imag();
+                    g.f[2 * b] = (float)v.real();
+                    g.f[2 * b + 1] = (float)v.imag();
                 }
                 int gi = (int)hp.cost_gates.size();
                 hp.cost_gates.push_back(g);
@@ -487,7 +534,8 @@ int build_plan(const pw_circuit* c, const pw_plan_opts& opts, HostPlan& hp) {
         for (int id : L.sections[m]) hp.exec_order.push_back(id);
         const int Wl = S * (m - 1);
         const int Wm = S * m;
-        auto bitf = [&](int j, int l) { return l < m - 1 ? j * (m - 1) + l : Wl + j; };
+        // forward tensor: top leg of slot j at bit j, lower legs above bit S
+        auto bitf = [&](int j, int l) { return l == m - 1 ? j : S + j * (m - 1) + l; };
         auto bitb = [&](int j, int l) { return j * (m - 1) + l; };
         auto mk = [&](uint8_t kind, uint8_t rcp, std::initializer_list<int> bits, int qa, int qb, int layer,
                       const std::vector<int>& gl, int fixed_top) {
@@ -548,9 +596,16 @@ int build_plan(const pw_circuit* c, const pw_plan_opts& opts, HostPlan& hp) {
                     }
                 }
             }
-            br.fwd_end = (int)hp.micro.size();
+            {
+                int mb = br.fwd_begin, me = (int)hp.micro.size();
+                br.fwd_begin = (int)hp.fused.size();
+                br.fwd_tab = fuse_range(hp, mb, me);
+                br.fwd_end = (int)hp.fused.size();
+            }
             // backward (R_k -> R_{k-1}); not needed for k = 0
-            br.bwd_begin = br.bwd_end = (int)hp.micro.size();
+            br.bwd_begin = br.bwd_end = (int)hp.fused.size();
+            br.bwd_tab = 0;
+            const int bwd_micro_begin = (int)hp.micro.size();
             if (k >= 1) {
                 std::vector<int> consts;
                 for (int g : level_gates[m - 1]) {
@@ -593,7 +648,9 @@ int build_plan(const pw_circuit* c, const pw_plan_opts& opts, HostPlan& hp) {
                             break;
                     }
                 }
-                br.bwd_end = (int)hp.micro.size();
+                br.bwd_begin = (int)hp.fused.size();
+                br.bwd_tab = fuse_range(hp, bwd_micro_begin, (int)hp.micro.size());
+                br.bwd_end = (int)hp.fused.size();
             }
         }
         // readout metadata and block sites
@@ -636,14 +693,14 @@ int build_plan(const pw_circuit* c, const pw_plan_opts& opts, HostPlan& hp) {
     }
     for (int id : L.sections[P + 1]) hp.exec_order.push_back(id);
     // algorithmic real flops per sample: a 2x2 on one bit costs 14 flops per
-    // entry (two complex multiplies and one add), a diagonal or scalar factor 6,
+    // entry (two complex multiplies and one add), the fused diagonal factor 6,
     // the readout's dot product with R_k 8 per entry of L
     for (int m = 1; m <= P; ++m) {
         double NF = std::ldexp(1.0, S * m), NB = std::ldexp(1.0, S * (m - 1));
         for (int k = 0; k < K; ++k) {
             const DevBlockRange& br = hp.block_ranges[(size_t)m * K + k];
-            for (int i = br.fwd_begin; i < br.fwd_end; ++i) flops += (hp.micro[i].kind == MK_MAT1 ? 14.0 : 6.0) * NF;
-            for (int i = br.bwd_begin; i < br.bwd_end; ++i) flops += (hp.micro[i].kind == MK_MAT1 ? 14.0 : 6.0) * NB;
+            for (int i = br.fwd_begin; i < br.fwd_end; ++i) flops += (14.0 * hp.fused[i].nmat + 6.0) * NF;
+            for (int i = br.bwd_begin; i < br.bwd_end; ++i) flops += (14.0 * hp.fused[i].nmat + 6.0) * NB;
             flops += 8.0 * NF;
         }
     }
@@ -662,6 +719,8 @@ int build_plan(const pw_circuit* c, const pw_plan_opts& opts, HostPlan& hp) {
     hp.hdr.has_segfac = has_segfac ? 1 : 0;
     hp.hdr.has_frame = has_frame ? 1 : 0;
     hp.hdr.words = (n + 63) / 64;
+    hp.hdr.max_tab = 1;
+    for (const auto& br : hp.block_ranges) hp.hdr.max_tab = std::max({hp.hdr.max_tab, br.fwd_tab, br.bwd_tab});
     hp.W = S * std::max(P, 1);
     hp.W_low = S * std::max(P - 1, 0);
     return PW_OK;

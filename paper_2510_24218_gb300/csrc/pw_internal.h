@@ -66,6 +66,7 @@ struct DevMicroOp {
     uint8_t nbits;
     uint8_t fixed_top;   // RC_SITE: top segment fixed to s (backward sweep)
     uint8_t bits[4];
+    uint8_t fpos[4];     // positions of bits[] inside the fused op's diagonal bits
     int16_t qa, qb;
     int16_t layer;       // mixer layer of the top weight (-1: none); RC_SITE: number of segments
     int16_t pad0;
@@ -73,12 +74,28 @@ struct DevMicroOp {
     int32_t gcount;
 };
 
+// A fused pass: up to two 2x2 matrices on distinct bits, then one diagonal
+// table over up to 5 bits (the product of the constituent diagonal factors).
+// Its constituents are micro-ops [op_begin, op_end): first the nmat MAT1 ops,
+// then DIAG / CONST ops. Table layout at tab_off: nmat x 4 entries, then 2^ndiag.
+struct DevFused {
+    uint8_t nmat;
+    uint8_t ndiag;
+    uint8_t mbits[2];
+    int8_t mpos[2];      // position of mbits[i] inside dbits, -1 if absent
+    uint8_t dbits[5];
+    uint8_t pad[5];
+    int32_t op_begin, op_end;
+    int32_t tab_off;     // complex entries from the start of the block's table area
+};
+
 // A diagonal cost gate (1 or 2 qubits) with its table; level = segment index.
 struct DevCostGate {
     int16_t q0, q1;      // q1 < 0 for a one-qubit gate
     int16_t level;
     int16_t pad;
-    double d[8];         // 4 complex (re, im) entries, local index b0 + 2 b1
+    float f[8];          // 4 complex (re, im) entries, local index b0 + 2 b1 (FP32 copy)
+    double d[8];         // the same in FP64
 };
 
 // Items of a cost section, processed in circuit order by one thread per chain.
@@ -124,10 +141,11 @@ struct DevLiveSlot {
 
 // Per (layer m >= 1, block k) ranges.
 struct DevBlockRange {
-    int32_t fwd_begin, fwd_end;
-    int32_t bwd_begin, bwd_end;     // backward micro-ops turning R_k into R_{k-1}
+    int32_t fwd_begin, fwd_end;     // DevFused of the forward absorption of block k
+    int32_t bwd_begin, bwd_end;     // DevFused turning R_k into R_{k-1}
     int32_t site_begin, site_end;   // DevBlockSite
     int32_t live_begin, live_end;   // DevLiveSlot
+    int32_t fwd_tab, bwd_tab;       // table entries of the two programs
 };
 
 struct DevPlanHeader {
@@ -142,11 +160,12 @@ struct DevPlanHeader {
     int32_t has_segfac;        // 1-qubit diagonal gates or channels present
     int32_t has_frame;         // channels present
     int32_t words;             // uint64 words per bitstring
+    int32_t max_tab;           // max table entries of one block program
 };
 
 // Offsets (in bytes) of the arrays inside the device blob.
 struct DevPlanOffsets {
-    int64_t micro, gate_refs, cost_gates, cost_items, cost_ranges, channels, cum, factors;
+    int64_t micro, fused, gate_refs, cost_gates, cost_items, cost_ranges, channels, cum, factors;
     int64_t mix_d, mix_f, mix0_order, mix0_opid, mix_mono;
     int64_t block_ranges, block_sites, live_slots;
 };
@@ -164,6 +183,7 @@ struct HostPlan {
     DevPlanHeader hdr{};
     // blob pieces (host copies)
     std::vector<DevMicroOp> micro;
+    std::vector<DevFused> fused;
     std::vector<int32_t> gate_refs;
     std::vector<DevCostGate> cost_gates;
     std::vector<DevCostItem> cost_items;

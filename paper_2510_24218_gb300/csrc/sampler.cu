@@ -4,10 +4,14 @@
 // one Markov chain (Alg. 1 / Alg. 2) for its whole life: it walks every layer
 // of the circuit, keeps the frontier tensor of the plan's sweep in shared
 // memory, evaluates the candidate amplitudes amp(C_t, y) of each resampled
-// qubit with the plan's micro-op program, and draws the update from the
+// qubit with the plan's program of fused passes, and draws the update from the
 // normalised conditional with a counter-based Philox stream. Only the packed
 // output bits (and the optional amplitude trace) reach HBM: the kernel is
 // bound by shared-memory traffic and FP32 arithmetic, not by DRAM.
+//
+// Per block of resampled qubits the group first builds every table the block
+// needs (one parallel phase), then runs the fused passes back to back with one
+// group barrier each, then reads out the block's conditional amplitudes.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -16,6 +20,7 @@
 #include <cstring>
 
 #include "pw_internal.h"
+#include "smem_layout.h"
 
 namespace pw {
 
@@ -24,8 +29,8 @@ template <typename R> struct CT;
 template <> struct CT<float> { using T = float2; };
 template <> struct CT<double> { using T = double2; };
 
-template <typename C> __device__ __forceinline__ C cmk(double re, double im) {
-    C c;
+template <typename R> __device__ __forceinline__ typename CT<R>::T mk(R re, R im) {
+    typename CT<R>::T c;
     c.x = re;
     c.y = im;
     return c;
@@ -49,6 +54,16 @@ __device__ __forceinline__ float rmax(float a, float b) { return fmaxf(a, b); }
 __device__ __forceinline__ double rmax(double a, double b) { return fmax(a, b); }
 __device__ __forceinline__ float rabs(float a) { return fabsf(a); }
 __device__ __forceinline__ double rabs(double a) { return fabs(a); }
+__device__ __forceinline__ int rexp(float v) {
+    int e;
+    frexpf(v, &e);
+    return e;
+}
+__device__ __forceinline__ int rexp(double v) {
+    int e;
+    frexp(v, &e);
+    return e;
+}
 
 // ---------------------------------------------------------------- Philox
 // Philox4x32-10 (Salmon et al., SC'11): the two round multipliers and the two
@@ -76,10 +91,6 @@ __device__ __forceinline__ double draw_u(uint64_t seed, uint64_t sample, uint32_
 }
 
 // ----------------------------------------------------------- parameters
-struct SmemLayout {
-    int L, R, Rexp, rowdot, T, tab, fslot, red, s, x, xmix, gframe, segfac, misc, group_bytes;
-};
-
 struct KParams {
     const unsigned char* blob;
     DevPlanOffsets off;
@@ -115,12 +126,13 @@ __device__ __forceinline__ void gsync(const KParams& p, int gid) {
 // Per-chain view of the shared-memory group.
 template <typename R> struct Chain {
     using C = typename CT<R>::T;
-    C* L;         // frontier tensor, 2^W
+    C* L;         // frontier tensor, 2^W (top legs in the low S bits)
     C* Rt;        // right environments, K x 2^Wl
     int* Rexp;    // their power-of-two exponents
     C* rowdot;    // 2^S
     C* T;         // 2^max_block
-    C* tab;       // 2 x 16 micro-op tables
+    C* tab;       // tables of one block program
+    C* part;      // tpc partial sums
     C* fslot;     // S x 2 per-slot readout factors
     R* red;       // 32 reduction scratch
     uint8_t* s;   // chain state s
@@ -134,39 +146,43 @@ template <typename R> struct Chain {
 // Frame-conjugated one-qubit gate A'_{m,q}[o][i] = A[o^x][i^x] (PropagateX).
 template <typename R>
 __device__ __forceinline__ typename CT<R>::T mixel(const KParams& p, const Chain<R>& ch, int m, int q, int o, int i) {
-    int xb = p.hdr.has_frame ? ch.xmix[m * p.hdr.n + q] : 0;
-    size_t base = ((size_t)m * p.hdr.n + q) * 8 + 2 * (((o ^ xb) << 1) | (i ^ xb));
-    if (sizeof(R) == 4) {
-        const float* f = P_<float>(p, p.off.mix_f);
-        return cmk<typename CT<R>::T>(f[base], f[base + 1]);
+    const int xb = p.hdr.has_frame ? ch.xmix[m * p.hdr.n + q] : 0;
+    const size_t base = ((size_t)m * p.hdr.n + q) * 8 + 2 * (((o ^ xb) << 1) | (i ^ xb));
+    if constexpr (sizeof(R) == 4) {
+        const float2 v = *reinterpret_cast<const float2*>(P_<float>(p, p.off.mix_f) + base);
+        return v;
     } else {
-        const double* d = P_<double>(p, p.off.mix_d);
-        return cmk<typename CT<R>::T>(d[base], d[base + 1]);
+        const double2 v = *reinterpret_cast<const double2*>(P_<double>(p, p.off.mix_d) + base);
+        return v;
     }
 }
 
 // D'_g(a0 on q0, a1 on q1): a diagonal gate conjugated by the frame at its time.
 template <typename R>
 __device__ __forceinline__ typename CT<R>::T gatel(const KParams& p, const Chain<R>& ch, int g, int a0, int a1) {
-    const DevCostGate& G = P_<DevCostGate>(p, p.off.cost_gates)[g];
-    int f = p.hdr.has_frame ? ch.gframe[g] : 0;
-    int idx = (a0 ^ (f & 1)) | ((a1 ^ ((f >> 1) & 1)) << 1);
-    return cmk<typename CT<R>::T>(G.d[2 * idx], G.d[2 * idx + 1]);
+    const DevCostGate* G = P_<DevCostGate>(p, p.off.cost_gates) + g;
+    const int f = p.hdr.has_frame ? ch.gframe[g] : 0;
+    const int idx = (a0 ^ (f & 1)) | ((a1 ^ ((f >> 1) & 1)) << 1);
+    if constexpr (sizeof(R) == 4) {
+        return *reinterpret_cast<const float2*>(G->f + 2 * idx);
+    } else {
+        return *reinterpret_cast<const double2*>(G->d + 2 * idx);
+    }
 }
 
 // D'_g with qubit qa set to va and the other qubit of g set to vb.
 template <typename R>
 __device__ __forceinline__ typename CT<R>::T gate_pair(const KParams& p, const Chain<R>& ch, int g, int qa, int va, int vb) {
-    const DevCostGate& G = P_<DevCostGate>(p, p.off.cost_gates)[g];
-    return G.q0 == qa ? gatel<R>(p, ch, g, va, vb) : gatel<R>(p, ch, g, vb, va);
+    const DevCostGate* G = P_<DevCostGate>(p, p.off.cost_gates) + g;
+    return G->q0 == qa ? gatel<R>(p, ch, g, va, vb) : gatel<R>(p, ch, g, vb, va);
 }
 
-// Entry e of micro-op o's table (MAT1: e = out*2 + in; DIAG: gathered bits).
+// Entry e of micro-op o's table (MAT1: e = out*2 + in; DIAG: its own bits).
 template <typename R>
 __device__ typename CT<R>::T build_entry(const KParams& p, const Chain<R>& ch, const DevMicroOp& o, int e) {
     using C = typename CT<R>::T;
     const int32_t* gref = P_<int32_t>(p, p.off.gate_refs);
-    const C one = cmk<C>(1.0, 0.0), zero = cmk<C>(0.0, 0.0);
+    const C one = mk<R>(1, 0), zero = mk<R>(0, 0);
     switch (o.recipe) {
         case RC_EXPAND:
             return (e & 1) == 0 ? one : zero;
@@ -175,19 +191,19 @@ __device__ typename CT<R>::T build_entry(const KParams& p, const Chain<R>& ch, c
         case RC_SUMOUT_MIX:
             return (e >> 1) == 0 ? mixel<R>(p, ch, o.layer, o.qa, ch.s[o.qa], e & 1) : zero;
         case RC_REPLACE: {
-            int aout = e >> 1, ain = e & 1;   // out: new site qb, in: eliminated site qa
+            const int aout = e >> 1, ain = e & 1;   // out: new site qb, in: eliminated site qa
             C v = o.layer >= 0 ? mixel<R>(p, ch, o.layer, o.qa, ch.s[o.qa], ain) : one;
             for (int i = 0; i < o.gcount; ++i) v = cmul(v, gate_pair<R>(p, ch, gref[o.glist + i], o.qa, ain, aout));
             return v;
         }
         case RC_BREPLACE: {
-            int aout = e >> 1, ain = e & 1;   // out: site qa, in: site qb
+            const int aout = e >> 1, ain = e & 1;   // out: site qa, in: site qb
             C v = one;
             for (int i = 0; i < o.gcount; ++i) v = cmul(v, gate_pair<R>(p, ch, gref[o.glist + i], o.qa, aout, ain));
             return v;
         }
         case RC_EDGE: {
-            int a = e & 1, b = (e >> 1) & 1;
+            const int a = e & 1, b = (e >> 1) & 1;
             C v = one;
             for (int i = 0; i < o.gcount; ++i) v = cmul(v, gate_pair<R>(p, ch, gref[o.glist + i], o.qa, a, b));
             return v;
@@ -196,14 +212,14 @@ __device__ typename CT<R>::T build_entry(const KParams& p, const Chain<R>& ch, c
             // Segments z^0..z^{layer-1} of qubit qa: the open ones are the low
             // bits of e, a fixed top takes the chain's bit. Value:
             // <z^0|A_0|0> prod_l A'_l[z^l][z^{l-1}] prod_l segfac(q, l)[z^l].
-            int q = o.qa, nseg = o.layer;
+            const int q = o.qa, nseg = o.layer;
             int z[8];
             for (int l = 0; l < nseg; ++l) z[l] = (e >> l) & 1;
             if (o.fixed_top) z[nseg - 1] = ch.s[q];
             C v = mixel<R>(p, ch, 0, q, z[0], 0);
             for (int l = 1; l < nseg; ++l) v = cmul(v, mixel<R>(p, ch, l, q, z[l], z[l - 1]));
             if (p.hdr.has_segfac) {
-                int P1 = p.hdr.P + 1;
+                const int P1 = p.hdr.P + 1;
                 for (int l = 0; l < nseg; ++l) v = cmul(v, ch.segfac[((size_t)q * P1 + l) * 2 + z[l]]);
             }
             return v;
@@ -212,7 +228,7 @@ __device__ typename CT<R>::T build_entry(const KParams& p, const Chain<R>& ch, c
             C v = one;
             const DevCostGate* G = P_<DevCostGate>(p, p.off.cost_gates);
             for (int i = 0; i < o.gcount; ++i) {
-                int g = gref[o.glist + i];
+                const int g = gref[o.glist + i];
                 v = cmul(v, gatel<R>(p, ch, g, ch.s[G[g].q0], ch.s[G[g].q1]));
             }
             return v;
@@ -221,54 +237,101 @@ __device__ typename CT<R>::T build_entry(const KParams& p, const Chain<R>& ch, c
     return one;
 }
 
-// Apply micro-ops [b, e) to the tensor buf of 2^W entries; pend_exp is a power
-// of two folded into the first op (exact rescaling).
+// Build the tables of fused ops [fb, fe) into ch.tab. pend_exp (a power of two)
+// is folded into the diagonal table of the first op.
 template <typename R>
-__device__ void apply_ops(const KParams& p, const Chain<R>& ch, int gid, int lt, int b, int e,
-                          typename CT<R>::T* buf, int W, int pend_exp) {
+__device__ void build_tables(const KParams& p, const Chain<R>& ch, int lt, int fb, int fe, int pend_exp) {
     using C = typename CT<R>::T;
+    const DevFused* F = P_<DevFused>(p, p.off.fused);
     const DevMicroOp* ops = P_<DevMicroOp>(p, p.off.micro);
-    const int N = 1 << W;
-    for (int i = b; i < e; ++i) {
-        const DevMicroOp o = ops[i];
-        C* tab = ch.tab + 16 * ((i - b) & 1);
-        const int ne = o.kind == MK_MAT1 ? 4 : (o.kind == MK_DIAG ? (1 << o.nbits) : 1);
-        for (int en = lt; en < ne; en += p.tpc) {
-            C v = build_entry<R>(p, ch, o, en);
-            if (i == b && pend_exp != 0) {
-                v.x = scl(v.x, pend_exp);
-                v.y = scl(v.y, pend_exp);
+    for (int fi = fb; fi < fe; ++fi) {
+        const DevFused f = F[fi];
+        const int nm = 4 * f.nmat, ne = nm + (1 << f.ndiag);
+        for (int e = lt; e < ne; e += p.tpc) {
+            C v;
+            if (e < nm) {
+                v = build_entry<R>(p, ch, ops[f.op_begin + (e >> 2)], e & 3);
+            } else {
+                const int de = e - nm;
+                v = mk<R>(1, 0);
+                for (int k = f.op_begin + f.nmat; k < f.op_end; ++k) {
+                    const DevMicroOp o = ops[k];
+                    int loc = 0;
+                    for (int j = 0; j < o.nbits; ++j) loc |= ((de >> o.fpos[j]) & 1) << j;
+                    v = cmul(v, build_entry<R>(p, ch, o, loc));
+                }
+                if (fi == fb && pend_exp != 0) {
+                    v.x = scl(v.x, pend_exp);
+                    v.y = scl(v.y, pend_exp);
+                }
             }
-            tab[en] = v;
-        }
-        gsync(p, gid);
-        if (o.kind == MK_MAT1) {
-            const int bt = o.bits[0];
-            const C m00 = tab[0], m01 = tab[1], m10 = tab[2], m11 = tab[3];
-            const int lomask = (1 << bt) - 1;
-            for (int pi = lt; pi < (N >> 1); pi += p.tpc) {
-                const int i0 = ((pi >> bt) << (bt + 1)) | (pi & lomask);
-                const int i1 = i0 | (1 << bt);
-                const C x0 = buf[i0], x1 = buf[i1];
-                buf[i0] = cfma(m00, x0, cmul(m01, x1));
-                buf[i1] = cfma(m10, x0, cmul(m11, x1));
-            }
-        } else if (o.kind == MK_DIAG) {
-            const int nb = o.nbits;
-            const int b0 = o.bits[0], b1 = o.bits[1], b2 = o.bits[2], b3 = o.bits[3];
-            for (int idx = lt; idx < N; idx += p.tpc) {
-                int t = (idx >> b0) & 1;
-                if (nb > 1) t |= ((idx >> b1) & 1) << 1;
-                if (nb > 2) t |= ((idx >> b2) & 1) << 2;
-                if (nb > 3) t |= ((idx >> b3) & 1) << 3;
-                buf[idx] = cmul(buf[idx], tab[t]);
-            }
-        } else {
-            const C c = tab[0];
-            for (int idx = lt; idx < N; idx += p.tpc) buf[idx] = cmul(buf[idx], c);
+            ch.tab[f.tab_off + e] = v;
         }
     }
-    gsync(p, gid);
+}
+
+__device__ __forceinline__ int gather_bits(int idx, const uint8_t* db, int nd) {
+    int t = 0;
+#pragma unroll
+    for (int j = 0; j < 5; ++j)
+        if (j < nd) t |= ((idx >> db[j]) & 1) << j;
+    return t;
+}
+
+// Run fused ops [fb, fe) on buf (2^W entries), one pass and one barrier each.
+template <typename R>
+__device__ void run_fused(const KParams& p, const Chain<R>& ch, int gid, int lt, int fb, int fe,
+                          typename CT<R>::T* buf, int W) {
+    using C = typename CT<R>::T;
+    const DevFused* F = P_<DevFused>(p, p.off.fused);
+    const int N = 1 << W;
+    for (int fi = fb; fi < fe; ++fi) {
+        const DevFused f = F[fi];
+        const C* tab = ch.tab + f.tab_off;
+        const C* D = tab + 4 * f.nmat;
+        const int nd = f.ndiag;
+        if (f.nmat == 2) {
+            const int ba = f.mbits[0], bb = f.mbits[1];
+            const int lo = min(ba, bb), hi = max(ba, bb);
+            const int pa = f.mpos[0] >= 0 ? 1 << f.mpos[0] : 0, pb = f.mpos[1] >= 0 ? 1 << f.mpos[1] : 0;
+            const C a00 = tab[0], a01 = tab[1], a10 = tab[2], a11 = tab[3];
+            const C b00 = tab[4], b01 = tab[5], b10 = tab[6], b11 = tab[7];
+            for (int qi = lt; qi < (N >> 2); qi += p.tpc) {
+                int i = ((qi >> lo) << (lo + 1)) | (qi & ((1 << lo) - 1));
+                i = ((i >> hi) << (hi + 1)) | (i & ((1 << hi) - 1));
+                const int ia = 1 << ba, ib = 1 << bb;
+                C x00 = buf[i], x10 = buf[i | ia], x01 = buf[i | ib], x11 = buf[i | ia | ib];
+                // matrix a on bit ba
+                C y00 = cfma(a00, x00, cmul(a01, x10)), y10 = cfma(a10, x00, cmul(a11, x10));
+                C y01 = cfma(a00, x01, cmul(a01, x11)), y11 = cfma(a10, x01, cmul(a11, x11));
+                // matrix b on bit bb
+                x00 = cfma(b00, y00, cmul(b01, y01));
+                x01 = cfma(b10, y00, cmul(b11, y01));
+                x10 = cfma(b00, y10, cmul(b01, y11));
+                x11 = cfma(b10, y10, cmul(b11, y11));
+                const int t = gather_bits(i, f.dbits, nd);
+                buf[i] = cmul(x00, D[t]);
+                buf[i | ia] = cmul(x10, D[t | pa]);
+                buf[i | ib] = cmul(x01, D[t | pb]);
+                buf[i | ia | ib] = cmul(x11, D[t | pa | pb]);
+            }
+        } else if (f.nmat == 1) {
+            const int bt = f.mbits[0];
+            const int pa = f.mpos[0] >= 0 ? 1 << f.mpos[0] : 0;
+            const C m00 = tab[0], m01 = tab[1], m10 = tab[2], m11 = tab[3];
+            for (int pi = lt; pi < (N >> 1); pi += p.tpc) {
+                const int i0 = ((pi >> bt) << (bt + 1)) | (pi & ((1 << bt) - 1));
+                const int i1 = i0 | (1 << bt);
+                const C x0 = buf[i0], x1 = buf[i1];
+                const int t = gather_bits(i0, f.dbits, nd);
+                buf[i0] = cmul(cfma(m00, x0, cmul(m01, x1)), D[t]);
+                buf[i1] = cmul(cfma(m10, x0, cmul(m11, x1)), D[t | pa]);
+            }
+        } else {
+            for (int idx = lt; idx < N; idx += p.tpc) buf[idx] = cmul(buf[idx], D[gather_bits(idx, f.dbits, nd)]);
+        }
+        gsync(p, gid);
+    }
 }
 
 // Group-wide max of a per-thread value (broadcast to every thread).
@@ -286,10 +349,8 @@ __device__ R group_max(const KParams& p, const Chain<R>& ch, int gid, int lt, R 
 
 // Exponent e with 2^-e * mx in [0.5, 1); 0 for zero or non-finite mx.
 template <typename R> __device__ __forceinline__ int scale_exp(R mx) {
-    if (!(mx > (R)0) || !isfinite((double)mx)) return 0;
-    int e;
-    frexp((double)mx, &e);
-    return e;
+    if (!(mx > (R)0) || !isfinite(mx)) return 0;
+    return rexp(mx);
 }
 
 // Kraus draw of Eq. (5) at the true bits s XOR x, then Alg. 2: every
@@ -320,9 +381,9 @@ __device__ void apply_channel(const KParams& p, const Chain<R>& ch, const DevCha
     for (int f = 0; f < c.nq; ++f) {
         const DevKrausFactor F = fac[c.fac_off + pick * c.nq + f];
         if (F.antidiag) ch.x[F.q] ^= 1;
-        C d0 = cmk<C>(F.d[0], F.d[1]), d1 = cmk<C>(F.d[2], F.d[3]);
+        C d0 = mk<R>((R)F.d[0], (R)F.d[1]), d1 = mk<R>((R)F.d[2], (R)F.d[3]);
         if (ch.x[F.q]) {
-            C t = d0;
+            const C t = d0;
             d0 = d1;
             d1 = t;
         }
@@ -332,10 +393,44 @@ __device__ void apply_channel(const KParams& p, const Chain<R>& ch, const DevCha
     }
 }
 
-// Readout of block k of layer m: T(tops of the block's sites) =
-// sum L * R_k * prod_slots f_slot, then the block's sites are resampled one
-// after another (Alg. 1's UpdateState), contracting each resampled top with
-// A'_m[s_new][.] before moving to the next site.
+// Per-slot readout factors of block k: cross edges of the top segment to
+// unabsorbed qubits (at their current bits) and, for sites resampled in an
+// earlier block, their mixer weight A'_m[s][top]. Also records which slot
+// holds the i-th site of the block.
+template <typename R>
+__device__ void build_fslot(const KParams& p, const Chain<R>& ch, int lt, int m, const DevBlockRange& br) {
+    using C = typename CT<R>::T;
+    const DevLiveSlot* live = P_<DevLiveSlot>(p, p.off.live_slots) + br.live_begin;
+    const int32_t* gref = P_<int32_t>(p, p.off.gate_refs);
+    const DevCostGate* G = P_<DevCostGate>(p, p.off.cost_gates);
+    for (int j = lt; j < p.hdr.S; j += p.tpc) {
+        const DevLiveSlot sl = live[j];
+        C f0 = mk<R>(1, 0), f1 = mk<R>(0, 0);
+        if (sl.q >= 0) {
+            f1 = mk<R>(1, 0);
+            for (int i = 0; i < sl.dcount; ++i) {
+                const int g = gref[sl.dlist + i];
+                const int w = G[g].q0 == sl.q ? G[g].q1 : G[g].q0;
+                f0 = cmul(f0, gate_pair<R>(p, ch, g, sl.q, 0, ch.s[w]));
+                f1 = cmul(f1, gate_pair<R>(p, ch, g, sl.q, 1, ch.s[w]));
+            }
+            if (sl.role < 0) {
+                f0 = cmul(f0, mixel<R>(p, ch, m, sl.q, ch.s[sl.q], 0));
+                f1 = cmul(f1, mixel<R>(p, ch, m, sl.q, ch.s[sl.q], 1));
+            } else {
+                ch.misc[2 + sl.role] = j;
+            }
+        }
+        ch.fslot[2 * j] = f0;
+        ch.fslot[2 * j + 1] = f1;
+    }
+}
+
+// Readout of block k of layer m. The frontier index is top legs (low S bits)
+// + lower legs (high bits): T(tops of the block's sites) =
+// sum_{l,h} L[l, h] R_k[l] prod_slots fslot[j][h_j], then the block's sites
+// are resampled one after another (UpdateState of Alg. 1), contracting each
+// resampled top with A'_m[s_new][.] before moving to the next site.
 template <typename R>
 __device__ void readout_and_sample(const KParams& p, const Chain<R>& ch, int gid, int lt, int m, int k,
                                    const DevBlockRange& br, uint64_t sample_id, uint64_t chain) {
@@ -343,39 +438,41 @@ __device__ void readout_and_sample(const KParams& p, const Chain<R>& ch, int gid
     const DevPlanHeader& h = p.hdr;
     const int S = h.S, Wl = S * (m - 1);
     const int NL = 1 << Wl, H = 1 << S;
-    const C zero = cmk<C>(0.0, 0.0), one = cmk<C>(1.0, 0.0);
+    const C zero = mk<R>(0, 0), one = mk<R>(1, 0);
     const C* Rk = ch.Rt + (size_t)k * NL;
     const C* L = ch.L;
 
-    // 1) rowdot[h] = sum_l L[h, l] R_k[l], and max |L| for the rescale
+    // 1) rowdot[h] = sum_l L[l*H + h] R_k[l] (coalesced), and max |L|
     R mx = 0;
-    if (NL >= 32 && p.tpc >= 32) {
-        const int nw = p.tpc >> 5, w = lt >> 5, lane = lt & 31;
-        for (int hr = w; hr < H; hr += nw) {
-            C acc = zero;
-            for (int l = lane; l < NL; l += 32) {
-                const C v = L[(size_t)hr * NL + l];
-                acc = cfma(v, Rk[l], acc);
-                mx = rmax(mx, rmax(rabs(v.x), rabs(v.y)));
-            }
-            for (int o = 16; o > 0; o >>= 1) {
-                acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
-                acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
-            }
-            if (lane == 0) ch.rowdot[hr] = acc;
+    if (p.tpc >= H) {
+        const int hh = lt & (H - 1), step = p.tpc / H;
+        C acc = zero;
+        for (int l = lt / H; l < NL; l += step) {
+            const C v = L[(size_t)l * H + hh];
+            acc = cfma(v, Rk[l], acc);
+            mx = rmax(mx, rmax(rabs(v.x), rabs(v.y)));
         }
+        ch.part[lt] = acc;
     } else {
-        for (int hr = lt; hr < H; hr += p.tpc) {
+        for (int hh = lt; hh < H; hh += p.tpc) {
             C acc = zero;
             for (int l = 0; l < NL; ++l) {
-                const C v = L[(size_t)hr * NL + l];
+                const C v = L[(size_t)l * H + hh];
                 acc = cfma(v, Rk[l], acc);
                 mx = rmax(mx, rmax(rabs(v.x), rabs(v.y)));
             }
-            ch.rowdot[hr] = acc;
+            ch.rowdot[hh] = acc;
         }
     }
-    mx = group_max<R>(p, ch, gid, lt, mx);   // also publishes rowdot
+    mx = group_max<R>(p, ch, gid, lt, mx);   // its barriers also publish part / rowdot
+    if (p.tpc >= H && lt < H) {
+        C acc = zero;
+        for (int j = lt; j < p.tpc; j += H) {
+            acc.x += ch.part[j].x;
+            acc.y += ch.part[j].y;
+        }
+        ch.rowdot[lt] = acc;
+    }
     const int eL = ch.misc[0];
     const int escale = eL + ch.Rexp[k];
     const bool target_block = p.mode == MODE_AMP && m == p.amp_layer && k == p.amp_block;
@@ -390,38 +487,9 @@ __device__ void readout_and_sample(const KParams& p, const Chain<R>& ch, int gid
         return;
     }
 
-    // 2) per-slot factors: cross edges of the top segment to unabsorbed qubits
-    //    (at their current bits) and, for sites resampled in earlier blocks,
-    //    their mixer weight A'_m[s][top]
-    const DevLiveSlot* live = P_<DevLiveSlot>(p, p.off.live_slots) + br.live_begin;
+    // 2) collapse onto the block's tops: T[t], bit i of t = top of block site i
     const DevBlockSite* sites = P_<DevBlockSite>(p, p.off.block_sites) + br.site_begin;
-    const int32_t* gref = P_<int32_t>(p, p.off.gate_refs);
-    const DevCostGate* G = P_<DevCostGate>(p, p.off.cost_gates);
     const int nb = br.site_end - br.site_begin;
-    for (int j = lt; j < S; j += p.tpc) {
-        const DevLiveSlot sl = live[j];
-        C f0 = one, f1 = zero;
-        if (sl.q >= 0) {
-            f1 = one;
-            for (int i = 0; i < sl.dcount; ++i) {
-                int g = gref[sl.dlist + i];
-                int w = G[g].q0 == sl.q ? G[g].q1 : G[g].q0;
-                f0 = cmul(f0, gate_pair<R>(p, ch, g, sl.q, 0, ch.s[w]));
-                f1 = cmul(f1, gate_pair<R>(p, ch, g, sl.q, 1, ch.s[w]));
-            }
-            if (sl.role < 0) {
-                f0 = cmul(f0, mixel<R>(p, ch, m, sl.q, ch.s[sl.q], 0));
-                f1 = cmul(f1, mixel<R>(p, ch, m, sl.q, ch.s[sl.q], 1));
-            } else {
-                ch.misc[2 + sl.role] = j;
-            }
-        }
-        ch.fslot[2 * j] = f0;
-        ch.fslot[2 * j + 1] = f1;
-    }
-    gsync(p, gid);
-
-    // 3) collapse onto the block's tops: T[t], bit i of t = top of block site i
     {
         int rmask = 0;
         for (int i = 0; i < nb; ++i) rmask |= 1 << ch.misc[2 + i];
@@ -443,7 +511,7 @@ __device__ void readout_and_sample(const KParams& p, const Chain<R>& ch, int gid
     }
     gsync(p, gid);
 
-    // 4) sequential resampling of the block's sites (FP64 conditionals)
+    // 3) sequential resampling of the block's sites (FP64 conditionals)
     if (lt == 0) {
         C* cur = ch.T;
         int size = 1 << nb;
@@ -452,11 +520,11 @@ __device__ void readout_and_sample(const KParams& p, const Chain<R>& ch, int gid
             const int q = st.q;
             int rest = 0;   // later sites keep their current bits (projection)
             for (int j = i + 1; j < nb; ++j) rest |= ch.s[sites[j].q] << (j - i);
-            const C A0y0 = mixel<R>(p, ch, m, q, 0, 0), A0y1 = mixel<R>(p, ch, m, q, 0, 1);
-            const C A1y0 = mixel<R>(p, ch, m, q, 1, 0), A1y1 = mixel<R>(p, ch, m, q, 1, 1);
+            const C A00 = mixel<R>(p, ch, m, q, 0, 0), A01 = mixel<R>(p, ch, m, q, 0, 1);
+            const C A10 = mixel<R>(p, ch, m, q, 1, 0), A11 = mixel<R>(p, ch, m, q, 1, 1);
             const C c0 = cur[rest], c1 = cur[rest | 1];
-            const C amp0 = cfma(A0y0, c0, cmul(A0y1, c1));
-            const C amp1 = cfma(A1y0, c0, cmul(A1y1, c1));
+            const C amp0 = cfma(A00, c0, cmul(A01, c1));
+            const C amp1 = cfma(A10, c0, cmul(A11, c1));
             if (p.mode == MODE_AMP) {
                 if (i == p.amp_pos) {
                     const C a = ch.s[q] ? amp1 : amp0;
@@ -466,7 +534,7 @@ __device__ void readout_and_sample(const KParams& p, const Chain<R>& ch, int gid
                 }
             } else if (st.monomial) {
                 // deterministic move: the nonzero of column s[q] of A'_m
-                const C a0 = mixel<R>(p, ch, m, q, 0, ch.s[q]);
+                const C a0 = ch.s[q] ? A01 : A00;
                 ch.s[q] = (a0.x != (R)0 || a0.y != (R)0) ? 0 : 1;
             } else {
                 const double a0r = amp0.x, a0i = amp0.y, a1r = amp1.x, a1i = amp1.y;
@@ -488,7 +556,7 @@ __device__ void readout_and_sample(const KParams& p, const Chain<R>& ch, int gid
                 }
             }
             // contract this site's top with its mixer weight at the new bit
-            const C w0 = mixel<R>(p, ch, m, q, ch.s[q], 0), w1 = mixel<R>(p, ch, m, q, ch.s[q], 1);
+            const C w0 = ch.s[q] ? A10 : A00, w1 = ch.s[q] ? A11 : A01;
             size >>= 1;
             for (int r = 0; r < size; ++r) cur[r] = cfma(w0, cur[2 * r], cmul(w1, cur[2 * r + 1]));
         }
@@ -503,15 +571,17 @@ __device__ void run_chain(const KParams& p, const Chain<R>& ch, int gid, int lt,
     const DevPlanHeader& h = p.hdr;
     const int n = h.n, P = h.P, S = h.S, K = h.K;
     const uint64_t sample_id = p.first + chain;
-    const C one = cmk<C>(1.0, 0.0);
+    const C one = mk<R>(1, 0);
     const DevBlockRange* BR = P_<DevBlockRange>(p, p.off.block_ranges);
 
     for (int q = lt; q < n; q += p.tpc) {
         ch.x[q] = 0;
         ch.s[q] = p.mode == MODE_AMP ? (uint8_t)((p.in_bits[chain * h.words + (q >> 6)] >> (q & 63)) & 1ull) : 0;
     }
-    for (int i = lt; i < (P + 1) * n; i += p.tpc) ch.xmix[i] = 0;
-    for (int i = lt; i < h.n_cost_gates; i += p.tpc) ch.gframe[i] = 0;
+    if (h.has_frame) {
+        for (int i = lt; i < (P + 1) * n; i += p.tpc) ch.xmix[i] = 0;
+        for (int i = lt; i < h.n_cost_gates; i += p.tpc) ch.gframe[i] = 0;
+    }
     if (h.has_segfac)
         for (int i = lt; i < n * (P + 1) * 2; i += p.tpc) ch.segfac[i] = one;
     gsync(p, gid);
@@ -555,14 +625,15 @@ __device__ void run_chain(const KParams& p, const Chain<R>& ch, int gid, int lt,
                 } else if (ci.kind == CI_GATE1) {
                     const int q = G[ci.idx].q0, xb = ch.x[q];
                     C* sf = ch.segfac + ((size_t)q * (P + 1) + (m - 1)) * 2;
-                    sf[0] = cmul(sf[0], cmk<C>(G[ci.idx].d[2 * xb], G[ci.idx].d[2 * xb + 1]));
-                    sf[1] = cmul(sf[1], cmk<C>(G[ci.idx].d[2 * (1 ^ xb)], G[ci.idx].d[2 * (1 ^ xb) + 1]));
+                    sf[0] = cmul(sf[0], mk<R>((R)G[ci.idx].d[2 * xb], (R)G[ci.idx].d[2 * xb + 1]));
+                    sf[1] = cmul(sf[1], mk<R>((R)G[ci.idx].d[2 * (1 ^ xb)], (R)G[ci.idx].d[2 * (1 ^ xb) + 1]));
                 } else if (p.mode == MODE_SAMPLE) {
                     apply_channel<R>(p, ch, P_<DevChannel>(p, p.off.channels)[ci.idx], P_<double>(p, p.off.cum),
                                      P_<DevKrausFactor>(p, p.off.factors), sample_id, m - 1);
                 }
             }
-            for (int q = 0; q < n; ++q) ch.xmix[m * n + q] = ch.x[q];
+            if (h.has_frame)
+                for (int q = 0; q < n; ++q) ch.xmix[m * n + q] = ch.x[q];
         }
         gsync(p, gid);
         if (p.mode == MODE_AMP && m < p.amp_layer) continue;
@@ -575,14 +646,15 @@ __device__ void run_chain(const KParams& p, const Chain<R>& ch, int gid, int lt,
         C* RK = ch.Rt + (size_t)(K - 1) * NL;
         for (int i = lt; i < NL; i += p.tpc) RK[i] = one;
         if (lt == 0) ch.Rexp[K - 1] = 0;
-        gsync(p, gid);
         for (int k = K - 1; k > kstop; --k) {
+            const DevBlockRange br = BR[(size_t)m * K + k];
             const C* src = ch.Rt + (size_t)k * NL;
             C* dst = ch.Rt + (size_t)(k - 1) * NL;
+            build_tables<R>(p, ch, lt, br.bwd_begin, br.bwd_end, 0);
+            gsync(p, gid);   // tables ready, previous environment complete
             for (int i = lt; i < NL; i += p.tpc) dst[i] = src[i];
             gsync(p, gid);
-            const DevBlockRange br = BR[(size_t)m * K + k];
-            apply_ops<R>(p, ch, gid, lt, br.bwd_begin, br.bwd_end, dst, Wl, 0);
+            run_fused<R>(p, ch, gid, lt, br.bwd_begin, br.bwd_end, dst, Wl);
             R mx = 0;
             for (int i = lt; i < NL; i += p.tpc) mx = rmax(mx, rmax(rabs(dst[i].x), rabs(dst[i].y)));
             mx = group_max<R>(p, ch, gid, lt, mx);
@@ -593,11 +665,10 @@ __device__ void run_chain(const KParams& p, const Chain<R>& ch, int gid, int lt,
                     dst[i].y = scl(dst[i].y, -e);
                 }
             if (lt == 0) ch.Rexp[k - 1] = ch.Rexp[k] + e;
-            gsync(p, gid);
         }
 
         // forward sweep with a readout after every block
-        for (int i = lt; i < N; i += p.tpc) ch.L[i] = cmk<C>(i == 0 ? 1.0 : 0.0, 0.0);
+        for (int i = lt; i < N; i += p.tpc) ch.L[i] = mk<R>(i == 0 ? 1 : 0, 0);
         if (lt == 0) {
             ch.misc[0] = 0;
             ch.misc[1] = 0;
@@ -607,8 +678,10 @@ __device__ void run_chain(const KParams& p, const Chain<R>& ch, int gid, int lt,
         for (int k = 0; k <= kend; ++k) {
             const DevBlockRange br = BR[(size_t)m * K + k];
             const int pend = ch.misc[1];
+            build_tables<R>(p, ch, lt, br.fwd_begin, br.fwd_end, pend);
+            build_fslot<R>(p, ch, lt, m, br);
             gsync(p, gid);
-            apply_ops<R>(p, ch, gid, lt, br.fwd_begin, br.fwd_end, ch.L, W, pend);
+            run_fused<R>(p, ch, gid, lt, br.fwd_begin, br.fwd_end, ch.L, W);
             readout_and_sample<R>(p, ch, gid, lt, m, k, br, sample_id, chain);
         }
     }
@@ -634,7 +707,7 @@ __device__ void run_chain(const KParams& p, const Chain<R>& ch, int gid, int lt,
 }
 
 template <typename R>
-__global__ void __launch_bounds__(512) pw_chain_kernel(const KParams p) {
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 3 : 2) pw_chain_kernel(const KParams p) {
     using C = typename CT<R>::T;
     extern __shared__ __align__(16) unsigned char smem[];
     const int gid = threadIdx.x / p.tpc;
@@ -647,6 +720,7 @@ __global__ void __launch_bounds__(512) pw_chain_kernel(const KParams p) {
     ch.rowdot = reinterpret_cast<C*>(g + p.sm.rowdot);
     ch.T = reinterpret_cast<C*>(g + p.sm.T);
     ch.tab = reinterpret_cast<C*>(g + p.sm.tab);
+    ch.part = reinterpret_cast<C*>(g + p.sm.part);
     ch.fslot = reinterpret_cast<C*>(g + p.sm.fslot);
     ch.red = reinterpret_cast<R*>(g + p.sm.red);
     ch.s = g + p.sm.s;
@@ -663,36 +737,6 @@ __global__ void __launch_bounds__(512) pw_chain_kernel(const KParams p) {
 // ================================================================= host
 namespace {
 
-size_t align16(size_t v) { return (v + 15) & ~(size_t)15; }
-
-SmemLayout make_layout(const HostPlan& hp, size_t csz) {
-    const DevPlanHeader& h = hp.hdr;
-    SmemLayout L{};
-    size_t o = 0;
-    auto take = [&](size_t bytes) {
-        size_t at = o;
-        o = align16(o + bytes);
-        return (int)at;
-    };
-    const int S = h.S, P = std::max(h.P, 1), K = std::max(h.K, 1);
-    L.L = take(csz << (S * P));
-    L.R = take((size_t)K * (csz << (S * (P - 1))));
-    L.Rexp = take(sizeof(int) * K);
-    L.rowdot = take(csz << S);
-    L.T = take(csz << h.max_block);
-    L.tab = take(csz * 32);
-    L.fslot = take(csz * 2 * S);
-    L.red = take((csz / 2) * 32);
-    L.s = take(h.n);
-    L.x = take(h.n);
-    L.xmix = take((size_t)(h.P + 1) * h.n);
-    L.gframe = take(std::max(1, h.n_cost_gates));
-    L.segfac = take(h.has_segfac ? csz * 2 * (size_t)h.n * (h.P + 1) : 16);
-    L.misc = take(sizeof(int) * (2 + 16));
-    L.group_bytes = (int)align16(o);
-    return L;
-}
-
 template <typename T> void put(std::vector<unsigned char>& blob, int64_t& off, const std::vector<T>& v) {
     size_t at = align16(blob.size());
     blob.resize(at + std::max<size_t>(sizeof(T) * v.size(), 16));
@@ -707,6 +751,7 @@ int cuda_fail(cudaError_t e, const char* what) {
 std::vector<unsigned char> make_blob(const HostPlan& hp, DevPlanOffsets& o) {
     std::vector<unsigned char> blob;
     put(blob, o.micro, hp.micro);
+    put(blob, o.fused, hp.fused);
     put(blob, o.gate_refs, hp.gate_refs);
     put(blob, o.cost_gates, hp.cost_gates);
     put(blob, o.cost_items, hp.cost_items);
@@ -762,8 +807,7 @@ template <typename R> int launch(pw_plan* plan, KParams& kp, cudaStream_t st, ui
     if (kp.sm.group_bytes > maxsm)
         return set_error(PW_ERR_TOO_LARGE, "per-chain shared memory (" + std::to_string(kp.sm.group_bytes) +
                                                " B) exceeds 227 KB");
-    int gpc = std::max(1, std::min({8, 512 / kp.tpc, maxsm / kp.sm.group_bytes}));
-    if (kp.tpc == 32) gpc = std::max(1, std::min({8, maxsm / kp.sm.group_bytes}));
+    const int gpc = groups_per_cta(kp.tpc, kp.sm.group_bytes);
     kp.gpc = gpc;
     const int threads = kp.tpc * gpc;
     const size_t smem = (size_t)kp.sm.group_bytes * gpc;
