@@ -3,6 +3,7 @@
 #pragma once
 
 #include <complex>
+#include <cstddef>
 #include <cstdint>
 #include <string>
 #include <vector>
@@ -90,13 +91,17 @@ struct DevFused {
 };
 
 // A diagonal cost gate (1 or 2 qubits) with its table; level = segment index.
-struct DevCostGate {
+// The kernel loads d[] as double2 and f[] as float2: d must start on a 16-byte
+// boundary and the struct size must keep that true along an array.
+struct alignas(16) DevCostGate {
+    double d[8];         // 4 complex (re, im) entries, local index b0 + 2 b1
+    float f[8];          // the same in FP32
     int16_t q0, q1;      // q1 < 0 for a one-qubit gate
     int16_t level;
     int16_t pad;
-    float f[8];          // 4 complex (re, im) entries, local index b0 + 2 b1 (FP32 copy)
-    double d[8];         // the same in FP64
 };
+static_assert(offsetof(DevCostGate, d) % 16 == 0 && offsetof(DevCostGate, f) % 8 == 0, "vector loads");
+static_assert(sizeof(DevCostGate) % 16 == 0, "array stride keeps d aligned");
 
 // Items of a cost section, processed in circuit order by one thread per chain.
 enum CostItemKind : int16_t { CI_GATE2 = 0, CI_GATE1 = 1, CI_CHANNEL = 2 };
