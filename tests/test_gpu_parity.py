@@ -249,21 +249,37 @@ def test_heavy_hex_400_zz_closed_form(pw):
 
 
 def test_heavy_hex_400_amplitudes_against_elimination(pw):
+    """400 qubits: FP64 amplitudes of random strings (full circuit) against the
+    elimination oracle, and the FP64 sampler's candidate pairs along one
+    sampled chain (rows spread over the sweep)."""
     import torch
+    from oracle.philox import draw
     spec = W.heavy_hex_400_p1()
     circ = _circ(pw, spec)
-    plan = pw.pw_plan_build(circ)
+    plan = pw.pw_plan_build(circ, precision=pw.PW_PREC_FP64)
     order = pw.pw_plan_exec_order(plan)
     ops = OC.qaoa_circuit(spec)
     xs = W.random_bitstrings(3, spec.n, seed=73)
     d_bits = torch.from_numpy(pw.pack_bits(xs).view(np.int64)).cuda()
     amp = torch.zeros((3, 2), dtype=torch.float64, device="cuda")
-    t = len(order)   # the full circuit
-    pw.pw_amplitudes(plan, t, d_bits, amp)
+    pw.pw_amplitudes(plan, len(order), d_bits, amp)
     got = amp.cpu().numpy()
-    pre = [ops[i] for i in order[:t]]
+    pre = [ops[i] for i in order]
     for k in range(3):
         a = TN.amplitudes(spec.n, pre, xs[k])
-        assert abs(got[k, 0] + 1j * got[k, 1] - a) <= 1e-5 * abs(a)
+        assert abs(got[k, 0] + 1j * got[k, 1] - a) <= 1e-10 * abs(a)
     pw.pw_plan_destroy(plan)
     pw.pw_circuit_destroy(circ)
+    # FP32 trace of one chain: the state before the r-th mixer gate is the
+    # final bit for qubits already resampled and the H-layer bit for the rest
+    g = run_gpu(pw, spec, 1, seed=8, precision=pw.PW_PREC_FP64)
+    final = g["bits"][0]
+    h_bits = np.array([0 if draw(8, 0, q, 0) < 0.5 else 1 for q in range(spec.n)], dtype=np.uint8)
+    mix_pos = [t for t, oi in enumerate(order) if t >= spec.n and ops[oi].kind == "gate" and len(ops[oi].qubits) == 1]
+    for r in (0, 133, 266, 399):
+        t = mix_pos[r]
+        q = ops[order[t]].qubits[0]
+        done = {ops[order[u]].qubits[0] for u in mix_pos[:r]}
+        state = np.array([final[j] if j in done else h_bits[j] for j in range(spec.n)], dtype=np.uint8)
+        tab = TN.amplitudes(spec.n, [ops[i] for i in order[:t + 1]], state, open_qubits=(q,))
+        assert pair_err([tab[0], tab[1]], g["trace"][0, r]) < TOL[1], r
