@@ -283,48 +283,101 @@ std::vector<int> greedy_order(const std::vector<std::vector<int>>& adj, int star
     return order;
 }
 
-// Group consecutive micro-ops into fused passes: up to two 2x2 matrices on
-// distinct bits, followed by diagonal/scalar factors whose bits (together)
-// number at most 5. Returns the table entries of the range.
-int fuse_range(HostPlan& hp, int b, int e) {
+// Group consecutive micro-ops into tiled passes: the 2x2 matrices of a pass
+// act on at most 4 distinct bits (its tile), at most 8 stages per pass, and
+// consecutive diagonal/scalar ops merge into one stage while their bits number
+// at most 5. Returns the table entries of the range; *nst gets its stages.
+int fuse_range(HostPlan& hp, int b, int e, int* nst_out) {
     int tab = 0;
     int i = b;
+    const int st0 = (int)hp.stages.size();
     while (i < e) {
         DevFused f{};
-        f.op_begin = i;
-        while (i < e && hp.micro[i].kind == MK_MAT1 && f.nmat < 2 &&
-               (f.nmat == 0 || hp.micro[i].bits[0] != f.mbits[0])) {
-            f.mbits[f.nmat++] = hp.micro[i].bits[0];
-            ++i;
-        }
-        std::vector<int> db;
-        while (i < e && hp.micro[i].kind != MK_MAT1) {
+        f.st_begin = (int)hp.stages.size();
+        std::vector<int> tiles;
+        std::vector<std::vector<int>> sbits;   // per stage: diagonal bits
+        while (i < e) {
             const DevMicroOp& o = hp.micro[i];
-            std::vector<int> u = db;
-            for (int j = 0; j < o.nbits; ++j)
-                if (std::find(u.begin(), u.end(), (int)o.bits[j]) == u.end()) u.push_back(o.bits[j]);
-            if (u.size() > 5) break;
-            db = u;
+            if (o.kind == MK_MAT1) {
+                int bit = o.bits[0];
+                auto it = std::find(tiles.begin(), tiles.end(), bit);
+                int k;
+                if (it == tiles.end()) {
+                    if (tiles.size() == 4) break;
+                    tiles.push_back(bit);
+                    k = (int)tiles.size() - 1;
+                } else {
+                    k = (int)(it - tiles.begin());
+                }
+                if (f.nst == 8) break;
+                DevStage st{};
+                st.type = ST_MAT;
+                st.arg = (uint8_t)k;
+                st.op_begin = i;
+                st.op_end = i + 1;
+                hp.stages.push_back(st);
+                sbits.emplace_back();
+                ++f.nst;
+                ++i;
+                continue;
+            }
+            bool merged = false;
+            if (f.nst > 0 && hp.stages.back().type == ST_DIAG) {
+                std::vector<int> u = sbits.back();
+                for (int j = 0; j < o.nbits; ++j)
+                    if (std::find(u.begin(), u.end(), (int)o.bits[j]) == u.end()) u.push_back(o.bits[j]);
+                if (u.size() <= 5) {
+                    sbits.back() = u;
+                    hp.stages.back().op_end = i + 1;
+                    merged = true;
+                }
+            }
+            if (!merged) {
+                if (f.nst == 8) break;
+                DevStage st{};
+                st.type = ST_DIAG;
+                st.op_begin = i;
+                st.op_end = i + 1;
+                hp.stages.push_back(st);
+                std::vector<int> u;
+                for (int j = 0; j < o.nbits; ++j)
+                    if (std::find(u.begin(), u.end(), (int)o.bits[j]) == u.end()) u.push_back(o.bits[j]);
+                sbits.push_back(u);
+                ++f.nst;
+            }
             ++i;
         }
-        f.op_end = i;
-        f.ndiag = (uint8_t)db.size();
-        for (size_t j = 0; j < db.size(); ++j) f.dbits[j] = (uint8_t)db[j];
-        for (int m = 0; m < 2; ++m) {
-            f.mpos[m] = -1;
-            if (m < f.nmat)
-                for (size_t j = 0; j < db.size(); ++j)
-                    if (db[j] == f.mbits[m]) f.mpos[m] = (int8_t)j;
+        f.ntb = (uint8_t)tiles.size();
+        for (size_t k = 0; k < tiles.size(); ++k) f.tbits[k] = (uint8_t)tiles[k];
+        for (int s = 0; s < f.nst; ++s) {
+            DevStage& st = hp.stages[f.st_begin + s];
+            for (int k = 0; k < 4; ++k) {
+                st.tpos[k] = 0xFF;
+                if (st.type == ST_DIAG && k < (int)tiles.size())
+                    for (size_t j = 0; j < sbits[s].size(); ++j)
+                        if (sbits[s][j] == tiles[k]) st.tpos[k] = (uint8_t)j;
+            }
         }
-        for (int k = f.op_begin + f.nmat; k < f.op_end; ++k) {
-            DevMicroOp& o = hp.micro[k];
-            for (int j = 0; j < o.nbits; ++j)
-                o.fpos[j] = (uint8_t)(std::find(db.begin(), db.end(), (int)o.bits[j]) - db.begin());
+        for (int s = 0; s < f.nst; ++s) {
+            DevStage& st = hp.stages[f.st_begin + s];
+            st.tab_off = tab;
+            if (st.type == ST_MAT) {
+                tab += 4;
+                continue;
+            }
+            const std::vector<int>& db = sbits[s];
+            st.arg = (uint8_t)db.size();
+            for (size_t j = 0; j < db.size(); ++j) st.dbits[j] = (uint8_t)db[j];
+            tab += 1 << db.size();
+            for (int k = st.op_begin; k < st.op_end; ++k) {
+                DevMicroOp& o = hp.micro[k];
+                for (int j = 0; j < o.nbits; ++j)
+                    o.fpos[j] = (uint8_t)(std::find(db.begin(), db.end(), (int)o.bits[j]) - db.begin());
+            }
         }
-        f.tab_off = tab;
-        tab += 4 * f.nmat + (1 << f.ndiag);
         hp.fused.push_back(f);
     }
+    *nst_out = (int)hp.stages.size() - st0;
     return tab;
 }
 
@@ -599,12 +652,15 @@ int build_plan(const pw_circuit* c, const pw_plan_opts& opts, HostPlan& hp) {
             {
                 int mb = br.fwd_begin, me = (int)hp.micro.size();
                 br.fwd_begin = (int)hp.fused.size();
-                br.fwd_tab = fuse_range(hp, mb, me);
+                br.fwd_st = (int)hp.stages.size();
+                br.fwd_tab = fuse_range(hp, mb, me, &br.fwd_nst);
                 br.fwd_end = (int)hp.fused.size();
             }
             // backward (R_k -> R_{k-1}); not needed for k = 0
             br.bwd_begin = br.bwd_end = (int)hp.fused.size();
             br.bwd_tab = 0;
+            br.bwd_st = (int)hp.stages.size();
+            br.bwd_nst = 0;
             const int bwd_micro_begin = (int)hp.micro.size();
             if (k >= 1) {
                 std::vector<int> consts;
@@ -649,7 +705,8 @@ int build_plan(const pw_circuit* c, const pw_plan_opts& opts, HostPlan& hp) {
                     }
                 }
                 br.bwd_begin = (int)hp.fused.size();
-                br.bwd_tab = fuse_range(hp, bwd_micro_begin, (int)hp.micro.size());
+                br.bwd_st = (int)hp.stages.size();
+                br.bwd_tab = fuse_range(hp, bwd_micro_begin, (int)hp.micro.size(), &br.bwd_nst);
                 br.bwd_end = (int)hp.fused.size();
             }
         }
@@ -663,6 +720,7 @@ int build_plan(const pw_circuit* c, const pw_plan_opts& opts, HostPlan& hp) {
                 bs.monomial = hp.mix_mono[(size_t)m * n + q];
                 bs.op_id = L.mixer_op_of[(size_t)m * n + q];
                 bs.trace_row = bs.monomial ? -1 : trace_row++;
+                if (!bs.monomial) hp.row_opid.push_back(bs.op_id);
                 hp.block_sites.push_back(bs);
                 hp.exec_order.push_back(bs.op_id);
                 hp.exec_layer[bs.op_id] = m;
@@ -699,8 +757,8 @@ int build_plan(const pw_circuit* c, const pw_plan_opts& opts, HostPlan& hp) {
         double NF = std::ldexp(1.0, S * m), NB = std::ldexp(1.0, S * (m - 1));
         for (int k = 0; k < K; ++k) {
             const DevBlockRange& br = hp.block_ranges[(size_t)m * K + k];
-            for (int i = br.fwd_begin; i < br.fwd_end; ++i) flops += (14.0 * hp.fused[i].nmat + 6.0) * NF;
-            for (int i = br.bwd_begin; i < br.bwd_end; ++i) flops += (14.0 * hp.fused[i].nmat + 6.0) * NB;
+            for (int i = br.fwd_st; i < br.fwd_st + br.fwd_nst; ++i) flops += (hp.stages[i].type == ST_MAT ? 14.0 : 6.0) * NF;
+            for (int i = br.bwd_st; i < br.bwd_st + br.bwd_nst; ++i) flops += (hp.stages[i].type == ST_MAT ? 14.0 : 6.0) * NB;
             flops += 8.0 * NF;
         }
     }
@@ -720,7 +778,11 @@ int build_plan(const pw_circuit* c, const pw_plan_opts& opts, HostPlan& hp) {
     hp.hdr.has_frame = has_frame ? 1 : 0;
     hp.hdr.words = (n + 63) / 64;
     hp.hdr.max_tab = 1;
-    for (const auto& br : hp.block_ranges) hp.hdr.max_tab = std::max({hp.hdr.max_tab, br.fwd_tab, br.bwd_tab});
+    hp.hdr.max_stages = 1;
+    for (const auto& br : hp.block_ranges) {
+        hp.hdr.max_tab = std::max({hp.hdr.max_tab, br.fwd_tab, br.bwd_tab});
+        hp.hdr.max_stages = std::max({hp.hdr.max_stages, br.fwd_nst, br.bwd_nst});
+    }
     hp.W = S * std::max(P, 1);
     hp.W_low = S * std::max(P - 1, 0);
     return PW_OK;

@@ -75,19 +75,27 @@ struct DevMicroOp {
     int32_t gcount;
 };
 
-// A fused pass: up to two 2x2 matrices on distinct bits, then one diagonal
-// table over up to 5 bits (the product of the constituent diagonal factors).
-// Its constituents are micro-ops [op_begin, op_end): first the nmat MAT1 ops,
-// then DIAG / CONST ops. Table layout at tab_off: nmat x 4 entries, then 2^ndiag.
+// A tiled pass: every thread loads tiles of 2^ntb entries (the index bits
+// tbits[] varying, the others fixed), runs the pass's stages on them in
+// registers and stores them back. A stage is a 2x2 matrix on one tile bit, or
+// a diagonal factor over up to 5 bits (tile bits or fixed bits), the product
+// of consecutive diagonal/scalar micro-ops.
+enum StageType : uint8_t { ST_MAT = 0, ST_DIAG = 1 };
+struct DevStage {
+    uint8_t type;
+    uint8_t arg;         // ST_MAT: index into tbits; ST_DIAG: number of diagonal bits
+    uint8_t dbits[5];    // ST_DIAG: index bits of the table, entry bit j <- index bit dbits[j]
+    uint8_t tpos[4];     // ST_DIAG: position in dbits of tile bit k, 0xFF if absent
+    uint8_t pad;
+    int32_t op_begin, op_end;   // constituent micro-ops
+    int32_t tab_off;            // complex entries from the start of the block's table area
+};
 struct DevFused {
-    uint8_t nmat;
-    uint8_t ndiag;
-    uint8_t mbits[2];
-    int8_t mpos[2];      // position of mbits[i] inside dbits, -1 if absent
-    uint8_t dbits[5];
-    uint8_t pad[5];
-    int32_t op_begin, op_end;
-    int32_t tab_off;     // complex entries from the start of the block's table area
+    uint8_t ntb;         // tile bits (0..4)
+    uint8_t tbits[4];
+    uint8_t nst;         // stages (1..8)
+    uint8_t pad[2];
+    int32_t st_begin;    // first DevStage
 };
 
 // A diagonal cost gate (1 or 2 qubits) with its table; level = segment index.
@@ -151,6 +159,8 @@ struct DevBlockRange {
     int32_t site_begin, site_end;   // DevBlockSite
     int32_t live_begin, live_end;   // DevLiveSlot
     int32_t fwd_tab, bwd_tab;       // table entries of the two programs
+    int32_t fwd_st, bwd_st;         // first stage of the two programs
+    int32_t fwd_nst, bwd_nst;       // their stage counts
 };
 
 struct DevPlanHeader {
@@ -166,11 +176,12 @@ struct DevPlanHeader {
     int32_t has_frame;         // channels present
     int32_t words;             // uint64 words per bitstring
     int32_t max_tab;           // max table entries of one block program
+    int32_t max_stages;        // max stages of one block program
 };
 
 // Offsets (in bytes) of the arrays inside the device blob.
 struct DevPlanOffsets {
-    int64_t micro, fused, gate_refs, cost_gates, cost_items, cost_ranges, channels, cum, factors;
+    int64_t micro, fused, stages, row_opid, gate_refs, cost_gates, cost_items, cost_ranges, channels, cum, factors;
     int64_t mix_d, mix_f, mix0_order, mix0_opid, mix_mono;
     int64_t block_ranges, block_sites, live_slots;
 };
@@ -189,6 +200,8 @@ struct HostPlan {
     // blob pieces (host copies)
     std::vector<DevMicroOp> micro;
     std::vector<DevFused> fused;
+    std::vector<DevStage> stages;
+    std::vector<int32_t> row_opid;        // op id of each sampled gate (trace row)
     std::vector<int32_t> gate_refs;
     std::vector<DevCostGate> cost_gates;
     std::vector<DevCostItem> cost_items;

@@ -114,14 +114,20 @@ template <typename T> __device__ __forceinline__ const T* P_(const KParams& p, i
     return reinterpret_cast<const T*>(p.blob + off);
 }
 
-// Barrier of one chain's thread group.
-__device__ __forceinline__ void gsync(const KParams& p, int gid) {
-    if (p.tpc == 32) {
-        __syncwarp();
-    } else {
-        asm volatile("bar.sync %0, %1;" ::"r"(gid + 1), "r"(p.tpc) : "memory");
+// The threads that run one phase of one chain: the whole group (named
+// barrier over tpc threads) or only its first warp (warp barrier), used for
+// tensors too small to feed the group.
+struct Grp {
+    int lt, nt, gid, tpc;
+    bool warp;
+    __device__ __forceinline__ void sync() const {
+        if (warp || tpc == 32) {
+            __syncwarp();
+        } else {
+            asm volatile("bar.sync %0, %1;" ::"r"(gid + 1), "r"(tpc) : "memory");
+        }
     }
-}
+};
 
 // Per-chain view of the shared-memory group.
 template <typename R> struct Chain {
@@ -132,7 +138,9 @@ template <typename R> struct Chain {
     C* rowdot;    // 2^S
     C* T;         // 2^max_block
     C* tab;       // tables of one block program
-    C* part;      // tpc partial sums
+    DevStage* stg;    // stage descriptors of one block program
+    double* ud;   // the chain's UpdateState draws, one per sampled gate
+    C* part;      // partial sums, one per thread
     C* fslot;     // S x 2 per-slot readout factors
     R* red;       // 32 reduction scratch
     uint8_t* s;   // chain state s
@@ -149,11 +157,9 @@ __device__ __forceinline__ typename CT<R>::T mixel(const KParams& p, const Chain
     const int xb = p.hdr.has_frame ? ch.xmix[m * p.hdr.n + q] : 0;
     const size_t base = ((size_t)m * p.hdr.n + q) * 8 + 2 * (((o ^ xb) << 1) | (i ^ xb));
     if constexpr (sizeof(R) == 4) {
-        const float2 v = *reinterpret_cast<const float2*>(P_<float>(p, p.off.mix_f) + base);
-        return v;
+        return *reinterpret_cast<const float2*>(P_<float>(p, p.off.mix_f) + base);
     } else {
-        const double2 v = *reinterpret_cast<const double2*>(P_<double>(p, p.off.mix_d) + base);
-        return v;
+        return *reinterpret_cast<const double2*>(P_<double>(p, p.off.mix_d) + base);
     }
 }
 
@@ -237,113 +243,149 @@ __device__ typename CT<R>::T build_entry(const KParams& p, const Chain<R>& ch, c
     return one;
 }
 
-// Build the tables of fused ops [fb, fe) into ch.tab. pend_exp (a power of two)
-// is folded into the diagonal table of the first op.
+// Tables and stage descriptors of one block program (stages [sb, sb + ns)).
+// pend_exp (a power of two) is folded into the program's first stage.
 template <typename R>
-__device__ void build_tables(const KParams& p, const Chain<R>& ch, int lt, int fb, int fe, int pend_exp) {
+__device__ void build_tables(const KParams& p, const Chain<R>& ch, const Grp& g, int sb, int ns, int pend_exp) {
     using C = typename CT<R>::T;
-    const DevFused* F = P_<DevFused>(p, p.off.fused);
+    const DevStage* ST = P_<DevStage>(p, p.off.stages) + sb;
     const DevMicroOp* ops = P_<DevMicroOp>(p, p.off.micro);
-    for (int fi = fb; fi < fe; ++fi) {
-        const DevFused f = F[fi];
-        const int nm = 4 * f.nmat, ne = nm + (1 << f.ndiag);
-        for (int e = lt; e < ne; e += p.tpc) {
+    for (int i = g.lt; i < ns; i += g.nt) ch.stg[i] = ST[i];
+    for (int si = 0; si < ns; ++si) {
+        const DevStage st = ST[si];
+        const int ne = st.type == ST_MAT ? 4 : (1 << st.arg);
+        for (int e = g.lt; e < ne; e += g.nt) {
             C v;
-            if (e < nm) {
-                v = build_entry<R>(p, ch, ops[f.op_begin + (e >> 2)], e & 3);
+            if (st.type == ST_MAT) {
+                v = build_entry<R>(p, ch, ops[st.op_begin], e);
             } else {
-                const int de = e - nm;
                 v = mk<R>(1, 0);
-                for (int k = f.op_begin + f.nmat; k < f.op_end; ++k) {
+                for (int k = st.op_begin; k < st.op_end; ++k) {
                     const DevMicroOp o = ops[k];
                     int loc = 0;
-                    for (int j = 0; j < o.nbits; ++j) loc |= ((de >> o.fpos[j]) & 1) << j;
+                    for (int j = 0; j < o.nbits; ++j) loc |= ((e >> o.fpos[j]) & 1) << j;
                     v = cmul(v, build_entry<R>(p, ch, o, loc));
                 }
-                if (fi == fb && pend_exp != 0) {
-                    v.x = scl(v.x, pend_exp);
-                    v.y = scl(v.y, pend_exp);
-                }
             }
-            ch.tab[f.tab_off + e] = v;
+            if (si == 0 && pend_exp != 0) {
+                v.x = scl(v.x, pend_exp);
+                v.y = scl(v.y, pend_exp);
+            }
+            ch.tab[st.tab_off + e] = v;
         }
     }
 }
 
-__device__ __forceinline__ int gather_bits(int idx, const uint8_t* db, int nd) {
-    int t = 0;
+// (x[e], x[e | 1<<K]) <- M (x[e], x[e | 1<<K]) for every e with bit K clear.
+template <typename C, int T, int K>
+__device__ __forceinline__ void mat_stage(C (&x)[1 << T], C m00, C m01, C m10, C m11) {
 #pragma unroll
-    for (int j = 0; j < 5; ++j)
-        if (j < nd) t |= ((idx >> db[j]) & 1) << j;
-    return t;
+    for (int e = 0; e < (1 << T); ++e) {
+        if (e & (1 << K)) continue;
+        const C x0 = x[e], x1 = x[e | (1 << K)];
+        x[e] = cfma(m00, x0, cmul(m01, x1));
+        x[e | (1 << K)] = cfma(m10, x0, cmul(m11, x1));
+    }
 }
 
-// Run fused ops [fb, fe) on buf (2^W entries), one pass and one barrier each.
-template <typename R>
-__device__ void run_fused(const KParams& p, const Chain<R>& ch, int gid, int lt, int fb, int fe,
+// One tiled pass over buf (2^W entries) by the threads of g.
+template <typename R, int T>
+__device__ void tile_pass(const KParams& p, const Chain<R>& ch, const Grp& g, const DevFused& f, int sb,
                           typename CT<R>::T* buf, int W) {
     using C = typename CT<R>::T;
-    const DevFused* F = P_<DevFused>(p, p.off.fused);
+    constexpr int E = 1 << T;
     const int N = 1 << W;
-    for (int fi = fb; fi < fe; ++fi) {
-        const DevFused f = F[fi];
-        const C* tab = ch.tab + f.tab_off;
-        const C* D = tab + 4 * f.nmat;
-        const int nd = f.ndiag;
-        if (f.nmat == 2) {
-            const int ba = f.mbits[0], bb = f.mbits[1];
-            const int lo = min(ba, bb), hi = max(ba, bb);
-            const int pa = f.mpos[0] >= 0 ? 1 << f.mpos[0] : 0, pb = f.mpos[1] >= 0 ? 1 << f.mpos[1] : 0;
-            const C a00 = tab[0], a01 = tab[1], a10 = tab[2], a11 = tab[3];
-            const C b00 = tab[4], b01 = tab[5], b10 = tab[6], b11 = tab[7];
-            for (int qi = lt; qi < (N >> 2); qi += p.tpc) {
-                int i = ((qi >> lo) << (lo + 1)) | (qi & ((1 << lo) - 1));
-                i = ((i >> hi) << (hi + 1)) | (i & ((1 << hi) - 1));
-                const int ia = 1 << ba, ib = 1 << bb;
-                C x00 = buf[i], x10 = buf[i | ia], x01 = buf[i | ib], x11 = buf[i | ia | ib];
-                // matrix a on bit ba
-                C y00 = cfma(a00, x00, cmul(a01, x10)), y10 = cfma(a10, x00, cmul(a11, x10));
-                C y01 = cfma(a00, x01, cmul(a01, x11)), y11 = cfma(a10, x01, cmul(a11, x11));
-                // matrix b on bit bb
-                x00 = cfma(b00, y00, cmul(b01, y01));
-                x01 = cfma(b10, y00, cmul(b11, y01));
-                x10 = cfma(b00, y10, cmul(b01, y11));
-                x11 = cfma(b10, y10, cmul(b11, y11));
-                const int t = gather_bits(i, f.dbits, nd);
-                buf[i] = cmul(x00, D[t]);
-                buf[i | ia] = cmul(x10, D[t | pa]);
-                buf[i | ib] = cmul(x01, D[t | pb]);
-                buf[i | ia | ib] = cmul(x11, D[t | pa | pb]);
+    int off[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        int o = 0;
+#pragma unroll
+        for (int k = 0; k < T; ++k)
+            if (e & (1 << k)) o |= 1 << f.tbits[k];
+        off[e] = o;
+    }
+    int sb4[4] = {f.tbits[0], f.tbits[1], f.tbits[2], f.tbits[3]};
+#pragma unroll
+    for (int a = 1; a < T; ++a)
+#pragma unroll
+        for (int b = a; b > 0; --b)
+            if (sb4[b] < sb4[b - 1]) {
+                const int t = sb4[b];
+                sb4[b] = sb4[b - 1];
+                sb4[b - 1] = t;
             }
-        } else if (f.nmat == 1) {
-            const int bt = f.mbits[0];
-            const int pa = f.mpos[0] >= 0 ? 1 << f.mpos[0] : 0;
-            const C m00 = tab[0], m01 = tab[1], m10 = tab[2], m11 = tab[3];
-            for (int pi = lt; pi < (N >> 1); pi += p.tpc) {
-                const int i0 = ((pi >> bt) << (bt + 1)) | (pi & ((1 << bt) - 1));
-                const int i1 = i0 | (1 << bt);
-                const C x0 = buf[i0], x1 = buf[i1];
-                const int t = gather_bits(i0, f.dbits, nd);
-                buf[i0] = cmul(cfma(m00, x0, cmul(m01, x1)), D[t]);
-                buf[i1] = cmul(cfma(m10, x0, cmul(m11, x1)), D[t | pa]);
+    const DevStage* stg = ch.stg + sb;
+    for (int tile = g.lt; tile < (N >> T); tile += g.nt) {
+        int base = tile;
+#pragma unroll
+        for (int k = 0; k < T; ++k) base = ((base >> sb4[k]) << (sb4[k] + 1)) | (base & ((1 << sb4[k]) - 1));
+        C x[E];
+#pragma unroll
+        for (int e = 0; e < E; ++e) x[e] = buf[base | off[e]];
+        for (int s = 0; s < f.nst; ++s) {
+            const DevStage st = stg[s];
+            const C* tab = ch.tab + st.tab_off;
+            if (st.type == ST_MAT) {
+                const C m00 = tab[0], m01 = tab[1], m10 = tab[2], m11 = tab[3];
+                if constexpr (T >= 1) {
+                    switch (st.arg) {
+                        case 0: mat_stage<C, T, 0>(x, m00, m01, m10, m11); break;
+                        case 1: if constexpr (T >= 2) mat_stage<C, T, (T >= 2 ? 1 : 0)>(x, m00, m01, m10, m11); break;
+                        case 2: if constexpr (T >= 3) mat_stage<C, T, (T >= 3 ? 2 : 0)>(x, m00, m01, m10, m11); break;
+                        default: if constexpr (T >= 4) mat_stage<C, T, (T >= 4 ? 3 : 0)>(x, m00, m01, m10, m11); break;
+                    }
+                }
+            } else {
+                int tb = 0;
+                for (int j = 0; j < st.arg; ++j) tb |= ((base >> st.dbits[j]) & 1) << j;
+                int pm[4];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) pm[k] = st.tpos[k] != 0xFF ? 1 << st.tpos[k] : 0;
+#pragma unroll
+                for (int e = 0; e < E; ++e) {
+                    int t = tb;
+#pragma unroll
+                    for (int k = 0; k < T; ++k)
+                        if (e & (1 << k)) t |= pm[k];
+                    x[e] = cmul(x[e], tab[t]);
+                }
             }
-        } else {
-            for (int idx = lt; idx < N; idx += p.tpc) buf[idx] = cmul(buf[idx], D[gather_bits(idx, f.dbits, nd)]);
         }
-        gsync(p, gid);
+#pragma unroll
+        for (int e = 0; e < E; ++e) buf[base | off[e]] = x[e];
     }
 }
 
-// Group-wide max of a per-thread value (broadcast to every thread).
+// Run passes [fb, fe) (their stages start at stage sb0 of the block) on buf.
 template <typename R>
-__device__ R group_max(const KParams& p, const Chain<R>& ch, int gid, int lt, R v) {
+__device__ void run_passes(const KParams& p, const Chain<R>& ch, const Grp& g, int fb, int fe, int sb0,
+                           typename CT<R>::T* buf, int W) {
+    const DevFused* F = P_<DevFused>(p, p.off.fused);
+    for (int fi = fb; fi < fe; ++fi) {
+        const DevFused f = F[fi];
+        const int sb = f.st_begin - sb0;
+        switch (f.ntb) {
+            case 0: tile_pass<R, 0>(p, ch, g, f, sb, buf, W); break;
+            case 1: tile_pass<R, 1>(p, ch, g, f, sb, buf, W); break;
+            case 2: tile_pass<R, 2>(p, ch, g, f, sb, buf, W); break;
+            case 3: tile_pass<R, 3>(p, ch, g, f, sb, buf, W); break;
+            default: tile_pass<R, 4>(p, ch, g, f, sb, buf, W); break;
+        }
+        g.sync();
+    }
+}
+
+// Max over the threads of g of a per-thread value (broadcast).
+template <typename R>
+__device__ R group_max(const Chain<R>& ch, const Grp& g, R v) {
     for (int o = 16; o > 0; o >>= 1) v = rmax(v, __shfl_xor_sync(0xffffffffu, v, o));
-    const int nw = (p.tpc + 31) >> 5;
-    if ((lt & 31) == 0) ch.red[lt >> 5] = v;
-    gsync(p, gid);
+    if (g.warp || g.nt <= 32) return v;
+    const int nw = (g.nt + 31) >> 5;
+    if ((g.lt & 31) == 0) ch.red[g.lt >> 5] = v;
+    g.sync();
     R m = ch.red[0];
     for (int w = 1; w < nw; ++w) m = rmax(m, ch.red[w]);
-    gsync(p, gid);
+    g.sync();
     return m;
 }
 
@@ -398,21 +440,21 @@ __device__ void apply_channel(const KParams& p, const Chain<R>& ch, const DevCha
 // earlier block, their mixer weight A'_m[s][top]. Also records which slot
 // holds the i-th site of the block.
 template <typename R>
-__device__ void build_fslot(const KParams& p, const Chain<R>& ch, int lt, int m, const DevBlockRange& br) {
+__device__ void build_fslot(const KParams& p, const Chain<R>& ch, const Grp& g, int m, const DevBlockRange& br) {
     using C = typename CT<R>::T;
     const DevLiveSlot* live = P_<DevLiveSlot>(p, p.off.live_slots) + br.live_begin;
     const int32_t* gref = P_<int32_t>(p, p.off.gate_refs);
     const DevCostGate* G = P_<DevCostGate>(p, p.off.cost_gates);
-    for (int j = lt; j < p.hdr.S; j += p.tpc) {
+    for (int j = g.lt; j < p.hdr.S; j += g.nt) {
         const DevLiveSlot sl = live[j];
         C f0 = mk<R>(1, 0), f1 = mk<R>(0, 0);
         if (sl.q >= 0) {
             f1 = mk<R>(1, 0);
             for (int i = 0; i < sl.dcount; ++i) {
-                const int g = gref[sl.dlist + i];
-                const int w = G[g].q0 == sl.q ? G[g].q1 : G[g].q0;
-                f0 = cmul(f0, gate_pair<R>(p, ch, g, sl.q, 0, ch.s[w]));
-                f1 = cmul(f1, gate_pair<R>(p, ch, g, sl.q, 1, ch.s[w]));
+                const int gg = gref[sl.dlist + i];
+                const int w = G[gg].q0 == sl.q ? G[gg].q1 : G[gg].q0;
+                f0 = cmul(f0, gate_pair<R>(p, ch, gg, sl.q, 0, ch.s[w]));
+                f1 = cmul(f1, gate_pair<R>(p, ch, gg, sl.q, 1, ch.s[w]));
             }
             if (sl.role < 0) {
                 f0 = cmul(f0, mixel<R>(p, ch, m, sl.q, ch.s[sl.q], 0));
@@ -432,8 +474,8 @@ __device__ void build_fslot(const KParams& p, const Chain<R>& ch, int lt, int m,
 // are resampled one after another (UpdateState of Alg. 1), contracting each
 // resampled top with A'_m[s_new][.] before moving to the next site.
 template <typename R>
-__device__ void readout_and_sample(const KParams& p, const Chain<R>& ch, int gid, int lt, int m, int k,
-                                   const DevBlockRange& br, uint64_t sample_id, uint64_t chain) {
+__device__ void readout_and_sample(const KParams& p, const Chain<R>& ch, const Grp& g, int m, int k,
+                                   const DevBlockRange& br, uint64_t chain) {
     using C = typename CT<R>::T;
     const DevPlanHeader& h = p.hdr;
     const int S = h.S, Wl = S * (m - 1);
@@ -444,17 +486,17 @@ __device__ void readout_and_sample(const KParams& p, const Chain<R>& ch, int gid
 
     // 1) rowdot[h] = sum_l L[l*H + h] R_k[l] (coalesced), and max |L|
     R mx = 0;
-    if (p.tpc >= H) {
-        const int hh = lt & (H - 1), step = p.tpc / H;
+    if (g.nt >= H) {
+        const int hh = g.lt & (H - 1), step = g.nt / H;
         C acc = zero;
-        for (int l = lt / H; l < NL; l += step) {
+        for (int l = g.lt / H; l < NL; l += step) {
             const C v = L[(size_t)l * H + hh];
             acc = cfma(v, Rk[l], acc);
             mx = rmax(mx, rmax(rabs(v.x), rabs(v.y)));
         }
-        ch.part[lt] = acc;
+        ch.part[g.lt] = acc;
     } else {
-        for (int hh = lt; hh < H; hh += p.tpc) {
+        for (int hh = g.lt; hh < H; hh += g.nt) {
             C acc = zero;
             for (int l = 0; l < NL; ++l) {
                 const C v = L[(size_t)l * H + hh];
@@ -464,26 +506,27 @@ __device__ void readout_and_sample(const KParams& p, const Chain<R>& ch, int gid
             ch.rowdot[hh] = acc;
         }
     }
-    mx = group_max<R>(p, ch, gid, lt, mx);   // its barriers also publish part / rowdot
-    if (p.tpc >= H && lt < H) {
+    mx = group_max<R>(ch, g, mx);
+    g.sync();
+    if (g.nt >= H && g.lt < H) {
         C acc = zero;
-        for (int j = lt; j < p.tpc; j += H) {
+        for (int j = g.lt; j < g.nt; j += H) {
             acc.x += ch.part[j].x;
             acc.y += ch.part[j].y;
         }
-        ch.rowdot[lt] = acc;
+        ch.rowdot[g.lt] = acc;
     }
     const int eL = ch.misc[0];
     const int escale = eL + ch.Rexp[k];
     const bool target_block = p.mode == MODE_AMP && m == p.amp_layer && k == p.amp_block;
-    gsync(p, gid);
-    if (lt == 0) {
+    g.sync();
+    if (g.lt == 0) {
         const int e = scale_exp<R>(mx);
         ch.misc[1] = -e;
         ch.misc[0] = eL + e;
     }
     if (p.mode == MODE_AMP && !target_block) {
-        gsync(p, gid);
+        g.sync();
         return;
     }
 
@@ -494,7 +537,7 @@ __device__ void readout_and_sample(const KParams& p, const Chain<R>& ch, int gid
         int rmask = 0;
         for (int i = 0; i < nb; ++i) rmask |= 1 << ch.misc[2 + i];
         const int NT = 1 << nb, nother = S - nb;
-        for (int t = lt; t < NT; t += p.tpc) {
+        for (int t = g.lt; t < NT; t += g.nt) {
             int hbase = 0;
             for (int i = 0; i < nb; ++i) hbase |= ((t >> i) & 1) << ch.misc[2 + i];
             C acc = zero;
@@ -509,59 +552,74 @@ __device__ void readout_and_sample(const KParams& p, const Chain<R>& ch, int gid
             ch.T[t] = acc;
         }
     }
-    gsync(p, gid);
+    g.sync();
 
-    // 3) sequential resampling of the block's sites (FP64 conditionals)
-    if (lt == 0) {
+    // 3) sequential resampling of the block's sites by the first warp: lane 0
+    //    decides (FP64 conditional, the chain's precomputed Philox draw), the
+    //    lanes contract the resampled top away in parallel
+    const int wsz = g.nt < 32 ? g.nt : 32;
+    if (g.lt < wsz) {
+        const int lane = g.lt;
         C* cur = ch.T;
         int size = 1 << nb;
         for (int i = 0; i < nb; ++i) {
             const DevBlockSite st = sites[i];
             const int q = st.q;
-            int rest = 0;   // later sites keep their current bits (projection)
-            for (int j = i + 1; j < nb; ++j) rest |= ch.s[sites[j].q] << (j - i);
             const C A00 = mixel<R>(p, ch, m, q, 0, 0), A01 = mixel<R>(p, ch, m, q, 0, 1);
             const C A10 = mixel<R>(p, ch, m, q, 1, 0), A11 = mixel<R>(p, ch, m, q, 1, 1);
-            const C c0 = cur[rest], c1 = cur[rest | 1];
-            const C amp0 = cfma(A00, c0, cmul(A01, c1));
-            const C amp1 = cfma(A10, c0, cmul(A11, c1));
-            if (p.mode == MODE_AMP) {
-                if (i == p.amp_pos) {
-                    const C a = ch.s[q] ? amp1 : amp0;
-                    p.amp_out[2 * chain] = ldexp((double)a.x, escale);
-                    p.amp_out[2 * chain + 1] = ldexp((double)a.y, escale);
-                    break;
-                }
-            } else if (st.monomial) {
-                // deterministic move: the nonzero of column s[q] of A'_m
-                const C a0 = ch.s[q] ? A01 : A00;
-                ch.s[q] = (a0.x != (R)0 || a0.y != (R)0) ? 0 : 1;
-            } else {
-                const double a0r = amp0.x, a0i = amp0.y, a1r = amp1.x, a1i = amp1.y;
-                const double p0 = a0r * a0r + a0i * a0i, p1 = a1r * a1r + a1i * a1i;
-                const double Pt = p0 + p1;
-                if (p.trace) {
-                    double* tr = p.trace + ((size_t)chain * h.n_sampled + st.trace_row) * 4;
-                    tr[0] = ldexp(a0r, escale);
-                    tr[1] = ldexp(a0i, escale);
-                    tr[2] = ldexp(a1r, escale);
-                    tr[3] = ldexp(a1i, escale);
-                }
-                if (Pt > 0.0) {
-                    const double u = draw_u(p.seed, sample_id, (uint32_t)st.op_id, 0u);
-                    ch.s[q] = (u * Pt < p0) ? 0 : 1;
-                    if (fabs(u * Pt - p0) < 1e-6 * Pt) atomicAdd(&p.counters[CNT_NEAR], 1ull);
+            bool stop = false;
+            if (lane == 0) {
+                int rest = 0;   // later sites keep their current bits (projection)
+                for (int j = i + 1; j < nb; ++j) rest |= ch.s[sites[j].q] << (j - i);
+                const C c0 = cur[rest], c1 = cur[rest | 1];
+                const C amp0 = cfma(A00, c0, cmul(A01, c1));
+                const C amp1 = cfma(A10, c0, cmul(A11, c1));
+                if (p.mode == MODE_AMP) {
+                    if (i == p.amp_pos) {
+                        const C a = ch.s[q] ? amp1 : amp0;
+                        p.amp_out[2 * chain] = ldexp((double)a.x, escale);
+                        p.amp_out[2 * chain + 1] = ldexp((double)a.y, escale);
+                        stop = true;
+                    }
+                } else if (st.monomial) {
+                    // deterministic move: the nonzero of column s[q] of A'_m
+                    const C a0 = ch.s[q] ? A01 : A00;
+                    ch.s[q] = (a0.x != (R)0 || a0.y != (R)0) ? 0 : 1;
                 } else {
-                    atomicAdd(&p.counters[CNT_ZERO], 1ull);   // zero-mass block: stay (Sec. 2)
+                    const double a0r = amp0.x, a0i = amp0.y, a1r = amp1.x, a1i = amp1.y;
+                    const double p0 = a0r * a0r + a0i * a0i, p1 = a1r * a1r + a1i * a1i;
+                    const double Pt = p0 + p1;
+                    if (p.trace) {
+                        double* tr = p.trace + ((size_t)chain * h.n_sampled + st.trace_row) * 4;
+                        tr[0] = ldexp(a0r, escale);
+                        tr[1] = ldexp(a0i, escale);
+                        tr[2] = ldexp(a1r, escale);
+                        tr[3] = ldexp(a1i, escale);
+                    }
+                    if (Pt > 0.0) {
+                        const double u = ch.ud[st.trace_row];
+                        ch.s[q] = (u * Pt < p0) ? 0 : 1;
+                        if (fabs(u * Pt - p0) < 1e-6 * Pt) atomicAdd(&p.counters[CNT_NEAR], 1ull);
+                    } else {
+                        atomicAdd(&p.counters[CNT_ZERO], 1ull);   // zero-mass block: stay (Sec. 2)
+                    }
                 }
             }
+            stop = __shfl_sync(0xffffffffu, stop, 0);
+            __syncwarp();
+            if (stop) break;
             // contract this site's top with its mixer weight at the new bit
-            const C w0 = ch.s[q] ? A10 : A00, w1 = ch.s[q] ? A11 : A01;
+            // (ping-pong between the two halves of the T area)
+            const int sq = ch.s[q];
+            const C w0 = sq ? A10 : A00, w1 = sq ? A11 : A01;
             size >>= 1;
-            for (int r = 0; r < size; ++r) cur[r] = cfma(w0, cur[2 * r], cmul(w1, cur[2 * r + 1]));
+            C* nxt = cur == ch.T ? ch.T + (1 << h.max_block) : ch.T;
+            for (int r = lane; r < size; r += wsz) nxt[r] = cfma(w0, cur[2 * r], cmul(w1, cur[2 * r + 1]));
+            cur = nxt;
+            __syncwarp();
         }
     }
-    gsync(p, gid);
+    g.sync();
 }
 
 // ---------------------------------------------------------------- chain
@@ -573,6 +631,7 @@ __device__ void run_chain(const KParams& p, const Chain<R>& ch, int gid, int lt,
     const uint64_t sample_id = p.first + chain;
     const C one = mk<R>(1, 0);
     const DevBlockRange* BR = P_<DevBlockRange>(p, p.off.block_ranges);
+    const Grp G{lt, p.tpc, gid, p.tpc, false};
 
     for (int q = lt; q < n; q += p.tpc) {
         ch.x[q] = 0;
@@ -584,17 +643,17 @@ __device__ void run_chain(const KParams& p, const Chain<R>& ch, int gid, int lt,
     }
     if (h.has_segfac)
         for (int i = lt; i < n * (P + 1) * 2; i += p.tpc) ch.segfac[i] = one;
-    gsync(p, gid);
-
-    // Layer 0 acts on |0^n>: the prefix state is a product state, so the
-    // conditional of qubit q is |<y|A_0|0>|^2 normalised (same draw rule).
-    if (p.mode == MODE_SAMPLE && lt == 0) {
-        const int32_t* order = P_<int32_t>(p, p.off.mix0_order);
+    if (p.mode == MODE_SAMPLE) {
+        // the UpdateState draws of every sampled gate (they depend only on
+        // (seed, sample, op id), so they are drawn up front in parallel)
+        const int32_t* rop = P_<int32_t>(p, p.off.row_opid);
+        for (int r = lt; r < h.n_sampled; r += p.tpc) ch.ud[r] = draw_u(p.seed, sample_id, (uint32_t)rop[r], 0u);
+        // Layer 0 acts on |0^n>: the prefix state is a product state, so the
+        // conditional of qubit q is |<y|A_0|0>|^2 normalised (same draw rule).
         const int32_t* opid = P_<int32_t>(p, p.off.mix0_opid);
         const int8_t* mono = P_<int8_t>(p, p.off.mix_mono);
         const double* md = P_<double>(p, p.off.mix_d);
-        for (int t = 0; t < n; ++t) {
-            const int q = order[t];
+        for (int q = lt; q < n; q += p.tpc) {
             const double* A = md + (size_t)q * 8;
             if (mono[q]) {
                 ch.s[q] = (A[0] != 0.0 || A[1] != 0.0) ? 0 : 1;
@@ -608,7 +667,7 @@ __device__ void run_chain(const KParams& p, const Chain<R>& ch, int gid, int lt,
             if (fabs(u * Pt - p0) < 1e-6 * Pt) atomicAdd(&p.counters[CNT_NEAR], 1ull);
         }
     }
-    gsync(p, gid);
+    G.sync();
 
     const int mhi = p.mode == MODE_AMP ? p.amp_layer : P;
     for (int m = 1; m <= mhi; ++m) {
@@ -617,16 +676,16 @@ __device__ void run_chain(const KParams& p, const Chain<R>& ch, int gid, int lt,
         if (lt == 0 && (h.has_segfac || h.has_frame)) {
             const int32_t* cr = P_<int32_t>(p, p.off.cost_ranges);
             const DevCostItem* items = P_<DevCostItem>(p, p.off.cost_items);
-            const DevCostGate* G = P_<DevCostGate>(p, p.off.cost_gates);
+            const DevCostGate* CG = P_<DevCostGate>(p, p.off.cost_gates);
             for (int it = cr[m]; it < cr[m + 1]; ++it) {
                 const DevCostItem ci = items[it];
                 if (ci.kind == CI_GATE2) {
-                    ch.gframe[ci.idx] = (uint8_t)(ch.x[G[ci.idx].q0] | (ch.x[G[ci.idx].q1] << 1));
+                    ch.gframe[ci.idx] = (uint8_t)(ch.x[CG[ci.idx].q0] | (ch.x[CG[ci.idx].q1] << 1));
                 } else if (ci.kind == CI_GATE1) {
-                    const int q = G[ci.idx].q0, xb = ch.x[q];
+                    const int q = CG[ci.idx].q0, xb = ch.x[q];
                     C* sf = ch.segfac + ((size_t)q * (P + 1) + (m - 1)) * 2;
-                    sf[0] = cmul(sf[0], mk<R>((R)G[ci.idx].d[2 * xb], (R)G[ci.idx].d[2 * xb + 1]));
-                    sf[1] = cmul(sf[1], mk<R>((R)G[ci.idx].d[2 * (1 ^ xb)], (R)G[ci.idx].d[2 * (1 ^ xb) + 1]));
+                    sf[0] = cmul(sf[0], mk<R>((R)CG[ci.idx].d[2 * xb], (R)CG[ci.idx].d[2 * xb + 1]));
+                    sf[1] = cmul(sf[1], mk<R>((R)CG[ci.idx].d[2 * (1 ^ xb)], (R)CG[ci.idx].d[2 * (1 ^ xb) + 1]));
                 } else if (p.mode == MODE_SAMPLE) {
                     apply_channel<R>(p, ch, P_<DevChannel>(p, p.off.channels)[ci.idx], P_<double>(p, p.off.cum),
                                      P_<DevKrausFactor>(p, p.off.factors), sample_id, m - 1);
@@ -635,55 +694,66 @@ __device__ void run_chain(const KParams& p, const Chain<R>& ch, int gid, int lt,
             if (h.has_frame)
                 for (int q = 0; q < n; ++q) ch.xmix[m * n + q] = ch.x[q];
         }
-        gsync(p, gid);
+        G.sync();
         if (p.mode == MODE_AMP && m < p.amp_layer) continue;
 
         const int Wl = S * (m - 1), W = S * m;
         const int NL = 1 << Wl, N = 1 << W;
         const int kstop = p.mode == MODE_AMP ? p.amp_block : 0;   // R_k needed for k >= kstop
+        // small tensors run on the first warp only
+        const int w32 = p.tpc < 32 ? p.tpc : 32;
+        const Grp GB{lt, NL <= 1024 ? w32 : p.tpc, gid, p.tpc, NL <= 1024 && p.tpc > 32};
+        const Grp GF{lt, N <= 1024 ? w32 : p.tpc, gid, p.tpc, N <= 1024 && p.tpc > 32};
 
         // backward sweep: R_{K-1} = 1, R_{k-1} from R_k by block k's reversed program
-        C* RK = ch.Rt + (size_t)(K - 1) * NL;
-        for (int i = lt; i < NL; i += p.tpc) RK[i] = one;
-        if (lt == 0) ch.Rexp[K - 1] = 0;
-        for (int k = K - 1; k > kstop; --k) {
-            const DevBlockRange br = BR[(size_t)m * K + k];
-            const C* src = ch.Rt + (size_t)k * NL;
-            C* dst = ch.Rt + (size_t)(k - 1) * NL;
-            build_tables<R>(p, ch, lt, br.bwd_begin, br.bwd_end, 0);
-            gsync(p, gid);   // tables ready, previous environment complete
-            for (int i = lt; i < NL; i += p.tpc) dst[i] = src[i];
-            gsync(p, gid);
-            run_fused<R>(p, ch, gid, lt, br.bwd_begin, br.bwd_end, dst, Wl);
-            R mx = 0;
-            for (int i = lt; i < NL; i += p.tpc) mx = rmax(mx, rmax(rabs(dst[i].x), rabs(dst[i].y)));
-            mx = group_max<R>(p, ch, gid, lt, mx);
-            const int e = scale_exp<R>(mx);
-            if (e != 0)
-                for (int i = lt; i < NL; i += p.tpc) {
-                    dst[i].x = scl(dst[i].x, -e);
-                    dst[i].y = scl(dst[i].y, -e);
-                }
-            if (lt == 0) ch.Rexp[k - 1] = ch.Rexp[k] + e;
+        if (lt < GB.nt) {
+            C* RK = ch.Rt + (size_t)(K - 1) * NL;
+            for (int i = lt; i < NL; i += GB.nt) RK[i] = one;
+            if (lt == 0) ch.Rexp[K - 1] = 0;
+            for (int k = K - 1; k > kstop; --k) {
+                const DevBlockRange br = BR[(size_t)m * K + k];
+                const C* src = ch.Rt + (size_t)k * NL;
+                C* dst = ch.Rt + (size_t)(k - 1) * NL;
+                build_tables<R>(p, ch, GB, br.bwd_st, br.bwd_nst, 0);
+                GB.sync();   // tables ready, previous environment complete
+                for (int i = lt; i < NL; i += GB.nt) dst[i] = src[i];
+                GB.sync();
+                run_passes<R>(p, ch, GB, br.bwd_begin, br.bwd_end, br.bwd_st, dst, Wl);
+                R mx = 0;
+                for (int i = lt; i < NL; i += GB.nt) mx = rmax(mx, rmax(rabs(dst[i].x), rabs(dst[i].y)));
+                mx = group_max<R>(ch, GB, mx);
+                const int e = scale_exp<R>(mx);
+                if (e != 0)
+                    for (int i = lt; i < NL; i += GB.nt) {
+                        dst[i].x = scl(dst[i].x, -e);
+                        dst[i].y = scl(dst[i].y, -e);
+                    }
+                if (lt == 0) ch.Rexp[k - 1] = ch.Rexp[k] + e;
+                GB.sync();
+            }
         }
+        G.sync();
 
         // forward sweep with a readout after every block
-        for (int i = lt; i < N; i += p.tpc) ch.L[i] = mk<R>(i == 0 ? 1 : 0, 0);
-        if (lt == 0) {
-            ch.misc[0] = 0;
-            ch.misc[1] = 0;
+        if (lt < GF.nt) {
+            for (int i = lt; i < N; i += GF.nt) ch.L[i] = mk<R>(i == 0 ? 1 : 0, 0);
+            if (lt == 0) {
+                ch.misc[0] = 0;
+                ch.misc[1] = 0;
+            }
+            GF.sync();
+            const int kend = p.mode == MODE_AMP ? p.amp_block : K - 1;
+            for (int k = 0; k <= kend; ++k) {
+                const DevBlockRange br = BR[(size_t)m * K + k];
+                const int pend = ch.misc[1];
+                build_tables<R>(p, ch, GF, br.fwd_st, br.fwd_nst, pend);
+                build_fslot<R>(p, ch, GF, m, br);
+                GF.sync();
+                run_passes<R>(p, ch, GF, br.fwd_begin, br.fwd_end, br.fwd_st, ch.L, W);
+                readout_and_sample<R>(p, ch, GF, m, k, br, chain);
+            }
         }
-        gsync(p, gid);
-        const int kend = p.mode == MODE_AMP ? p.amp_block : K - 1;
-        for (int k = 0; k <= kend; ++k) {
-            const DevBlockRange br = BR[(size_t)m * K + k];
-            const int pend = ch.misc[1];
-            build_tables<R>(p, ch, lt, br.fwd_begin, br.fwd_end, pend);
-            build_fslot<R>(p, ch, lt, m, br);
-            gsync(p, gid);
-            run_fused<R>(p, ch, gid, lt, br.fwd_begin, br.fwd_end, ch.L, W);
-            readout_and_sample<R>(p, ch, gid, lt, m, k, br, sample_id, chain);
-        }
+        G.sync();
     }
     if (p.mode == MODE_AMP) return;
 
@@ -696,18 +766,18 @@ __device__ void run_chain(const KParams& p, const Chain<R>& ch, int gid, int lt,
                 apply_channel<R>(p, ch, P_<DevChannel>(p, p.off.channels)[items[it].idx], P_<double>(p, p.off.cum),
                                  P_<DevKrausFactor>(p, p.off.factors), sample_id, P);
     }
-    gsync(p, gid);
+    G.sync();
     // sample = s XOR x (Alg. 2), packed 64 qubits per word
     for (int w = lt; w < h.words; w += p.tpc) {
         uint64_t v = 0;
         for (int b = 0; b < 64 && w * 64 + b < n; ++b) v |= (uint64_t)(ch.s[w * 64 + b] ^ ch.x[w * 64 + b]) << b;
         p.out_bits[chain * h.words + w] = v;
     }
-    gsync(p, gid);
+    G.sync();
 }
 
 template <typename R>
-__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 3 : 2) pw_chain_kernel(const KParams p) {
+__global__ void __launch_bounds__(256, 2) pw_chain_kernel(const KParams p) {
     using C = typename CT<R>::T;
     extern __shared__ __align__(16) unsigned char smem[];
     const int gid = threadIdx.x / p.tpc;
@@ -720,6 +790,8 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 3 : 2) pw_chain_kernel(c
     ch.rowdot = reinterpret_cast<C*>(g + p.sm.rowdot);
     ch.T = reinterpret_cast<C*>(g + p.sm.T);
     ch.tab = reinterpret_cast<C*>(g + p.sm.tab);
+    ch.stg = reinterpret_cast<DevStage*>(g + p.sm.stg);
+    ch.ud = reinterpret_cast<double*>(g + p.sm.ud);
     ch.part = reinterpret_cast<C*>(g + p.sm.part);
     ch.fslot = reinterpret_cast<C*>(g + p.sm.fslot);
     ch.red = reinterpret_cast<R*>(g + p.sm.red);
@@ -752,6 +824,8 @@ std::vector<unsigned char> make_blob(const HostPlan& hp, DevPlanOffsets& o) {
     std::vector<unsigned char> blob;
     put(blob, o.micro, hp.micro);
     put(blob, o.fused, hp.fused);
+    put(blob, o.stages, hp.stages);
+    put(blob, o.row_opid, hp.row_opid);
     put(blob, o.gate_refs, hp.gate_refs);
     put(blob, o.cost_gates, hp.cost_gates);
     put(blob, o.cost_items, hp.cost_items);
@@ -816,6 +890,7 @@ template <typename R> int launch(pw_plan* plan, KParams& kp, cudaStream_t st, ui
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
     int dev = plan->device, nsm = 0, occ = 0;
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, smem);
     if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
     occ = std::max(occ, 1);

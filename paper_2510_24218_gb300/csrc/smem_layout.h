@@ -9,7 +9,7 @@
 namespace pw {
 
 struct SmemLayout {
-    int L, R, Rexp, rowdot, T, tab, part, fslot, red, s, x, xmix, gframe, segfac, misc, group_bytes;
+    int L, R, Rexp, rowdot, T, tab, stg, ud, part, fslot, red, s, x, xmix, gframe, segfac, misc, group_bytes;
 };
 
 inline size_t align16(size_t v) { return (v + 15) & ~(size_t)15; }
@@ -29,9 +29,11 @@ inline SmemLayout make_layout(const HostPlan& hp, size_t csz) {
     L.R = take((size_t)K * (csz << (S * (P - 1))));    // right environments
     L.Rexp = take(sizeof(int) * K);
     L.rowdot = take(csz << S);
-    L.T = take(csz << h.max_block);
+    L.T = take(csz << (h.max_block + 1));   // two halves (ping-pong)
     L.tab = take(csz * (size_t)std::max(1, h.max_tab));
-    L.part = take(csz * 256);
+    L.stg = take(sizeof(DevStage) * (size_t)std::max(1, h.max_stages));
+    L.ud = take(sizeof(double) * (size_t)std::max(1, h.n_sampled));
+    L.part = take(csz * (size_t)std::max(32, hp.threads_per_chain));
     L.fslot = take(csz * 2 * S);
     L.red = take((csz / 2) * 32);
     L.s = take(h.n);
@@ -44,11 +46,22 @@ inline SmemLayout make_layout(const HostPlan& hp, size_t csz) {
     return L;
 }
 
-// Chains per CTA: at most 256 threads per CTA (the kernel's launch bounds),
-// and enough shared memory left for 3 CTAs per SM when possible.
+// Chains per CTA, chosen to maximise the chains resident on one SM: 228 KB
+// of shared memory per SM (1 KB reserved per CTA), at most 512 resident
+// threads (128 registers each, the kernel's launch bounds) and 256 threads per
+// CTA.
 inline int groups_per_cta(int tpc, int group_bytes) {
-    const int maxsm = 227 * 1024;
-    return std::max(1, std::min({8, 256 / tpc, (maxsm / 3) / std::max(1, group_bytes)}));
+    int best = 1, best_chains = 0;
+    for (int g = 1; g <= 8 && g * tpc <= 256; ++g) {
+        const int by_smem = (228 * 1024) / (g * group_bytes + 1024);
+        const int by_threads = 512 / (g * tpc);
+        const int ctas = std::min(by_smem, by_threads);
+        if (ctas * g > best_chains) {
+            best_chains = ctas * g;
+            best = g;
+        }
+    }
+    return best;
 }
 
 }  // namespace pw
