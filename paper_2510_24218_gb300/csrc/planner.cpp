@@ -381,6 +381,176 @@ int fuse_range(HostPlan& hp, int b, int e, int* nst_out) {
     return tab;
 }
 
+// ---------------------------------------------------------------------------
+// Host precompute of the tables of noiseless plans. Without channels the only
+// chain-dependent inputs of a stage's table are the current bits of at most a
+// few qubits (the top weight A_m[s_u][.] of an eliminated site, or a fixed top
+// segment in the backward sweep); every variant of those bits is evaluated
+// here in FP64 once, and the kernel only gathers. Scalar factors (RC_CONST_EDGES)
+// are left out: they only change the overall scale of the amplitudes.
+struct HostEval {
+    const HostPlan& hp;
+    std::vector<cd> segfac;   // [n][P+1][2] static one-qubit diagonal factors
+    int n, P;
+    const int* sq;            // qubit -> position in deps, -1 if not a dependency
+    int var;                  // variant bits
+
+    int sbit(int q) const { return sq[q] >= 0 ? (var >> sq[q]) & 1 : 0; }
+    cd mix(int m, int q, int o, int i) const {
+        const double* d = hp.mix_d.data() + ((size_t)m * n + q) * 8 + 2 * ((o << 1) | i);
+        return cd(d[0], d[1]);
+    }
+    cd gate(int g, int a0, int a1) const {
+        const DevCostGate& G = hp.cost_gates[g];
+        int idx = a0 | (a1 << 1);
+        return cd(G.d[2 * idx], G.d[2 * idx + 1]);
+    }
+    cd gpair(int g, int qa, int va, int vb) const {
+        return hp.cost_gates[g].q0 == qa ? gate(g, va, vb) : gate(g, vb, va);
+    }
+    cd entry(const DevMicroOp& o, int e) const {
+        const int32_t* gref = hp.gate_refs.data();
+        switch (o.recipe) {
+            case RC_EXPAND: return (e & 1) == 0 ? 1.0 : 0.0;
+            case RC_SUMOUT1: return (e >> 1) == 0 ? 1.0 : 0.0;
+            case RC_SUMOUT_MIX: return (e >> 1) == 0 ? mix(o.layer, o.qa, sbit(o.qa), e & 1) : cd(0.0);
+            case RC_REPLACE: {
+                int aout = e >> 1, ain = e & 1;
+                cd v = o.layer >= 0 ? mix(o.layer, o.qa, sbit(o.qa), ain) : cd(1.0);
+                for (int i = 0; i < o.gcount; ++i) v *= gpair(gref[o.glist + i], o.qa, ain, aout);
+                return v;
+            }
+            case RC_BREPLACE: {
+                int aout = e >> 1, ain = e & 1;
+                cd v = 1.0;
+                for (int i = 0; i < o.gcount; ++i) v *= gpair(gref[o.glist + i], o.qa, aout, ain);
+                return v;
+            }
+            case RC_EDGE: {
+                cd v = 1.0;
+                for (int i = 0; i < o.gcount; ++i) v *= gpair(gref[o.glist + i], o.qa, e & 1, (e >> 1) & 1);
+                return v;
+            }
+            case RC_SITE: {
+                int q = o.qa, nseg = o.layer, z[8];
+                for (int l = 0; l < nseg; ++l) z[l] = (e >> l) & 1;
+                if (o.fixed_top) z[nseg - 1] = sbit(q);
+                cd v = mix(0, q, z[0], 0);
+                for (int l = 1; l < nseg; ++l) v *= mix(l, q, z[l], z[l - 1]);
+                for (int l = 0; l < nseg; ++l) v *= segfac[((size_t)q * (P + 1) + l) * 2 + z[l]];
+                return v;
+            }
+            default: return 1.0;   // RC_CONST_EDGES: scale only
+        }
+    }
+};
+
+void push_var(HostPlan& hp, cd v) {
+    hp.vtab_d.push_back(v.real());
+    hp.vtab_d.push_back(v.imag());
+    hp.vtab_f.push_back((float)v.real());
+    hp.vtab_f.push_back((float)v.imag());
+}
+
+void precompute_tables(HostPlan& hp) {
+    const int n = hp.hdr.n, P = hp.hdr.P;
+    HostEval ev{hp, std::vector<cd>((size_t)n * (P + 1) * 2, cd(1.0)), n, P, nullptr, 0};
+    for (int m = 1; m <= P; ++m)
+        for (int it = hp.cost_ranges[m]; it < hp.cost_ranges[m + 1]; ++it)
+            if (hp.cost_items[it].kind == CI_GATE1) {
+                const DevCostGate& G = hp.cost_gates[hp.cost_items[it].idx];
+                for (int b = 0; b < 2; ++b) ev.segfac[((size_t)G.q0 * (P + 1) + (m - 1)) * 2 + b] *= cd(G.d[2 * b], G.d[2 * b + 1]);
+            }
+    std::vector<int> sq(n, -1);
+    ev.sq = sq.data();
+    auto deps_of = [&](const DevMicroOp& o, std::vector<int>& deps) {
+        bool dep = o.recipe == RC_SUMOUT_MIX || (o.recipe == RC_REPLACE && o.layer >= 0) ||
+                   (o.recipe == RC_SITE && o.fixed_top);
+        if (dep && std::find(deps.begin(), deps.end(), (int)o.qa) == deps.end()) deps.push_back(o.qa);
+    };
+    for (DevStage& st : hp.stages) {
+        std::vector<int> deps;
+        for (int k = st.op_begin; k < st.op_end; ++k) deps_of(hp.micro[k], deps);
+        if (deps.size() > 4) {
+            st.ndep = 0xFF;
+            continue;
+        }
+        st.ndep = (uint8_t)deps.size();
+        for (size_t j = 0; j < deps.size(); ++j) {
+            st.dep[j] = (int16_t)deps[j];
+            sq[deps[j]] = (int)j;
+        }
+        st.var_off = (int32_t)(hp.vtab_d.size() / 2);
+        const int size = st.type == ST_MAT ? 4 : (1 << st.arg);
+        for (int v = 0; v < (1 << deps.size()); ++v) {
+            ev.var = v;
+            for (int e = 0; e < size; ++e) {
+                cd val;
+                if (st.type == ST_MAT) {
+                    val = ev.entry(hp.micro[st.op_begin], e);
+                } else {
+                    val = 1.0;
+                    for (int k = st.op_begin; k < st.op_end; ++k) {
+                        const DevMicroOp& o = hp.micro[k];
+                        int loc = 0;
+                        for (int j = 0; j < o.nbits; ++j) loc |= ((e >> o.fpos[j]) & 1) << j;
+                        val *= ev.entry(o, loc);
+                    }
+                }
+                push_var(hp, val);
+            }
+        }
+        for (int q : deps) sq[q] = -1;
+    }
+    // readout factors of the live slots (layer of each block range)
+    for (int m = 1; m <= P; ++m)
+        for (int k = 0; k < hp.hdr.K; ++k) {
+            const DevBlockRange& br = hp.block_ranges[(size_t)m * hp.hdr.K + k];
+            for (int j = br.live_begin; j < br.live_end; ++j) {
+                DevLiveSlot& sl = hp.live_slots[j];
+                if (sl.q < 0) {
+                    sl.ndep = 0;
+                    sl.var_off = (int32_t)(hp.vtab_d.size() / 2);
+                    push_var(hp, 1.0);
+                    push_var(hp, 0.0);
+                    continue;
+                }
+                std::vector<int> deps;
+                for (int i = 0; i < sl.dcount; ++i) {
+                    const DevCostGate& G = hp.cost_gates[hp.gate_refs[sl.dlist + i]];
+                    int w = G.q0 == sl.q ? G.q1 : G.q0;
+                    if (std::find(deps.begin(), deps.end(), w) == deps.end()) deps.push_back(w);
+                }
+                if (sl.role < 0) deps.push_back(sl.q);
+                if (deps.size() > 5) {
+                    sl.ndep = 0xFF;
+                    continue;
+                }
+                sl.ndep = (int16_t)deps.size();
+                for (size_t i = 0; i < deps.size(); ++i) {
+                    sl.dep[i] = (int16_t)deps[i];
+                    sq[deps[i]] = (int)i;
+                }
+                sl.var_off = (int32_t)(hp.vtab_d.size() / 2);
+                for (int v = 0; v < (1 << deps.size()); ++v) {
+                    ev.var = v;
+                    for (int top = 0; top < 2; ++top) {
+                        cd f = 1.0;
+                        for (int i = 0; i < sl.dcount; ++i) {
+                            const int g = hp.gate_refs[sl.dlist + i];
+                            const DevCostGate& G = hp.cost_gates[g];
+                            int w = G.q0 == sl.q ? G.q1 : G.q0;
+                            f *= ev.gpair(g, sl.q, top, ev.sbit(w));
+                        }
+                        if (sl.role < 0) f *= ev.mix(m, sl.q, ev.sbit(sl.q), top);
+                        push_var(hp, f);
+                    }
+                }
+                for (int q : deps) sq[q] = -1;
+            }
+        }
+}
+
 }  // namespace
 
 int build_plan(const pw_circuit* c, const pw_plan_opts& opts, HostPlan& hp) {
@@ -777,6 +947,10 @@ int build_plan(const pw_circuit* c, const pw_plan_opts& opts, HostPlan& hp) {
     hp.hdr.has_segfac = has_segfac ? 1 : 0;
     hp.hdr.has_frame = has_frame ? 1 : 0;
     hp.hdr.words = (n + 63) / 64;
+    // tables: precomputed for noiseless plans, built per chain otherwise
+    for (auto& st : hp.stages) st.ndep = 0xFF;
+    for (auto& sl : hp.live_slots) sl.ndep = 0xFF;
+    if (!has_frame) precompute_tables(hp);
     hp.hdr.max_tab = 1;
     hp.hdr.max_stages = 1;
     for (const auto& br : hp.block_ranges) {

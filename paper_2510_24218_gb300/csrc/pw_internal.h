@@ -86,9 +86,11 @@ struct DevStage {
     uint8_t arg;         // ST_MAT: index into tbits; ST_DIAG: number of diagonal bits
     uint8_t dbits[5];    // ST_DIAG: index bits of the table, entry bit j <- index bit dbits[j]
     uint8_t tpos[4];     // ST_DIAG: position in dbits of tile bit k, 0xFF if absent
-    uint8_t pad;
+    uint8_t ndep;        // precomputed table: chain bits it depends on (0..4); 0xFF: built at run time
     int32_t op_begin, op_end;   // constituent micro-ops
     int32_t tab_off;            // complex entries from the start of the block's table area
+    int16_t dep[4];             // qubits whose current bits select the variant
+    int32_t var_off;            // first entry of variant 0 in the precomputed tables
 };
 struct DevFused {
     uint8_t ntb;         // tile bits (0..4)
@@ -149,7 +151,9 @@ struct DevLiveSlot {
     int16_t role;        // index of the site inside the block, or -1 (done earlier)
     int32_t dlist;       // gate refs of the cross edges to unabsorbed qubits
     int32_t dcount;
-    int32_t pad;
+    int16_t ndep;        // precomputed factor: chain bits it depends on; 0xFF: run time
+    int16_t dep[5];
+    int32_t var_off;     // 2 entries per variant in the precomputed tables
 };
 
 // Per (layer m >= 1, block k) ranges.
@@ -181,7 +185,7 @@ struct DevPlanHeader {
 
 // Offsets (in bytes) of the arrays inside the device blob.
 struct DevPlanOffsets {
-    int64_t micro, fused, stages, row_opid, gate_refs, cost_gates, cost_items, cost_ranges, channels, cum, factors;
+    int64_t micro, fused, stages, row_opid, vtab_f, vtab_d, gate_refs, cost_gates, cost_items, cost_ranges, channels, cum, factors;
     int64_t mix_d, mix_f, mix0_order, mix0_opid, mix_mono;
     int64_t block_ranges, block_sites, live_slots;
 };
@@ -202,6 +206,8 @@ struct HostPlan {
     std::vector<DevFused> fused;
     std::vector<DevStage> stages;
     std::vector<int32_t> row_opid;        // op id of each sampled gate (trace row)
+    std::vector<float> vtab_f;            // precomputed stage / slot tables (complex), FP32
+    std::vector<double> vtab_d;           // the same in FP64
     std::vector<int32_t> gate_refs;
     std::vector<DevCostGate> cost_gates;
     std::vector<DevCostItem> cost_items;

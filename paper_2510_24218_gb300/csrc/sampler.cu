@@ -243,36 +243,60 @@ __device__ typename CT<R>::T build_entry(const KParams& p, const Chain<R>& ch, c
     return one;
 }
 
-// Tables and stage descriptors of one block program (stages [sb, sb + ns)).
-// pend_exp (a power of two) is folded into the program's first stage.
+// Tables and stage descriptors of one block program (stages [sb, sb + ns),
+// ntab entries). Every entry is produced by one thread: precomputed stages
+// select the variant of their dependency bits, the others are built from the
+// chain's state. pend_exp (a power of two) is folded into the first stage;
+// with exact = false the scalar-only factors (RC_CONST_EDGES), which change
+// the amplitudes' overall scale but no conditional, are skipped.
 template <typename R>
-__device__ void build_tables(const KParams& p, const Chain<R>& ch, const Grp& g, int sb, int ns, int pend_exp) {
+__device__ void build_tables(const KParams& p, const Chain<R>& ch, const Grp& g, int sb, int ns, int ntab,
+                             int pend_exp, bool exact) {
     using C = typename CT<R>::T;
     const DevStage* ST = P_<DevStage>(p, p.off.stages) + sb;
     const DevMicroOp* ops = P_<DevMicroOp>(p, p.off.micro);
     for (int i = g.lt; i < ns; i += g.nt) ch.stg[i] = ST[i];
-    for (int si = 0; si < ns; ++si) {
+    for (int ef = g.lt; ef < ntab; ef += g.nt) {
+        int si = 0;
+        while (si + 1 < ns && ST[si + 1].tab_off <= ef) ++si;
         const DevStage st = ST[si];
-        const int ne = st.type == ST_MAT ? 4 : (1 << st.arg);
-        for (int e = g.lt; e < ne; e += g.nt) {
-            C v;
-            if (st.type == ST_MAT) {
-                v = build_entry<R>(p, ch, ops[st.op_begin], e);
+        const int e = ef - st.tab_off;
+        C v;
+        if (st.ndep != 0xFF) {
+            int var = 0;
+            for (int j = 0; j < st.ndep; ++j) var |= ch.s[st.dep[j]] << j;
+            const int size = st.type == ST_MAT ? 4 : (1 << st.arg);
+            const size_t at = (size_t)st.var_off + (size_t)var * size + e;
+            if constexpr (sizeof(R) == 4) {
+                v = *reinterpret_cast<const float2*>(P_<float>(p, p.off.vtab_f) + 2 * at);
             } else {
-                v = mk<R>(1, 0);
-                for (int k = st.op_begin; k < st.op_end; ++k) {
-                    const DevMicroOp o = ops[k];
-                    int loc = 0;
-                    for (int j = 0; j < o.nbits; ++j) loc |= ((e >> o.fpos[j]) & 1) << j;
-                    v = cmul(v, build_entry<R>(p, ch, o, loc));
+                v = *reinterpret_cast<const double2*>(P_<double>(p, p.off.vtab_d) + 2 * at);
+            }
+            if (exact && si == 0) {
+                // scale factors left out of the precomputed tables of this program
+                for (int s2 = 0; s2 < ns; ++s2) {
+                    if (ST[s2].ndep == 0xFF) continue;
+                    for (int k = ST[s2].op_begin; k < ST[s2].op_end; ++k)
+                        if (ops[k].recipe == RC_CONST_EDGES) v = cmul(v, build_entry<R>(p, ch, ops[k], 0));
                 }
             }
-            if (si == 0 && pend_exp != 0) {
-                v.x = scl(v.x, pend_exp);
-                v.y = scl(v.y, pend_exp);
+        } else if (st.type == ST_MAT) {
+            v = build_entry<R>(p, ch, ops[st.op_begin], e);
+        } else {
+            v = mk<R>(1, 0);
+            for (int k = st.op_begin; k < st.op_end; ++k) {
+                const DevMicroOp o = ops[k];
+                if (!exact && o.recipe == RC_CONST_EDGES) continue;
+                int loc = 0;
+                for (int j = 0; j < o.nbits; ++j) loc |= ((e >> o.fpos[j]) & 1) << j;
+                v = cmul(v, build_entry<R>(p, ch, o, loc));
             }
-            ch.tab[st.tab_off + e] = v;
         }
+        if (si == 0 && pend_exp != 0) {
+            v.x = scl(v.x, pend_exp);
+            v.y = scl(v.y, pend_exp);
+        }
+        ch.tab[ef] = v;
     }
 }
 
@@ -447,6 +471,22 @@ __device__ void build_fslot(const KParams& p, const Chain<R>& ch, const Grp& g, 
     const DevCostGate* G = P_<DevCostGate>(p, p.off.cost_gates);
     for (int j = g.lt; j < p.hdr.S; j += g.nt) {
         const DevLiveSlot sl = live[j];
+        if (sl.q >= 0 && sl.role >= 0) ch.misc[2 + sl.role] = j;
+        if (sl.ndep != 0xFF) {
+            int var = 0;
+            for (int d = 0; d < sl.ndep; ++d) var |= ch.s[sl.dep[d]] << d;
+            const size_t at = (size_t)sl.var_off + 2 * (size_t)var;
+            if constexpr (sizeof(R) == 4) {
+                const float4 v = *reinterpret_cast<const float4*>(P_<float>(p, p.off.vtab_f) + 2 * at);
+                ch.fslot[2 * j] = mk<R>(v.x, v.y);
+                ch.fslot[2 * j + 1] = mk<R>(v.z, v.w);
+            } else {
+                const double* d = P_<double>(p, p.off.vtab_d) + 2 * at;
+                ch.fslot[2 * j] = mk<R>(d[0], d[1]);
+                ch.fslot[2 * j + 1] = mk<R>(d[2], d[3]);
+            }
+            continue;
+        }
         C f0 = mk<R>(1, 0), f1 = mk<R>(0, 0);
         if (sl.q >= 0) {
             f1 = mk<R>(1, 0);
@@ -632,6 +672,8 @@ __device__ void run_chain(const KParams& p, const Chain<R>& ch, int gid, int lt,
     const C one = mk<R>(1, 0);
     const DevBlockRange* BR = P_<DevBlockRange>(p, p.off.block_ranges);
     const Grp G{lt, p.tpc, gid, p.tpc, false};
+    // amplitudes leave the kernel (trace, amplitude mode): keep every scale factor
+    const bool exact = p.mode == MODE_AMP || p.trace != nullptr;
 
     for (int q = lt; q < n; q += p.tpc) {
         ch.x[q] = 0;
@@ -705,8 +747,17 @@ __device__ void run_chain(const KParams& p, const Chain<R>& ch, int gid, int lt,
         const Grp GB{lt, NL <= 1024 ? w32 : p.tpc, gid, p.tpc, NL <= 1024 && p.tpc > 32};
         const Grp GF{lt, N <= 1024 ? w32 : p.tpc, gid, p.tpc, N <= 1024 && p.tpc > 32};
 
-        // backward sweep: R_{K-1} = 1, R_{k-1} from R_k by block k's reversed program
-        if (lt < GB.nt) {
+        // backward sweep: R_{K-1} = 1, R_{k-1} from R_k by block k's reversed
+        // program. For m = 1 the environments are scalars (no summed segment on
+        // the right), needed only for the exact scale.
+        const bool skip_bwd = m == 1 && !exact;
+        if (skip_bwd && lt < GB.nt) {
+            for (int k = lt; k < K; k += GB.nt) {
+                ch.Rt[k] = one;
+                ch.Rexp[k] = 0;
+            }
+        }
+        if (!skip_bwd && lt < GB.nt) {
             C* RK = ch.Rt + (size_t)(K - 1) * NL;
             for (int i = lt; i < NL; i += GB.nt) RK[i] = one;
             if (lt == 0) ch.Rexp[K - 1] = 0;
@@ -714,7 +765,7 @@ __device__ void run_chain(const KParams& p, const Chain<R>& ch, int gid, int lt,
                 const DevBlockRange br = BR[(size_t)m * K + k];
                 const C* src = ch.Rt + (size_t)k * NL;
                 C* dst = ch.Rt + (size_t)(k - 1) * NL;
-                build_tables<R>(p, ch, GB, br.bwd_st, br.bwd_nst, 0);
+                build_tables<R>(p, ch, GB, br.bwd_st, br.bwd_nst, br.bwd_tab, 0, exact);
                 GB.sync();   // tables ready, previous environment complete
                 for (int i = lt; i < NL; i += GB.nt) dst[i] = src[i];
                 GB.sync();
@@ -746,7 +797,7 @@ __device__ void run_chain(const KParams& p, const Chain<R>& ch, int gid, int lt,
             for (int k = 0; k <= kend; ++k) {
                 const DevBlockRange br = BR[(size_t)m * K + k];
                 const int pend = ch.misc[1];
-                build_tables<R>(p, ch, GF, br.fwd_st, br.fwd_nst, pend);
+                build_tables<R>(p, ch, GF, br.fwd_st, br.fwd_nst, br.fwd_tab, pend, exact);
                 build_fslot<R>(p, ch, GF, m, br);
                 GF.sync();
                 run_passes<R>(p, ch, GF, br.fwd_begin, br.fwd_end, br.fwd_st, ch.L, W);
@@ -826,6 +877,8 @@ std::vector<unsigned char> make_blob(const HostPlan& hp, DevPlanOffsets& o) {
     put(blob, o.fused, hp.fused);
     put(blob, o.stages, hp.stages);
     put(blob, o.row_opid, hp.row_opid);
+    put(blob, o.vtab_f, hp.vtab_f);
+    put(blob, o.vtab_d, hp.vtab_d);
     put(blob, o.gate_refs, hp.gate_refs);
     put(blob, o.cost_gates, hp.cost_gates);
     put(blob, o.cost_items, hp.cost_items);
