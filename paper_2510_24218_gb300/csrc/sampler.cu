@@ -312,22 +312,19 @@ __device__ __forceinline__ void mat_stage(C (&x)[1 << T], C m00, C m01, C m10, C
     }
 }
 
-// One tiled pass over buf (2^W entries) by the threads of g.
+// One tiled pass over buf (2^W entries) by the threads of g. Every thread
+// takes two tiles at a time (independent work to hide latency) and reads each
+// stage's descriptor and matrix once per pair of tiles.
 template <typename R, int T>
 __device__ void tile_pass(const KParams& p, const Chain<R>& ch, const Grp& g, const DevFused& f, int sb,
                           typename CT<R>::T* buf, int W) {
     using C = typename CT<R>::T;
     constexpr int E = 1 << T;
-    const int N = 1 << W;
-    int off[E];
+    constexpr bool TWO = sizeof(R) == 4;   // FP64 tiles take twice the registers: one at a time
+    const int ntiles = (1 << W) >> T;
+    int msk[4] = {0, 0, 0, 0};
 #pragma unroll
-    for (int e = 0; e < E; ++e) {
-        int o = 0;
-#pragma unroll
-        for (int k = 0; k < T; ++k)
-            if (e & (1 << k)) o |= 1 << f.tbits[k];
-        off[e] = o;
-    }
+    for (int k = 0; k < T; ++k) msk[k] = 1 << f.tbits[k];
     int sb4[4] = {f.tbits[0], f.tbits[1], f.tbits[2], f.tbits[3]};
 #pragma unroll
     for (int a = 1; a < T; ++a)
@@ -339,44 +336,87 @@ __device__ void tile_pass(const KParams& p, const Chain<R>& ch, const Grp& g, co
                 sb4[b - 1] = t;
             }
     const DevStage* stg = ch.stg + sb;
-    for (int tile = g.lt; tile < (N >> T); tile += g.nt) {
-        int base = tile;
+    for (int t0 = g.lt; t0 < ntiles; t0 += (TWO ? 2 : 1) * g.nt) {
+        const int t1 = (TWO && t0 + g.nt < ntiles) ? t0 + g.nt : t0;
+        int b0 = t0, b1 = t1;
 #pragma unroll
-        for (int k = 0; k < T; ++k) base = ((base >> sb4[k]) << (sb4[k] + 1)) | (base & ((1 << sb4[k]) - 1));
-        C x[E];
+        for (int k = 0; k < T; ++k) {
+            b0 = ((b0 >> sb4[k]) << (sb4[k] + 1)) | (b0 & ((1 << sb4[k]) - 1));
+            b1 = ((b1 >> sb4[k]) << (sb4[k] + 1)) | (b1 & ((1 << sb4[k]) - 1));
+        }
+        C x[E], y[E];
 #pragma unroll
-        for (int e = 0; e < E; ++e) x[e] = buf[base | off[e]];
+        for (int e = 0; e < E; ++e) {
+            int o = 0;
+#pragma unroll
+            for (int k = 0; k < T; ++k)
+                if (e & (1 << k)) o |= msk[k];
+            x[e] = buf[b0 | o];
+            if constexpr (TWO) y[e] = buf[b1 | o];
+        }
         for (int s = 0; s < f.nst; ++s) {
-            const DevStage st = stg[s];
-            const C* tab = ch.tab + st.tab_off;
-            if (st.type == ST_MAT) {
+            const uint8_t type = stg[s].type, arg = stg[s].arg;
+            const C* tab = ch.tab + stg[s].tab_off;
+            if (type == ST_MAT) {
                 const C m00 = tab[0], m01 = tab[1], m10 = tab[2], m11 = tab[3];
                 if constexpr (T >= 1) {
-                    switch (st.arg) {
-                        case 0: mat_stage<C, T, 0>(x, m00, m01, m10, m11); break;
-                        case 1: if constexpr (T >= 2) mat_stage<C, T, (T >= 2 ? 1 : 0)>(x, m00, m01, m10, m11); break;
-                        case 2: if constexpr (T >= 3) mat_stage<C, T, (T >= 3 ? 2 : 0)>(x, m00, m01, m10, m11); break;
-                        default: if constexpr (T >= 4) mat_stage<C, T, (T >= 4 ? 3 : 0)>(x, m00, m01, m10, m11); break;
+                    switch (arg) {
+                        case 0:
+                            mat_stage<C, T, 0>(x, m00, m01, m10, m11);
+                            if constexpr (TWO) mat_stage<C, T, 0>(y, m00, m01, m10, m11);
+                            break;
+                        case 1:
+                            if constexpr (T >= 2) {
+                                mat_stage<C, T, (T >= 2 ? 1 : 0)>(x, m00, m01, m10, m11);
+                                if constexpr (TWO) mat_stage<C, T, (T >= 2 ? 1 : 0)>(y, m00, m01, m10, m11);
+                            }
+                            break;
+                        case 2:
+                            if constexpr (T >= 3) {
+                                mat_stage<C, T, (T >= 3 ? 2 : 0)>(x, m00, m01, m10, m11);
+                                if constexpr (TWO) mat_stage<C, T, (T >= 3 ? 2 : 0)>(y, m00, m01, m10, m11);
+                            }
+                            break;
+                        default:
+                            if constexpr (T >= 4) {
+                                mat_stage<C, T, (T >= 4 ? 3 : 0)>(x, m00, m01, m10, m11);
+                                if constexpr (TWO) mat_stage<C, T, (T >= 4 ? 3 : 0)>(y, m00, m01, m10, m11);
+                            }
+                            break;
                     }
                 }
             } else {
-                int tb = 0;
-                for (int j = 0; j < st.arg; ++j) tb |= ((base >> st.dbits[j]) & 1) << j;
+                int tb0 = 0, tb1 = 0;
+                for (int j = 0; j < arg; ++j) {
+                    const int db = stg[s].dbits[j];
+                    tb0 |= ((b0 >> db) & 1) << j;
+                    tb1 |= ((b1 >> db) & 1) << j;
+                }
                 int pm[4];
 #pragma unroll
-                for (int k = 0; k < 4; ++k) pm[k] = st.tpos[k] != 0xFF ? 1 << st.tpos[k] : 0;
+                for (int k = 0; k < 4; ++k) pm[k] = stg[s].tpos[k] != 0xFF ? 1 << stg[s].tpos[k] : 0;
 #pragma unroll
                 for (int e = 0; e < E; ++e) {
-                    int t = tb;
+                    int t = 0;
 #pragma unroll
                     for (int k = 0; k < T; ++k)
                         if (e & (1 << k)) t |= pm[k];
-                    x[e] = cmul(x[e], tab[t]);
+                    x[e] = cmul(x[e], tab[tb0 | t]);
+                    if constexpr (TWO) y[e] = cmul(y[e], tab[tb1 | t]);
                 }
             }
         }
 #pragma unroll
-        for (int e = 0; e < E; ++e) buf[base | off[e]] = x[e];
+        for (int e = 0; e < E; ++e) {
+            int o = 0;
+#pragma unroll
+            for (int k = 0; k < T; ++k)
+                if (e & (1 << k)) o |= msk[k];
+            buf[b0 | o] = x[e];
+            if constexpr (TWO) {
+                if (t1 != t0) buf[b1 | o] = y[e];
+            }
+        }
     }
 }
 
