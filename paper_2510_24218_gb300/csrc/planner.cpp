@@ -916,6 +916,12 @@ int build_plan(const pw_circuit* c, const pw_plan_opts& opts, HostPlan& hp) {
             }
             for (auto& s : ls) hp.live_slots.push_back(s);
             br.live_end = (int)hp.live_slots.size();
+            br.rmask = 0;
+            for (int j = 0; j < S; ++j)
+                if (ls[j].q >= 0 && ls[j].role >= 0) {
+                    br.rslot[ls[j].role] = (int8_t)j;
+                    br.rmask |= 1 << j;
+                }
         }
         (void)Wm;
     }

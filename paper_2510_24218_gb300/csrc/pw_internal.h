@@ -165,6 +165,8 @@ struct DevBlockRange {
     int32_t fwd_tab, bwd_tab;       // table entries of the two programs
     int32_t fwd_st, bwd_st;         // first stage of the two programs
     int32_t fwd_nst, bwd_nst;       // their stage counts
+    int32_t rmask;                  // slots holding the block's sites
+    int8_t rslot[12];               // slot of the i-th site of the block
 };
 
 struct DevPlanHeader {

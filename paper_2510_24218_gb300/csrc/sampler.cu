@@ -315,12 +315,11 @@ __device__ __forceinline__ void mat_stage(C (&x)[1 << T], C m00, C m01, C m10, C
 // One tiled pass over buf (2^W entries) by the threads of g. Every thread
 // takes two tiles at a time (independent work to hide latency) and reads each
 // stage's descriptor and matrix once per pair of tiles.
-template <typename R, int T>
+template <typename R, int T, bool TWO>
 __device__ void tile_pass(const KParams& p, const Chain<R>& ch, const Grp& g, const DevFused& f, int sb,
                           typename CT<R>::T* buf, int W) {
     using C = typename CT<R>::T;
     constexpr int E = 1 << T;
-    constexpr bool TWO = sizeof(R) == 4;   // FP64 tiles take twice the registers: one at a time
     const int ntiles = (1 << W) >> T;
     int msk[4] = {0, 0, 0, 0};
 #pragma unroll
@@ -420,6 +419,52 @@ __device__ void tile_pass(const KParams& p, const Chain<R>& ch, const Grp& g, co
     }
 }
 
+// A pass on a tensor with fewer tiles than threads: its stages run one after
+// another over the whole tensor (a pair per thread for a matrix, an entry per
+// thread for a diagonal), with a barrier between stages.
+template <typename R>
+__device__ void flat_pass(const KParams& p, const Chain<R>& ch, const Grp& g, const DevFused& f, int sb,
+                          typename CT<R>::T* buf, int W) {
+    using C = typename CT<R>::T;
+    const int N = 1 << W;
+    const DevStage* stg = ch.stg + sb;
+    for (int s = 0; s < f.nst; ++s) {
+        const uint8_t type = stg[s].type, arg = stg[s].arg;
+        const C* tab = ch.tab + stg[s].tab_off;
+        if (type == ST_MAT) {
+            const int bt = f.tbits[arg];
+            const C m00 = tab[0], m01 = tab[1], m10 = tab[2], m11 = tab[3];
+            for (int pi = g.lt; pi < (N >> 1); pi += g.nt) {
+                const int i0 = ((pi >> bt) << (bt + 1)) | (pi & ((1 << bt) - 1));
+                const int i1 = i0 | (1 << bt);
+                const C x0 = buf[i0], x1 = buf[i1];
+                buf[i0] = cfma(m00, x0, cmul(m01, x1));
+                buf[i1] = cfma(m10, x0, cmul(m11, x1));
+            }
+        } else {
+            for (int idx = g.lt; idx < N; idx += g.nt) {
+                int t = 0;
+                for (int j = 0; j < arg; ++j) t |= ((idx >> stg[s].dbits[j]) & 1) << j;
+                buf[idx] = cmul(buf[idx], tab[t]);
+            }
+        }
+        if (s + 1 < f.nst) g.sync();
+    }
+}
+
+template <typename R, int T>
+__device__ __forceinline__ void tile_pass_any(const KParams& p, const Chain<R>& ch, const Grp& g, const DevFused& f,
+                                              int sb, typename CT<R>::T* buf, int W) {
+    const int ntiles = (1 << W) >> T;
+    if (ntiles < g.nt) {
+        flat_pass<R>(p, ch, g, f, sb, buf, W);
+    } else if (sizeof(R) == 4 && ntiles >= 2 * g.nt) {
+        tile_pass<R, T, sizeof(R) == 4>(p, ch, g, f, sb, buf, W);   // two tiles per iteration (FP32)
+    } else {
+        tile_pass<R, T, false>(p, ch, g, f, sb, buf, W);
+    }
+}
+
 // Run passes [fb, fe) (their stages start at stage sb0 of the block) on buf.
 template <typename R>
 __device__ void run_passes(const KParams& p, const Chain<R>& ch, const Grp& g, int fb, int fe, int sb0,
@@ -429,11 +474,11 @@ __device__ void run_passes(const KParams& p, const Chain<R>& ch, const Grp& g, i
         const DevFused f = F[fi];
         const int sb = f.st_begin - sb0;
         switch (f.ntb) {
-            case 0: tile_pass<R, 0>(p, ch, g, f, sb, buf, W); break;
-            case 1: tile_pass<R, 1>(p, ch, g, f, sb, buf, W); break;
-            case 2: tile_pass<R, 2>(p, ch, g, f, sb, buf, W); break;
-            case 3: tile_pass<R, 3>(p, ch, g, f, sb, buf, W); break;
-            default: tile_pass<R, 4>(p, ch, g, f, sb, buf, W); break;
+            case 0: tile_pass_any<R, 0>(p, ch, g, f, sb, buf, W); break;
+            case 1: tile_pass_any<R, 1>(p, ch, g, f, sb, buf, W); break;
+            case 2: tile_pass_any<R, 2>(p, ch, g, f, sb, buf, W); break;
+            case 3: tile_pass_any<R, 3>(p, ch, g, f, sb, buf, W); break;
+            default: tile_pass_any<R, 4>(p, ch, g, f, sb, buf, W); break;
         }
         g.sync();
     }
@@ -568,13 +613,14 @@ __device__ void readout_and_sample(const KParams& p, const Chain<R>& ch, const G
     R mx = 0;
     if (g.nt >= H) {
         const int hh = g.lt & (H - 1), step = g.nt / H;
-        C acc = zero;
-        for (int l = g.lt / H; l < NL; l += step) {
+        C acc[4] = {zero, zero, zero, zero};   // independent chains for latency
+        int l = g.lt / H, a = 0;
+        for (; l < NL; l += step, a = (a + 1) & 3) {
             const C v = L[(size_t)l * H + hh];
-            acc = cfma(v, Rk[l], acc);
+            acc[a] = cfma(v, Rk[l], acc[a]);
             mx = rmax(mx, rmax(rabs(v.x), rabs(v.y)));
         }
-        ch.part[g.lt] = acc;
+        ch.part[g.lt] = mk<R>(acc[0].x + acc[1].x + acc[2].x + acc[3].x, acc[0].y + acc[1].y + acc[2].y + acc[3].y);
     } else {
         for (int hh = g.lt; hh < H; hh += g.nt) {
             C acc = zero;
@@ -614,12 +660,11 @@ __device__ void readout_and_sample(const KParams& p, const Chain<R>& ch, const G
     const DevBlockSite* sites = P_<DevBlockSite>(p, p.off.block_sites) + br.site_begin;
     const int nb = br.site_end - br.site_begin;
     {
-        int rmask = 0;
-        for (int i = 0; i < nb; ++i) rmask |= 1 << ch.misc[2 + i];
+        const int rmask = br.rmask;
         const int NT = 1 << nb, nother = S - nb;
         for (int t = g.lt; t < NT; t += g.nt) {
             int hbase = 0;
-            for (int i = 0; i < nb; ++i) hbase |= ((t >> i) & 1) << ch.misc[2 + i];
+            for (int i = 0; i < nb; ++i) hbase |= ((t >> i) & 1) << br.rslot[i];
             C acc = zero;
             for (int hh = 0; hh < (1 << nother); ++hh) {
                 int hv = hbase, bit = 0;
@@ -634,70 +679,85 @@ __device__ void readout_and_sample(const KParams& p, const Chain<R>& ch, const G
     }
     g.sync();
 
-    // 3) sequential resampling of the block's sites by the first warp: lane 0
-    //    decides (FP64 conditional, the chain's precomputed Philox draw), the
-    //    lanes contract the resampled top away in parallel
+    // 3) sequential resampling of the block's sites by the first warp. Lane i
+    //    holds site i's data; lane 0 takes each decision (FP64 conditional, the
+    //    chain's precomputed Philox draw); the lanes then contract the
+    //    resampled top away in parallel. The block's bits live in a register
+    //    mask until they are written back.
     const int wsz = g.nt < 32 ? g.nt : 32;
     if (g.lt < wsz) {
         const int lane = g.lt;
+        C* sa = ch.part;   // site i's mixer A'_m at sa[4i .. 4i+3]
+        for (int i = lane; i < nb; i += wsz) {
+            const int q = sites[i].q;
+            sa[4 * i] = mixel<R>(p, ch, m, q, 0, 0);
+            sa[4 * i + 1] = mixel<R>(p, ch, m, q, 0, 1);
+            sa[4 * i + 2] = mixel<R>(p, ch, m, q, 1, 0);
+            sa[4 * i + 3] = mixel<R>(p, ch, m, q, 1, 1);
+        }
+        unsigned sbits = 0;
+        for (int i = 0; i < nb; ++i) sbits |= (unsigned)ch.s[sites[i].q] << i;
+        __syncwarp();
         C* cur = ch.T;
         int size = 1 << nb;
         for (int i = 0; i < nb; ++i) {
-            const DevBlockSite st = sites[i];
-            const int q = st.q;
-            const C A00 = mixel<R>(p, ch, m, q, 0, 0), A01 = mixel<R>(p, ch, m, q, 0, 1);
-            const C A10 = mixel<R>(p, ch, m, q, 1, 0), A11 = mixel<R>(p, ch, m, q, 1, 1);
+            const C A00 = sa[4 * i], A01 = sa[4 * i + 1], A10 = sa[4 * i + 2], A11 = sa[4 * i + 3];
+            const int sold = (sbits >> i) & 1;
+            int snew = sold;
             bool stop = false;
             if (lane == 0) {
-                int rest = 0;   // later sites keep their current bits (projection)
-                for (int j = i + 1; j < nb; ++j) rest |= ch.s[sites[j].q] << (j - i);
+                const DevBlockSite st = sites[i];
+                const int row = st.trace_row, mono = st.monomial;
+                const int rest = (int)((sbits >> (i + 1)) << 1);   // later sites keep their bits
                 const C c0 = cur[rest], c1 = cur[rest | 1];
                 const C amp0 = cfma(A00, c0, cmul(A01, c1));
                 const C amp1 = cfma(A10, c0, cmul(A11, c1));
                 if (p.mode == MODE_AMP) {
                     if (i == p.amp_pos) {
-                        const C a = ch.s[q] ? amp1 : amp0;
+                        const C a = sold ? amp1 : amp0;
                         p.amp_out[2 * chain] = ldexp((double)a.x, escale);
                         p.amp_out[2 * chain + 1] = ldexp((double)a.y, escale);
                         stop = true;
                     }
-                } else if (st.monomial) {
+                } else if (mono) {
                     // deterministic move: the nonzero of column s[q] of A'_m
-                    const C a0 = ch.s[q] ? A01 : A00;
-                    ch.s[q] = (a0.x != (R)0 || a0.y != (R)0) ? 0 : 1;
+                    const C a0 = sold ? A01 : A00;
+                    snew = (a0.x != (R)0 || a0.y != (R)0) ? 0 : 1;
                 } else {
                     const double a0r = amp0.x, a0i = amp0.y, a1r = amp1.x, a1i = amp1.y;
-                    const double p0 = a0r * a0r + a0i * a0i, p1 = a1r * a1r + a1i * a1i;
+                    const double p0 = fma(a0r, a0r, a0i * a0i), p1 = fma(a1r, a1r, a1i * a1i);
                     const double Pt = p0 + p1;
                     if (p.trace) {
-                        double* tr = p.trace + ((size_t)chain * h.n_sampled + st.trace_row) * 4;
+                        double* tr = p.trace + ((size_t)chain * h.n_sampled + row) * 4;
                         tr[0] = ldexp(a0r, escale);
                         tr[1] = ldexp(a0i, escale);
                         tr[2] = ldexp(a1r, escale);
                         tr[3] = ldexp(a1i, escale);
                     }
                     if (Pt > 0.0) {
-                        const double u = ch.ud[st.trace_row];
-                        ch.s[q] = (u * Pt < p0) ? 0 : 1;
-                        if (fabs(u * Pt - p0) < 1e-6 * Pt) atomicAdd(&p.counters[CNT_NEAR], 1ull);
+                        const double up = ch.ud[row] * Pt;
+                        snew = up < p0 ? 0 : 1;
+                        if (fabs(up - p0) < 1e-6 * Pt) atomicAdd(&p.counters[CNT_NEAR], 1ull);
                     } else {
                         atomicAdd(&p.counters[CNT_ZERO], 1ull);   // zero-mass block: stay (Sec. 2)
                     }
                 }
             }
-            stop = __shfl_sync(0xffffffffu, stop, 0);
-            __syncwarp();
+            stop = __shfl_sync(0xffffffffu, (int)stop, 0, wsz);
             if (stop) break;
+            snew = __shfl_sync(0xffffffffu, snew, 0, wsz);
+            sbits = (sbits & ~(1u << i)) | ((unsigned)snew << i);
             // contract this site's top with its mixer weight at the new bit
             // (ping-pong between the two halves of the T area)
-            const int sq = ch.s[q];
-            const C w0 = sq ? A10 : A00, w1 = sq ? A11 : A01;
+            const C w0 = snew ? A10 : A00, w1 = snew ? A11 : A01;
             size >>= 1;
             C* nxt = cur == ch.T ? ch.T + (1 << h.max_block) : ch.T;
             for (int r = lane; r < size; r += wsz) nxt[r] = cfma(w0, cur[2 * r], cmul(w1, cur[2 * r + 1]));
             cur = nxt;
             __syncwarp();
         }
+        if (p.mode == MODE_SAMPLE)
+            for (int i = lane; i < nb; i += wsz) ch.s[sites[i].q] = (uint8_t)((sbits >> i) & 1);
     }
     g.sync();
 }

@@ -33,7 +33,7 @@ inline SmemLayout make_layout(const HostPlan& hp, size_t csz) {
     L.tab = take(csz * (size_t)std::max(1, h.max_tab));
     L.stg = take(sizeof(DevStage) * (size_t)std::max(1, h.max_stages));
     L.ud = take(sizeof(double) * (size_t)std::max(1, h.n_sampled));
-    L.part = take(csz * (size_t)std::max(32, hp.threads_per_chain));
+    L.part = take(csz * (size_t)std::max(64, hp.threads_per_chain));   // also the resampling scratch (4 per site)
     L.fslot = take(csz * 2 * S);
     L.red = take((csz / 2) * 32);
     L.s = take(h.n);
