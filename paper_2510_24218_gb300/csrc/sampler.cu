@@ -562,9 +562,10 @@ __device__ void build_fslot(const KParams& p, const Chain<R>& ch, const Grp& g, 
             for (int d = 0; d < sl.ndep; ++d) var |= ch.s[sl.dep[d]] << d;
             const size_t at = (size_t)sl.var_off + 2 * (size_t)var;
             if constexpr (sizeof(R) == 4) {
-                const float4 v = *reinterpret_cast<const float4*>(P_<float>(p, p.off.vtab_f) + 2 * at);
-                ch.fslot[2 * j] = mk<R>(v.x, v.y);
-                ch.fslot[2 * j + 1] = mk<R>(v.z, v.w);
+                // 8-byte loads: variant tables start at any complex entry
+                const float2* v = reinterpret_cast<const float2*>(P_<float>(p, p.off.vtab_f) + 2 * at);
+                ch.fslot[2 * j] = v[0];
+                ch.fslot[2 * j + 1] = v[1];
             } else {
                 const double* d = P_<double>(p, p.off.vtab_d) + 2 * at;
                 ch.fslot[2 * j] = mk<R>(d[0], d[1]);
