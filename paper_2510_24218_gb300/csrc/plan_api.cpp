@@ -19,7 +19,7 @@ int choose_threads(const HostPlan& hp, int requested) {
         return requested;
     }
     long N = 1L << hp.W;
-    long t = N / 64;
+    long t = N / 32;
     t = std::max(32L, std::min(256L, t));
     long pw2 = 32;
     while (pw2 < t) pw2 <<= 1;

@@ -140,6 +140,7 @@ template <typename R> struct Chain {
     C* tab;       // tables of one block program
     DevStage* stg;    // stage descriptors of one block program
     double* ud;   // the chain's UpdateState draws, one per sampled gate
+    float* uf;    // the same draws rounded to FP32 (fast path of the decision)
     C* part;      // partial sums, one per thread
     C* fslot;     // S x 2 per-slot readout factors
     R* red;       // 32 reduction scratch
@@ -615,10 +616,20 @@ __device__ void readout_and_sample(const KParams& p, const Chain<R>& ch, const G
     if (g.nt >= H) {
         const int hh = g.lt & (H - 1), step = g.nt / H;
         C acc[4] = {zero, zero, zero, zero};   // independent chains for latency
-        int l = g.lt / H, a = 0;
-        for (; l < NL; l += step, a = (a + 1) & 3) {
+        int l = g.lt / H;
+        for (; l + 3 * step < NL; l += 4 * step) {
+            C v[4];
+#pragma unroll
+            for (int a = 0; a < 4; ++a) v[a] = L[(size_t)(l + a * step) * H + hh];
+#pragma unroll
+            for (int a = 0; a < 4; ++a) {
+                acc[a] = cfma(v[a], Rk[l + a * step], acc[a]);
+                mx = rmax(mx, rmax(rabs(v[a].x), rabs(v[a].y)));
+            }
+        }
+        for (; l < NL; l += step) {
             const C v = L[(size_t)l * H + hh];
-            acc[a] = cfma(v, Rk[l], acc[a]);
+            acc[0] = cfma(v, Rk[l], acc[0]);
             mx = rmax(mx, rmax(rabs(v.x), rabs(v.y)));
         }
         ch.part[g.lt] = mk<R>(acc[0].x + acc[1].x + acc[2].x + acc[3].x, acc[0].y + acc[1].y + acc[2].y + acc[3].y);
@@ -725,22 +736,34 @@ __device__ void readout_and_sample(const KParams& p, const Chain<R>& ch, const G
                     const C a0 = sold ? A01 : A00;
                     snew = (a0.x != (R)0 || a0.y != (R)0) ? 0 : 1;
                 } else {
-                    const double a0r = amp0.x, a0i = amp0.y, a1r = amp1.x, a1i = amp1.y;
-                    const double p0 = fma(a0r, a0r, a0i * a0i), p1 = fma(a1r, a1r, a1i * a1i);
-                    const double Pt = p0 + p1;
                     if (p.trace) {
                         double* tr = p.trace + ((size_t)chain * h.n_sampled + row) * 4;
-                        tr[0] = ldexp(a0r, escale);
-                        tr[1] = ldexp(a0i, escale);
-                        tr[2] = ldexp(a1r, escale);
-                        tr[3] = ldexp(a1i, escale);
+                        tr[0] = ldexp((double)amp0.x, escale);
+                        tr[1] = ldexp((double)amp0.y, escale);
+                        tr[2] = ldexp((double)amp1.x, escale);
+                        tr[3] = ldexp((double)amp1.y, escale);
                     }
-                    if (Pt > 0.0) {
-                        const double up = ch.ud[row] * Pt;
-                        snew = up < p0 ? 0 : 1;
-                        if (fabs(up - p0) < 1e-6 * Pt) atomicAdd(&p.counters[CNT_NEAR], 1ull);
+                    // The draw is decided in FP64: u*P < p0 with p_y = |amp_y|^2.
+                    // When the FP32 evaluation of the same quantities is farther
+                    // than 4e-6 P from the boundary (its error is below 1e-6 P)
+                    // it gives the same answer, and no FP64 work is needed.
+                    const float f0 = fmaf((float)amp0.x, (float)amp0.x, (float)amp0.y * (float)amp0.y);
+                    const float f1 = fmaf((float)amp1.x, (float)amp1.x, (float)amp1.y * (float)amp1.y);
+                    const float fP = f0 + f1;
+                    const float fd = fmaf(ch.uf[row], fP, -f0);
+                    if (fP > 0.0f && isfinite(fP) && fabsf(fd) > 4e-6f * fP) {
+                        snew = fd < 0.0f ? 0 : 1;
                     } else {
-                        atomicAdd(&p.counters[CNT_ZERO], 1ull);   // zero-mass block: stay (Sec. 2)
+                        const double a0r = amp0.x, a0i = amp0.y, a1r = amp1.x, a1i = amp1.y;
+                        const double p0 = fma(a0r, a0r, a0i * a0i), p1 = fma(a1r, a1r, a1i * a1i);
+                        const double Pt = p0 + p1;
+                        if (Pt > 0.0) {
+                            const double up = ch.ud[row] * Pt;
+                            snew = up < p0 ? 0 : 1;
+                            if (fabs(up - p0) < 1e-6 * Pt) atomicAdd(&p.counters[CNT_NEAR], 1ull);
+                        } else {
+                            atomicAdd(&p.counters[CNT_ZERO], 1ull);   // zero-mass block: stay (Sec. 2)
+                        }
                     }
                 }
             }
@@ -790,7 +813,11 @@ __device__ void run_chain(const KParams& p, const Chain<R>& ch, int gid, int lt,
         // the UpdateState draws of every sampled gate (they depend only on
         // (seed, sample, op id), so they are drawn up front in parallel)
         const int32_t* rop = P_<int32_t>(p, p.off.row_opid);
-        for (int r = lt; r < h.n_sampled; r += p.tpc) ch.ud[r] = draw_u(p.seed, sample_id, (uint32_t)rop[r], 0u);
+        for (int r = lt; r < h.n_sampled; r += p.tpc) {
+            const double u = draw_u(p.seed, sample_id, (uint32_t)rop[r], 0u);
+            ch.ud[r] = u;
+            ch.uf[r] = (float)u;
+        }
         // Layer 0 acts on |0^n>: the prefix state is a product state, so the
         // conditional of qubit q is |<y|A_0|0>|^2 normalised (same draw rule).
         const int32_t* opid = P_<int32_t>(p, p.off.mix0_opid);
@@ -944,6 +971,7 @@ __global__ void __launch_bounds__(256, 2) pw_chain_kernel(const KParams p) {
     ch.tab = reinterpret_cast<C*>(g + p.sm.tab);
     ch.stg = reinterpret_cast<DevStage*>(g + p.sm.stg);
     ch.ud = reinterpret_cast<double*>(g + p.sm.ud);
+    ch.uf = reinterpret_cast<float*>(g + p.sm.uf);
     ch.part = reinterpret_cast<C*>(g + p.sm.part);
     ch.fslot = reinterpret_cast<C*>(g + p.sm.fslot);
     ch.red = reinterpret_cast<R*>(g + p.sm.red);

@@ -9,7 +9,7 @@
 namespace pw {
 
 struct SmemLayout {
-    int L, R, Rexp, rowdot, T, tab, stg, ud, part, fslot, red, s, x, xmix, gframe, segfac, misc, group_bytes;
+    int L, R, Rexp, rowdot, T, tab, stg, ud, uf, part, fslot, red, s, x, xmix, gframe, segfac, misc, group_bytes;
 };
 
 inline size_t align16(size_t v) { return (v + 15) & ~(size_t)15; }
@@ -33,6 +33,7 @@ inline SmemLayout make_layout(const HostPlan& hp, size_t csz) {
     L.tab = take(csz * (size_t)std::max(1, h.max_tab));
     L.stg = take(sizeof(DevStage) * (size_t)std::max(1, h.max_stages));
     L.ud = take(sizeof(double) * (size_t)std::max(1, h.n_sampled));
+    L.uf = take(sizeof(float) * (size_t)std::max(1, h.n_sampled));
     L.part = take(csz * (size_t)std::max(64, hp.threads_per_chain));   // also the resampling scratch (4 per site)
     L.fslot = take(csz * 2 * S);
     L.red = take((csz / 2) * 32);
