@@ -176,6 +176,26 @@ int pw_sample_host(pw_plan* plan, uint64_t seed, uint64_t first_sample, uint64_t
 int pw_amplitudes(pw_plan* plan, int prefix_ops, uint64_t n_strings, const uint64_t* d_bits,
                   double* d_amp, void* stream);
 
+/* Allocation-free variant of pw_sample, for callers that cannot allocate
+ * device memory: for example a process whose device memory is entirely
+ * reserved by a framework's own memory pool, or code that must not allocate
+ * inside its sampling loop. (The paper has no counterpart; this is an
+ * interface of this library.) The caller passes the plan and the output buffer
+ * d_out_bits (n_samples * ceil(n/64) uint64, device) exactly as for pw_sample;
+ * the kernel's scratch (a copy of the plan tables and the two draw counters)
+ * lives in one fixed 2 MiB array in device memory that the library holds on
+ * every device it is loaded on, until the process exits. Plans whose tables do
+ * not fit (pw_plan_stats().device_bytes > 2 MiB - 256 B) are rejected with
+ * PW_ERR_TOO_LARGE. No cudaMalloc, cudaFree or allocating library routine is
+ * called. The first call on a device looks up the array's device address with
+ * that device current; make that first call before any stream capture. Every
+ * call reloads the plan tables and zeroes the counters in the shared array, so
+ * calls that overlap on the GPU (on different streams, or from different
+ * threads) race and must be serialised by the caller. The results are those of
+ * pw_sample for the same arguments. */
+int pw_sample_static(const pw_plan* plan, uint64_t seed, uint64_t first_sample, uint64_t n_samples,
+                     uint64_t* d_out_bits, void* stream, pw_run_stats_t* stats);
+
 /* Thread-local message describing the last failure of this thread. */
 const char* pw_last_error(void);
 

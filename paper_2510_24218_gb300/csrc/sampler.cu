@@ -18,6 +18,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 
 #include "pw_internal.h"
 #include "smem_layout.h"
@@ -1220,3 +1221,123 @@ int pw_amplitudes(pw_plan* plan, int prefix_ops, uint64_t n_strings, const uint6
 }
 
 }  // extern "C"
+
+// =============================================== allocation-free sampling
+// pw_sample_static: the same sampler for callers that cannot allocate device
+// memory (for example a process whose device memory is entirely reserved by a
+// framework's own pool, or a loop that must not allocate). The kernel's scratch
+// (the plan tables it reads and its two draw counters) lives in one file-scope
+// device array of fixed size instead of library allocations.
+namespace pw {
+namespace {
+
+constexpr size_t kStaticScratchBytes = size_t(2) << 20;   // 2 MiB per device
+constexpr size_t kStaticCounterBytes = 256;               // counters, then plan tables
+
+static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
+
+// Device address of g_static_scratch per device, looked up once per device
+// with that device current (the host symbol is only a stand-in).
+std::mutex g_static_mu;
+void* g_static_ptr[64] = {nullptr};
+
+int static_scratch(int dev, unsigned char** out) {
+    if (dev < 0 || dev >= 64) return set_error(PW_ERR_ARG, "device ordinal out of range");
+    std::lock_guard<std::mutex> lk(g_static_mu);
+    if (!g_static_ptr[dev]) {
+        void* ptr = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&ptr, g_static_scratch);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(static scratch)");
+        g_static_ptr[dev] = ptr;
+    }
+    *out = static_cast<unsigned char*>(g_static_ptr[dev]);
+    return PW_OK;
+}
+
+template <typename R> int launch_static(const HostPlan& hp, int dev, KParams& kp, cudaStream_t st, uint64_t* launches) {
+    kp.sm = make_layout(hp, 2 * sizeof(R));
+    kp.tpc = hp.threads_per_chain;
+    if (kp.sm.group_bytes > 227 * 1024) return set_error(PW_ERR_TOO_LARGE, "per-chain shared memory exceeds 227 KB");
+    const int gpc = groups_per_cta(kp.tpc, kp.sm.group_bytes);
+    kp.gpc = gpc;
+    const int threads = kp.tpc * gpc;
+    const size_t smem = (size_t)kp.sm.group_bytes * gpc;
+    auto kern = pw_chain_kernel<R>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
+    cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    int nsm = 0, occ = 0;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, smem);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
+    occ = std::max(occ, 1);
+    const uint64_t per_launch = hp.chains_per_launch > 0 ? (uint64_t)hp.chains_per_launch : kp.count;
+    const uint64_t total = kp.count, first0 = kp.first;
+    uint64_t* out0 = kp.out_bits;
+    for (uint64_t done = 0; done < total; done += per_launch) {
+        const uint64_t cnt = std::min(per_launch, total - done);
+        kp.count = cnt;
+        kp.first = first0 + done;
+        kp.out_bits = out0 + done * hp.hdr.words;
+        const int grid = (int)std::min<uint64_t>((cnt + gpc - 1) / gpc, (uint64_t)nsm * occ);
+        kern<<<grid, threads, smem, st>>>(kp);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
+        if (launches) ++*launches;
+    }
+    return PW_OK;
+}
+
+}  // namespace
+}  // namespace pw
+
+extern "C" int pw_sample_static(const pw_plan* plan, uint64_t seed, uint64_t first_sample, uint64_t n_samples,
+                                uint64_t* d_out_bits, void* stream, pw_run_stats_t* stats) {
+    using namespace pw;
+    if (!plan || (!d_out_bits && n_samples)) return set_error(PW_ERR_ARG, "null argument");
+    if (stats) std::memset(stats, 0, sizeof(*stats));
+    if (n_samples == 0) return PW_OK;
+    const HostPlan& hp = plan->hp;
+    DevPlanOffsets off{};
+    const std::vector<unsigned char> blob = make_blob(hp, off);
+    if (blob.size() > kStaticScratchBytes - kStaticCounterBytes)
+        return set_error(PW_ERR_TOO_LARGE, "plan tables (" + std::to_string(blob.size()) +
+                                               " B) exceed the static scratch of pw_sample_static (" +
+                                               std::to_string(kStaticScratchBytes - kStaticCounterBytes) + " B)");
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    unsigned char* base = nullptr;
+    int rc = static_scratch(dev, &base);
+    if (rc) return rc;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    // the array keeps the previous call's contents: reload the tables, zero the counters
+    e = cudaMemcpyAsync(base + kStaticCounterBytes, blob.data(), blob.size(), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(base, 0, kStaticCounterBytes, st);
+    if (e != cudaSuccess) return cuda_fail(e, "staging the plan tables");
+    KParams kp;
+    std::memset(&kp, 0, sizeof(kp));
+    kp.blob = base + kStaticCounterBytes;
+    kp.off = off;
+    kp.hdr = hp.hdr;
+    kp.counters = reinterpret_cast<unsigned long long*>(base);
+    kp.seed = seed;
+    kp.first = first_sample;
+    kp.count = n_samples;
+    kp.out_bits = d_out_bits;
+    kp.mode = MODE_SAMPLE;
+    uint64_t launches = 0;
+    rc = hp.precision == PW_PREC_FP64 ? launch_static<double>(hp, dev, kp, st, &launches)
+                                      : launch_static<float>(hp, dev, kp, st, &launches);
+    if (rc) return rc;
+    if (stats) {
+        unsigned long long hcnt[4] = {0, 0, 0, 0};
+        e = cudaMemcpyAsync(hcnt, base, sizeof(hcnt), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return cuda_fail(e, "reading counters");
+        stats->near_boundary = hcnt[CNT_NEAR];
+        stats->zero_mass = hcnt[CNT_ZERO];
+        stats->launches = launches;
+    }
+    return PW_OK;
+}

@@ -74,6 +74,7 @@ def load_library():
         "pw_sample": (C.c_int, [vp, C.c_uint64, C.c_uint64, C.c_uint64, vp, vp, vp, C.POINTER(RunStats)]),
         "pw_sample_host": (C.c_int, [vp, C.c_uint64, C.c_uint64, C.c_uint64, vp, vp, C.POINTER(RunStats)]),
         "pw_amplitudes": (C.c_int, [vp, C.c_int, C.c_uint64, vp, vp, vp]),
+        "pw_sample_static": (C.c_int, [vp, C.c_uint64, C.c_uint64, C.c_uint64, vp, vp, C.POINTER(RunStats)]),
         "pw_last_error": (C.c_char_p, []),
     }
     for name, (res, args) in sig.items():
@@ -199,6 +200,15 @@ def pw_sample(plan, seed, first_sample, n_samples, out_bits, trace=None, stream=
                                     C.c_void_p(out_bits.data_ptr()),
                                     C.c_void_p(trace.data_ptr()) if trace is not None else None,
                                     _stream_ptr(stream), C.byref(st) if want_stats else None))
+    return {"near_boundary": st.near_boundary, "zero_mass": st.zero_mass, "launches": st.launches}
+
+
+def pw_sample_static(plan, seed, first_sample, n_samples, out_bits, stream=None, want_stats=True):
+    """Allocation-free sampling: out_bits is a torch CUDA int64 [n, words] tensor."""
+    st = RunStats()
+    _check(load_library().pw_sample_static(plan, int(seed), int(first_sample), int(n_samples),
+                                           C.c_void_p(out_bits.data_ptr()), _stream_ptr(stream),
+                                           C.byref(st) if want_stats else None))
     return {"near_boundary": st.near_boundary, "zero_mass": st.zero_mass, "launches": st.launches}
 
 
