@@ -460,9 +460,8 @@ __device__ __forceinline__ void tile_pass_any(const KParams& p, const Chain<R>& 
     const int ntiles = (1 << W) >> T;
     if (ntiles < g.nt) {
         flat_pass<R>(p, ch, g, f, sb, buf, W);
-    } else if (sizeof(R) == 4 && ntiles >= 2 * g.nt) {
-        tile_pass<R, T, sizeof(R) == 4>(p, ch, g, f, sb, buf, W);   // two tiles per iteration (FP32)
     } else {
+        // one tile per iteration: pairing tiles forces spills at 128 registers
         tile_pass<R, T, false>(p, ch, g, f, sb, buf, W);
     }
 }
