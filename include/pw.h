@@ -67,7 +67,10 @@ typedef struct {
     int max_block;          /* max sites resampled per readout block; 0 -> 8 */
     int threads_per_chain;  /* CUDA threads cooperating on one chain; 0 -> auto */
     int chains_per_launch;  /* chains per kernel launch; 0 -> all requested samples */
-    int reserved[7];
+    int ctas_per_chain;     /* 0 -> auto (a thread-block cluster only when one CTA's
+                               shared memory cannot hold the frontier); 2, 4 or 8
+                               force that split of the frontier over a cluster */
+    int reserved[6];
 } pw_plan_opts;
 
 /* Shape and cost of a plan (pw_plan_stats). */
@@ -89,6 +92,7 @@ typedef struct {
     double flops_per_sample;   /* real flops of the contraction per sample */
     double amps_per_sample;    /* amplitudes evaluated per sample */
     double device_bytes;       /* bytes of plan tables copied to the device on first use */
+    int ctas_per_chain;        /* > 1: one chain per thread-block cluster of that many CTAs */
 } pw_plan_stats_t;
 
 /* Counters of one pw_sample call. */

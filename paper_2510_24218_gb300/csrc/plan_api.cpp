@@ -53,6 +53,35 @@ int pw_plan_build(const pw_circuit* c, const pw_plan_opts* opts, pw_plan** out) 
         return set_error(PW_ERR_ARG, "threads_per_chain must be a power of two in 32..256");
     }
     plan->hp.threads_per_chain = tpc;
+    {
+        // A frontier too large for one CTA's shared memory is spread over a
+        // thread-block cluster: each CTA holds 2^wloc entries (128 KB) and the
+        // top log2(ctas) index bits (lower legs) select the CTA.
+        HostPlan& hp = plan->hp;
+        const size_t csz = hp.precision == PW_PREC_FP64 ? 16 : 8;
+        const int forced = o.ctas_per_chain;
+        if (forced != 0 && forced != 2 && forced != 4 && forced != 8) {
+            delete plan;
+            return set_error(PW_ERR_ARG, "ctas_per_chain must be 0, 2, 4 or 8");
+        }
+        if ((forced > 1 || make_layout(hp, csz).group_bytes > 200 * 1024) && hp.hdr.P >= 1) {
+            int wloc = hp.precision == PW_PREC_FP64 ? 13 : 14;
+            if (forced > 1) wloc = hp.W - (forced == 2 ? 1 : forced == 4 ? 2 : 3);
+            const int c = hp.W - wloc;
+            if (c > 3 || wloc < hp.hdr.S) {
+                delete plan;
+                return set_error(PW_ERR_TOO_LARGE, "frontier of 2^" + std::to_string(hp.W) +
+                                                       " entries needs more than 8 CTAs per chain");
+            }
+            hp.ctas_per_chain = 1 << c;
+            hp.wloc = wloc;
+            if (o.threads_per_chain <= 0) hp.threads_per_chain = 256;
+            if (make_layout(hp, csz).group_bytes > 227 * 1024) {
+                delete plan;
+                return set_error(PW_ERR_TOO_LARGE, "per-CTA shared memory exceeds 227 KB");
+            }
+        }
+    }
     if (o.chains_per_launch < 0) {
         delete plan;
         return set_error(PW_ERR_ARG, "chains_per_launch must be >= 0");
@@ -81,7 +110,8 @@ int pw_plan_stats(const pw_plan* plan, pw_plan_stats_t* s) {
     s->device_bytes = (double)plan_device_bytes(hp);
     // shared memory of the kernel's layout
     const SmemLayout L = make_layout(hp, hp.precision == PW_PREC_FP64 ? 16 : 8);
-    const int gpc = groups_per_cta(hp.threads_per_chain, L.group_bytes);
+    const int gpc = hp.ctas_per_chain > 1 ? 1 : groups_per_cta(hp.threads_per_chain, L.group_bytes);
+    s->ctas_per_chain = hp.ctas_per_chain;
     s->chains_per_cta = gpc;
     s->smem_bytes_per_cta = L.group_bytes * gpc;
     return PW_OK;

@@ -236,6 +236,8 @@ struct HostPlan {
     int threads_per_chain = 0;
     int chains_per_cta = 1;
     int chains_per_launch = 0;
+    int ctas_per_chain = 1;               // > 1: one thread-block cluster per chain
+    int wloc = 0;                         // log2 of the frontier entries per CTA then
     size_t smem_per_chain = 0;
     bool noisy = false;
     // amplitude API helpers: position of every executed mixer op (layer, block, index)

@@ -106,6 +106,8 @@ struct KParams {
     const uint64_t* in_bits;
     double* amp_out;
     int amp_layer, amp_block, amp_pos;
+    int cr;             // CTAs (one thread-block cluster) per chain; 1: one group per chain
+    int wloc;           // log2 of the frontier entries held by one CTA when cr > 1
 };
 
 enum { MODE_SAMPLE = 0, MODE_AMP = 1 };
@@ -121,8 +123,11 @@ template <typename T> __device__ __forceinline__ const T* P_(const KParams& p, i
 struct Grp {
     int lt, nt, gid, tpc;
     bool warp;
+    bool clus;   // the phase spans the CTAs of a cluster (distributed frontier)
     __device__ __forceinline__ void sync() const {
-        if (warp || tpc == 32) {
+        if (clus) {
+            asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+        } else if (warp || tpc == 32) {
             __syncwarp();
         } else {
             asm volatile("bar.sync %0, %1;" ::"r"(gid + 1), "r"(tpc) : "memory");
@@ -151,6 +156,11 @@ template <typename R> struct Chain {
     uint8_t* gframe;  // frame bits of each diagonal gate at its time
     C* segfac;    // one-qubit diagonal factors per (qubit, segment), [n][P+1][2]
     int* misc;    // [0] exponent of L, [1] pending rescale, [2..] role slots
+    // distributed frontier (cluster of p.cr CTAs per chain)
+    int rank;            // this CTA's rank in the cluster (0 when cr == 1)
+    C** rL;              // every rank's part of L (generic addresses, table in shared memory)
+    double2* pd;         // this CTA's FP64 partial readout sums, 2^S
+    float* cmax;         // this CTA's max |L|
 };
 
 // Frame-conjugated one-qubit gate A'_{m,q}[o][i] = A[o^x][i^x] (PropagateX).
@@ -314,15 +324,30 @@ __device__ __forceinline__ void mat_stage(C (&x)[1 << T], C m00, C m01, C m10, C
     }
 }
 
-// One tiled pass over buf (2^W entries) by the threads of g. Every thread
-// takes two tiles at a time (independent work to hide latency) and reads each
-// stage's descriptor and matrix once per pair of tiles.
-template <typename R, int T, bool TWO>
+// Frontier access: a CTA's own shared memory, or the parts held by the CTAs of
+// a cluster (entry idx in rank idx >> wloc at offset idx & (2^wloc - 1)).
+template <typename C> struct LocalAcc {
+    C* buf;
+    __device__ __forceinline__ C& operator()(int idx) const { return buf[idx]; }
+};
+template <typename C> struct DistAcc {
+    C* const* rl;   // every rank's part (a table in shared memory)
+    C* loc;         // this CTA's part
+    int wloc, rank;
+    __device__ __forceinline__ C& operator()(int idx) const {
+        const int r = idx >> wloc, o = idx & ((1 << wloc) - 1);
+        return r == rank ? loc[o] : rl[r][o];
+    }
+};
+
+// One tiled pass over tiles [t0, t1) of a 2^W-entry frontier by the threads of
+// g: each thread loads tiles of 2^T entries (the pass's tile bits varying),
+// runs the pass's stages on them in registers and stores them back.
+template <typename R, int T, typename Acc>
 __device__ void tile_pass(const KParams& p, const Chain<R>& ch, const Grp& g, const DevFused& f, int sb,
-                          typename CT<R>::T* buf, int W) {
+                          const Acc& acc, int t_begin, int t_end) {
     using C = typename CT<R>::T;
     constexpr int E = 1 << T;
-    const int ntiles = (1 << W) >> T;
     int msk[4] = {0, 0, 0, 0};
 #pragma unroll
     for (int k = 0; k < T; ++k) msk[k] = 1 << f.tbits[k];
@@ -337,23 +362,18 @@ __device__ void tile_pass(const KParams& p, const Chain<R>& ch, const Grp& g, co
                 sb4[b - 1] = t;
             }
     const DevStage* stg = ch.stg + sb;
-    for (int t0 = g.lt; t0 < ntiles; t0 += (TWO ? 2 : 1) * g.nt) {
-        const int t1 = (TWO && t0 + g.nt < ntiles) ? t0 + g.nt : t0;
-        int b0 = t0, b1 = t1;
+    for (int t0 = t_begin + g.lt; t0 < t_end; t0 += g.nt) {
+        int b0 = t0;
 #pragma unroll
-        for (int k = 0; k < T; ++k) {
-            b0 = ((b0 >> sb4[k]) << (sb4[k] + 1)) | (b0 & ((1 << sb4[k]) - 1));
-            b1 = ((b1 >> sb4[k]) << (sb4[k] + 1)) | (b1 & ((1 << sb4[k]) - 1));
-        }
-        C x[E], y[E];
+        for (int k = 0; k < T; ++k) b0 = ((b0 >> sb4[k]) << (sb4[k] + 1)) | (b0 & ((1 << sb4[k]) - 1));
+        C x[E];
 #pragma unroll
         for (int e = 0; e < E; ++e) {
             int o = 0;
 #pragma unroll
             for (int k = 0; k < T; ++k)
                 if (e & (1 << k)) o |= msk[k];
-            x[e] = buf[b0 | o];
-            if constexpr (TWO) y[e] = buf[b1 | o];
+            x[e] = acc(b0 | o);
         }
         for (int s = 0; s < f.nst; ++s) {
             const uint8_t type = stg[s].type, arg = stg[s].arg;
@@ -362,37 +382,15 @@ __device__ void tile_pass(const KParams& p, const Chain<R>& ch, const Grp& g, co
                 const C m00 = tab[0], m01 = tab[1], m10 = tab[2], m11 = tab[3];
                 if constexpr (T >= 1) {
                     switch (arg) {
-                        case 0:
-                            mat_stage<C, T, 0>(x, m00, m01, m10, m11);
-                            if constexpr (TWO) mat_stage<C, T, 0>(y, m00, m01, m10, m11);
-                            break;
-                        case 1:
-                            if constexpr (T >= 2) {
-                                mat_stage<C, T, (T >= 2 ? 1 : 0)>(x, m00, m01, m10, m11);
-                                if constexpr (TWO) mat_stage<C, T, (T >= 2 ? 1 : 0)>(y, m00, m01, m10, m11);
-                            }
-                            break;
-                        case 2:
-                            if constexpr (T >= 3) {
-                                mat_stage<C, T, (T >= 3 ? 2 : 0)>(x, m00, m01, m10, m11);
-                                if constexpr (TWO) mat_stage<C, T, (T >= 3 ? 2 : 0)>(y, m00, m01, m10, m11);
-                            }
-                            break;
-                        default:
-                            if constexpr (T >= 4) {
-                                mat_stage<C, T, (T >= 4 ? 3 : 0)>(x, m00, m01, m10, m11);
-                                if constexpr (TWO) mat_stage<C, T, (T >= 4 ? 3 : 0)>(y, m00, m01, m10, m11);
-                            }
-                            break;
+                        case 0: mat_stage<C, T, 0>(x, m00, m01, m10, m11); break;
+                        case 1: if constexpr (T >= 2) mat_stage<C, T, (T >= 2 ? 1 : 0)>(x, m00, m01, m10, m11); break;
+                        case 2: if constexpr (T >= 3) mat_stage<C, T, (T >= 3 ? 2 : 0)>(x, m00, m01, m10, m11); break;
+                        default: if constexpr (T >= 4) mat_stage<C, T, (T >= 4 ? 3 : 0)>(x, m00, m01, m10, m11); break;
                     }
                 }
             } else {
-                int tb0 = 0, tb1 = 0;
-                for (int j = 0; j < arg; ++j) {
-                    const int db = stg[s].dbits[j];
-                    tb0 |= ((b0 >> db) & 1) << j;
-                    tb1 |= ((b1 >> db) & 1) << j;
-                }
+                int tb0 = 0;
+                for (int j = 0; j < arg; ++j) tb0 |= ((b0 >> stg[s].dbits[j]) & 1) << j;
                 int pm[4];
 #pragma unroll
                 for (int k = 0; k < 4; ++k) pm[k] = stg[s].tpos[k] != 0xFF ? 1 << stg[s].tpos[k] : 0;
@@ -403,7 +401,6 @@ __device__ void tile_pass(const KParams& p, const Chain<R>& ch, const Grp& g, co
                     for (int k = 0; k < T; ++k)
                         if (e & (1 << k)) t |= pm[k];
                     x[e] = cmul(x[e], tab[tb0 | t]);
-                    if constexpr (TWO) y[e] = cmul(y[e], tab[tb1 | t]);
                 }
             }
         }
@@ -413,10 +410,7 @@ __device__ void tile_pass(const KParams& p, const Chain<R>& ch, const Grp& g, co
 #pragma unroll
             for (int k = 0; k < T; ++k)
                 if (e & (1 << k)) o |= msk[k];
-            buf[b0 | o] = x[e];
-            if constexpr (TWO) {
-                if (t1 != t0) buf[b1 | o] = y[e];
-            }
+            acc(b0 | o) = x[e];
         }
     }
 }
@@ -456,30 +450,35 @@ __device__ void flat_pass(const KParams& p, const Chain<R>& ch, const Grp& g, co
 
 template <typename R, int T>
 __device__ __forceinline__ void tile_pass_any(const KParams& p, const Chain<R>& ch, const Grp& g, const DevFused& f,
-                                              int sb, typename CT<R>::T* buf, int W) {
+                                              int sb, typename CT<R>::T* buf, int W, bool dist) {
+    using C = typename CT<R>::T;
     const int ntiles = (1 << W) >> T;
-    if (ntiles < g.nt) {
+    if (dist) {
+        // rank r takes the tiles whose number has r in its top bits: a pass whose
+        // tile bits avoid the rank bits stays inside this CTA's shared memory
+        const int per = ntiles / p.cr;
+        tile_pass<R, T>(p, ch, g, f, sb, DistAcc<C>{ch.rL, ch.L, p.wloc, ch.rank}, ch.rank * per, (ch.rank + 1) * per);
+    } else if (ntiles < g.nt) {
         flat_pass<R>(p, ch, g, f, sb, buf, W);
     } else {
-        // one tile per iteration: pairing tiles forces spills at 128 registers
-        tile_pass<R, T, false>(p, ch, g, f, sb, buf, W);
+        tile_pass<R, T>(p, ch, g, f, sb, LocalAcc<C>{buf}, 0, ntiles);
     }
 }
 
 // Run passes [fb, fe) (their stages start at stage sb0 of the block) on buf.
 template <typename R>
 __device__ void run_passes(const KParams& p, const Chain<R>& ch, const Grp& g, int fb, int fe, int sb0,
-                           typename CT<R>::T* buf, int W) {
+                           typename CT<R>::T* buf, int W, bool dist = false) {
     const DevFused* F = P_<DevFused>(p, p.off.fused);
     for (int fi = fb; fi < fe; ++fi) {
         const DevFused f = F[fi];
         const int sb = f.st_begin - sb0;
         switch (f.ntb) {
-            case 0: tile_pass_any<R, 0>(p, ch, g, f, sb, buf, W); break;
-            case 1: tile_pass_any<R, 1>(p, ch, g, f, sb, buf, W); break;
-            case 2: tile_pass_any<R, 2>(p, ch, g, f, sb, buf, W); break;
-            case 3: tile_pass_any<R, 3>(p, ch, g, f, sb, buf, W); break;
-            default: tile_pass_any<R, 4>(p, ch, g, f, sb, buf, W); break;
+            case 0: tile_pass_any<R, 0>(p, ch, g, f, sb, buf, W, dist); break;
+            case 1: tile_pass_any<R, 1>(p, ch, g, f, sb, buf, W, dist); break;
+            case 2: tile_pass_any<R, 2>(p, ch, g, f, sb, buf, W, dist); break;
+            case 3: tile_pass_any<R, 3>(p, ch, g, f, sb, buf, W, dist); break;
+            default: tile_pass_any<R, 4>(p, ch, g, f, sb, buf, W, dist); break;
         }
         g.sync();
     }
@@ -526,7 +525,7 @@ __device__ void apply_channel(const KParams& p, const Chain<R>& ch, const DevCha
         }
     for (int i = 0; i + 1 < c.k; ++i)
         if (fabs(u * total - row[i]) < 1e-6 * total) {
-            atomicAdd(&p.counters[CNT_NEAR], 1ull);
+            if (ch.rank == 0) atomicAdd(&p.counters[CNT_NEAR], 1ull);
             break;
         }
     const int P1 = p.hdr.P + 1;
@@ -602,7 +601,7 @@ __device__ void build_fslot(const KParams& p, const Chain<R>& ch, const Grp& g, 
 // resampled top with A'_m[s_new][.] before moving to the next site.
 template <typename R>
 __device__ void readout_and_sample(const KParams& p, const Chain<R>& ch, const Grp& g, int m, int k,
-                                   const DevBlockRange& br, uint64_t chain) {
+                                   const DevBlockRange& br, uint64_t chain, bool dist = false) {
     using C = typename CT<R>::T;
     const DevPlanHeader& h = p.hdr;
     const int S = h.S, Wl = S * (m - 1);
@@ -611,41 +610,47 @@ __device__ void readout_and_sample(const KParams& p, const Chain<R>& ch, const G
     const C* Rk = ch.Rt + (size_t)k * NL;
     const C* L = ch.L;
 
-    // 1) rowdot[h] = sum_l L[l*H + h] R_k[l] (coalesced), and max |L|
+    // 1) rowdot[h] = sum_l L[l*H + h] R_k[l] (coalesced), and max |L|. With a
+    //    distributed frontier every CTA sums its own rows l (its share of the
+    //    lower legs); the partial sums are then added across the cluster in
+    //    FP64, in rank order, identically in every CTA.
     R mx = 0;
+    const int NLl = dist ? NL / p.cr : NL;    // rows held by this CTA
+    const int l0 = dist ? ch.rank * NLl : 0;  // first of them
     if (g.nt >= H) {
         const int hh = g.lt & (H - 1), step = g.nt / H;
         C acc[4] = {zero, zero, zero, zero};   // independent chains for latency
         int l = g.lt / H;
-        for (; l + 3 * step < NL; l += 4 * step) {
+        for (; l + 3 * step < NLl; l += 4 * step) {
             C v[4];
 #pragma unroll
             for (int a = 0; a < 4; ++a) v[a] = L[(size_t)(l + a * step) * H + hh];
 #pragma unroll
             for (int a = 0; a < 4; ++a) {
-                acc[a] = cfma(v[a], Rk[l + a * step], acc[a]);
+                acc[a] = cfma(v[a], Rk[l0 + l + a * step], acc[a]);
                 mx = rmax(mx, rmax(rabs(v[a].x), rabs(v[a].y)));
             }
         }
-        for (; l < NL; l += step) {
+        for (; l < NLl; l += step) {
             const C v = L[(size_t)l * H + hh];
-            acc[0] = cfma(v, Rk[l], acc[0]);
+            acc[0] = cfma(v, Rk[l0 + l], acc[0]);
             mx = rmax(mx, rmax(rabs(v.x), rabs(v.y)));
         }
         ch.part[g.lt] = mk<R>(acc[0].x + acc[1].x + acc[2].x + acc[3].x, acc[0].y + acc[1].y + acc[2].y + acc[3].y);
     } else {
         for (int hh = g.lt; hh < H; hh += g.nt) {
             C acc = zero;
-            for (int l = 0; l < NL; ++l) {
+            for (int l = 0; l < NLl; ++l) {
                 const C v = L[(size_t)l * H + hh];
-                acc = cfma(v, Rk[l], acc);
+                acc = cfma(v, Rk[l0 + l], acc);
                 mx = rmax(mx, rmax(rabs(v.x), rabs(v.y)));
             }
             ch.rowdot[hh] = acc;
         }
     }
-    mx = group_max<R>(ch, g, mx);
-    g.sync();
+    const Grp gl{g.lt, g.nt, g.gid, g.tpc, g.warp, false};   // this CTA only
+    mx = group_max<R>(ch, gl, mx);
+    gl.sync();
     if (g.nt >= H && g.lt < H) {
         C acc = zero;
         for (int j = g.lt; j < g.nt; j += H) {
@@ -653,6 +658,24 @@ __device__ void readout_and_sample(const KParams& p, const Chain<R>& ch, const G
             acc.y += ch.part[j].y;
         }
         ch.rowdot[g.lt] = acc;
+    }
+    if (dist) {
+        gl.sync();
+        for (int hh = g.lt; hh < H; hh += g.nt) ch.pd[hh] = make_double2((double)ch.rowdot[hh].x, (double)ch.rowdot[hh].y);
+        if (g.lt == 0) ch.cmax[0] = (float)mx;
+        g.sync();   // cluster: every partial written
+        for (int hh = g.lt; hh < H; hh += g.nt) {
+            double sx = 0.0, sy = 0.0;
+            for (int r = 0; r < p.cr; ++r) {
+                const double2 v = static_cast<const double2*>(__cluster_map_shared_rank(ch.pd, r))[hh];
+                sx += v.x;
+                sy += v.y;
+            }
+            ch.rowdot[hh] = mk<R>((R)sx, (R)sy);
+        }
+        for (int r = 0; r < p.cr; ++r)
+            mx = rmax(mx, (R) static_cast<const float*>(__cluster_map_shared_rank(ch.cmax, r))[0]);
+        g.sync();   // cluster: partials consumed before anyone overwrites them
     }
     const int eL = ch.misc[0];
     const int escale = eL + ch.Rexp[k];
@@ -727,8 +750,10 @@ __device__ void readout_and_sample(const KParams& p, const Chain<R>& ch, const G
                 if (p.mode == MODE_AMP) {
                     if (i == p.amp_pos) {
                         const C a = sold ? amp1 : amp0;
-                        p.amp_out[2 * chain] = ldexp((double)a.x, escale);
-                        p.amp_out[2 * chain + 1] = ldexp((double)a.y, escale);
+                        if (ch.rank == 0) {
+                            p.amp_out[2 * chain] = ldexp((double)a.x, escale);
+                            p.amp_out[2 * chain + 1] = ldexp((double)a.y, escale);
+                        }
                         stop = true;
                     }
                 } else if (mono) {
@@ -736,7 +761,7 @@ __device__ void readout_and_sample(const KParams& p, const Chain<R>& ch, const G
                     const C a0 = sold ? A01 : A00;
                     snew = (a0.x != (R)0 || a0.y != (R)0) ? 0 : 1;
                 } else {
-                    if (p.trace) {
+                    if (p.trace && ch.rank == 0) {
                         double* tr = p.trace + ((size_t)chain * h.n_sampled + row) * 4;
                         tr[0] = ldexp((double)amp0.x, escale);
                         tr[1] = ldexp((double)amp0.y, escale);
@@ -760,8 +785,8 @@ __device__ void readout_and_sample(const KParams& p, const Chain<R>& ch, const G
                         if (Pt > 0.0) {
                             const double up = ch.ud[row] * Pt;
                             snew = up < p0 ? 0 : 1;
-                            if (fabs(up - p0) < 1e-6 * Pt) atomicAdd(&p.counters[CNT_NEAR], 1ull);
-                        } else {
+                            if (fabs(up - p0) < 1e-6 * Pt && ch.rank == 0) atomicAdd(&p.counters[CNT_NEAR], 1ull);
+                        } else if (ch.rank == 0) {
                             atomicAdd(&p.counters[CNT_ZERO], 1ull);   // zero-mass block: stay (Sec. 2)
                         }
                     }
@@ -795,7 +820,7 @@ __device__ void run_chain(const KParams& p, const Chain<R>& ch, int gid, int lt,
     const uint64_t sample_id = p.first + chain;
     const C one = mk<R>(1, 0);
     const DevBlockRange* BR = P_<DevBlockRange>(p, p.off.block_ranges);
-    const Grp G{lt, p.tpc, gid, p.tpc, false};
+    const Grp G{lt, p.tpc, gid, p.tpc, false, false};
     // amplitudes leave the kernel (trace, amplitude mode): keep every scale factor
     const bool exact = p.mode == MODE_AMP || p.trace != nullptr;
 
@@ -834,7 +859,7 @@ __device__ void run_chain(const KParams& p, const Chain<R>& ch, int gid, int lt,
             const double Pt = p0 + p1;
             const double u = draw_u(p.seed, sample_id, (uint32_t)opid[q], 0u);
             ch.s[q] = (u * Pt < p0) ? 0 : 1;
-            if (fabs(u * Pt - p0) < 1e-6 * Pt) atomicAdd(&p.counters[CNT_NEAR], 1ull);
+            if (fabs(u * Pt - p0) < 1e-6 * Pt && ch.rank == 0) atomicAdd(&p.counters[CNT_NEAR], 1ull);
         }
     }
     G.sync();
@@ -872,8 +897,9 @@ __device__ void run_chain(const KParams& p, const Chain<R>& ch, int gid, int lt,
         const int kstop = p.mode == MODE_AMP ? p.amp_block : 0;   // R_k needed for k >= kstop
         // small tensors run on the first warp only
         const int w32 = p.tpc < 32 ? p.tpc : 32;
-        const Grp GB{lt, NL <= 1024 ? w32 : p.tpc, gid, p.tpc, NL <= 1024 && p.tpc > 32};
-        const Grp GF{lt, N <= 1024 ? w32 : p.tpc, gid, p.tpc, N <= 1024 && p.tpc > 32};
+        const bool dist = p.cr > 1 && W > p.wloc;   // frontier spread over the cluster
+        const Grp GB{lt, NL <= 1024 ? w32 : p.tpc, gid, p.tpc, NL <= 1024 && p.tpc > 32, false};
+        const Grp GF{lt, (N <= 1024 && !dist) ? w32 : p.tpc, gid, p.tpc, N <= 1024 && p.tpc > 32 && !dist, dist};
 
         // backward sweep: R_{K-1} = 1, R_{k-1} from R_k by block k's reversed
         // program. For m = 1 the environments are scalars (no summed segment on
@@ -915,7 +941,8 @@ __device__ void run_chain(const KParams& p, const Chain<R>& ch, int gid, int lt,
 
         // forward sweep with a readout after every block
         if (lt < GF.nt) {
-            for (int i = lt; i < N; i += GF.nt) ch.L[i] = mk<R>(i == 0 ? 1 : 0, 0);
+            const int Nl = dist ? (1 << p.wloc) : N;   // entries held by this CTA
+            for (int i = lt; i < Nl; i += GF.nt) ch.L[i] = mk<R>(i == 0 && (!dist || ch.rank == 0) ? 1 : 0, 0);
             if (lt == 0) {
                 ch.misc[0] = 0;
                 ch.misc[1] = 0;
@@ -928,8 +955,8 @@ __device__ void run_chain(const KParams& p, const Chain<R>& ch, int gid, int lt,
                 build_tables<R>(p, ch, GF, br.fwd_st, br.fwd_nst, br.fwd_tab, pend, exact);
                 build_fslot<R>(p, ch, GF, m, br);
                 GF.sync();
-                run_passes<R>(p, ch, GF, br.fwd_begin, br.fwd_end, br.fwd_st, ch.L, W);
-                readout_and_sample<R>(p, ch, GF, m, k, br, chain);
+                run_passes<R>(p, ch, GF, br.fwd_begin, br.fwd_end, br.fwd_st, ch.L, W, dist);
+                readout_and_sample<R>(p, ch, GF, m, k, br, chain, dist);
             }
         }
         G.sync();
@@ -947,7 +974,7 @@ __device__ void run_chain(const KParams& p, const Chain<R>& ch, int gid, int lt,
     }
     G.sync();
     // sample = s XOR x (Alg. 2), packed 64 qubits per word
-    for (int w = lt; w < h.words; w += p.tpc) {
+    for (int w = lt; w < h.words && ch.rank == 0; w += p.tpc) {
         uint64_t v = 0;
         for (int b = 0; b < 64 && w * 64 + b < n; ++b) v |= (uint64_t)(ch.s[w * 64 + b] ^ ch.x[w * 64 + b]) << b;
         p.out_bits[chain * h.words + w] = v;
@@ -981,6 +1008,22 @@ __global__ void __launch_bounds__(256, 2) pw_chain_kernel(const KParams p) {
     ch.gframe = g + p.sm.gframe;
     ch.segfac = reinterpret_cast<C*>(g + p.sm.segfac);
     ch.misc = reinterpret_cast<int*>(g + p.sm.misc);
+    ch.pd = reinterpret_cast<double2*>(g + p.sm.pd);
+    ch.rL = reinterpret_cast<C**>(g + p.sm.rlp);
+    ch.cmax = reinterpret_cast<float*>(g + p.sm.cmax);
+    if (p.cr > 1) {
+        // one chain per cluster of p.cr CTAs (gpc == 1): every CTA keeps a copy
+        // of the chain's small state and 1/cr of the frontier
+        ch.rank = (int)__clusterRelativeBlockRank();
+        if (lt < p.cr) ch.rL[lt] = static_cast<C*>(__cluster_map_shared_rank(ch.L, lt));
+        asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+        for (uint64_t chain = blockIdx.x / p.cr; chain < p.count; chain += gridDim.x / p.cr)
+            run_chain<R>(p, ch, 0, lt, chain);
+        // no CTA leaves while a peer may still read its shared memory
+        asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+        return;
+    }
+    ch.rank = 0;
     for (uint64_t chain = (uint64_t)blockIdx.x * p.gpc + gid; chain < p.count;
          chain += (uint64_t)gridDim.x * p.gpc)
         run_chain<R>(p, ch, gid, lt, chain);
@@ -1063,12 +1106,60 @@ template <typename R> int launch(pw_plan* plan, KParams& kp, cudaStream_t st, ui
     if (kp.sm.group_bytes > maxsm)
         return set_error(PW_ERR_TOO_LARGE, "per-chain shared memory (" + std::to_string(kp.sm.group_bytes) +
                                                " B) exceeds 227 KB");
+    auto kern = pw_chain_kernel<R>;
+    cudaError_t e;
+    if (hp.ctas_per_chain > 1) {
+        // one chain per thread-block cluster
+        kp.cr = hp.ctas_per_chain;
+        kp.wloc = hp.wloc;
+        kp.gpc = 1;
+        const size_t smem = (size_t)kp.sm.group_bytes;
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = (unsigned)kp.cr;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.blockDim = dim3((unsigned)kp.tpc);
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = st;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        cfg.gridDim = dim3((unsigned)kp.cr);
+        int maxc = 0;
+        e = cudaOccupancyMaxActiveClusters(&maxc, kern, &cfg);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveClusters");
+        if (maxc < 1) return set_error(PW_ERR_TOO_LARGE, "no cluster of this size fits on the device");
+        const uint64_t per_launch = hp.chains_per_launch > 0 ? (uint64_t)hp.chains_per_launch : kp.count;
+        const uint64_t total = kp.count, first0 = kp.first;
+        uint64_t* out0 = kp.out_bits;
+        double* tr0 = kp.trace;
+        const uint64_t* in0 = kp.in_bits;
+        double* amp0 = kp.amp_out;
+        for (uint64_t done = 0; done < total; done += per_launch) {
+            const uint64_t cnt = std::min(per_launch, total - done);
+            kp.count = cnt;
+            kp.first = first0 + done;
+            kp.out_bits = out0 ? out0 + done * hp.hdr.words : nullptr;
+            kp.trace = tr0 ? tr0 + done * (uint64_t)hp.hdr.n_sampled * 4 : nullptr;
+            kp.in_bits = in0 ? in0 + done * hp.hdr.words : nullptr;
+            kp.amp_out = amp0 ? amp0 + 2 * done : nullptr;
+            cfg.gridDim = dim3((unsigned)(std::min<uint64_t>(cnt, (uint64_t)maxc) * kp.cr));
+            e = cudaLaunchKernelEx(&cfg, kern, kp);
+            if (e != cudaSuccess) return cuda_fail(e, "cluster kernel launch");
+            if (launches) ++*launches;
+        }
+        return PW_OK;
+    }
+    kp.cr = 1;
+    kp.wloc = 0;
     const int gpc = groups_per_cta(kp.tpc, kp.sm.group_bytes);
     kp.gpc = gpc;
     const int threads = kp.tpc * gpc;
     const size_t smem = (size_t)kp.sm.group_bytes * gpc;
-    auto kern = pw_chain_kernel<R>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
     int dev = plan->device, nsm = 0, occ = 0;
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
@@ -1297,6 +1388,8 @@ extern "C" int pw_sample_static(const pw_plan* plan, uint64_t seed, uint64_t fir
     if (stats) std::memset(stats, 0, sizeof(*stats));
     if (n_samples == 0) return PW_OK;
     const HostPlan& hp = plan->hp;
+    if (hp.ctas_per_chain > 1)
+        return set_error(PW_ERR_UNSUPPORTED, "pw_sample_static runs plans of one CTA per chain only");
     DevPlanOffsets off{};
     const std::vector<unsigned char> blob = make_blob(hp, off);
     if (blob.size() > kStaticScratchBytes - kStaticCounterBytes)
@@ -1325,6 +1418,7 @@ extern "C" int pw_sample_static(const pw_plan* plan, uint64_t seed, uint64_t fir
     kp.count = n_samples;
     kp.out_bits = d_out_bits;
     kp.mode = MODE_SAMPLE;
+    kp.cr = 1;
     uint64_t launches = 0;
     rc = hp.precision == PW_PREC_FP64 ? launch_static<double>(hp, dev, kp, st, &launches)
                                       : launch_static<float>(hp, dev, kp, st, &launches);

@@ -9,7 +9,7 @@
 namespace pw {
 
 struct SmemLayout {
-    int L, R, Rexp, rowdot, T, tab, stg, ud, uf, part, fslot, red, s, x, xmix, gframe, segfac, misc, group_bytes;
+    int L, R, Rexp, rowdot, T, tab, stg, ud, uf, pd, cmax, rlp, part, fslot, red, s, x, xmix, gframe, segfac, misc, group_bytes;
 };
 
 inline size_t align16(size_t v) { return (v + 15) & ~(size_t)15; }
@@ -25,7 +25,7 @@ inline SmemLayout make_layout(const HostPlan& hp, size_t csz) {
         return (int)at;
     };
     const int S = h.S, P = std::max(h.P, 1), K = std::max(h.K, 1);
-    L.L = take(csz << (S * P));                        // frontier tensor
+    L.L = take(hp.ctas_per_chain > 1 ? csz << hp.wloc : csz << (S * P));   // frontier tensor (this CTA's part)
     L.R = take((size_t)K * (csz << (S * (P - 1))));    // right environments
     L.Rexp = take(sizeof(int) * K);
     L.rowdot = take(csz << S);
@@ -34,6 +34,9 @@ inline SmemLayout make_layout(const HostPlan& hp, size_t csz) {
     L.stg = take(sizeof(DevStage) * (size_t)std::max(1, h.max_stages));
     L.ud = take(sizeof(double) * (size_t)std::max(1, h.n_sampled));
     L.uf = take(sizeof(float) * (size_t)std::max(1, h.n_sampled));
+    L.pd = take(hp.ctas_per_chain > 1 ? (size_t)16 << S : 16);   // FP64 partial readout sums
+    L.cmax = take(16);
+    L.rlp = take(16 * sizeof(void*));   // the cluster ranks' frontier parts
     L.part = take(csz * (size_t)std::max(64, hp.threads_per_chain));   // also the resampling scratch (4 per site)
     L.fslot = take(csz * 2 * S);
     L.red = take((csz / 2) * 32);

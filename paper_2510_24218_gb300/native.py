@@ -33,7 +33,7 @@ class PwError(RuntimeError):
 class PlanOpts(C.Structure):
     _fields_ = [("precision", C.c_int), ("order", C.c_int), ("max_block", C.c_int),
                 ("threads_per_chain", C.c_int), ("chains_per_launch", C.c_int),
-                ("reserved", C.c_int * 7)]
+                ("ctas_per_chain", C.c_int), ("reserved", C.c_int * 6)]
 
 
 class PlanStats(C.Structure):
@@ -42,7 +42,7 @@ class PlanStats(C.Structure):
                 ("sampled_gates", C.c_int), ("threads_per_chain", C.c_int), ("chains_per_cta", C.c_int),
                 ("smem_bytes_per_cta", C.c_int), ("noisy", C.c_int), ("flops_per_sample", C.c_double),
                 ("amps_per_sample", C.c_double),
-                ("device_bytes", C.c_double)]
+                ("device_bytes", C.c_double), ("ctas_per_chain", C.c_int)]
 
 
 class RunStats(C.Structure):
@@ -164,10 +164,11 @@ def pw_circuit_destroy(circ):
 # --------------------------------------------------------------------- plan
 
 def pw_plan_build(circ, precision=PW_PREC_FP32, order=PW_ORDER_AUTO, max_block=0, threads_per_chain=0,
-                  chains_per_launch=0):
+                  chains_per_launch=0, ctas_per_chain=0):
     o = PlanOpts()
     o.precision, o.order, o.max_block = precision, order, max_block
     o.threads_per_chain, o.chains_per_launch = threads_per_chain, chains_per_launch
+    o.ctas_per_chain = ctas_per_chain
     h = C.c_void_p()
     _check(load_library().pw_plan_build(circ, C.byref(o), C.byref(h)))
     return h
