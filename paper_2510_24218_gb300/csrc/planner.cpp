@@ -452,6 +452,67 @@ void push_var(HostPlan& hp, cd v) {
     hp.vtab_f.push_back((float)v.imag());
 }
 
+// Group the items of every cost section into waves. Per qubit there are two
+// resources: its frame bit x (read by every item on the qubit, written by a
+// channel) and its one-qubit factor of the segment (written by one-qubit
+// gates and channels). An item goes one wave after the last writer of what it
+// reads and after the last reader or writer of what it writes (a factor is
+// only read by its own read-modify-write); within a wave the circuit order is
+// kept.
+void build_cost_waves(HostPlan& hp, int n, int P) {
+    hp.cost_waves.clear();
+    hp.cost_wave_ranges.assign(P + 3, 0);
+    for (int m = 1; m <= P + 1; ++m) {
+        hp.cost_wave_ranges[m] = (int)hp.cost_waves.size();
+        const int b = hp.cost_ranges[m], e = hp.cost_ranges[m + 1];
+        std::vector<int> wx(n, -1), rx(n, -1), wf(n, -1);
+        std::vector<int> wave(e - b);
+        int nw = 0;
+        for (int it = b; it < e; ++it) {
+            const DevCostItem ci = hp.cost_items[it];
+            int qs[2], nq = 0;
+            bool writes_x = false, writes_f = false;
+            if (ci.kind == CI_CHANNEL) {
+                const DevChannel& c = hp.channels[ci.idx];
+                for (int i = 0; i < c.nq; ++i) qs[nq++] = c.q[i];
+                writes_x = writes_f = true;
+            } else {
+                const DevCostGate& g = hp.cost_gates[ci.idx];
+                qs[nq++] = g.q0;
+                if (g.q1 >= 0) qs[nq++] = g.q1;
+                writes_f = ci.kind == CI_GATE1;
+            }
+            int w = 0;
+            for (int i = 0; i < nq; ++i) {
+                const int q = qs[i];
+                w = std::max(w, wx[q] + 1);
+                if (writes_x) w = std::max(w, rx[q] + 1);
+                if (writes_f) w = std::max(w, wf[q] + 1);
+            }
+            for (int i = 0; i < nq; ++i) {
+                const int q = qs[i];
+                rx[q] = std::max(rx[q], w);
+                if (writes_x) wx[q] = w;
+                if (writes_f) wf[q] = w;
+            }
+            wave[it - b] = w;
+            nw = std::max(nw, w + 1);
+        }
+        std::vector<int> idx(e - b);
+        std::iota(idx.begin(), idx.end(), 0);
+        std::stable_sort(idx.begin(), idx.end(), [&](int x, int y) { return wave[x] < wave[y]; });
+        std::vector<DevCostItem> sorted(e - b);
+        for (int i = 0; i < e - b; ++i) sorted[i] = hp.cost_items[b + idx[i]];
+        std::copy(sorted.begin(), sorted.end(), hp.cost_items.begin() + b);
+        for (int w = 0, i = 0; w < nw; ++w) {
+            hp.cost_waves.push_back(b + i);
+            while (i < e - b && wave[idx[i]] == w) ++i;
+        }
+    }
+    hp.cost_wave_ranges[P + 2] = (int)hp.cost_waves.size();
+    hp.cost_waves.push_back((int)hp.cost_items.size());
+}
+
 void precompute_tables(HostPlan& hp) {
     const int n = hp.hdr.n, P = hp.hdr.P;
     HostEval ev{hp, std::vector<cd>((size_t)n * (P + 1) * 2, cd(1.0)), n, P, nullptr, 0};
@@ -681,6 +742,7 @@ int build_plan(const pw_circuit* c, const pw_plan_opts& opts, HostPlan& hp) {
     }
     hp.cost_ranges[P + 2] = (int)hp.cost_items.size();
     hp.noisy = has_frame;
+    build_cost_waves(hp, n, P);
 
     // ------------------------------------------------ sweep order and blocks
     std::vector<int> order(n);

@@ -113,7 +113,10 @@ struct alignas(16) DevCostGate {
 static_assert(offsetof(DevCostGate, d) % 16 == 0 && offsetof(DevCostGate, f) % 8 == 0, "vector loads");
 static_assert(sizeof(DevCostGate) % 16 == 0, "array stride keeps d aligned");
 
-// Items of a cost section, processed in circuit order by one thread per chain.
+// Items of a cost section. Within a section they are grouped into waves: the
+// items of one wave touch disjoint frame bits and one-qubit factors, so the
+// kernel runs a wave in parallel; waves run in order, and every item comes
+// after the items it depends on (same result as circuit order).
 enum CostItemKind : int16_t { CI_GATE2 = 0, CI_GATE1 = 1, CI_CHANNEL = 2 };
 struct DevCostItem {
     int16_t kind;
@@ -187,7 +190,8 @@ struct DevPlanHeader {
 
 // Offsets (in bytes) of the arrays inside the device blob.
 struct DevPlanOffsets {
-    int64_t micro, fused, stages, row_opid, vtab_f, vtab_d, gate_refs, cost_gates, cost_items, cost_ranges, channels, cum, factors;
+    int64_t micro, fused, stages, row_opid, vtab_f, vtab_d, gate_refs, cost_gates, cost_items, cost_ranges, cost_waves, cost_wave_ranges, channels, cum,
+        factors;
     int64_t mix_d, mix_f, mix0_order, mix0_opid, mix_mono;
     int64_t block_ranges, block_sites, live_slots;
 };
@@ -214,6 +218,8 @@ struct HostPlan {
     std::vector<DevCostGate> cost_gates;
     std::vector<DevCostItem> cost_items;
     std::vector<int32_t> cost_ranges;      // [P+2]: items of section m in [r[m], r[m+1]) (m = 1..P+1 used)
+    std::vector<int32_t> cost_waves;       // first item of every wave, then the item count
+    std::vector<int32_t> cost_wave_ranges; // [P+3]: waves of section m in [w[m], w[m+1])
     std::vector<DevChannel> channels;
     std::vector<double> cum;
     std::vector<DevKrausFactor> factors;

@@ -142,6 +142,7 @@ template <typename R> struct Chain {
     C* Rt;        // right environments, K x 2^Wl
     int* Rexp;    // their power-of-two exponents
     C* rowdot;    // 2^S
+    C* wt;        // readout slot weights: products over the low S/2 and the high S - S/2 slots
     C* T;         // 2^max_block
     C* tab;       // tables of one block program
     DevStage* stg;    // stage descriptors of one block program
@@ -648,6 +649,18 @@ __device__ void readout_and_sample(const KParams& p, const Chain<R>& ch, const G
             ch.rowdot[hh] = acc;
         }
     }
+    // The readout weight of a top configuration hv is the product over the S
+    // slots of fslot[slot][bit]; it factorises into a product over the low S/2
+    // slots and one over the rest, tabulated here (fslot is final since the
+    // block's passes began).
+    const int Sa = S >> 1, Na = 1 << Sa, Nw = Na + (1 << (S - Sa));
+    for (int e = g.lt; e < Nw; e += g.nt) {
+        const bool lo = e < Na;
+        const int v = lo ? e : e - Na, j0 = lo ? 0 : Sa, j1 = lo ? Sa : S;
+        C w = one;
+        for (int j = j0; j < j1; ++j) w = cmul(w, ch.fslot[2 * j + ((v >> (j - j0)) & 1)]);
+        ch.wt[e] = w;
+    }
     const Grp gl{g.lt, g.nt, g.gid, g.tpc, g.warp, false};   // this CTA only
     mx = group_max<R>(ch, gl, mx);
     gl.sync();
@@ -691,25 +704,45 @@ __device__ void readout_and_sample(const KParams& p, const Chain<R>& ch, const G
         return;
     }
 
-    // 2) collapse onto the block's tops: T[t], bit i of t = top of block site i
+    // 2) collapse onto the block's tops: T[t] = sum over the other top slots
+    //    of rowdot[hv] times the weight of hv, bit i of t = top of block site i.
+    //    Work item u = (bin t, chunk c): the chunk fixes the lowest cb of the
+    //    other slots' bits and enumerates the rest (subset walk of mask mh).
+    //    With several chunks per bin the partials go to part[] and the
+    //    resampling warp adds them in chunk order.
     const DevBlockSite* sites = P_<DevBlockSite>(p, p.off.block_sites) + br.site_begin;
     const int nb = br.site_end - br.site_begin;
+    const int NT = 1 << nb;
+    int cb = 31 - __clz(g.nt) - nb;
+    cb = cb < 0 ? 0 : (cb > S - nb ? S - nb : cb);
+    const int ncb = 1 << cb;
     {
-        const int rmask = br.rmask;
-        const int NT = 1 << nb, nother = S - nb;
-        for (int t = g.lt; t < NT; t += g.nt) {
-            int hbase = 0;
-            for (int i = 0; i < nb; ++i) hbase |= ((t >> i) & 1) << br.rslot[i];
-            C acc = zero;
-            for (int hh = 0; hh < (1 << nother); ++hh) {
-                int hv = hbase, bit = 0;
-                for (int j = 0; j < S; ++j)
-                    if (!((rmask >> j) & 1)) hv |= ((hh >> bit++) & 1) << j;
-                C wgt = one;
-                for (int j = 0; j < S; ++j) wgt = cmul(wgt, ch.fslot[2 * j + ((hv >> j) & 1)]);
-                acc = cfma(ch.rowdot[hv], wgt, acc);
+        int mh = ~br.rmask & (H - 1), mc = 0;
+        for (int b = 0; b < cb; ++b) {
+            const int low = mh & -mh;
+            mc |= low;
+            mh ^= low;
+        }
+        for (int u = g.lt; u < NT * ncb; u += g.nt) {
+            const int t = u & (NT - 1), c = u >> nb;
+            int base = 0;
+            for (int i = 0; i < nb; ++i) base |= ((t >> i) & 1) << br.rslot[i];
+            for (int b = 0, mm = mc; b < cb; ++b) {
+                const int low = mm & -mm;
+                if ((c >> b) & 1) base |= low;
+                mm ^= low;
             }
-            ch.T[t] = acc;
+            C acc = zero;
+            int xh = 0;
+            do {
+                const int hv = base | xh;
+                acc = cfma(ch.rowdot[hv], cmul(ch.wt[hv & (Na - 1)], ch.wt[Na + (hv >> Sa)]), acc);
+                xh = (xh - mh) & mh;
+            } while (xh != 0);
+            if (ncb == 1)
+                ch.T[t] = acc;
+            else
+                ch.part[u] = acc;
         }
     }
     g.sync();
@@ -722,6 +755,17 @@ __device__ void readout_and_sample(const KParams& p, const Chain<R>& ch, const G
     const int wsz = g.nt < 32 ? g.nt : 32;
     if (g.lt < wsz) {
         const int lane = g.lt;
+        if (ncb > 1) {
+            for (int t = lane; t < NT; t += wsz) {
+                C a = ch.part[t];
+                for (int c = 1; c < ncb; ++c) {
+                    a.x += ch.part[t + c * NT].x;
+                    a.y += ch.part[t + c * NT].y;
+                }
+                ch.T[t] = a;
+            }
+            __syncwarp();
+        }
         C* sa = ch.part;   // site i's mixer A'_m at sa[4i .. 4i+3]
         for (int i = lane; i < nb; i += wsz) {
             const int q = sites[i].q;
@@ -811,6 +855,38 @@ __device__ void readout_and_sample(const KParams& p, const Chain<R>& ch, const G
     g.sync();
 }
 
+// Cost section m (1..P+1), one wave after the other: the frame bits of the
+// diagonal gates at their time, the one-qubit diagonal factors of segment m-1
+// and the Kraus draws of the channels (Eq. 5; the channels after the last
+// layer act on segment P). The items of a wave touch disjoint qubits and run
+// in parallel over the group.
+template <typename R>
+__device__ void cost_section(const KParams& p, const Chain<R>& ch, const Grp& G, int m, uint64_t sample_id) {
+    using C = typename CT<R>::T;
+    const int P1 = p.hdr.P + 1;
+    const int32_t* wr = P_<int32_t>(p, p.off.cost_wave_ranges);
+    const int32_t* wv = P_<int32_t>(p, p.off.cost_waves);
+    const DevCostItem* items = P_<DevCostItem>(p, p.off.cost_items);
+    const DevCostGate* CG = P_<DevCostGate>(p, p.off.cost_gates);
+    for (int w = wr[m]; w < wr[m + 1]; ++w) {
+        for (int it = wv[w] + G.lt; it < wv[w + 1]; it += G.nt) {
+            const DevCostItem ci = items[it];
+            if (ci.kind == CI_GATE2) {
+                ch.gframe[ci.idx] = (uint8_t)(ch.x[CG[ci.idx].q0] | (ch.x[CG[ci.idx].q1] << 1));
+            } else if (ci.kind == CI_GATE1) {
+                const int q = CG[ci.idx].q0, xb = ch.x[q];
+                C* sf = ch.segfac + ((size_t)q * P1 + (m - 1)) * 2;
+                sf[0] = cmul(sf[0], mk<R>((R)CG[ci.idx].d[2 * xb], (R)CG[ci.idx].d[2 * xb + 1]));
+                sf[1] = cmul(sf[1], mk<R>((R)CG[ci.idx].d[2 * (1 ^ xb)], (R)CG[ci.idx].d[2 * (1 ^ xb) + 1]));
+            } else if (p.mode == MODE_SAMPLE) {
+                apply_channel<R>(p, ch, P_<DevChannel>(p, p.off.channels)[ci.idx], P_<double>(p, p.off.cum),
+                                 P_<DevKrausFactor>(p, p.off.factors), sample_id, m - 1);
+            }
+        }
+        G.sync();
+    }
+}
+
 // ---------------------------------------------------------------- chain
 template <typename R>
 __device__ void run_chain(const KParams& p, const Chain<R>& ch, int gid, int lt, uint64_t chain) {
@@ -866,28 +942,10 @@ __device__ void run_chain(const KParams& p, const Chain<R>& ch, int gid, int lt,
 
     const int mhi = p.mode == MODE_AMP ? p.amp_layer : P;
     for (int m = 1; m <= mhi; ++m) {
-        // cost section m: frame bits of the diagonal gates at their time, the
-        // one-qubit diagonal factors of segment m-1, and the Kraus draws.
-        if (lt == 0 && (h.has_segfac || h.has_frame)) {
-            const int32_t* cr = P_<int32_t>(p, p.off.cost_ranges);
-            const DevCostItem* items = P_<DevCostItem>(p, p.off.cost_items);
-            const DevCostGate* CG = P_<DevCostGate>(p, p.off.cost_gates);
-            for (int it = cr[m]; it < cr[m + 1]; ++it) {
-                const DevCostItem ci = items[it];
-                if (ci.kind == CI_GATE2) {
-                    ch.gframe[ci.idx] = (uint8_t)(ch.x[CG[ci.idx].q0] | (ch.x[CG[ci.idx].q1] << 1));
-                } else if (ci.kind == CI_GATE1) {
-                    const int q = CG[ci.idx].q0, xb = ch.x[q];
-                    C* sf = ch.segfac + ((size_t)q * (P + 1) + (m - 1)) * 2;
-                    sf[0] = cmul(sf[0], mk<R>((R)CG[ci.idx].d[2 * xb], (R)CG[ci.idx].d[2 * xb + 1]));
-                    sf[1] = cmul(sf[1], mk<R>((R)CG[ci.idx].d[2 * (1 ^ xb)], (R)CG[ci.idx].d[2 * (1 ^ xb) + 1]));
-                } else if (p.mode == MODE_SAMPLE) {
-                    apply_channel<R>(p, ch, P_<DevChannel>(p, p.off.channels)[ci.idx], P_<double>(p, p.off.cum),
-                                     P_<DevKrausFactor>(p, p.off.factors), sample_id, m - 1);
-                }
-            }
+        if (h.has_segfac || h.has_frame) {
+            cost_section<R>(p, ch, G, m, sample_id);
             if (h.has_frame)
-                for (int q = 0; q < n; ++q) ch.xmix[m * n + q] = ch.x[q];
+                for (int q = lt; q < n; q += p.tpc) ch.xmix[m * n + q] = ch.x[q];
         }
         G.sync();
         if (p.mode == MODE_AMP && m < p.amp_layer) continue;
@@ -964,14 +1022,7 @@ __device__ void run_chain(const KParams& p, const Chain<R>& ch, int gid, int lt,
     if (p.mode == MODE_AMP) return;
 
     // channels after the last layer (they can only move the frame)
-    if (lt == 0 && h.has_frame) {
-        const int32_t* cr = P_<int32_t>(p, p.off.cost_ranges);
-        const DevCostItem* items = P_<DevCostItem>(p, p.off.cost_items);
-        for (int it = cr[P + 1]; it < cr[P + 2]; ++it)
-            if (items[it].kind == CI_CHANNEL)
-                apply_channel<R>(p, ch, P_<DevChannel>(p, p.off.channels)[items[it].idx], P_<double>(p, p.off.cum),
-                                 P_<DevKrausFactor>(p, p.off.factors), sample_id, P);
-    }
+    if (h.has_frame) cost_section<R>(p, ch, G, P + 1, sample_id);
     G.sync();
     // sample = s XOR x (Alg. 2), packed 64 qubits per word
     for (int w = lt; w < h.words && ch.rank == 0; w += p.tpc) {
@@ -994,6 +1045,7 @@ __global__ void __launch_bounds__(256, 2) pw_chain_kernel(const KParams p) {
     ch.Rt = reinterpret_cast<C*>(g + p.sm.R);
     ch.Rexp = reinterpret_cast<int*>(g + p.sm.Rexp);
     ch.rowdot = reinterpret_cast<C*>(g + p.sm.rowdot);
+    ch.wt = reinterpret_cast<C*>(g + p.sm.wt);
     ch.T = reinterpret_cast<C*>(g + p.sm.T);
     ch.tab = reinterpret_cast<C*>(g + p.sm.tab);
     ch.stg = reinterpret_cast<DevStage*>(g + p.sm.stg);
@@ -1055,6 +1107,8 @@ std::vector<unsigned char> make_blob(const HostPlan& hp, DevPlanOffsets& o) {
     put(blob, o.cost_gates, hp.cost_gates);
     put(blob, o.cost_items, hp.cost_items);
     put(blob, o.cost_ranges, hp.cost_ranges);
+    put(blob, o.cost_waves, hp.cost_waves);
+    put(blob, o.cost_wave_ranges, hp.cost_wave_ranges);
     put(blob, o.channels, hp.channels);
     put(blob, o.cum, hp.cum);
     put(blob, o.factors, hp.factors);
