@@ -270,8 +270,14 @@ __device__ void build_tables(const KParams& p, const Chain<R>& ch, const Grp& g,
     const DevMicroOp* ops = P_<DevMicroOp>(p, p.off.micro);
     for (int i = g.lt; i < ns; i += g.nt) ch.stg[i] = ST[i];
     for (int ef = g.lt; ef < ntab; ef += g.nt) {
-        int si = 0;
-        while (si + 1 < ns && ST[si + 1].tab_off <= ef) ++si;
+        int si = 0;   // last stage with tab_off <= ef (offsets ascend)
+        for (int hi = ns - 1; si < hi;) {
+            const int mid = (si + hi + 1) >> 1;
+            if (ST[mid].tab_off <= ef)
+                si = mid;
+            else
+                hi = mid - 1;
+        }
         const DevStage st = ST[si];
         const int e = ef - st.tab_off;
         C v;
@@ -325,18 +331,24 @@ __device__ __forceinline__ void mat_stage(C (&x)[1 << T], C m00, C m01, C m10, C
     }
 }
 
+// Shared-memory position of frontier / environment entry i: bits 4..7 of i
+// are XORed into bits 0..3, so that warps striding over low index bits (a
+// pass whose tile bits include them) spread over the banks. A bijection on
+// [0, 2^W) for every W; entry 0 stays at position 0.
+__device__ __forceinline__ int swz(int i) { return i ^ ((i >> 4) & 15); }
+
 // Frontier access: a CTA's own shared memory, or the parts held by the CTAs of
 // a cluster (entry idx in rank idx >> wloc at offset idx & (2^wloc - 1)).
 template <typename C> struct LocalAcc {
     C* buf;
-    __device__ __forceinline__ C& operator()(int idx) const { return buf[idx]; }
+    __device__ __forceinline__ C& operator()(int idx) const { return buf[swz(idx)]; }
 };
 template <typename C> struct DistAcc {
     C* const* rl;   // every rank's part (a table in shared memory)
     C* loc;         // this CTA's part
     int wloc, rank;
     __device__ __forceinline__ C& operator()(int idx) const {
-        const int r = idx >> wloc, o = idx & ((1 << wloc) - 1);
+        const int r = idx >> wloc, o = swz(idx & ((1 << wloc) - 1));
         return r == rank ? loc[o] : rl[r][o];
     }
 };
@@ -433,16 +445,16 @@ __device__ void flat_pass(const KParams& p, const Chain<R>& ch, const Grp& g, co
             const C m00 = tab[0], m01 = tab[1], m10 = tab[2], m11 = tab[3];
             for (int pi = g.lt; pi < (N >> 1); pi += g.nt) {
                 const int i0 = ((pi >> bt) << (bt + 1)) | (pi & ((1 << bt) - 1));
-                const int i1 = i0 | (1 << bt);
-                const C x0 = buf[i0], x1 = buf[i1];
-                buf[i0] = cfma(m00, x0, cmul(m01, x1));
+                const int i1 = swz(i0 | (1 << bt)), j0 = swz(i0);
+                const C x0 = buf[j0], x1 = buf[i1];
+                buf[j0] = cfma(m00, x0, cmul(m01, x1));
                 buf[i1] = cfma(m10, x0, cmul(m11, x1));
             }
         } else {
             for (int idx = g.lt; idx < N; idx += g.nt) {
                 int t = 0;
                 for (int j = 0; j < arg; ++j) t |= ((idx >> stg[s].dbits[j]) & 1) << j;
-                buf[idx] = cmul(buf[idx], tab[t]);
+                buf[swz(idx)] = cmul(buf[swz(idx)], tab[t]);
             }
         }
         if (s + 1 < f.nst) g.sync();
@@ -625,16 +637,16 @@ __device__ void readout_and_sample(const KParams& p, const Chain<R>& ch, const G
         for (; l + 3 * step < NLl; l += 4 * step) {
             C v[4];
 #pragma unroll
-            for (int a = 0; a < 4; ++a) v[a] = L[(size_t)(l + a * step) * H + hh];
+            for (int a = 0; a < 4; ++a) v[a] = L[swz((l + a * step) * H + hh)];
 #pragma unroll
             for (int a = 0; a < 4; ++a) {
-                acc[a] = cfma(v[a], Rk[l0 + l + a * step], acc[a]);
+                acc[a] = cfma(v[a], Rk[swz(l0 + l + a * step)], acc[a]);
                 mx = rmax(mx, rmax(rabs(v[a].x), rabs(v[a].y)));
             }
         }
         for (; l < NLl; l += step) {
-            const C v = L[(size_t)l * H + hh];
-            acc[0] = cfma(v, Rk[l0 + l], acc[0]);
+            const C v = L[swz(l * H + hh)];
+            acc[0] = cfma(v, Rk[swz(l0 + l)], acc[0]);
             mx = rmax(mx, rmax(rabs(v.x), rabs(v.y)));
         }
         ch.part[g.lt] = mk<R>(acc[0].x + acc[1].x + acc[2].x + acc[3].x, acc[0].y + acc[1].y + acc[2].y + acc[3].y);
@@ -642,8 +654,8 @@ __device__ void readout_and_sample(const KParams& p, const Chain<R>& ch, const G
         for (int hh = g.lt; hh < H; hh += g.nt) {
             C acc = zero;
             for (int l = 0; l < NLl; ++l) {
-                const C v = L[(size_t)l * H + hh];
-                acc = cfma(v, Rk[l0 + l], acc);
+                const C v = L[swz(l * H + hh)];
+                acc = cfma(v, Rk[swz(l0 + l)], acc);
                 mx = rmax(mx, rmax(rabs(v.x), rabs(v.y)));
             }
             ch.rowdot[hh] = acc;
@@ -767,16 +779,24 @@ __device__ void readout_and_sample(const KParams& p, const Chain<R>& ch, const G
             __syncwarp();
         }
         C* sa = ch.part;   // site i's mixer A'_m at sa[4i .. 4i+3]
+        // then the sites' qubit, trace row and monomial flag (a block has at
+        // most 10 sites: 40 complex + 30 ints fit the 64-entry scratch)
+        int* sq = reinterpret_cast<int*>(sa + 4 * nb);
+        int* srow = sq + nb;
+        int* smono = srow + nb;
         for (int i = lane; i < nb; i += wsz) {
-            const int q = sites[i].q;
-            sa[4 * i] = mixel<R>(p, ch, m, q, 0, 0);
-            sa[4 * i + 1] = mixel<R>(p, ch, m, q, 0, 1);
-            sa[4 * i + 2] = mixel<R>(p, ch, m, q, 1, 0);
-            sa[4 * i + 3] = mixel<R>(p, ch, m, q, 1, 1);
+            const DevBlockSite st = sites[i];
+            sa[4 * i] = mixel<R>(p, ch, m, st.q, 0, 0);
+            sa[4 * i + 1] = mixel<R>(p, ch, m, st.q, 0, 1);
+            sa[4 * i + 2] = mixel<R>(p, ch, m, st.q, 1, 0);
+            sa[4 * i + 3] = mixel<R>(p, ch, m, st.q, 1, 1);
+            sq[i] = st.q;
+            srow[i] = st.trace_row;
+            smono[i] = st.monomial;
         }
-        unsigned sbits = 0;
-        for (int i = 0; i < nb; ++i) sbits |= (unsigned)ch.s[sites[i].q] << i;
         __syncwarp();
+        unsigned sbits = 0;
+        for (int i = 0; i < nb; ++i) sbits |= (unsigned)ch.s[sq[i]] << i;
         C* cur = ch.T;
         int size = 1 << nb;
         for (int i = 0; i < nb; ++i) {
@@ -785,8 +805,7 @@ __device__ void readout_and_sample(const KParams& p, const Chain<R>& ch, const G
             int snew = sold;
             bool stop = false;
             if (lane == 0) {
-                const DevBlockSite st = sites[i];
-                const int row = st.trace_row, mono = st.monomial;
+                const int row = srow[i], mono = smono[i];
                 const int rest = (int)((sbits >> (i + 1)) << 1);   // later sites keep their bits
                 const C c0 = cur[rest], c1 = cur[rest | 1];
                 const C amp0 = cfma(A00, c0, cmul(A01, c1));
@@ -850,7 +869,7 @@ __device__ void readout_and_sample(const KParams& p, const Chain<R>& ch, const G
             __syncwarp();
         }
         if (p.mode == MODE_SAMPLE)
-            for (int i = lane; i < nb; i += wsz) ch.s[sites[i].q] = (uint8_t)((sbits >> i) & 1);
+            for (int i = lane; i < nb; i += wsz) ch.s[sq[i]] = (uint8_t)((sbits >> i) & 1);
     }
     g.sync();
 }
