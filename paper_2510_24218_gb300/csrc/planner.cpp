@@ -513,15 +513,40 @@ void build_cost_waves(HostPlan& hp, int n, int P) {
     hp.cost_waves.push_back((int)hp.cost_items.size());
 }
 
+// Variant tables of every stage and live slot, evaluated in FP64. For a noisy
+// plan they describe a clean chain: every Kraus draw so far took operator 0
+// (identity part of a Pauli channel, E0 of damping), so the frame is zero and
+// each segment carries the fixed factors of those operators; the kernel uses
+// them only while its chain is clean. The segment factors are kept for the
+// chain that leaves that state.
 void precompute_tables(HostPlan& hp) {
     const int n = hp.hdr.n, P = hp.hdr.P;
     HostEval ev{hp, std::vector<cd>((size_t)n * (P + 1) * 2, cd(1.0)), n, P, nullptr, 0};
     for (int m = 1; m <= P; ++m)
-        for (int it = hp.cost_ranges[m]; it < hp.cost_ranges[m + 1]; ++it)
-            if (hp.cost_items[it].kind == CI_GATE1) {
-                const DevCostGate& G = hp.cost_gates[hp.cost_items[it].idx];
+        for (int it = hp.cost_ranges[m]; it < hp.cost_ranges[m + 1]; ++it) {
+            const DevCostItem ci = hp.cost_items[it];
+            if (ci.kind == CI_GATE1) {
+                const DevCostGate& G = hp.cost_gates[ci.idx];
                 for (int b = 0; b < 2; ++b) ev.segfac[((size_t)G.q0 * (P + 1) + (m - 1)) * 2 + b] *= cd(G.d[2 * b], G.d[2 * b + 1]);
+            } else if (ci.kind == CI_CHANNEL) {
+                const DevChannel& c = hp.channels[ci.idx];
+                for (int f = 0; f < c.nq; ++f) {
+                    const DevKrausFactor& F = hp.factors[c.fac_off + f];   // operator 0
+                    for (int b = 0; b < 2; ++b)
+                        ev.segfac[((size_t)F.q * (P + 1) + (m - 1)) * 2 + b] *= cd(F.d[2 * b], F.d[2 * b + 1]);
+                }
             }
+        }
+    if (hp.hdr.has_frame) {
+        hp.segdef_d.clear();
+        hp.segdef_f.clear();
+        for (const cd& v : ev.segfac) {
+            hp.segdef_d.push_back(v.real());
+            hp.segdef_d.push_back(v.imag());
+            hp.segdef_f.push_back((float)v.real());
+            hp.segdef_f.push_back((float)v.imag());
+        }
+    }
     std::vector<int> sq(n, -1);
     ev.sq = sq.data();
     auto deps_of = [&](const DevMicroOp& o, std::vector<int>& deps) {
@@ -1015,10 +1040,17 @@ int build_plan(const pw_circuit* c, const pw_plan_opts& opts, HostPlan& hp) {
     hp.hdr.has_segfac = has_segfac ? 1 : 0;
     hp.hdr.has_frame = has_frame ? 1 : 0;
     hp.hdr.words = (n + 63) / 64;
-    // tables: precomputed for noiseless plans, built per chain otherwise
+    // tables: precomputed for noiseless plans and for the clean chains of a
+    // noisy plan (possible when no Kraus operator 0 flips the frame); chains
+    // with a frame or other Kraus factors build theirs
     for (auto& st : hp.stages) st.ndep = 0xFF;
     for (auto& sl : hp.live_slots) sl.ndep = 0xFF;
-    if (!has_frame) precompute_tables(hp);
+    bool clean_ok = has_frame;
+    for (const DevChannel& ch : hp.channels)
+        for (int f = 0; f < ch.nq; ++f)
+            if (hp.factors[ch.fac_off + f].antidiag) clean_ok = false;
+    hp.hdr.clean_tables = clean_ok ? 1 : 0;
+    if (!has_frame || clean_ok) precompute_tables(hp);
     hp.hdr.max_tab = 1;
     hp.hdr.max_stages = 1;
     for (const auto& br : hp.block_ranges) {

@@ -186,13 +186,14 @@ struct DevPlanHeader {
     int32_t words;             // uint64 words per bitstring
     int32_t max_tab;           // max table entries of one block program
     int32_t max_stages;        // max stages of one block program
+    int32_t clean_tables;      // noisy plan whose variant tables assume Kraus pick 0 everywhere
 };
 
 // Offsets (in bytes) of the arrays inside the device blob.
 struct DevPlanOffsets {
     int64_t micro, fused, stages, row_opid, vtab_f, vtab_d, gate_refs, cost_gates, cost_items, cost_ranges, cost_waves, cost_wave_ranges, channels, cum,
         factors;
-    int64_t mix_d, mix_f, mix0_order, mix0_opid, mix_mono;
+    int64_t mix_d, mix_f, mix0_order, mix0_opid, mix_mono, segdef_d, segdef_f;
     int64_t block_ranges, block_sites, live_slots;
 };
 
@@ -228,6 +229,8 @@ struct HostPlan {
     std::vector<int32_t> mix0_order;       // qubits of mixer layer 0 in circuit order
     std::vector<int32_t> mix0_opid;        // op id of mixer-0 gate per qubit
     std::vector<int8_t> mix_mono;          // [(P+1) * n]: 1 if the mixer is monomial
+    std::vector<double> segdef_d;          // [n][P+1][2] complex: segment factors of a clean chain
+    std::vector<float> segdef_f;
     std::vector<DevBlockRange> block_ranges;   // [(P+1) * K] (layer 0 unused)
     std::vector<DevBlockSite> block_sites;
     std::vector<DevLiveSlot> live_slots;

@@ -156,13 +156,23 @@ template <typename R> struct Chain {
     uint8_t* xmix;    // frame during each one-qubit layer, [(P+1) n]
     uint8_t* gframe;  // frame bits of each diagonal gate at its time
     C* segfac;    // one-qubit diagonal factors per (qubit, segment), [n][P+1][2]
-    int* misc;    // [0] exponent of L, [1] pending rescale, [2..] role slots
+    int* misc;    // [0] exponent of L, [1] pending rescale, [2..17] role slots, [18..19] clean state
     // distributed frontier (cluster of p.cr CTAs per chain)
     int rank;            // this CTA's rank in the cluster (0 when cr == 1)
     C** rL;              // every rank's part of L (generic addresses, table in shared memory)
     double2* pd;         // this CTA's FP64 partial readout sums, 2^S
     float* cmax;         // this CTA's max |L|
 };
+
+// A chain is clean while every Kraus draw took operator 0 (misc[18] = 1):
+// its frame is zero and its segment factors are the plan's fixed ones, so
+// the host-evaluated variant tables hold for it.
+enum { MISC_CLEAN = 18, MISC_DIRTY_EVENT = 19 };
+
+template <typename R>
+__device__ __forceinline__ bool chain_clean(const KParams& p, const Chain<R>& ch) {
+    return !p.hdr.has_frame || (p.hdr.clean_tables && p.mode == MODE_SAMPLE && ch.misc[MISC_CLEAN] != 0);
+}
 
 // Frame-conjugated one-qubit gate A'_{m,q}[o][i] = A[o^x][i^x] (PropagateX).
 template <typename R>
@@ -268,6 +278,7 @@ __device__ void build_tables(const KParams& p, const Chain<R>& ch, const Grp& g,
     using C = typename CT<R>::T;
     const DevStage* ST = P_<DevStage>(p, p.off.stages) + sb;
     const DevMicroOp* ops = P_<DevMicroOp>(p, p.off.micro);
+    const bool clean = chain_clean<R>(p, ch);
     for (int i = g.lt; i < ns; i += g.nt) ch.stg[i] = ST[i];
     for (int ef = g.lt; ef < ntab; ef += g.nt) {
         int si = 0;   // last stage with tab_off <= ef (offsets ascend)
@@ -281,7 +292,7 @@ __device__ void build_tables(const KParams& p, const Chain<R>& ch, const Grp& g,
         const DevStage st = ST[si];
         const int e = ef - st.tab_off;
         C v;
-        if (st.ndep != 0xFF) {
+        if (st.ndep != 0xFF && clean) {
             int var = 0;
             for (int j = 0; j < st.ndep; ++j) var |= ch.s[st.dep[j]] << j;
             const int size = st.type == ST_MAT ? 4 : (1 << st.arg);
@@ -294,7 +305,7 @@ __device__ void build_tables(const KParams& p, const Chain<R>& ch, const Grp& g,
             if (exact && si == 0) {
                 // scale factors left out of the precomputed tables of this program
                 for (int s2 = 0; s2 < ns; ++s2) {
-                    if (ST[s2].ndep == 0xFF) continue;
+                    if (ST[s2].ndep == 0xFF) continue;   // (built below, with its scale factors)
                     for (int k = ST[s2].op_begin; k < ST[s2].op_end; ++k)
                         if (ops[k].recipe == RC_CONST_EDGES) v = cmul(v, build_entry<R>(p, ch, ops[k], 0));
                 }
@@ -517,14 +528,12 @@ template <typename R> __device__ __forceinline__ int scale_exp(R mx) {
     return rexp(mx);
 }
 
-// Kraus draw of Eq. (5) at the true bits s XOR x, then Alg. 2: every
-// anti-diagonal factor flips x[q] and becomes the diagonal M sigma_X; each
-// diagonal factor is conjugated by the (updated) frame and multiplied into the
-// qubit's current segment.
+// Kraus draw of Eq. (5) at the true bits s XOR x: the smallest i with
+// u * total < cum[cb][i] (same rule as UpdateState). Draws within 1e-6 of a
+// boundary are counted when count_near is set.
 template <typename R>
-__device__ void apply_channel(const KParams& p, const Chain<R>& ch, const DevChannel& c, const double* cum,
-                              const DevKrausFactor* fac, uint64_t sample_id, int seg) {
-    using C = typename CT<R>::T;
+__device__ __forceinline__ int kraus_pick(const KParams& p, const Chain<R>& ch, const DevChannel& c, const double* cum,
+                                          uint64_t sample_id, bool count_near) {
     int cb = 0;
     for (int i = 0; i < c.nq; ++i) cb |= (ch.s[c.q[i]] ^ ch.x[c.q[i]]) << i;
     const double* row = cum + c.cum_off + (size_t)cb * c.k;
@@ -536,11 +545,23 @@ __device__ void apply_channel(const KParams& p, const Chain<R>& ch, const DevCha
             pick = i;
             break;
         }
-    for (int i = 0; i + 1 < c.k; ++i)
-        if (fabs(u * total - row[i]) < 1e-6 * total) {
-            if (ch.rank == 0) atomicAdd(&p.counters[CNT_NEAR], 1ull);
-            break;
-        }
+    if (count_near)
+        for (int i = 0; i + 1 < c.k; ++i)
+            if (fabs(u * total - row[i]) < 1e-6 * total) {
+                if (ch.rank == 0) atomicAdd(&p.counters[CNT_NEAR], 1ull);
+                break;
+            }
+    return pick;
+}
+
+// The drawn Kraus operator, then Alg. 2: every anti-diagonal factor flips
+// x[q] and becomes the diagonal M sigma_X; each diagonal factor is conjugated
+// by the (updated) frame and multiplied into the qubit's current segment.
+template <typename R>
+__device__ void apply_channel(const KParams& p, const Chain<R>& ch, const DevChannel& c, const double* cum,
+                              const DevKrausFactor* fac, uint64_t sample_id, int seg, bool count_near) {
+    using C = typename CT<R>::T;
+    const int pick = kraus_pick<R>(p, ch, c, cum, sample_id, count_near);
     const int P1 = p.hdr.P + 1;
     for (int f = 0; f < c.nq; ++f) {
         const DevKrausFactor F = fac[c.fac_off + pick * c.nq + f];
@@ -567,10 +588,11 @@ __device__ void build_fslot(const KParams& p, const Chain<R>& ch, const Grp& g, 
     const DevLiveSlot* live = P_<DevLiveSlot>(p, p.off.live_slots) + br.live_begin;
     const int32_t* gref = P_<int32_t>(p, p.off.gate_refs);
     const DevCostGate* G = P_<DevCostGate>(p, p.off.cost_gates);
+    const bool clean = chain_clean<R>(p, ch);
     for (int j = g.lt; j < p.hdr.S; j += g.nt) {
         const DevLiveSlot sl = live[j];
         if (sl.q >= 0 && sl.role >= 0) ch.misc[2 + sl.role] = j;
-        if (sl.ndep != 0xFF) {
+        if (sl.ndep != 0xFF && clean) {
             int var = 0;
             for (int d = 0; d < sl.ndep; ++d) var |= ch.s[sl.dep[d]] << d;
             const size_t at = (size_t)sl.var_off + 2 * (size_t)var;
@@ -879,14 +901,42 @@ __device__ void readout_and_sample(const KParams& p, const Chain<R>& ch, const G
 // and the Kraus draws of the channels (Eq. 5; the channels after the last
 // layer act on segment P). The items of a wave touch disjoint qubits and run
 // in parallel over the group.
+//
+// A clean chain first draws every channel of the section at once: with a zero
+// frame a draw depends only on s, so the order does not matter. If all draws
+// give operator 0 the chain stays clean and nothing else changes (its gate
+// frame bits stay zero and its segment factors are the fixed ones). Otherwise
+// it becomes dirty: it takes the fixed factors of the earlier segments and
+// runs the section wave by wave, which redraws the same counters in order.
 template <typename R>
 __device__ void cost_section(const KParams& p, const Chain<R>& ch, const Grp& G, int m, uint64_t sample_id) {
     using C = typename CT<R>::T;
     const int P1 = p.hdr.P + 1;
+    const int32_t* cr = P_<int32_t>(p, p.off.cost_ranges);
     const int32_t* wr = P_<int32_t>(p, p.off.cost_wave_ranges);
     const int32_t* wv = P_<int32_t>(p, p.off.cost_waves);
     const DevCostItem* items = P_<DevCostItem>(p, p.off.cost_items);
     const DevCostGate* CG = P_<DevCostGate>(p, p.off.cost_gates);
+    const DevChannel* chans = P_<DevChannel>(p, p.off.channels);
+    const double* cum = P_<double>(p, p.off.cum);
+    bool count_near = true;
+    if (p.hdr.has_frame && chain_clean<R>(p, ch)) {
+        for (int it = cr[m] + G.lt; it < cr[m + 1]; it += G.nt)
+            if (items[it].kind == CI_CHANNEL && kraus_pick<R>(p, ch, chans[items[it].idx], cum, sample_id, true) != 0)
+                ch.misc[MISC_DIRTY_EVENT] = 1;
+        G.sync();
+        if (ch.misc[MISC_DIRTY_EVENT] == 0) return;
+        // leaves the clean state in this section: segments m-1 .. P restart
+        // from one (the earlier ones keep the fixed factors they hold)
+        const int nseg = P1 - (m - 1);
+        for (int i = G.lt; i < p.hdr.n * nseg * 2; i += G.nt) {
+            const int q = i / (nseg * 2), r = i - q * nseg * 2;
+            ch.segfac[((size_t)q * P1 + (m - 1)) * 2 + r] = mk<R>(1, 0);
+        }
+        if (G.lt == 0) ch.misc[MISC_CLEAN] = 0;
+        count_near = false;   // these draws were counted above
+        G.sync();
+    }
     for (int w = wr[m]; w < wr[m + 1]; ++w) {
         for (int it = wv[w] + G.lt; it < wv[w + 1]; it += G.nt) {
             const DevCostItem ci = items[it];
@@ -898,8 +948,8 @@ __device__ void cost_section(const KParams& p, const Chain<R>& ch, const Grp& G,
                 sf[0] = cmul(sf[0], mk<R>((R)CG[ci.idx].d[2 * xb], (R)CG[ci.idx].d[2 * xb + 1]));
                 sf[1] = cmul(sf[1], mk<R>((R)CG[ci.idx].d[2 * (1 ^ xb)], (R)CG[ci.idx].d[2 * (1 ^ xb) + 1]));
             } else if (p.mode == MODE_SAMPLE) {
-                apply_channel<R>(p, ch, P_<DevChannel>(p, p.off.channels)[ci.idx], P_<double>(p, p.off.cum),
-                                 P_<DevKrausFactor>(p, p.off.factors), sample_id, m - 1);
+                apply_channel<R>(p, ch, chans[ci.idx], cum, P_<DevKrausFactor>(p, p.off.factors), sample_id, m - 1,
+                                 count_near);
             }
         }
         G.sync();
@@ -927,8 +977,19 @@ __device__ void run_chain(const KParams& p, const Chain<R>& ch, int gid, int lt,
         for (int i = lt; i < (P + 1) * n; i += p.tpc) ch.xmix[i] = 0;
         for (int i = lt; i < h.n_cost_gates; i += p.tpc) ch.gframe[i] = 0;
     }
-    if (h.has_segfac)
-        for (int i = lt; i < n * (P + 1) * 2; i += p.tpc) ch.segfac[i] = one;
+    if (h.has_segfac) {
+        // a chain that starts clean holds the fixed segment factors of its
+        // plan (one-qubit diagonal gates, Kraus operators 0); tables built at
+        // run time read them from here
+        const bool starts_clean = h.has_frame && h.clean_tables && p.mode == MODE_SAMPLE;
+        const C* def = reinterpret_cast<const C*>(sizeof(R) == 4 ? P_<unsigned char>(p, p.off.segdef_f)
+                                                                  : P_<unsigned char>(p, p.off.segdef_d));
+        for (int i = lt; i < n * (P + 1) * 2; i += p.tpc) ch.segfac[i] = starts_clean ? def[i] : one;
+    }
+    if (lt == 0) {
+        ch.misc[MISC_CLEAN] = 1;
+        ch.misc[MISC_DIRTY_EVENT] = 0;
+    }
     if (p.mode == MODE_SAMPLE) {
         // the UpdateState draws of every sampled gate (they depend only on
         // (seed, sample, op id), so they are drawn up front in parallel)
@@ -963,7 +1024,7 @@ __device__ void run_chain(const KParams& p, const Chain<R>& ch, int gid, int lt,
     for (int m = 1; m <= mhi; ++m) {
         if (h.has_segfac || h.has_frame) {
             cost_section<R>(p, ch, G, m, sample_id);
-            if (h.has_frame)
+            if (h.has_frame && !chain_clean<R>(p, ch))   // (a clean chain's frame rows stay zero)
                 for (int q = lt; q < n; q += p.tpc) ch.xmix[m * n + q] = ch.x[q];
         }
         G.sync();
@@ -1136,6 +1197,8 @@ std::vector<unsigned char> make_blob(const HostPlan& hp, DevPlanOffsets& o) {
     put(blob, o.mix0_order, hp.mix0_order);
     put(blob, o.mix0_opid, hp.mix0_opid);
     put(blob, o.mix_mono, hp.mix_mono);
+    put(blob, o.segdef_d, hp.segdef_d);
+    put(blob, o.segdef_f, hp.segdef_f);
     put(blob, o.block_ranges, hp.block_ranges);
     put(blob, o.block_sites, hp.block_sites);
     put(blob, o.live_slots, hp.live_slots);

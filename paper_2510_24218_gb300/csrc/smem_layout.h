@@ -46,7 +46,7 @@ inline SmemLayout make_layout(const HostPlan& hp, size_t csz) {
     L.xmix = take((size_t)(h.P + 1) * h.n);
     L.gframe = take(std::max(1, h.n_cost_gates));
     L.segfac = take(h.has_segfac ? csz * 2 * (size_t)h.n * (h.P + 1) : 16);
-    L.misc = take(sizeof(int) * (2 + 16));
+    L.misc = take(sizeof(int) * (2 + 16 + 2));
     L.group_bytes = (int)align16(o);
     return L;
 }

@@ -94,3 +94,28 @@ def test_grid8x8_noisy_chain_against_alg2(pw):
     assert len(rows) == g["plan_stats"]["sampled_gates"]
     worst = max(pair_err(rows[r][1], g["trace"][3, r]) for r in range(len(rows)))
     assert worst < 1e-5
+
+
+def test_grid8x8_noisy_dirty_chains_against_alg2(pw):
+    """The 8x8 p=2 cluster plan with noise rates raised to 4e-3: chains that
+    draw a Kraus operator other than 0 midway leave the clean state (from then
+    on tables built per chain and draws in dependency waves), the others keep
+    the host-evaluated tables. Every chain must follow Alg. 2 bit for bit and
+    amplitude pair by amplitude pair."""
+    spec = W.grid_8x8_p2_noisy()
+    spec.depol2 = 0.004
+    spec.ad_gamma = 0.004
+    g = run_gpu(pw, spec, 3, seed=77)
+    assert g["plan_stats"]["ctas_per_chain"] > 1
+    ops = OC.qaoa_circuit(spec)
+    dirty = 0
+    for k in range(3):
+        trace, events = [], []
+        s, st = OS.noisy_sample(spec.n, ops, 77, k, order=g["order"], backend="tn", trace=trace, events=events)
+        dirty += int(any(i != 0 for _, i in events))
+        if st.near_boundary == 0:
+            assert np.array_equal(s, g["bits"][k])
+        rows = [t for t in trace if len(t[0]) == 2][spec.n:]
+        worst = max(pair_err(rows[r][1], g["trace"][k, r]) for r in range(len(rows)))
+        assert worst < 1e-5
+    assert dirty >= 1

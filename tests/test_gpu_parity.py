@@ -187,6 +187,35 @@ def test_noisy_bitwise_against_alg2(pw, spec):
     assert mism <= max(near, g["stats"]["near_boundary"])
 
 
+@pytest.mark.parametrize("spec", [W.random_qaoa(10, 2, seed=55, depol2=0.01, ad_gamma=0.03),
+                                  W.random_qaoa(8, 3, seed=56, depol2=0.02, ad_gamma=0.05)])
+def test_noisy_clean_and_dirty_chains_against_alg2(pw, spec):
+    """Low noise rates: most chains draw only Kraus operator 0 (clean: the
+    kernel uses host-evaluated tables and one parallel draw per layer), the
+    others leave that state midway (tables built per chain, draws in dependency
+    waves). Both kinds must give Alg. 2's bits and amplitudes."""
+    N = 64
+    g = run_gpu(pw, spec, N, seed=63, trace=True)
+    ops = OC.qaoa_circuit(spec)
+    clean = dirty = mism = near = 0
+    worst = 0.0
+    for k in range(N):
+        trace, events = [], []
+        s, st = OS.noisy_sample(spec.n, ops, 63, k, order=g["order"], trace=trace, events=events)
+        near += st.near_boundary
+        mism += int(not np.array_equal(s, g["bits"][k]))
+        if all(i == 0 for _, i in events):
+            clean += 1
+        else:
+            dirty += 1
+        rows = [t for t in trace if len(t[0]) == 2][spec.n:]
+        if np.array_equal(s, g["bits"][k]):
+            worst = max(worst, max(pair_err(rows[r][1], g["trace"][k, r]) for r in range(len(rows))))
+    assert clean >= 8 and dirty >= 8
+    assert mism <= max(near, g["stats"]["near_boundary"])
+    assert worst < 1e-5
+
+
 def test_noisy_distribution_against_density_matrix(pw):
     spec = W.random_qaoa(4, 2, seed=54, depol2=0.2, ad_gamma=0.5)
     N = 40000
