@@ -65,7 +65,9 @@ typedef struct {
     int precision;          /* PW_PREC_FP32 (default) or PW_PREC_FP64 */
     int order;              /* PW_ORDER_AUTO (default) or PW_ORDER_NATURAL */
     int max_block;          /* max sites resampled per readout block; 0 -> 8 */
-    int threads_per_chain;  /* CUDA threads cooperating on one chain; 0 -> auto */
+    int threads_per_chain;  /* CUDA threads cooperating on one chain (per CTA of a cluster);
+                               0 -> auto (32..256, 512 per CTA of a cluster); else a power
+                               of two in 32..256 */
     int chains_per_launch;  /* chains per kernel launch; 0 -> all requested samples */
     int ctas_per_chain;     /* 0 -> auto (a thread-block cluster only when one CTA's
                                shared memory cannot hold the frontier); 2, 4 or 8

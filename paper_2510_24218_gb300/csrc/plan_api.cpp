@@ -75,7 +75,9 @@ int pw_plan_build(const pw_circuit* c, const pw_plan_opts* opts, pw_plan** out) 
             }
             hp.ctas_per_chain = 1 << c;
             hp.wloc = wloc;
-            if (o.threads_per_chain <= 0) hp.threads_per_chain = 256;
+            // one CTA per SM: 512 threads (16 warps, 128 registers each) hide
+            // more shared-memory latency than 256
+            if (o.threads_per_chain <= 0) hp.threads_per_chain = 512;
             if (make_layout(hp, csz).group_bytes > 227 * 1024) {
                 delete plan;
                 return set_error(PW_ERR_TOO_LARGE, "per-CTA shared memory exceeds 227 KB");

@@ -1114,7 +1114,7 @@ __device__ void run_chain(const KParams& p, const Chain<R>& ch, int gid, int lt,
 }
 
 template <typename R>
-__global__ void __launch_bounds__(256, 2) pw_chain_kernel(const KParams p) {
+__global__ void __launch_bounds__(512, 1) pw_chain_kernel(const KParams p) {
     using C = typename CT<R>::T;
     extern __shared__ __align__(16) unsigned char smem[];
     const int gid = threadIdx.x / p.tpc;

@@ -53,7 +53,7 @@ inline SmemLayout make_layout(const HostPlan& hp, size_t csz) {
 
 // Chains per CTA, chosen to maximise the chains resident on one SM: 228 KB
 // of shared memory per SM (1 KB reserved per CTA), at most 512 resident
-// threads (128 registers each, the kernel's launch bounds) and 256 threads per
+// threads (128 registers each, the kernel's register budget) and 256 threads per
 // CTA.
 inline int groups_per_cta(int tpc, int group_bytes) {
     int best = 1, best_chains = 0;
