@@ -144,6 +144,8 @@ template <typename R> struct Chain {
     C* rowdot;    // 2^S
     C* wt;        // readout slot weights: products over the low S/2 and the high S - S/2 slots
     C* T;         // 2^max_block
+    C* sa;        // the current block's sites: mixer A'_m of site i at sa[4i .. 4i+3]
+    int* sinfo;   // then their qubit, trace row and monomial flag, max_block each
     C* tab;       // tables of one block program
     DevStage* stg;    // stage descriptors of one block program
     double* ud;   // the chain's UpdateState draws, one per sampled gate
@@ -280,19 +282,22 @@ __device__ void build_tables(const KParams& p, const Chain<R>& ch, const Grp& g,
     const DevMicroOp* ops = P_<DevMicroOp>(p, p.off.micro);
     const bool clean = chain_clean<R>(p, ch);
     for (int i = g.lt; i < ns; i += g.nt) ch.stg[i] = ST[i];
+    const Grp gl{g.lt, g.nt, g.gid, g.tpc, g.warp, false};
+    gl.sync();   // the lookups below read this CTA's shared copy
+    const DevStage* SS = ch.stg;
     for (int ef = g.lt; ef < ntab; ef += g.nt) {
         int si = 0;   // last stage with tab_off <= ef (offsets ascend)
         for (int hi = ns - 1; si < hi;) {
             const int mid = (si + hi + 1) >> 1;
-            if (ST[mid].tab_off <= ef)
+            if (SS[mid].tab_off <= ef)
                 si = mid;
             else
                 hi = mid - 1;
         }
-        const DevStage st = ST[si];
+        const DevStage st = SS[si];
         const int e = ef - st.tab_off;
         C v;
-        if (st.ndep != 0xFF && clean) {
+        if (st.ndep != 0xFF && clean) {   // precomputed variant
             int var = 0;
             for (int j = 0; j < st.ndep; ++j) var |= ch.s[st.dep[j]] << j;
             const int size = st.type == ST_MAT ? 4 : (1 << st.arg);
@@ -301,14 +306,6 @@ __device__ void build_tables(const KParams& p, const Chain<R>& ch, const Grp& g,
                 v = *reinterpret_cast<const float2*>(P_<float>(p, p.off.vtab_f) + 2 * at);
             } else {
                 v = *reinterpret_cast<const double2*>(P_<double>(p, p.off.vtab_d) + 2 * at);
-            }
-            if (exact && si == 0) {
-                // scale factors left out of the precomputed tables of this program
-                for (int s2 = 0; s2 < ns; ++s2) {
-                    if (ST[s2].ndep == 0xFF) continue;   // (built below, with its scale factors)
-                    for (int k = ST[s2].op_begin; k < ST[s2].op_end; ++k)
-                        if (ops[k].recipe == RC_CONST_EDGES) v = cmul(v, build_entry<R>(p, ch, ops[k], 0));
-                }
             }
         } else if (st.type == ST_MAT) {
             v = build_entry<R>(p, ch, ops[st.op_begin], e);
@@ -320,6 +317,15 @@ __device__ void build_tables(const KParams& p, const Chain<R>& ch, const Grp& g,
                 int loc = 0;
                 for (int j = 0; j < o.nbits; ++j) loc |= ((e >> o.fpos[j]) & 1) << j;
                 v = cmul(v, build_entry<R>(p, ch, o, loc));
+            }
+        }
+        if (exact && clean && si == 0) {
+            // scale factors left out of the precomputed tables of this
+            // program (the stages built here include their own)
+            for (int s2 = 0; s2 < ns; ++s2) {
+                if (SS[s2].ndep == 0xFF) continue;
+                for (int k = SS[s2].op_begin; k < SS[s2].op_end; ++k)
+                    if (ops[k].recipe == RC_CONST_EDGES) v = cmul(v, build_entry<R>(p, ch, ops[k], 0));
             }
         }
         if (si == 0 && pend_exp != 0) {
@@ -414,7 +420,12 @@ __device__ void tile_pass(const KParams& p, const Chain<R>& ch, const Grp& g, co
                 }
             } else {
                 int tb0 = 0;
-                for (int j = 0; j < arg; ++j) tb0 |= ((b0 >> stg[s].dbits[j]) & 1) << j;
+                int db[5];
+#pragma unroll
+                for (int j = 0; j < 5; ++j) db[j] = stg[s].dbits[j];
+#pragma unroll
+                for (int j = 0; j < 5; ++j)
+                    if (j < arg) tb0 |= ((b0 >> db[j]) & 1) << j;
                 int pm[4];
 #pragma unroll
                 for (int k = 0; k < 4; ++k) pm[k] = stg[s].tpos[k] != 0xFF ? 1 << stg[s].tpos[k] : 0;
@@ -441,7 +452,9 @@ __device__ void tile_pass(const KParams& p, const Chain<R>& ch, const Grp& g, co
 
 // A pass on a tensor with fewer tiles than threads: its stages run one after
 // another over the whole tensor (a pair per thread for a matrix, an entry per
-// thread for a diagonal), with a barrier between stages.
+// thread for a diagonal), with a barrier between stages. Each stage's fields
+// are read into registers once (the element loop stores to shared memory, so
+// they would otherwise be reloaded for every element).
 template <typename R>
 __device__ void flat_pass(const KParams& p, const Chain<R>& ch, const Grp& g, const DevFused& f, int sb,
                           typename CT<R>::T* buf, int W) {
@@ -452,7 +465,7 @@ __device__ void flat_pass(const KParams& p, const Chain<R>& ch, const Grp& g, co
         const uint8_t type = stg[s].type, arg = stg[s].arg;
         const C* tab = ch.tab + stg[s].tab_off;
         if (type == ST_MAT) {
-            const int bt = f.tbits[arg];
+            const int bt = arg == 0 ? f.tbits[0] : arg == 1 ? f.tbits[1] : arg == 2 ? f.tbits[2] : f.tbits[3];
             const C m00 = tab[0], m01 = tab[1], m10 = tab[2], m11 = tab[3];
             for (int pi = g.lt; pi < (N >> 1); pi += g.nt) {
                 const int i0 = ((pi >> bt) << (bt + 1)) | (pi & ((1 << bt) - 1));
@@ -462,9 +475,14 @@ __device__ void flat_pass(const KParams& p, const Chain<R>& ch, const Grp& g, co
                 buf[i1] = cfma(m10, x0, cmul(m11, x1));
             }
         } else {
+            int db[5];
+#pragma unroll
+            for (int j = 0; j < 5; ++j) db[j] = stg[s].dbits[j];
             for (int idx = g.lt; idx < N; idx += g.nt) {
                 int t = 0;
-                for (int j = 0; j < arg; ++j) t |= ((idx >> stg[s].dbits[j]) & 1) << j;
+#pragma unroll
+                for (int j = 0; j < 5; ++j)
+                    if (j < arg) t |= ((idx >> db[j]) & 1) << j;
                 buf[swz(idx)] = cmul(buf[swz(idx)], tab[t]);
             }
         }
@@ -494,8 +512,11 @@ template <typename R>
 __device__ void run_passes(const KParams& p, const Chain<R>& ch, const Grp& g, int fb, int fe, int sb0,
                            typename CT<R>::T* buf, int W, bool dist = false) {
     const DevFused* F = P_<DevFused>(p, p.off.fused);
+    if (fb >= fe) return;
+    DevFused fnext = F[fb];
     for (int fi = fb; fi < fe; ++fi) {
-        const DevFused f = F[fi];
+        const DevFused f = fnext;
+        if (fi + 1 < fe) fnext = F[fi + 1];   // in flight during this pass
         const int sb = f.st_begin - sb0;
         switch (f.ntb) {
             case 0: tile_pass_any<R, 0>(p, ch, g, f, sb, buf, W, dist); break;
@@ -627,6 +648,20 @@ __device__ void build_fslot(const KParams& p, const Chain<R>& ch, const Grp& g, 
         ch.fslot[2 * j] = f0;
         ch.fslot[2 * j + 1] = f1;
     }
+    // the block's sites for the resampling warp (loaded here, ahead of the
+    // passes, so that their global-memory latency is off its path)
+    const DevBlockSite* sites = P_<DevBlockSite>(p, p.off.block_sites) + br.site_begin;
+    const int nb = br.site_end - br.site_begin, mb = p.hdr.max_block;
+    for (int i = g.lt; i < nb; i += g.nt) {
+        const DevBlockSite st = sites[i];
+        ch.sa[4 * i] = mixel<R>(p, ch, m, st.q, 0, 0);
+        ch.sa[4 * i + 1] = mixel<R>(p, ch, m, st.q, 0, 1);
+        ch.sa[4 * i + 2] = mixel<R>(p, ch, m, st.q, 1, 0);
+        ch.sa[4 * i + 3] = mixel<R>(p, ch, m, st.q, 1, 1);
+        ch.sinfo[i] = st.q;
+        ch.sinfo[mb + i] = st.trace_row;
+        ch.sinfo[2 * mb + i] = st.monomial;
+    }
 }
 
 // Readout of block k of layer m. The frontier index is top legs (low S bits)
@@ -744,7 +779,6 @@ __device__ void readout_and_sample(const KParams& p, const Chain<R>& ch, const G
     //    other slots' bits and enumerates the rest (subset walk of mask mh).
     //    With several chunks per bin the partials go to part[] and the
     //    resampling warp adds them in chunk order.
-    const DevBlockSite* sites = P_<DevBlockSite>(p, p.off.block_sites) + br.site_begin;
     const int nb = br.site_end - br.site_begin;
     const int NT = 1 << nb;
     int cb = 31 - __clz(g.nt) - nb;
@@ -781,11 +815,12 @@ __device__ void readout_and_sample(const KParams& p, const Chain<R>& ch, const G
     }
     g.sync();
 
-    // 3) sequential resampling of the block's sites by the first warp. Lane i
-    //    holds site i's data; lane 0 takes each decision (FP64 conditional, the
-    //    chain's precomputed Philox draw); the lanes then contract the
-    //    resampled top away in parallel. The block's bits live in a register
-    //    mask until they are written back.
+    // 3) sequential resampling of the block's sites by the first warp (their
+    //    mixers and descriptors were staged in shared memory by build_fslot):
+    //    lane 0 takes each decision (FP64 conditional, the chain's
+    //    precomputed Philox draw); the lanes then contract the resampled top
+    //    away in parallel. The block's bits live in a register mask until they
+    //    are written back.
     const int wsz = g.nt < 32 ? g.nt : 32;
     if (g.lt < wsz) {
         const int lane = g.lt;
@@ -800,23 +835,10 @@ __device__ void readout_and_sample(const KParams& p, const Chain<R>& ch, const G
             }
             __syncwarp();
         }
-        C* sa = ch.part;   // site i's mixer A'_m at sa[4i .. 4i+3]
-        // then the sites' qubit, trace row and monomial flag (a block has at
-        // most 10 sites: 40 complex + 30 ints fit the 64-entry scratch)
-        int* sq = reinterpret_cast<int*>(sa + 4 * nb);
-        int* srow = sq + nb;
-        int* smono = srow + nb;
-        for (int i = lane; i < nb; i += wsz) {
-            const DevBlockSite st = sites[i];
-            sa[4 * i] = mixel<R>(p, ch, m, st.q, 0, 0);
-            sa[4 * i + 1] = mixel<R>(p, ch, m, st.q, 0, 1);
-            sa[4 * i + 2] = mixel<R>(p, ch, m, st.q, 1, 0);
-            sa[4 * i + 3] = mixel<R>(p, ch, m, st.q, 1, 1);
-            sq[i] = st.q;
-            srow[i] = st.trace_row;
-            smono[i] = st.monomial;
-        }
-        __syncwarp();
+        const C* sa = ch.sa;   // staged by build_fslot
+        const int* sq = ch.sinfo;
+        const int* srow = sq + h.max_block;
+        const int* smono = srow + h.max_block;
         unsigned sbits = 0;
         for (int i = 0; i < nb; ++i) sbits |= (unsigned)ch.s[sq[i]] << i;
         C* cur = ch.T;
@@ -1127,6 +1149,8 @@ __global__ void __launch_bounds__(512, 1) pw_chain_kernel(const KParams p) {
     ch.rowdot = reinterpret_cast<C*>(g + p.sm.rowdot);
     ch.wt = reinterpret_cast<C*>(g + p.sm.wt);
     ch.T = reinterpret_cast<C*>(g + p.sm.T);
+    ch.sa = reinterpret_cast<C*>(g + p.sm.sit);
+    ch.sinfo = reinterpret_cast<int*>(ch.sa + 4 * p.hdr.max_block);
     ch.tab = reinterpret_cast<C*>(g + p.sm.tab);
     ch.stg = reinterpret_cast<DevStage*>(g + p.sm.stg);
     ch.ud = reinterpret_cast<double*>(g + p.sm.ud);

@@ -9,7 +9,7 @@
 namespace pw {
 
 struct SmemLayout {
-    int L, R, Rexp, rowdot, wt, T, tab, stg, ud, uf, pd, cmax, rlp, part, fslot, red, s, x, xmix, gframe, segfac, misc, group_bytes;
+    int L, R, Rexp, rowdot, wt, T, sit, tab, stg, ud, uf, pd, cmax, rlp, part, fslot, red, s, x, xmix, gframe, segfac, misc, group_bytes;
 };
 
 inline size_t align16(size_t v) { return (v + 15) & ~(size_t)15; }
@@ -31,6 +31,7 @@ inline SmemLayout make_layout(const HostPlan& hp, size_t csz) {
     L.rowdot = take(csz << S);
     L.wt = take(csz * ((size_t(1) << (S / 2)) + (size_t(1) << (S - S / 2))));   // readout weights, two halves
     L.T = take(csz << (h.max_block + 1));   // two halves (ping-pong)
+    L.sit = take(csz * 4 * (size_t)h.max_block + sizeof(int) * 3 * (size_t)h.max_block);   // block's site data
     L.tab = take(csz * (size_t)std::max(1, h.max_tab));
     L.stg = take(sizeof(DevStage) * (size_t)std::max(1, h.max_stages));
     L.ud = take(sizeof(double) * (size_t)std::max(1, h.n_sampled));
