@@ -1256,6 +1256,18 @@ int ensure_device_plan(pw_plan* plan) {
     return PW_OK;
 }
 
+// Shared-memory carveout for `resident` CTAs of `smem` bytes each: only what
+// they need (plus the 1 KB the runtime reserves per CTA), so that the rest of
+// the SM's unified L1 / shared storage stays L1, which caches the plan tables.
+// The carveout is a preference that the driver rounds up to a supported size.
+static int carveout_percent(int dev, int resident, size_t smem) {
+    int maxsm = 0;
+    cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    if (maxsm <= 0 || resident <= 0) return 100;
+    const size_t need = (size_t)resident * (smem + 1024);
+    return (int)std::min<size_t>(100, (need * 100 + (size_t)maxsm - 1) / (size_t)maxsm);
+}
+
 template <typename R> int launch(pw_plan* plan, KParams& kp, cudaStream_t st, uint64_t* launches) {
     const HostPlan& hp = plan->hp;
     const size_t csz = 2 * sizeof(R);
@@ -1289,9 +1301,18 @@ template <typename R> int launch(pw_plan* plan, KParams& kp, cudaStream_t st, ui
         cfg.numAttrs = 1;
         cfg.gridDim = dim3((unsigned)kp.cr);
         int maxc = 0;
+        cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
         e = cudaOccupancyMaxActiveClusters(&maxc, kern, &cfg);
         if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveClusters");
         if (maxc < 1) return set_error(PW_ERR_TOO_LARGE, "no cluster of this size fits on the device");
+        {
+            // one CTA per SM: the carveout it needs, if that keeps every cluster
+            int maxc2 = 0;
+            cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 carveout_percent(plan->device, 1, smem));
+            if (cudaOccupancyMaxActiveClusters(&maxc2, kern, &cfg) != cudaSuccess || maxc2 < maxc)
+                cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+        }
         const uint64_t per_launch = hp.chains_per_launch > 0 ? (uint64_t)hp.chains_per_launch : kp.count;
         const uint64_t total = kp.count, first0 = kp.first;
         uint64_t* out0 = kp.out_bits;
@@ -1327,6 +1348,12 @@ template <typename R> int launch(pw_plan* plan, KParams& kp, cudaStream_t st, ui
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, smem);
     if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
     occ = std::max(occ, 1);
+    {
+        int occ2 = 0;
+        cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, carveout_percent(dev, occ, smem));
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ2, kern, threads, smem) != cudaSuccess || occ2 < occ)
+            cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    }
     const uint64_t per_launch = hp.chains_per_launch > 0 ? (uint64_t)hp.chains_per_launch : kp.count;
     const uint64_t total = kp.count, first0 = kp.first;
     uint64_t* out0 = kp.out_bits;
