@@ -225,6 +225,43 @@ def run_ours(args, rank, world):
                 e2e=e2e_value, h2d=h2d, d2h=n_samples * words * 8, wall=t_wall)
 
 
+KERNEL_SOURCES = ("paper_2510_24218_gb300/csrc/sampler.cu", "paper_2510_24218_gb300/csrc/pw_internal.h",
+                  "paper_2510_24218_gb300/csrc/smem_layout.h", "paper_2510_24218_gb300/csrc/planner.cpp")
+PROFILE_OF = {"grid6x6": "pw_chain_kernel_grid6x6_p2.md", "grid8x8noisy": "pw_chain_kernel_grid8x8_p2_noisy.md"}
+
+
+def kernel_sources_sha256():
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def profiled_traffic(workload_name, chains_per_launch):
+    """DRAM bytes (read + write) of one launch, from the ncu capture summarised
+    under profiles/, or None when there is none for this workload and launch
+    size or the kernel sources have changed since it was taken."""
+    name = PROFILE_OF.get(workload_name)
+    if name is None:
+        return None
+    path = os.path.join(ROOT, "profiles", name)
+    if not os.path.exists(path):
+        return None
+    fields = {}
+    for ln in open(path):
+        if ":" in ln and ln.startswith("    ") and ln.strip().split(":")[0] in (
+                "kernel-sources-sha256", "dram-bytes-per-launch", "chains-per-launch"):
+            k, v = ln.strip().split(":", 1)
+            fields[k] = v.strip()
+    if fields.get("kernel-sources-sha256") != kernel_sources_sha256():
+        return None
+    if int(fields.get("chains-per-launch", -1)) != chains_per_launch:
+        return None
+    return float(fields["dram-bytes-per-launch"])
+
+
 def _plan_blob_bytes(pw, plan):
     # size of the plan tables uploaded to the device (read from the stats:
     # the upload is the only host->device copy of a step)
@@ -291,7 +328,8 @@ def main():
                                                          "chains_per_cta", "flops_per_sample")},
                        "near_boundary_draws_in_warmup": int(r["near"])},
             "roofline": {"bound": "alu", "achieved": r["achieved"], "peak": peak, "unit": "TFLOP/s",
-                         "frac": (r["achieved"] / peak) if peak else None, "traffic": None,
+                         "frac": (r["achieved"] / peak) if peak else None,
+                         "traffic": profiled_traffic(args.workload, r["B"]),
                          "kernel": "pw_chain_kernel<float>",
                          "peak_note": "FP32 FMA peak derived: 152 SMs x 128 lanes x 2 x 2.07 GHz"},
             "cpu_baseline": cpu,
