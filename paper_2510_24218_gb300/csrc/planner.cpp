@@ -315,6 +315,10 @@ int fuse_range(HostPlan& hp, int b, int e, int* nst_out) {
                 st.arg = (uint8_t)k;
                 st.op_begin = i;
                 st.op_end = i + 1;
+                {
+                    const int rc = hp.micro[i].recipe;
+                    st.form = rc == RC_EXPAND ? MF_EXPAND : (rc == RC_SUMOUT1 || rc == RC_SUMOUT_MIX) ? MF_ROW0 : MF_GENERAL;
+                }
                 hp.stages.push_back(st);
                 sbits.emplace_back();
                 ++f.nst;
@@ -1013,15 +1017,20 @@ int build_plan(const pw_circuit* c, const pw_plan_opts& opts, HostPlan& hp) {
         (void)Wm;
     }
     for (int id : L.sections[P + 1]) hp.exec_order.push_back(id);
-    // algorithmic real flops per sample: a 2x2 on one bit costs 14 flops per
-    // entry (two complex multiplies and one add), the fused diagonal factor 6,
-    // the readout's dot product with R_k 8 per entry of L
+    // algorithmic real flops per sample: a general 2x2 on one bit costs 14
+    // flops per entry (two complex multiplies and one add), a row-0 one half
+    // of that (its other row is zero), an expand none (a copy); the fused
+    // diagonal factor 6; the readout's dot product with R_k 8 per entry of L
+    auto stage_flops = [&](const DevStage& st) {
+        if (st.type != ST_MAT) return 6.0;
+        return st.form == MF_EXPAND ? 0.0 : st.form == MF_ROW0 ? 7.0 : 14.0;
+    };
     for (int m = 1; m <= P; ++m) {
         double NF = std::ldexp(1.0, S * m), NB = std::ldexp(1.0, S * (m - 1));
         for (int k = 0; k < K; ++k) {
             const DevBlockRange& br = hp.block_ranges[(size_t)m * K + k];
-            for (int i = br.fwd_st; i < br.fwd_st + br.fwd_nst; ++i) flops += (hp.stages[i].type == ST_MAT ? 14.0 : 6.0) * NF;
-            for (int i = br.bwd_st; i < br.bwd_st + br.bwd_nst; ++i) flops += (hp.stages[i].type == ST_MAT ? 14.0 : 6.0) * NB;
+            for (int i = br.fwd_st; i < br.fwd_st + br.fwd_nst; ++i) flops += stage_flops(hp.stages[i]) * NF;
+            for (int i = br.bwd_st; i < br.bwd_st + br.bwd_nst; ++i) flops += stage_flops(hp.stages[i]) * NB;
             flops += 8.0 * NF;
         }
     }

@@ -81,12 +81,17 @@ struct DevMicroOp {
 // a diagonal factor over up to 5 bits (tile bits or fixed bits), the product
 // of consecutive diagonal/scalar micro-ops.
 enum StageType : uint8_t { ST_MAT = 0, ST_DIAG = 1 };
+// Shape of a 2x2 stage's matrix M[out][in], known from its micro-op: general;
+// expand (M = c [[1,0],[1,0]], c real: 1, or the program's pending power of
+// two when it is the first stage); row 0 (M = [[w0,w1],[0,0]]).
+enum MatForm : uint8_t { MF_GENERAL = 0, MF_EXPAND = 1, MF_ROW0 = 2 };
 struct DevStage {
     uint8_t type;
     uint8_t arg;         // ST_MAT: index into tbits; ST_DIAG: number of diagonal bits
     uint8_t dbits[5];    // ST_DIAG: index bits of the table, entry bit j <- index bit dbits[j]
     uint8_t tpos[4];     // ST_DIAG: position in dbits of tile bit k, 0xFF if absent
     uint8_t ndep;        // precomputed table: chain bits it depends on (0..4); 0xFF: built at run time
+    uint8_t form;        // ST_MAT: MatForm
     int32_t op_begin, op_end;   // constituent micro-ops
     int32_t tab_off;            // complex entries from the start of the block's table area
     int16_t dep[4];             // qubits whose current bits select the variant

@@ -337,6 +337,8 @@ __device__ void build_tables(const KParams& p, const Chain<R>& ch, const Grp& g,
 }
 
 // (x[e], x[e | 1<<K]) <- M (x[e], x[e | 1<<K]) for every e with bit K clear.
+// (The tiled pass treats every shape of M as general: branching on the shape
+// inside the unrolled tile code made it spill and ran slower.)
 template <typename C, int T, int K>
 __device__ __forceinline__ void mat_stage(C (&x)[1 << T], C m00, C m01, C m10, C m11) {
 #pragma unroll
@@ -347,7 +349,6 @@ __device__ __forceinline__ void mat_stage(C (&x)[1 << T], C m00, C m01, C m10, C
         x[e | (1 << K)] = cfma(m10, x0, cmul(m11, x1));
     }
 }
-
 // Shared-memory position of frontier / environment entry i: bits 4..7 of i
 // are XORed into bits 0..3, so that warps striding over low index bits (a
 // pass whose tile bits include them) spread over the banks. A bijection on
@@ -466,13 +467,27 @@ __device__ void flat_pass(const KParams& p, const Chain<R>& ch, const Grp& g, co
         const C* tab = ch.tab + stg[s].tab_off;
         if (type == ST_MAT) {
             const int bt = arg == 0 ? f.tbits[0] : arg == 1 ? f.tbits[1] : arg == 2 ? f.tbits[2] : f.tbits[3];
+            const uint8_t form = stg[s].form;
             const C m00 = tab[0], m01 = tab[1], m10 = tab[2], m11 = tab[3];
             for (int pi = g.lt; pi < (N >> 1); pi += g.nt) {
                 const int i0 = ((pi >> bt) << (bt + 1)) | (pi & ((1 << bt) - 1));
                 const int i1 = swz(i0 | (1 << bt)), j0 = swz(i0);
-                const C x0 = buf[j0], x1 = buf[i1];
-                buf[j0] = cfma(m00, x0, cmul(m01, x1));
-                buf[i1] = cfma(m10, x0, cmul(m11, x1));
+                const C x0 = buf[j0];
+                if (form == MF_EXPAND) {
+                    // a copy; the first stage of a block program also carries the
+                    // pending power of two and, in exact mode, the scale-only
+                    // factors of the program (any complex value), so it multiplies
+                    const C y = sb + s == 0 ? cmul(m00, x0) : x0;
+                    buf[j0] = y;
+                    buf[i1] = y;
+                } else if (form == MF_ROW0) {
+                    buf[j0] = cfma(m00, x0, cmul(m01, buf[i1]));
+                    buf[i1] = mk<R>(0, 0);
+                } else {
+                    const C x1 = buf[i1];
+                    buf[j0] = cfma(m00, x0, cmul(m01, x1));
+                    buf[i1] = cfma(m10, x0, cmul(m11, x1));
+                }
             }
         } else {
             int db[5];
