@@ -312,3 +312,40 @@ def test_heavy_hex_400_amplitudes_against_elimination(pw):
         state = np.array([final[j] if j in done else h_bits[j] for j in range(spec.n)], dtype=np.uint8)
         tab = TN.amplitudes(spec.n, [ops[i] for i in order[:t + 1]], state, open_qubits=(q,))
         assert pair_err([tab[0], tab[1]], g["trace"][0, r]) < TOL[1], r
+
+
+def test_heavy_hex_400_fp32_amplitudes_within_1e5(pw):
+    """400 qubits on the FP32 path: full-string amplitudes and the candidate
+    pairs of one sampled chain, spread over the sweep, against the elimination
+    oracle within 1e-5. The FP32 error there is almost entirely a common
+    magnitude drift (the same rounded constants act at every site); it grows
+    with the number of sites and is the reason the FP64 path exists."""
+    import torch
+    from oracle.philox import draw
+    spec = W.heavy_hex_400_p1()
+    circ = _circ(pw, spec)
+    plan = pw.pw_plan_build(circ, precision=pw.PW_PREC_FP32)
+    order = pw.pw_plan_exec_order(plan)
+    ops = OC.qaoa_circuit(spec)
+    pre = [ops[i] for i in order]
+    xs = W.random_bitstrings(2, spec.n, seed=74)
+    d_bits = torch.from_numpy(pw.pack_bits(xs).view(np.int64)).cuda()
+    amp = torch.zeros((2, 2), dtype=torch.float64, device="cuda")
+    pw.pw_amplitudes(plan, len(order), d_bits, amp)
+    got = amp.cpu().numpy()
+    for k in range(2):
+        a = TN.amplitudes(spec.n, pre, xs[k])
+        assert abs(got[k, 0] + 1j * got[k, 1] - a) <= 1e-5 * abs(a)
+    pw.pw_plan_destroy(plan)
+    pw.pw_circuit_destroy(circ)
+    g = run_gpu(pw, spec, 1, seed=8)
+    final = g["bits"][0]
+    h_bits = np.array([0 if draw(8, 0, q, 0) < 0.5 else 1 for q in range(spec.n)], dtype=np.uint8)
+    mix_pos = [t for t, oi in enumerate(order) if t >= spec.n and ops[oi].kind == "gate" and len(ops[oi].qubits) == 1]
+    for r in (0, 114, 285, 399):
+        t = mix_pos[r]
+        q = ops[order[t]].qubits[0]
+        done = {ops[order[u]].qubits[0] for u in mix_pos[:r]}
+        state = np.array([final[j] if j in done else h_bits[j] for j in range(spec.n)], dtype=np.uint8)
+        tab = TN.amplitudes(spec.n, [ops[i] for i in order[:t + 1]], state, open_qubits=(q,))
+        assert pair_err([tab[0], tab[1]], g["trace"][0, r]) < 1e-5, r
