@@ -12,17 +12,26 @@ using namespace pw;
 
 namespace {
 
-int choose_threads(const HostPlan& hp, int requested) {
+// Threads per chain: at most one per 16-entry tile of the widest frontier
+// (32..256), and no more than lets every chain that shared memory admits on
+// an SM be resident at once (512 threads of 128 registers per SM). Chains
+// then overlap each other's serial phases (resampling, table gathers).
+int choose_threads(HostPlan& hp, int requested) {
     if (requested > 0) {
         if (requested % 32 || requested > 256 || (requested & (requested - 1)))
             return -1;
         return requested;
     }
-    long N = 1L << hp.W;
-    long t = N / 32;
-    t = std::max(32L, std::min(256L, t));
+    const long N = 1L << hp.W;
+    const long by_work = std::max(32L, std::min(256L, N / 16));
+    hp.threads_per_chain = 256;   // (the layout's scratch size depends on it)
+    const size_t csz = hp.precision == PW_PREC_FP64 ? 16 : 8;
+    const long group = (long)make_layout(hp, csz).group_bytes;
+    const long chains = std::max(1L, (228L * 1024) / (group + 1024));
+    const long by_regs = std::max(32L, 512L / chains);
+    const long t = std::min(by_work, by_regs);
     long pw2 = 32;
-    while (pw2 < t) pw2 <<= 1;
+    while (pw2 * 2 <= t) pw2 <<= 1;
     return (int)pw2;
 }
 

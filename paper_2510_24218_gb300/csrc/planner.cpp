@@ -52,6 +52,40 @@ struct Layered {
     std::vector<std::vector<int>> sections;    // [P+2], sections[m] m = 1..P+1
 };
 
+// FP32 copy of a complex FP64 constant. Among the pairs within one unit in
+// the last place (per part) of the nearest pair, and no farther from v than
+// one unit of the larger part, take the one whose modulus is closest to |v|
+// (ties: the nearest). The same rounded constants act at every site of a
+// sweep, so their modulus errors would add up coherently over hundreds of
+// sites (a common drift of the amplitudes' size); their phase errors stay
+// those of a near-nearest rounding, and conjugate constants keep conjugate
+// copies. Parts that are exactly zero stay zero.
+void round_c32(cd v, float& re, float& im) {
+    const float a0 = (float)v.real(), b0 = (float)v.imag();
+    re = a0;
+    im = b0;
+    if (!std::isfinite(a0) || !std::isfinite(b0)) return;
+    const double mod = std::abs(v);
+    const double ulp = std::max(std::fabs((double)std::nextafter(a0, INFINITY) - a0),
+                                std::fabs((double)std::nextafter(b0, INFINITY) - b0));
+    double best_m = std::fabs(std::hypot((double)a0, (double)b0) - mod), best_d = std::abs(cd(a0, b0) - v);
+    for (int i = -1; i <= 1; ++i)
+        for (int j = -1; j <= 1; ++j) {
+            if ((i && v.real() == 0.0) || (j && v.imag() == 0.0)) continue;
+            const float a = i < 0 ? std::nextafter(a0, -INFINITY) : i > 0 ? std::nextafter(a0, INFINITY) : a0;
+            const float b = j < 0 ? std::nextafter(b0, -INFINITY) : j > 0 ? std::nextafter(b0, INFINITY) : b0;
+            const double d = std::abs(cd(a, b) - v);
+            if (d > ulp) continue;
+            const double m = std::fabs(std::hypot((double)a, (double)b) - mod);
+            if (m < best_m || (m == best_m && d < best_d)) {
+                best_m = m;
+                best_d = d;
+                re = a;
+                im = b;
+            }
+        }
+}
+
 int parse_layers(const pw_circuit* c, Layered& L) {
     const int n = c->n;
     L.n = n;
@@ -452,8 +486,10 @@ struct HostEval {
 void push_var(HostPlan& hp, cd v) {
     hp.vtab_d.push_back(v.real());
     hp.vtab_d.push_back(v.imag());
-    hp.vtab_f.push_back((float)v.real());
-    hp.vtab_f.push_back((float)v.imag());
+    float re, im;
+    round_c32(v, re, im);
+    hp.vtab_f.push_back(re);
+    hp.vtab_f.push_back(im);
 }
 
 // Group the items of every cost section into waves. Per qubit there are two
@@ -547,8 +583,10 @@ void precompute_tables(HostPlan& hp) {
         for (const cd& v : ev.segfac) {
             hp.segdef_d.push_back(v.real());
             hp.segdef_d.push_back(v.imag());
-            hp.segdef_f.push_back((float)v.real());
-            hp.segdef_f.push_back((float)v.imag());
+            float re, im;
+            round_c32(v, re, im);
+            hp.segdef_f.push_back(re);
+            hp.segdef_f.push_back(im);
         }
     }
     std::vector<int> sq(n, -1);
@@ -668,7 +706,9 @@ int build_plan(const pw_circuit* c, const pw_plan_opts& opts, HostPlan& hp) {
             }
             hp.mix_mono[(size_t)m * n + q] = is_monomial(op.mat(0), 2) ? 1 : 0;
         }
-    hp.mix_f.assign(hp.mix_d.begin(), hp.mix_d.end());
+    hp.mix_f.assign(hp.mix_d.size(), 0.0f);
+    for (size_t i = 0; i + 1 < hp.mix_d.size(); i += 2)
+        round_c32(cd(hp.mix_d[i], hp.mix_d[i + 1]), hp.mix_f[i], hp.mix_f[i + 1]);
     for (int id : L.mixer_ops[0]) {
         hp.mix0_order.push_back(c->ops[id].qubits[0]);
     }
@@ -696,8 +736,7 @@ int build_plan(const pw_circuit* c, const pw_plan_opts& opts, HostPlan& hp) {
                     cd v = b < dim ? op.mats[(size_t)b * dim + b] : cd(1.0, 0.0);
                     g.d[2 * b] = v.real();
                     g.d[2 * b + 1] = v.imag();
-                    g.f[2 * b] = (float)v.real();
-                    g.f[2 * b + 1] = (float)v.imag();
+                    round_c32(v, g.f[2 * b], g.f[2 * b + 1]);
                 }
                 int gi = (int)hp.cost_gates.size();
                 hp.cost_gates.push_back(g);
