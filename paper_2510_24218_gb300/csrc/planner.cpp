@@ -706,6 +706,32 @@ int build_plan(const pw_circuit* c, const pw_plan_opts& opts, HostPlan& hp) {
             }
             hp.mix_mono[(size_t)m * n + q] = is_monomial(op.mat(0), 2) ? 1 : 0;
         }
+    // First-layer gates whose entries all have modulus 2^-1/2 (Hadamard-like):
+    // in pairs, their entries are stored times sqrt(2) (unit modulus, exact
+    // for +-1 and +-i) and the factor 2^-1 per pair goes to the amplitudes'
+    // power-of-two exponent. 1/sqrt(2) has no exact FP32 (or FP64) copy, and
+    // its rounding error would otherwise act once per qubit on every
+    // amplitude (about -7e-6 at 400 qubits in FP32).
+    {
+        std::vector<int> hq;
+        for (int q = 0; q < n; ++q) {
+            const double* A = hp.mix_d.data() + (size_t)q * 8;
+            bool h = true;
+            for (int i = 0; i < 4; ++i)
+                h = h && std::fabs(std::hypot(A[2 * i], A[2 * i + 1]) * std::sqrt(2.0) - 1.0) < 1e-14;
+            if (h) hq.push_back(q);
+        }
+        if (hq.size() % 2) hq.pop_back();
+        for (int q : hq) {
+            double* A = hp.mix_d.data() + (size_t)q * 8;
+            for (int i = 0; i < 4; ++i) {
+                const double r = std::hypot(A[2 * i], A[2 * i + 1]);
+                A[2 * i] /= r;
+                A[2 * i + 1] /= r;
+            }
+        }
+        hp.hdr.amp_exp = -(int)hq.size() / 2;
+    }
     hp.mix_f.assign(hp.mix_d.size(), 0.0f);
     for (size_t i = 0; i + 1 < hp.mix_d.size(); i += 2)
         round_c32(cd(hp.mix_d[i], hp.mix_d[i + 1]), hp.mix_f[i], hp.mix_f[i + 1]);

@@ -192,6 +192,7 @@ struct DevPlanHeader {
     int32_t max_tab;           // max table entries of one block program
     int32_t max_stages;        // max stages of one block program
     int32_t clean_tables;      // noisy plan whose variant tables assume Kraus pick 0 everywhere
+    int32_t amp_exp;           // power of two of every amplitude left out of the tables
 };
 
 // Offsets (in bytes) of the arrays inside the device blob.

@@ -775,7 +775,7 @@ __device__ void readout_and_sample(const KParams& p, const Chain<R>& ch, const G
         g.sync();   // cluster: partials consumed before anyone overwrites them
     }
     const int eL = ch.misc[0];
-    const int escale = eL + ch.Rexp[k];
+    const int escale = eL + ch.Rexp[k] + h.amp_exp;
     const bool target_block = p.mode == MODE_AMP && m == p.amp_layer && k == p.amp_block;
     g.sync();
     if (g.lt == 0) {
