@@ -1154,6 +1154,10 @@ template <typename R>
 __global__ void __launch_bounds__(512, 1) pw_chain_kernel(const KParams p) {
     using C = typename CT<R>::T;
     extern __shared__ __align__(16) unsigned char smem[];
+    // The launches of one sampling call take disjoint chains and read only the
+    // plan: the next one may start on the SMs this one no longer needs (it is
+    // launched as a programmatic dependent of this one; elsewhere a no-op).
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     const int gid = threadIdx.x / p.tpc;
     const int lt = threadIdx.x - gid * p.tpc;
     unsigned char* g = smem + (size_t)gid * p.sm.group_bytes;
@@ -1304,11 +1308,13 @@ template <typename R> int launch(pw_plan* plan, KParams& kp, cudaStream_t st, ui
         e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
         cudaLaunchConfig_t cfg = {};
-        cudaLaunchAttribute attr[1];
+        cudaLaunchAttribute attr[2];
         attr[0].id = cudaLaunchAttributeClusterDimension;
         attr[0].val.clusterDim.x = (unsigned)kp.cr;
         attr[0].val.clusterDim.y = 1;
         attr[0].val.clusterDim.z = 1;
+        attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[1].val.programmaticStreamSerializationAllowed = 1;
         cfg.blockDim = dim3((unsigned)kp.tpc);
         cfg.dynamicSmemBytes = smem;
         cfg.stream = st;
@@ -1343,6 +1349,7 @@ template <typename R> int launch(pw_plan* plan, KParams& kp, cudaStream_t st, ui
             kp.in_bits = in0 ? in0 + done * hp.hdr.words : nullptr;
             kp.amp_out = amp0 ? amp0 + 2 * done : nullptr;
             cfg.gridDim = dim3((unsigned)(std::min<uint64_t>(cnt, (uint64_t)maxc) * kp.cr));
+            cfg.numAttrs = done > 0 ? 2 : 1;   // later launches: programmatic dependents (see the kernel)
             e = cudaLaunchKernelEx(&cfg, kern, kp);
             if (e != cudaSuccess) return cuda_fail(e, "cluster kernel launch");
             if (launches) ++*launches;
@@ -1385,8 +1392,17 @@ template <typename R> int launch(pw_plan* plan, KParams& kp, cudaStream_t st, ui
         kp.amp_out = amp0 ? amp0 + 2 * done : nullptr;
         const uint64_t ctas_needed = (cnt + gpc - 1) / gpc;
         const int grid = (int)std::min<uint64_t>(ctas_needed, (uint64_t)nsm * occ);
-        kern<<<grid, threads, smem, st>>>(kp);
-        e = cudaGetLastError();
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)grid);
+        cfg.blockDim = dim3((unsigned)threads);
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = st;
+        cudaLaunchAttribute pdl[1];
+        pdl[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        pdl[0].val.programmaticStreamSerializationAllowed = 1;
+        cfg.attrs = pdl;
+        cfg.numAttrs = done > 0 ? 1 : 0;   // the first launch waits for all earlier work
+        e = cudaLaunchKernelEx(&cfg, kern, kp);
         if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
         if (launches) ++*launches;
     }
@@ -1572,8 +1588,17 @@ template <typename R> int launch_static(const HostPlan& hp, int dev, KParams& kp
         kp.first = first0 + done;
         kp.out_bits = out0 + done * hp.hdr.words;
         const int grid = (int)std::min<uint64_t>((cnt + gpc - 1) / gpc, (uint64_t)nsm * occ);
-        kern<<<grid, threads, smem, st>>>(kp);
-        e = cudaGetLastError();
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)grid);
+        cfg.blockDim = dim3((unsigned)threads);
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = st;
+        cudaLaunchAttribute pdl[1];
+        pdl[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        pdl[0].val.programmaticStreamSerializationAllowed = 1;
+        cfg.attrs = pdl;
+        cfg.numAttrs = done > 0 ? 1 : 0;   // the first launch waits for all earlier work
+        e = cudaLaunchKernelEx(&cfg, kern, kp);
         if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
         if (launches) ++*launches;
     }
