@@ -118,8 +118,9 @@ template <typename T> __device__ __forceinline__ const T* P_(const KParams& p, i
 }
 
 // The threads that run one phase of one chain: the whole group (named
-// barrier over tpc threads) or only its first warp (warp barrier), used for
-// tensors too small to feed the group.
+// barrier over tpc threads), its first four warps (another named barrier;
+// only when one group fills the CTA) or its first warp (warp barrier), the
+// smaller ones for tensors too small to feed the group.
 struct Grp {
     int lt, nt, gid, tpc;
     bool warp;
@@ -129,6 +130,10 @@ struct Grp {
             asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
         } else if (warp || tpc == 32) {
             __syncwarp();
+        } else if (nt < tpc) {
+            // a subgroup of the first nt threads (whole warps) of a group that
+            // fills its CTA: its own named barrier
+            asm volatile("bar.sync %0, %1;" ::"r"(gid + 9), "r"(nt) : "memory");
         } else {
             asm volatile("bar.sync %0, %1;" ::"r"(gid + 1), "r"(tpc) : "memory");
         }
@@ -1073,8 +1078,13 @@ __device__ void run_chain(const KParams& p, const Chain<R>& ch, int gid, int lt,
         // small tensors run on the first warp only
         const int w32 = p.tpc < 32 ? p.tpc : 32;
         const bool dist = p.cr > 1 && W > p.wloc;   // frontier spread over the cluster
-        const Grp GB{lt, NL <= 1024 ? w32 : p.tpc, gid, p.tpc, NL <= 1024 && p.tpc > 32, false};
-        const Grp GF{lt, (N <= 1024 && !dist) ? w32 : p.tpc, gid, p.tpc, N <= 1024 && p.tpc > 32 && !dist, dist};
+        // threads for a tensor of e entries: the whole group above 1024
+        // entries (or when split over a cluster), four warps from 256 entries
+        // when the group has at least 256 threads, else one warp
+        auto phase_nt = [&](int e, bool d) { return (d || e > 1024) ? p.tpc : (e >= 256 && p.tpc >= 256) ? 128 : w32; };
+        const int ntb = phase_nt(NL, false), ntf = phase_nt(N, dist);
+        const Grp GB{lt, ntb, gid, p.tpc, ntb == 32 && p.tpc > 32, false};
+        const Grp GF{lt, ntf, gid, p.tpc, ntf == 32 && p.tpc > 32, dist};
 
         // backward sweep: R_{K-1} = 1, R_{k-1} from R_k by block k's reversed
         // program. For m = 1 the environments are scalars (no summed segment on
