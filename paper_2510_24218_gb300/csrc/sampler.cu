@@ -704,10 +704,14 @@ __device__ void readout_and_sample(const KParams& p, const Chain<R>& ch, const G
     //    distributed frontier every CTA sums its own rows l (its share of the
     //    lower legs); the partial sums are then added across the cluster in
     //    FP64, in rank order, identically in every CTA.
+    //    With a single row (layer 1, one CTA) there is nothing to sum: the
+    //    collapse below reads L directly and finds max |L| on the way.
+    const bool direct = NL == 1 && !dist;
     R mx = 0;
     const int NLl = dist ? NL / p.cr : NL;    // rows held by this CTA
     const int l0 = dist ? ch.rank * NLl : 0;  // first of them
-    if (g.nt >= H) {
+    if (direct) {
+    } else if (g.nt >= H) {
         const int hh = g.lt & (H - 1), step = g.nt / H;
         C acc[4] = {zero, zero, zero, zero};   // independent chains for latency
         int l = g.lt / H;
@@ -751,9 +755,9 @@ __device__ void readout_and_sample(const KParams& p, const Chain<R>& ch, const G
         ch.wt[e] = w;
     }
     const Grp gl{g.lt, g.nt, g.gid, g.tpc, g.warp, false};   // this CTA only
-    mx = group_max<R>(ch, gl, mx);
+    if (!direct) mx = group_max<R>(ch, gl, mx);
     gl.sync();
-    if (g.nt >= H && g.lt < H) {
+    if (!direct && g.nt >= H && g.lt < H) {
         C acc = zero;
         for (int j = g.lt; j < g.nt; j += H) {
             acc.x += ch.part[j].x;
@@ -782,15 +786,17 @@ __device__ void readout_and_sample(const KParams& p, const Chain<R>& ch, const G
     const int eL = ch.misc[0];
     const int escale = eL + ch.Rexp[k] + h.amp_exp;
     const bool target_block = p.mode == MODE_AMP && m == p.amp_layer && k == p.amp_block;
-    g.sync();
-    if (g.lt == 0) {
-        const int e = scale_exp<R>(mx);
-        ch.misc[1] = -e;
-        ch.misc[0] = eL + e;
-    }
-    if (p.mode == MODE_AMP && !target_block) {
+    if (!direct) {
         g.sync();
-        return;
+        if (g.lt == 0) {
+            const int e = scale_exp<R>(mx);
+            ch.misc[1] = -e;
+            ch.misc[0] = eL + e;
+        }
+        if (p.mode == MODE_AMP && !target_block) {
+            g.sync();
+            return;
+        }
     }
 
     // 2) collapse onto the block's tops: T[t] = sum over the other top slots
@@ -824,13 +830,35 @@ __device__ void readout_and_sample(const KParams& p, const Chain<R>& ch, const G
             int xh = 0;
             do {
                 const int hv = base | xh;
-                acc = cfma(ch.rowdot[hv], cmul(ch.wt[hv & (Na - 1)], ch.wt[Na + (hv >> Sa)]), acc);
+                C v;
+                if (direct) {
+                    v = L[swz(hv)];
+                    mx = rmax(mx, rmax(rabs(v.x), rabs(v.y)));
+                } else {
+                    v = ch.rowdot[hv];
+                }
+                acc = cfma(v, cmul(ch.wt[hv & (Na - 1)], ch.wt[Na + (hv >> Sa)]), acc);
                 xh = (xh - mh) & mh;
             } while (xh != 0);
+            if (direct) acc = cmul(acc, Rk[0]);
             if (ncb == 1)
                 ch.T[t] = acc;
             else
                 ch.part[u] = acc;
+        }
+    }
+    if (direct) {
+        // every entry of L was read by exactly one work item
+        mx = group_max<R>(ch, gl, mx);
+        g.sync();
+        if (g.lt == 0) {
+            const int e = scale_exp<R>(mx);
+            ch.misc[1] = -e;
+            ch.misc[0] = eL + e;
+        }
+        if (p.mode == MODE_AMP && !target_block) {
+            g.sync();
+            return;
         }
     }
     g.sync();
