@@ -630,7 +630,11 @@ __device__ void build_fslot(const KParams& p, const Chain<R>& ch, const Grp& g, 
     const int32_t* gref = P_<int32_t>(p, p.off.gate_refs);
     const DevCostGate* G = P_<DevCostGate>(p, p.off.cost_gates);
     const bool clean = chain_clean<R>(p, ch);
-    for (int j = g.lt; j < p.hdr.S; j += g.nt) {
+    // (slots and sites start on other threads than the table entries of
+    // build_tables, so that their global-memory loads overlap)
+    const int lts = g.nt >= 64 ? (g.lt + g.nt / 2) % g.nt : g.lt;
+    const int lti = g.nt >= 64 ? (g.lt + 3 * g.nt / 4) % g.nt : g.lt;
+    for (int j = lts; j < p.hdr.S; j += g.nt) {
         const DevLiveSlot sl = live[j];
         if (sl.q >= 0 && sl.role >= 0) ch.misc[2 + sl.role] = j;
         if (sl.ndep != 0xFF && clean) {
@@ -672,7 +676,7 @@ __device__ void build_fslot(const KParams& p, const Chain<R>& ch, const Grp& g, 
     // passes, so that their global-memory latency is off its path)
     const DevBlockSite* sites = P_<DevBlockSite>(p, p.off.block_sites) + br.site_begin;
     const int nb = br.site_end - br.site_begin, mb = p.hdr.max_block;
-    for (int i = g.lt; i < nb; i += g.nt) {
+    for (int i = lti; i < nb; i += g.nt) {
         const DevBlockSite st = sites[i];
         ch.sa[4 * i] = mixel<R>(p, ch, m, st.q, 0, 0);
         ch.sa[4 * i + 1] = mixel<R>(p, ch, m, st.q, 0, 1);
