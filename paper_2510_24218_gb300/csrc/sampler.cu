@@ -869,9 +869,9 @@ __device__ void readout_and_sample(const KParams& p, const Chain<R>& ch, const G
 
     // 3) sequential resampling of the block's sites by the first warp (their
     //    mixers and descriptors were staged in shared memory by build_fslot):
-    //    lane 0 takes each decision (FP64 conditional, the chain's
-    //    precomputed Philox draw); the lanes then contract the resampled top
-    //    away in parallel. The block's bits live in a register mask until they
+    //    each decision (FP64 conditional, the chain's precomputed Philox draw)
+    //    is taken by every lane alike; the lanes then contract the resampled
+    //    top away in parallel. The block's bits live in a register mask until they
     //    are written back.
     const int wsz = g.nt < 32 ? g.nt : 32;
     if (g.lt < wsz) {
@@ -900,7 +900,10 @@ __device__ void readout_and_sample(const KParams& p, const Chain<R>& ch, const G
             const int sold = (sbits >> i) & 1;
             int snew = sold;
             bool stop = false;
-            if (lane == 0) {
+            // every lane takes the same decision from the same (broadcast)
+            // reads; only lane 0 writes outputs and counters
+            {
+                const bool w = lane == 0;
                 const int row = srow[i], mono = smono[i];
                 const int rest = (int)((sbits >> (i + 1)) << 1);   // later sites keep their bits
                 const C c0 = cur[rest], c1 = cur[rest | 1];
@@ -909,7 +912,7 @@ __device__ void readout_and_sample(const KParams& p, const Chain<R>& ch, const G
                 if (p.mode == MODE_AMP) {
                     if (i == p.amp_pos) {
                         const C a = sold ? amp1 : amp0;
-                        if (ch.rank == 0) {
+                        if (w && ch.rank == 0) {
                             p.amp_out[2 * chain] = ldexp((double)a.x, escale);
                             p.amp_out[2 * chain + 1] = ldexp((double)a.y, escale);
                         }
@@ -920,7 +923,7 @@ __device__ void readout_and_sample(const KParams& p, const Chain<R>& ch, const G
                     const C a0 = sold ? A01 : A00;
                     snew = (a0.x != (R)0 || a0.y != (R)0) ? 0 : 1;
                 } else {
-                    if (p.trace && ch.rank == 0) {
+                    if (w && p.trace && ch.rank == 0) {
                         double* tr = p.trace + ((size_t)chain * h.n_sampled + row) * 4;
                         tr[0] = ldexp((double)amp0.x, escale);
                         tr[1] = ldexp((double)amp0.y, escale);
@@ -944,17 +947,16 @@ __device__ void readout_and_sample(const KParams& p, const Chain<R>& ch, const G
                         if (Pt > 0.0) {
                             const double up = ch.ud[row] * Pt;
                             snew = up < p0 ? 0 : 1;
-                            if (fabs(up - p0) < 1e-6 * Pt && ch.rank == 0) atomicAdd(&p.counters[CNT_NEAR], 1ull);
-                        } else if (ch.rank == 0) {
+                            if (w && fabs(up - p0) < 1e-6 * Pt && ch.rank == 0) atomicAdd(&p.counters[CNT_NEAR], 1ull);
+                        } else if (w && ch.rank == 0) {
                             atomicAdd(&p.counters[CNT_ZERO], 1ull);   // zero-mass block: stay (Sec. 2)
                         }
                     }
                 }
             }
-            stop = __shfl_sync(0xffffffffu, (int)stop, 0, wsz);
             if (stop) break;
-            snew = __shfl_sync(0xffffffffu, snew, 0, wsz);
             sbits = (sbits & ~(1u << i)) | ((unsigned)snew << i);
+            if (i + 1 == nb) break;   // (nothing reads the last contraction)
             // contract this site's top with its mixer weight at the new bit
             // (ping-pong between the two halves of the T area)
             const C w0 = snew ? A10 : A00, w1 = snew ? A11 : A01;
