@@ -365,6 +365,9 @@ __device__ __forceinline__ int swz(int i) { return i ^ ((i >> 4) & 15); }
 template <typename C> struct LocalAcc {
     C* buf;
     __device__ __forceinline__ C& operator()(int idx) const { return buf[swz(idx)]; }
+    // entry b0 | o given swz(b0) and swz(o) (swz is linear over XOR, and b0
+    // and o have no common bit)
+    __device__ __forceinline__ C& at(int b0, int sb0, int o, int so) const { return buf[sb0 ^ so]; }
 };
 template <typename C> struct DistAcc {
     C* const* rl;   // every rank's part (a table in shared memory)
@@ -374,6 +377,7 @@ template <typename C> struct DistAcc {
         const int r = idx >> wloc, o = swz(idx & ((1 << wloc) - 1));
         return r == rank ? loc[o] : rl[r][o];
     }
+    __device__ __forceinline__ C& at(int b0, int sb0, int o, int so) const { return (*this)(b0 | o); }
 };
 
 // One tiled pass over tiles [t0, t1) of a 2^W-entry frontier by the threads of
@@ -384,9 +388,12 @@ __device__ void tile_pass(const KParams& p, const Chain<R>& ch, const Grp& g, co
                           const Acc& acc, int t_begin, int t_end) {
     using C = typename CT<R>::T;
     constexpr int E = 1 << T;
-    int msk[4] = {0, 0, 0, 0};
+    int msk[4] = {0, 0, 0, 0}, smk[4] = {0, 0, 0, 0};
 #pragma unroll
-    for (int k = 0; k < T; ++k) msk[k] = 1 << f.tbits[k];
+    for (int k = 0; k < T; ++k) {
+        msk[k] = 1 << f.tbits[k];
+        smk[k] = swz(msk[k]);
+    }
     int sb4[4] = {f.tbits[0], f.tbits[1], f.tbits[2], f.tbits[3]};
 #pragma unroll
     for (int a = 1; a < T; ++a)
@@ -402,14 +409,18 @@ __device__ void tile_pass(const KParams& p, const Chain<R>& ch, const Grp& g, co
         int b0 = t0;
 #pragma unroll
         for (int k = 0; k < T; ++k) b0 = ((b0 >> sb4[k]) << (sb4[k] + 1)) | (b0 & ((1 << sb4[k]) - 1));
+        const int sb0 = swz(b0);
         C x[E];
 #pragma unroll
         for (int e = 0; e < E; ++e) {
-            int o = 0;
+            int o = 0, so = 0;
 #pragma unroll
             for (int k = 0; k < T; ++k)
-                if (e & (1 << k)) o |= msk[k];
-            x[e] = acc(b0 | o);
+                if (e & (1 << k)) {
+                    o |= msk[k];
+                    so ^= smk[k];
+                }
+            x[e] = acc.at(b0, sb0, o, so);
         }
         for (int s = 0; s < f.nst; ++s) {
             const uint8_t type = stg[s].type, arg = stg[s].arg;
@@ -447,11 +458,14 @@ __device__ void tile_pass(const KParams& p, const Chain<R>& ch, const Grp& g, co
         }
 #pragma unroll
         for (int e = 0; e < E; ++e) {
-            int o = 0;
+            int o = 0, so = 0;
 #pragma unroll
             for (int k = 0; k < T; ++k)
-                if (e & (1 << k)) o |= msk[k];
-            acc(b0 | o) = x[e];
+                if (e & (1 << k)) {
+                    o |= msk[k];
+                    so ^= smk[k];
+                }
+            acc.at(b0, sb0, o, so) = x[e];
         }
     }
 }
