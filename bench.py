@@ -138,6 +138,26 @@ class ClockSampler:
 
 # -------------------------------------------------------------------- ours
 
+def replica_first(rank, n_samples, warmup, steps):
+    """First sample id of a replica: every rank draws its own range of sample
+    ids (warm-up, timed and end-to-end steps), disjoint from the other
+    ranks'; with the counter-based draws each sample is the same as on one
+    GPU."""
+    return rank * n_samples * (warmup + steps + 1)
+
+
+def max_over_ranks(value, world, device=None):
+    """The largest value over the ranks (the timed region of the slowest)."""
+    if world <= 1:
+        return float(value)
+    import torch
+    t = torch.tensor([value], dtype=torch.float64)
+    if device is not None and device.type == "cuda":
+        t = t.to(device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
 def run_ours(args, rank, world):
     import numpy as np
     import torch
@@ -158,7 +178,7 @@ def run_ours(args, rank, world):
     out = torch.empty((n_samples, words), dtype=torch.int64, device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # > L2 (129 MB)
     stream = torch.cuda.current_stream(dev)
-    first = rank * n_samples * (args.warmup + args.steps + 1)
+    first = replica_first(rank, n_samples, args.warmup, args.steps)
 
     def step(i, stats=False):
         return pw.pw_sample(plan, args.seed, first + i * n_samples, n_samples, out, None, stream, want_stats=stats)
@@ -188,11 +208,7 @@ def run_ours(args, rank, world):
         torch.distributed.barrier()
     torch.cuda.synchronize(dev)
     ms = sum(a.elapsed_time(b) for a, b in ev)
-    ms_t = torch.tensor([ms], dtype=torch.float64)
-    if world > 1:
-        ms_t = ms_t.to(dev)
-        torch.distributed.all_reduce(ms_t, op=torch.distributed.ReduceOp.MAX)
-    ms = float(ms_t.item())
+    ms = max_over_ranks(ms, world, dev)
     total = n_samples * args.steps * world
     value = total / (ms / 1e3)
     per_launch_ms = ms / max(1, launches)
