@@ -29,6 +29,10 @@ METRIC = "exact samples/s on 1 GB300 (mixed vs plain FP32, same accuracy); TC % 
 
 # FP32 FMA peak of the part: 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+# FP64 (non-tensor) rate of the part: the nominal 1.25 TFLOP/s
+FP64_PEAK_TFLOPS = 1.25
+# arithmetic of each workload's configuration (the 12-qubit one is complex128)
+DEFAULT_PRECISION = {"grid6x6": "fp32", "n12": "fp64", "heavyhex400": "fp32", "grid8x8noisy": "fp32"}
 
 
 def workload(name):
@@ -291,12 +295,15 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="grid6x6")
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--precision", default=None, choices=["fp32", "fp64"],
+                    help="default: the workload's own (fp64 for n12, fp32 otherwise)")
     ap.add_argument("--seed", type=int, default=20251203)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--samples", type=int, default=0, help="override samples per step (profiling)")
     args = ap.parse_args()
+    if args.precision is None:
+        args.precision = DEFAULT_PRECISION.get(args.workload, "fp32")
 
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
@@ -330,7 +337,7 @@ def main():
         torch.distributed.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     r = run_ours(args, rank, world)
     if rank == 0:
-        peak = FP32_PEAK_TFLOPS if args.precision == "fp32" else None
+        peak = FP32_PEAK_TFLOPS if args.precision == "fp32" else FP64_PEAK_TFLOPS
         line = {
             "metric": METRIC, "value": r["value"], "unit": "samples/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": r["ms"] / args.steps, "higher_is_better": True,
@@ -346,8 +353,9 @@ def main():
             "roofline": {"bound": "alu", "achieved": r["achieved"], "peak": peak, "unit": "TFLOP/s",
                          "frac": (r["achieved"] / peak) if peak else None,
                          "traffic": profiled_traffic(args.workload, r["B"]),
-                         "kernel": "pw_chain_kernel<float>",
-                         "peak_note": "FP32 FMA peak derived: 152 SMs x 128 lanes x 2 x 2.07 GHz"},
+                         "kernel": "pw_chain_kernel<float>" if args.precision == "fp32" else "pw_chain_kernel<double>",
+                         "peak_note": ("FP32 FMA peak derived: 152 SMs x 128 lanes x 2 x 2.07 GHz" if args.precision == "fp32"
+                                       else "nominal FP64 (non-tensor) rate, 1.25 TFLOP/s")},
             "cpu_baseline": cpu,
             "e2e": {"value": r["e2e"], "unit": "samples/s", "h2d_bytes_per_step": r["h2d"],
                     "d2h_bytes_per_step": r["d2h"]},
