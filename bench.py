@@ -260,9 +260,9 @@ def kernel_sources_sha256():
 
 
 def profiled_traffic(workload_name, chains_per_launch):
-    """DRAM bytes (read + write) of one launch, from the ncu capture summarised
-    under profiles/, or None when there is none for this workload and launch
-    size or the kernel sources have changed since it was taken."""
+    """DRAM bytes (read + write) of one FP32 launch, from the ncu capture
+    summarised under profiles/, or None when there is none for this workload
+    and launch size or the kernel sources have changed since it was taken."""
     name = PROFILE_OF.get(workload_name)
     if name is None:
         return None
@@ -352,7 +352,7 @@ def main():
                        "near_boundary_draws_in_warmup": int(r["near"])},
             "roofline": {"bound": "alu", "achieved": r["achieved"], "peak": peak, "unit": "TFLOP/s",
                          "frac": (r["achieved"] / peak) if peak else None,
-                         "traffic": profiled_traffic(args.workload, r["B"]),
+                         "traffic": profiled_traffic(args.workload, r["B"]) if args.precision == "fp32" else None,
                          "kernel": "pw_chain_kernel<float>" if args.precision == "fp32" else "pw_chain_kernel<double>",
                          "peak_note": ("FP32 FMA peak derived: 152 SMs x 128 lanes x 2 x 2.07 GHz" if args.precision == "fp32"
                                        else "nominal FP64 (non-tensor) rate, 1.25 TFLOP/s")},
