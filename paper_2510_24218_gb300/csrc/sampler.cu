@@ -1208,8 +1208,12 @@ __device__ void run_chain(const KParams& p, const Chain<R>& ch, int gid, int lt,
     G.sync();
 }
 
-template <typename R>
-__global__ void __launch_bounds__(512, 1) pw_chain_kernel(const KParams p) {
+// WIDE: the same kernel for CTAs of at most 64 threads with at most 5 of them
+// per SM (the chains that shared memory admits on the 6x6 grid): up to 204
+// registers per thread instead of 128, no occupancy lost when shared memory
+// is the limit.
+template <typename R, bool WIDE = false>
+__global__ void __launch_bounds__(WIDE ? 64 : 512, WIDE ? 5 : 1) pw_chain_kernel(const KParams p) {
     using C = typename CT<R>::T;
     extern __shared__ __align__(16) unsigned char smem[];
     // The launches of one sampling call take disjoint chains and read only the
@@ -1355,7 +1359,7 @@ template <typename R> int launch(pw_plan* plan, KParams& kp, cudaStream_t st, ui
     if (kp.sm.group_bytes > maxsm)
         return set_error(PW_ERR_TOO_LARGE, "per-chain shared memory (" + std::to_string(kp.sm.group_bytes) +
                                                " B) exceeds 227 KB");
-    auto kern = pw_chain_kernel<R>;
+    void (*kern)(const KParams) = pw_chain_kernel<R, false>;
     cudaError_t e;
     if (hp.ctas_per_chain > 1) {
         // one chain per thread-block cluster
@@ -1420,6 +1424,21 @@ template <typename R> int launch(pw_plan* plan, KParams& kp, cudaStream_t st, ui
     kp.gpc = gpc;
     const int threads = kp.tpc * gpc;
     const size_t smem = (size_t)kp.sm.group_bytes * gpc;
+    if constexpr (sizeof(R) == 4) {
+        // the wide-register build when it keeps at least as many CTAs per SM
+        if (threads <= 64) {
+            auto wide = pw_chain_kernel<R, true>;
+            int on = 0, ow = 0;
+            if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) == cudaSuccess &&
+                cudaFuncSetAttribute(wide, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) == cudaSuccess &&
+                cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100) == cudaSuccess &&
+                cudaFuncSetAttribute(wide, cudaFuncAttributePreferredSharedMemoryCarveout, 100) == cudaSuccess &&
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&on, kern, threads, smem) == cudaSuccess &&
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ow, wide, threads, smem) == cudaSuccess && ow >= on)
+                kern = wide;
+            cudaGetLastError();
+        }
+    }
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
     int dev = plan->device, nsm = 0, occ = 0;
