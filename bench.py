@@ -277,9 +277,12 @@ def profiled_traffic(workload_name, chains_per_launch):
             fields[k] = v.strip()
     if fields.get("kernel-sources-sha256") != kernel_sources_sha256():
         return None
-    if int(fields.get("chains-per-launch", -1)) != chains_per_launch:
+    try:
+        if int(fields.get("chains-per-launch", -1)) != chains_per_launch:
+            return None
+        return float(fields["dram-bytes-per-launch"])
+    except (KeyError, ValueError):
         return None
-    return float(fields["dram-bytes-per-launch"])
 
 
 def _plan_blob_bytes(pw, plan):
