@@ -364,10 +364,12 @@ __device__ __forceinline__ int swz(int i) { return i ^ ((i >> 4) & 15); }
 // a cluster (entry idx in rank idx >> wloc at offset idx & (2^wloc - 1)).
 template <typename C> struct LocalAcc {
     C* buf;
-    __device__ __forceinline__ C& operator()(int idx) const { return buf[swz(idx)]; }
+    int base = 0;   // first entry held in buf (a cluster rank's part: rank << wloc)
+    __device__ __forceinline__ C& operator()(int idx) const { return buf[swz(idx) - base]; }
     // entry b0 | o given swz(b0) and swz(o) (swz is linear over XOR, and b0
-    // and o have no common bit)
-    __device__ __forceinline__ C& at(int b0, int sb0, int o, int so) const { return buf[sb0 ^ so]; }
+    // and o have no common bit; it leaves bits above 7 alone, so subtracting
+    // a base of whole 256-entry multiples commutes with it)
+    __device__ __forceinline__ C& at(int b0, int sb0, int o, int so) const { return buf[(sb0 ^ so) - base]; }
 };
 template <typename C> struct DistAcc {
     C* const* rl;   // every rank's part (a table in shared memory)
@@ -529,15 +531,21 @@ __device__ __forceinline__ void tile_pass_any(const KParams& p, const Chain<R>& 
                                               int sb, typename CT<R>::T* buf, int W, bool dist) {
     using C = typename CT<R>::T;
     const int ntiles = (1 << W) >> T;
-    if (dist) {
-        // rank r takes the tiles whose number has r in its top bits: a pass whose
-        // tile bits avoid the rank bits stays inside this CTA's shared memory
+    bool crosses = false;   // split frontier, a tile bit among the rank bits: tiles span CTAs
+    if (dist)
+        for (int k = 0; k < T; ++k) crosses |= f.tbits[k] >= p.wloc;
+    if (crosses) {
+        // rank r takes the tiles whose number has r in its top bits
         const int per = ntiles / p.cr;
         tile_pass<R, T>(p, ch, g, f, sb, DistAcc<C>{ch.rL, ch.L, p.wloc, ch.rank}, ch.rank * per, (ch.rank + 1) * per);
-    } else if (ntiles < g.nt) {
+    } else if (!dist && ntiles < g.nt) {
         flat_pass<R>(p, ch, g, f, sb, buf, W);
     } else {
-        tile_pass<R, T>(p, ch, g, f, sb, LocalAcc<C>{buf}, 0, ntiles);
+        // this CTA's own entries: the whole tensor, or (split frontier, tile
+        // bits below the rank bits) the tiles of this rank's part
+        const int per = dist ? ntiles / p.cr : ntiles;
+        const int t0 = dist ? ch.rank * per : 0;
+        tile_pass<R, T>(p, ch, g, f, sb, LocalAcc<C>{dist ? ch.L : buf, dist ? ch.rank << p.wloc : 0}, t0, t0 + per);
     }
 }
 
