@@ -119,3 +119,37 @@ def test_grid8x8_noisy_dirty_chains_against_alg2(pw):
         worst = max(pair_err(rows[r][1], g["trace"][k, r]) for r in range(len(rows)))
         assert worst < 1e-5
     assert dirty >= 1
+
+
+@pytest.mark.parametrize("cr", [2, 8])
+def test_forced_cluster_split_fp64(pw, cr):
+    """The FP64 build on the cluster path (the 64-qubit grid's FP64 plan uses
+    it by itself): bits equal to Alg. 1 and candidate pairs to 1e-12."""
+    spec = _grid_spec(4, 4, 2, seed=110 + cr)
+    g = run_gpu(pw, spec, 48, seed=cr, precision=pw.PW_PREC_FP64, ctas_per_chain=cr, order=pw.PW_ORDER_NATURAL)
+    assert g["plan_stats"]["ctas_per_chain"] == cr
+    ops = OC.qaoa_circuit(spec)
+    traces = [[] for _ in range(48)]
+    want, ost = OS.sample_sv(spec.n, ops, cr, list(range(48)), order=g["order"], traces=traces)
+    mism = int((~(want == g["bits"]).all(axis=1)).sum())
+    assert mism <= max(ost.near_boundary, g["stats"]["near_boundary"])
+    worst = max(pair_err(traces[k][spec.n + r][1], g["trace"][k, r])
+                for k in range(48) if (want[k] == g["bits"][k]).all() for r in range(g["plan_stats"]["sampled_gates"]))
+    assert worst < 1e-12
+
+
+def test_grid8x8_noisy_fp64_plan_runs_on_eight_ctas(pw):
+    """The 64-qubit noisy workload in FP64 needs 8 CTAs per chain (2^13 of the
+    2^16 entries each): one chain against Alg. 2 bit for bit and its candidate
+    pairs to 1e-10 along the trajectory."""
+    spec = W.grid_8x8_p2_noisy()
+    g = run_gpu(pw, spec, 2, seed=2031, precision=pw.PW_PREC_FP64)
+    assert g["plan_stats"]["ctas_per_chain"] == 8
+    ops = OC.qaoa_circuit(spec)
+    trace = []
+    s, st = OS.noisy_sample(spec.n, ops, 2031, 1, order=g["order"], backend="tn", trace=trace)
+    if st.near_boundary == 0:
+        assert np.array_equal(s, g["bits"][1])
+    rows = [t for t in trace if len(t[0]) == 2][spec.n:]
+    worst = max(pair_err(rows[r][1], g["trace"][1, r]) for r in range(len(rows)))
+    assert worst < 1e-10
