@@ -256,8 +256,8 @@ std::vector<std::vector<int>> greedy_blocks(const std::vector<std::vector<int>>&
 std::vector<int> bfs_order(const std::vector<std::vector<int>>& adj, int start) {
     int n = (int)adj.size();
     std::vector<int> order, seen(n, 0);
-    for (int s0 = 0; s0 < n; ++s0) {
-        int s = (s0 == 0) ? start : s0;
+    for (int s0 = -1; s0 < n; ++s0) {   // roots: start, then every vertex in turn
+        const int s = s0 < 0 ? start : s0;
         if (seen[s]) continue;
         std::vector<int> q{s};
         seen[s] = 1;
@@ -858,6 +858,11 @@ int build_plan(const pw_circuit* c, const pw_plan_opts& opts, HostPlan& hp) {
             if (n <= 2048) cands.push_back(greedy_order(adj, s));
         }
         for (auto& o : cands) {
+            std::vector<int> chk = o;   // (every candidate must order every qubit once)
+            std::sort(chk.begin(), chk.end());
+            bool perm = (int)chk.size() == n;
+            for (int i = 0; perm && i < n; ++i) perm = chk[i] == i;
+            if (!perm) continue;
             double cst = 0;
             int wdt = width_singletons(adj, o, &cst);
             if (wdt < best_w || (wdt == best_w && cst < best_cost)) {

@@ -349,3 +349,22 @@ def test_heavy_hex_400_fp32_amplitudes_within_1e5(pw):
         state = np.array([final[j] if j in done else h_bits[j] for j in range(spec.n)], dtype=np.uint8)
         tab = TN.amplitudes(spec.n, [ops[i] for i in order[:t + 1]], state, open_qubits=(q,))
         assert pair_err([tab[0], tab[1]], g["trace"][0, r]) < 1e-5, r
+
+
+def _degenerate():
+    from tests import test_native_host as H
+    return H._degenerate_specs()
+
+
+@pytest.mark.parametrize("spec", _degenerate(), ids=lambda s: s.name)
+def test_degenerate_circuits_against_alg1(pw, spec):
+    """No edges, isolated qubits (qubit 0 among them), gamma = 0, beta = 0 and a
+    monomial mixer (a deterministic move, Sec. 2): bits equal to Alg. 1 on
+    the same draws; candidate pairs too where every mixer is sampled."""
+    if spec.name == "monomial_mixer":
+        g = run_gpu(pw, spec, 64, seed=12, trace=False)
+        want, ost = OS.sample_sv(spec.n, OC.qaoa_circuit(spec), 12, list(range(64)), order=g["order"])
+        mism = int((~(want == g["bits"]).all(axis=1)).sum())
+        assert mism <= max(g["stats"]["near_boundary"], ost.near_boundary)
+    else:
+        check_against_sv(pw, spec, 64, seed=12)

@@ -159,3 +159,37 @@ def test_bad_options(pw):
 def test_pack_roundtrip(pw):
     x = W.random_bitstrings(9, 130, seed=3)
     assert np.array_equal(pw.unpack_bits(pw.pack_bits(x), 130), x)
+
+
+def _degenerate_specs():
+    """Degenerate QAOA circuits: no edges at all, isolated qubits (qubit 0
+    among them), a monomial mixer (beta = pi/2: RX(pi) = -iX), gamma = 0 and
+    beta = 0 (identity mixers, nothing to sample)."""
+    def spec(n, edges, p, gammas, betas, name):
+        e = np.array(edges, dtype=np.int64).reshape(-1, 2)
+        return W.QaoaSpec(n=n, edges=e, weights=np.ones(len(e)), gammas=np.array(gammas, dtype=float),
+                          betas=np.array(betas, dtype=float), h=None, depol2=0.0, ad_gamma=0.0, name=name, extra={})
+    return [spec(1, [], 1, [0.3], [0.2], "n1_no_edges"),
+            spec(2, [], 2, [0.3, 0.1], [0.2, 0.5], "n2_no_edges_p2"),
+            spec(3, [(1, 2)], 2, [0.4, 0.2], [0.3, 0.6], "qubit0_isolated"),
+            spec(5, [(1, 2), (3, 4)], 3, [0.4, 0.2, 0.7], [0.3, 0.6, 0.1], "qubits_0_isolated_pairs"),
+            spec(4, [(0, 1), (1, 2), (2, 3)], 2, [0.4, 0.3], [np.pi / 2, 0.5], "monomial_mixer"),
+            spec(4, [(0, 1), (1, 2), (2, 3)], 2, [0.0, 0.0], [0.3, 0.7], "gamma0"),
+            spec(5, [(0, 1), (1, 2), (2, 3), (3, 4)], 1, [0.5], [0.0], "beta0")]
+
+
+@pytest.mark.parametrize("spec", _degenerate_specs(), ids=lambda s: s.name)
+def test_degenerate_circuits_plan_every_gate(pw, spec):
+    """Every op appears once in the execution order (an isolated qubit 0 was
+    once left out of the sweep order), and every non-diagonal mixer is a
+    sampled gate."""
+    from oracle import circuit as OC
+    c = _circ(pw, spec)
+    plan = pw.pw_plan_build(c)
+    order = pw.pw_plan_exec_order(plan)
+    assert sorted(order.tolist()) == list(range(pw.pw_circuit_num_ops(c)))
+    ops = OC.qaoa_circuit(spec)
+    mixers = sum(1 for o in ops[spec.n:] if o.kind == "gate" and len(o.qubits) == 1 and not OC.is_diagonal(o.mat))
+    assert pw.pw_plan_stats(plan)["sampled_gates"] == mixers
+    pw.pw_plan_destroy(plan)
+    pw.pw_circuit_destroy(c)
