@@ -368,3 +368,61 @@ def test_degenerate_circuits_against_alg1(pw, spec):
         assert mism <= max(g["stats"]["near_boundary"], ost.near_boundary)
     else:
         check_against_sv(pw, spec, 64, seed=12)
+
+
+def _general_circuit(n, edges, p, seed, monomial_at=None):
+    """Layers of random one-qubit unitaries separated by random diagonal
+    two-qubit gates on the edges and random one-qubit diagonal gates; the
+    first layer acts on |0^n>. monomial_at = (layer, qubit) puts a Pauli X
+    there (a deterministic move)."""
+    rng = np.random.default_rng(seed)
+
+    def su2():
+        z = rng.normal(size=(2, 2)) + 1j * rng.normal(size=(2, 2))
+        q, r = np.linalg.qr(z)
+        return q * (np.diag(r) / np.abs(np.diag(r)))
+
+    ops = []
+    for m in range(p + 1):
+        if m > 0:
+            for (a, b) in edges:
+                ops.append(OC.gate((a, b), np.diag(np.exp(1j * rng.uniform(0, 2 * np.pi, 4)))))
+            for q in range(0, n, 3):
+                ops.append(OC.gate((q,), np.diag(np.exp(1j * rng.uniform(0, 2 * np.pi, 2)))))
+        for q in range(n):
+            A = np.array([[0, 1], [1, 0]], dtype=complex) if monomial_at == (m, q) else su2()
+            ops.append(OC.gate((q,), A))
+    return ops
+
+
+@pytest.mark.parametrize("n,rows,p,seed,mono", [(8, 2, 2, 5, None), (9, 3, 2, 6, (1, 4)), (6, 2, 3, 7, None)])
+def test_general_circuits_through_the_c_abi(pw, n, rows, p, seed, mono):
+    """Circuits built gate by gate (pw_circuit_add_gate), not QAOA: random
+    one-qubit unitaries between random diagonal gates, on a grid. Bits equal
+    to Alg. 1 on the same draws; candidate pairs within 1e-5 (FP32)."""
+    import torch
+    edges = [(a, b) for a, b in W.grid_edges(rows, n // rows)]
+    ops = _general_circuit(n, edges, p, seed, monomial_at=mono)
+    circ = pw.pw_circuit_create(n)
+    for o in ops:
+        pw.pw_circuit_add_gate(circ, list(o.qubits), o.mat)
+    plan = pw.pw_plan_build(circ)
+    st = pw.pw_plan_stats(plan)
+    N = 64
+    bits = torch.zeros((N, 1), dtype=torch.int64, device="cuda")
+    tr = torch.zeros((N, st["sampled_gates"], 4), dtype=torch.float64, device="cuda")
+    stats = pw.pw_sample(plan, 21, 0, N, bits, tr)
+    torch.cuda.synchronize()
+    order = pw.pw_plan_exec_order(plan)
+    got = pw.unpack_bits(bits.cpu().numpy(), n)
+    trace = tr.cpu().numpy()
+    traces = [[] for _ in range(N)]
+    want, ost = OS.sample_sv(n, ops, 21, list(range(N)), order=order, traces=traces)
+    mism = int((~(want == got).all(axis=1)).sum())
+    assert mism <= max(stats["near_boundary"], ost.near_boundary)
+    if mono is None:
+        worst = max(pair_err(traces[k][n + r][1], trace[k, r])
+                    for k in range(N) if (want[k] == got[k]).all() for r in range(st["sampled_gates"]))
+        assert worst < 1e-5
+    pw.pw_plan_destroy(plan)
+    pw.pw_circuit_destroy(circ)
