@@ -426,3 +426,63 @@ def test_general_circuits_through_the_c_abi(pw, n, rows, p, seed, mono):
         assert worst < 1e-5
     pw.pw_plan_destroy(plan)
     pw.pw_circuit_destroy(circ)
+
+
+def _general_noisy(n, edges, p, seed):
+    """A general circuit with channels: a bit flip listed with its X operator
+    first (so no chain state has fixed tables: every chain builds its tables)
+    after every two-qubit diagonal gate's first qubit, phase damping on every
+    qubit after each one-qubit layer."""
+    ops = _general_circuit(n, edges, p, seed)
+    out = []
+    X = np.array([[0, 1], [1, 0]], dtype=complex)
+    for o in ops:
+        out.append(o)
+        if o.kind == "gate" and len(o.qubits) == 2:
+            out.append(OC.kraus((o.qubits[0],), [np.sqrt(0.15) * X, np.sqrt(0.85) * np.eye(2)]))
+    res = []
+    layer_end = {i for i, o in enumerate(out) if o.kind == "gate" and len(o.qubits) == 1
+                 and not OC.is_diagonal(o.mat) and o.qubits[0] == n - 1}
+    for i, o in enumerate(out):
+        res.append(o)
+        if i in layer_end:
+            for q in range(n):
+                res.append(OC.kraus((q,), OC.phase_damping_kraus(0.3)))
+    return res
+
+
+def test_general_noisy_circuit_without_fixed_tables(pw):
+    """Channels whose operator 0 flips the frame, and phase damping: bits
+    equal to Alg. 2 on the same draws, and the distribution of 30000 samples
+    against the density-matrix diagonal (TVD within the 99th percentile of
+    multinomial noise)."""
+    import torch
+    n = 4
+    ops = _general_noisy(n, [(0, 1), (1, 2), (2, 3)], 2, seed=9)
+    circ = pw.pw_circuit_create(n)
+    for o in ops:
+        if o.kind == "gate":
+            pw.pw_circuit_add_gate(circ, list(o.qubits), o.mat)
+        else:
+            pw.pw_circuit_add_kraus(circ, list(o.qubits), o.mats)
+    plan = pw.pw_plan_build(circ)
+    order = pw.pw_plan_exec_order(plan)
+    N = 30000
+    bits = torch.zeros((N, 1), dtype=torch.int64, device="cuda")
+    stats = pw.pw_sample(plan, 31, 0, N, bits)
+    torch.cuda.synchronize()
+    got = pw.unpack_bits(bits.cpu().numpy(), n)
+    mism = near = 0
+    for k in range(60):
+        s, st = OS.noisy_sample(n, ops, 31, k, order=order)
+        near += st.near_boundary
+        mism += int(not np.array_equal(s, got[k]))
+    assert mism <= max(near, stats["near_boundary"])
+    pdm = np.real(np.diag(SV.density_run(n, ops)))
+    idx = (got.astype(np.int64) << np.arange(n)).sum(axis=1)
+    emp = np.bincount(idx, minlength=1 << n) / N
+    rng = np.random.default_rng(2)
+    thr = np.quantile([0.5 * np.abs(rng.multinomial(N, pdm) / N - pdm).sum() for _ in range(200)], 0.99)
+    assert 0.5 * np.abs(emp - pdm).sum() < thr
+    pw.pw_plan_destroy(plan)
+    pw.pw_circuit_destroy(circ)
