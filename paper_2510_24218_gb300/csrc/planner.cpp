@@ -89,7 +89,7 @@ void round_c32(cd v, float& re, float& im) {
 int parse_layers(const pw_circuit* c, Layered& L) {
     const int n = c->n;
     L.n = n;
-    std::vector<int> pending;
+    std::vector<int> pending, deferred;
     std::vector<char> done(n, 0);
     int cur = -1, cur_count = 0;
     bool cost_in_layer = false;
@@ -120,12 +120,30 @@ int parse_layers(const pw_circuit* c, Layered& L) {
                 done[q] = 1;
                 ++cur_count;
                 L.mixer_ops[cur].push_back(id);
+                if (cur_count == n) {   // layer complete: the ops moved past it open the next section
+                    pending = deferred;
+                    deferred.clear();
+                }
                 continue;
             }
         }
         // diagonal gate or channel
         if (cur < 0) return set_error(PW_ERR_UNSUPPORTED, "operations before the first one-qubit gate layer");
         if (cur_count < n) {
+            // inside a one-qubit layer: it commutes with the layer's gates on
+            // other qubits (and resampling a qubit leaves the others' bits
+            // alone), so it moves past the layer when all its qubits already
+            // had their gate, or before it when none did
+            int nd = 0;
+            for (int q : op.qubits) nd += done[q] ? 1 : 0;
+            if (nd == m) {
+                deferred.push_back(id);
+                continue;
+            }
+            if (nd == 0 && cur >= 1) {
+                L.sections.back().push_back(id);
+                continue;
+            }
             cost_in_layer = true;
             return set_error(PW_ERR_UNSUPPORTED, "diagonal gates or channels inside a one-qubit gate layer");
         }

@@ -486,3 +486,73 @@ def test_general_noisy_circuit_without_fixed_tables(pw):
     assert 0.5 * np.abs(emp - pdm).sum() < thr
     pw.pw_plan_destroy(plan)
     pw.pw_circuit_destroy(circ)
+
+
+def _chip_noise_qaoa(spec, rates):
+    """A QAOA circuit under a device noise model built from LSM channels only:
+    a two-qubit Pauli channel with unequal rates after every RZZ, a one-qubit
+    Pauli channel with unequal X/Y/Z rates after every RX, amplitude plus phase
+    damping (T1/T2) on every qubit after each mixer layer, and a readout flip
+    (bit-flip channel) on every qubit at the end."""
+    from oracle.circuit import PAULI
+    p2, (px, py, pz), g1, lam, ro = rates
+    w2 = [1.0 - p2] + [p2 * (1 + (k % 3)) / 30.0 for k in range(1, 16)]   # unequal, sum p2
+    w2 = np.array(w2) / sum(w2) * 1.0
+    k2 = [np.sqrt(w2[k]) * np.kron(PAULI[k // 4], PAULI[k % 4]) for k in range(16)]
+    k1 = [np.sqrt(1 - px - py - pz) * PAULI[0], np.sqrt(px) * PAULI[1], np.sqrt(py) * PAULI[2], np.sqrt(pz) * PAULI[3]]
+    out = []
+    base = OC.qaoa_circuit(spec)
+    n = spec.n
+    for i, o in enumerate(base):
+        out.append(o)
+        if i < n:
+            continue   # the first (Hadamard) layer
+        if o.kind == "gate" and len(o.qubits) == 2:
+            out.append(OC.kraus(o.qubits, k2))
+        elif o.kind == "gate" and len(o.qubits) == 1 and not OC.is_diagonal(o.mat):
+            out.append(OC.kraus(o.qubits, k1))
+            if o.qubits[0] == n - 1:
+                for q in range(n):
+                    out.append(OC.kraus((q,), OC.amplitude_damping_kraus(g1)))
+                    out.append(OC.kraus((q,), OC.phase_damping_kraus(lam)))
+    for q in range(n):
+        out.append(OC.kraus((q,), [np.sqrt(1 - ro) * PAULI[0], np.sqrt(ro) * PAULI[1]]))
+    return out
+
+
+def test_chip_noise_model_qaoa(pw):
+    """The device noise model of the paper's hardware discussion, as channels
+    through pw_circuit_add_kraus (rates raised to make every event common):
+    bits equal to Alg. 2 on the same draws, and 30000 samples against the
+    density-matrix diagonal."""
+    import torch
+    spec = W.random_qaoa(4, 2, seed=57)
+    ops = _chip_noise_qaoa(spec, (0.06, (0.02, 0.03, 0.05), 0.1, 0.2, 0.04))
+    n = spec.n
+    circ = pw.pw_circuit_create(n)
+    for o in ops:
+        if o.kind == "gate":
+            pw.pw_circuit_add_gate(circ, list(o.qubits), o.mat)
+        else:
+            pw.pw_circuit_add_kraus(circ, list(o.qubits), o.mats)
+    plan = pw.pw_plan_build(circ)
+    order = pw.pw_plan_exec_order(plan)
+    N = 30000
+    bits = torch.zeros((N, 1), dtype=torch.int64, device="cuda")
+    stats = pw.pw_sample(plan, 41, 0, N, bits)
+    torch.cuda.synchronize()
+    got = pw.unpack_bits(bits.cpu().numpy(), n)
+    mism = near = 0
+    for k in range(60):
+        s, st = OS.noisy_sample(n, ops, 41, k, order=order)
+        near += st.near_boundary
+        mism += int(not np.array_equal(s, got[k]))
+    assert mism <= max(near, stats["near_boundary"])
+    pdm = np.real(np.diag(SV.density_run(n, ops)))
+    idx = (got.astype(np.int64) << np.arange(n)).sum(axis=1)
+    emp = np.bincount(idx, minlength=1 << n) / N
+    rng = np.random.default_rng(3)
+    thr = np.quantile([0.5 * np.abs(rng.multinomial(N, pdm) / N - pdm).sum() for _ in range(200)], 0.99)
+    assert 0.5 * np.abs(emp - pdm).sum() < thr
+    pw.pw_plan_destroy(plan)
+    pw.pw_circuit_destroy(circ)

@@ -193,3 +193,40 @@ def test_degenerate_circuits_plan_every_gate(pw, spec):
     assert pw.pw_plan_stats(plan)["sampled_gates"] == mixers
     pw.pw_plan_destroy(plan)
     pw.pw_circuit_destroy(c)
+
+
+def test_ops_inside_a_layer_move_out_exactly(pw):
+    """Channels right after each one-qubit gate of a layer (a device noise
+    model) are moved past the layer by the planner; the exported order must
+    give the same density matrix as circuit order (the moves commute)."""
+    from oracle import circuit as OC
+    from oracle import statevector as SV
+    from tests.test_gpu_parity import _chip_noise_qaoa
+    spec = W.random_qaoa(4, 2, seed=57)
+    ops = _chip_noise_qaoa(spec, (0.06, (0.02, 0.03, 0.05), 0.1, 0.2, 0.04))
+    c = pw.pw_circuit_create(spec.n)
+    for o in ops:
+        if o.kind == "gate":
+            pw.pw_circuit_add_gate(c, list(o.qubits), o.mat)
+        else:
+            pw.pw_circuit_add_kraus(c, list(o.qubits), o.mats)
+    plan = pw.pw_plan_build(c)
+    order = pw.pw_plan_exec_order(plan)
+    assert sorted(order.tolist()) == list(range(len(ops)))
+    assert order.tolist() != list(range(len(ops)))   # something did move
+    r1 = SV.density_run(spec.n, ops)
+    r2 = SV.density_run(spec.n, [ops[i] for i in order])
+    assert np.abs(r1 - r2).max() < 1e-14
+    # an op on one qubit that had its gate and one that had not cannot move
+    c2 = pw.pw_circuit_create(2)
+    H = OC.h_mat()
+    pw.pw_circuit_add_gate(c2, [0], H)
+    pw.pw_circuit_add_gate(c2, [1], H)
+    pw.pw_circuit_add_gate(c2, [0], OC.rx_mat(0.3))
+    pw.pw_circuit_add_gate(c2, [0, 1], OC.rzz_mat(0.4))
+    pw.pw_circuit_add_gate(c2, [1], OC.rx_mat(0.3))
+    with pytest.raises(pw.PwError):
+        pw.pw_plan_build(c2)
+    pw.pw_plan_destroy(plan)
+    pw.pw_circuit_destroy(c)
+    pw.pw_circuit_destroy(c2)
