@@ -142,9 +142,12 @@ void pw_circuit_destroy(pw_circuit* c);
 /* Build the contraction plan (host only, no CUDA call). Supported structure:
  * layers of one non-diagonal 1-qubit gate per qubit (the first acting on
  * |0^n>), separated by sections of diagonal 1- or 2-qubit gates and LSM
- * channels; channels may also follow the last layer. Anything else returns
- * PW_ERR_UNSUPPORTED. The plan fixes the order of the commuting one-qubit
- * gates inside each layer (see pw_plan_exec_order). */
+ * channels; channels may also follow the last layer. A diagonal gate or
+ * channel placed inside a layer is accepted when it commutes out of it: all
+ * its qubits already had their gate of that layer (it moves after the layer)
+ * or none did (it moves before). Anything else returns PW_ERR_UNSUPPORTED.
+ * The plan fixes the order of the commuting one-qubit gates inside each layer
+ * and of the moved operations (see pw_plan_exec_order). */
 int pw_plan_build(const pw_circuit* c, const pw_plan_opts* opts, pw_plan** out);
 
 int pw_plan_stats(const pw_plan* plan, pw_plan_stats_t* out);

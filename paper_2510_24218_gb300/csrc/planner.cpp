@@ -92,7 +92,6 @@ int parse_layers(const pw_circuit* c, Layered& L) {
     std::vector<int> pending, deferred;
     std::vector<char> done(n, 0);
     int cur = -1, cur_count = 0;
-    bool cost_in_layer = false;
     for (int id = 0; id < (int)c->ops.size(); ++id) {
         const Op& op = c->ops[id];
         int m = (int)op.qubits.size();
@@ -103,8 +102,6 @@ int parse_layers(const pw_circuit* c, Layered& L) {
             if (!diag) {
                 int q = op.qubits[0];
                 if (cur >= 0 && cur_count < n) {
-                    if (cost_in_layer)
-                        return set_error(PW_ERR_UNSUPPORTED, "diagonal gates or channels inside a one-qubit gate layer");
                     if (done[q]) return set_error(PW_ERR_UNSUPPORTED, "qubit repeated inside a one-qubit gate layer");
                 } else {
                     if (cur == -1 && !pending.empty())
@@ -115,7 +112,6 @@ int parse_layers(const pw_circuit* c, Layered& L) {
                     pending.clear();
                     std::fill(done.begin(), done.end(), 0);
                     cur_count = 0;
-                    cost_in_layer = false;
                 }
                 done[q] = 1;
                 ++cur_count;
@@ -144,8 +140,8 @@ int parse_layers(const pw_circuit* c, Layered& L) {
                 L.sections.back().push_back(id);
                 continue;
             }
-            cost_in_layer = true;
-            return set_error(PW_ERR_UNSUPPORTED, "diagonal gates or channels inside a one-qubit gate layer");
+            return set_error(PW_ERR_UNSUPPORTED, "a diagonal gate or channel inside a one-qubit gate layer couples "
+                                                 "qubits before and after their gate");
         }
         pending.push_back(id);
     }
