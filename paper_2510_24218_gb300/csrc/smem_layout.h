@@ -28,7 +28,8 @@ inline SmemLayout make_layout(const HostPlan& hp, size_t csz) {
     L.L = take(hp.ctas_per_chain > 1 ? csz << hp.wloc : csz << (S * P));   // frontier tensor (this CTA's part)
     L.R = take((size_t)K * (csz << (S * (P - 1))));    // right environments
     L.Rexp = take(sizeof(int) * K);
-    L.rowdot = take(csz << S);
+    // (one layer in one CTA: every readout collapses straight from L)
+    L.rowdot = take(h.P == 1 && hp.ctas_per_chain <= 1 ? 16 : csz << S);
     L.wt = take(csz * ((size_t(1) << (S / 2)) + (size_t(1) << (S - S / 2))));   // readout weights, two halves
     L.T = take(csz << (h.max_block + 1));   // two halves (ping-pong)
     L.sit = take(csz * 4 * (size_t)h.max_block + sizeof(int) * 3 * (size_t)h.max_block);   // block's site data
