@@ -251,11 +251,17 @@ PROFILE_OF = {"grid6x6": "pw_chain_kernel_grid6x6_p2.md", "grid8x8noisy": "pw_ch
 
 
 def kernel_sources_sha256():
+    """sha256 of the kernel's sources with comments and blank space removed:
+    it changes with the code, not with its comments."""
     import hashlib
+    import re
     h = hashlib.sha256()
     for f in KERNEL_SOURCES:
-        with open(os.path.join(ROOT, f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, f)) as fh:
+            src = fh.read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", "", src)
+        h.update(" ".join(src.split()).encode())
     return h.hexdigest()
 
 

@@ -1,13 +1,15 @@
 // Pilot-wave sampler kernel for sm_103a.
 //
-// One group of threads (a warp, or a named-barrier group inside a CTA) owns
+// One group of threads (a warp, a named-barrier group inside a CTA, or a
+// thread-block cluster when the frontier exceeds one CTA's shared memory) owns
 // one Markov chain (Alg. 1 / Alg. 2) for its whole life: it walks every layer
 // of the circuit, keeps the frontier tensor of the plan's sweep in shared
 // memory, evaluates the candidate amplitudes amp(C_t, y) of each resampled
 // qubit with the plan's program of fused passes, and draws the update from the
 // normalised conditional with a counter-based Philox stream. Only the packed
 // output bits (and the optional amplitude trace) reach HBM: the kernel is
-// bound by shared-memory traffic and FP32 arithmetic, not by DRAM.
+// bound by latency (group barriers, dependent shared-memory and arithmetic
+// chains of one chain) and FP32 arithmetic, not by DRAM.
 //
 // Per block of resampled qubits the group first builds every table the block
 // needs (one parallel phase), then runs the fused passes back to back with one
