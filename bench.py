@@ -177,7 +177,10 @@ def run_ours(args, rank, world):
     circ = pw.pw_circuit_qaoa(spec.n, spec.edges, spec.weights, spec.h, spec.p, spec.gammas, spec.betas,
                               spec.depol2, spec.ad_gamma)
     plan = pw.pw_plan_build(circ, precision=prec, chains_per_launch=B)
+    tuned = pw.pw_plan_autotune(plan, 0, torch.cuda.current_stream(dev)) if args.autotune else 0
     pst = pw.pw_plan_stats(plan)
+    # the end-to-end leg builds its plans with the tuned shape (single-CTA plans)
+    e2e_tpc = tuned if 0 < tuned <= 256 and pst["ctas_per_chain"] == 1 else 0
     words = (spec.n + 63) // 64
     out = torch.empty((n_samples, words), dtype=torch.int64, device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # > L2 (129 MB)
@@ -230,7 +233,7 @@ def run_ours(args, rank, world):
         t0 = time.perf_counter()
         c2 = pw.pw_circuit_qaoa(spec.n, spec.edges, spec.weights, spec.h, spec.p, spec.gammas, spec.betas,
                                 spec.depol2, spec.ad_gamma)
-        p2 = pw.pw_plan_build(c2, precision=prec, chains_per_launch=B)
+        p2 = pw.pw_plan_build(c2, precision=prec, chains_per_launch=B, threads_per_chain=e2e_tpc)
         pw.pw_sample_host(p2, args.seed, first + i * n_samples, n_samples, host_out)
         pw.pw_plan_destroy(p2)
         pw.pw_circuit_destroy(c2)
@@ -310,6 +313,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--samples", type=int, default=0, help="override samples per step (profiling)")
+    ap.add_argument("--no-autotune", dest="autotune", action="store_false",
+                    help="keep the plan's own threads per chain (default: tune it before the warm-up)")
     args = ap.parse_args()
     if args.precision is None:
         args.precision = DEFAULT_PRECISION.get(args.workload, "fp32")

@@ -171,6 +171,18 @@ void pw_plan_destroy(pw_plan* plan);
 int pw_sample(pw_plan* plan, uint64_t seed, uint64_t first_sample, uint64_t n_samples,
               uint64_t* d_out_bits, double* d_trace, void* stream, pw_run_stats_t* stats);
 
+/* Tune the plan's launch shape on this device (not in the paper: a runtime
+ * choice). Times sampling trial_samples chains (0: four times the plan's
+ * chains per launch, 4096 if unset; fastest of three calls after a warm-up)
+ * for every threads-per-chain value in 32..256 and keeps the fastest in the
+ * plan; *chosen (nullable) gets it.
+ * Plans on a thread-block cluster keep their shape. The sampled bits do not
+ * depend on the choice (counter-based draws), only the rounding of the
+ * amplitudes may. Allocates and frees a scratch output of trial_samples
+ * words per chain, synchronises the stream; returns PW_ERR_CUDA when no
+ * configuration runs. */
+int pw_plan_autotune(pw_plan* plan, uint64_t trial_samples, void* stream, int* chosen);
+
 /* The same with HOST buffers: h_out_bits (n_samples * ceil(n/64) uint64) and
  * the optional h_trace are written before return; device staging memory is
  * held by the plan and reused between calls. */

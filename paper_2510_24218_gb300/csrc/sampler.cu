@@ -1554,6 +1554,62 @@ int pw_sample(pw_plan* plan, uint64_t seed, uint64_t first_sample, uint64_t n_sa
     return PW_OK;
 }
 
+int pw_plan_autotune(pw_plan* plan, uint64_t trial_samples, void* stream, int* chosen) {
+    if (!plan) return set_error(PW_ERR_ARG, "null argument");
+    HostPlan& hp = plan->hp;
+    const int keep = hp.threads_per_chain;
+    if (chosen) *chosen = keep;
+    if (hp.ctas_per_chain > 1) return PW_OK;   // a cluster's CTAs keep their 512 threads
+    int rc = ensure_device_plan(plan);
+    if (rc) return rc;
+    const uint64_t cpl = hp.chains_per_launch > 0 ? (uint64_t)hp.chains_per_launch : 4096;
+    const uint64_t n = trial_samples ? trial_samples : 4 * cpl;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    uint64_t* d_out = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaMalloc(&d_out, n * hp.hdr.words * sizeof(uint64_t));
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (e != cudaSuccess) {
+        if (d_out) cudaFree(d_out);
+        if (e0) cudaEventDestroy(e0);
+        return cuda_fail(e, "autotune set-up");
+    }
+    int best = keep;
+    float best_ms = 0.0f;
+    for (int tpc = 32; tpc <= 256; tpc *= 2) {
+        hp.threads_per_chain = tpc;
+        // one warm-up call, then the fastest of three timed ones
+        rc = pw_sample(plan, 0x5eed, 0, n, d_out, nullptr, stream, nullptr);
+        float ms = 0.0f;
+        for (int rep = 0; rep < 3 && rc == PW_OK; ++rep) {
+            cudaEventRecord(e0, st);
+            rc = pw_sample(plan, 0x5eed, (rep + 1) * n, n, d_out, nullptr, stream, nullptr);
+            cudaEventRecord(e1, st);
+            float t = 0.0f;
+            if (rc == PW_OK && cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&t, e0, e1) == cudaSuccess)
+                ms = (rep == 0 || t < ms) ? t : ms;
+            else
+                rc = PW_ERR_CUDA;
+        }
+        if (rc == PW_OK && ms > 0.0f && (best_ms == 0.0f || ms < best_ms)) {
+            best_ms = ms;
+            best = tpc;
+        }
+        cudaGetLastError();   // (a configuration that does not fit is skipped)
+    }
+    hp.threads_per_chain = best;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(d_out);
+    if (best_ms == 0.0f) {
+        hp.threads_per_chain = keep;
+        return set_error(PW_ERR_CUDA, "autotune: no configuration ran");
+    }
+    if (chosen) *chosen = best;
+    return PW_OK;
+}
+
 int pw_sample_host(pw_plan* plan, uint64_t seed, uint64_t first_sample, uint64_t n_samples, uint64_t* h_out_bits,
                    double* h_trace, pw_run_stats_t* stats) {
     if (!plan || (!h_out_bits && n_samples)) return set_error(PW_ERR_ARG, "null argument");

@@ -72,6 +72,7 @@ def load_library():
         "pw_plan_exec_order": (C.c_int, [vp, ip]),
         "pw_plan_destroy": (None, [vp]),
         "pw_sample": (C.c_int, [vp, C.c_uint64, C.c_uint64, C.c_uint64, vp, vp, vp, C.POINTER(RunStats)]),
+        "pw_plan_autotune": (C.c_int, [vp, C.c_uint64, vp, C.POINTER(C.c_int)]),
         "pw_sample_host": (C.c_int, [vp, C.c_uint64, C.c_uint64, C.c_uint64, vp, vp, C.POINTER(RunStats)]),
         "pw_amplitudes": (C.c_int, [vp, C.c_int, C.c_uint64, vp, vp, vp]),
         "pw_sample_static": (C.c_int, [vp, C.c_uint64, C.c_uint64, C.c_uint64, vp, vp, C.POINTER(RunStats)]),
@@ -202,6 +203,14 @@ def pw_sample(plan, seed, first_sample, n_samples, out_bits, trace=None, stream=
                                     C.c_void_p(trace.data_ptr()) if trace is not None else None,
                                     _stream_ptr(stream), C.byref(st) if want_stats else None))
     return {"near_boundary": st.near_boundary, "zero_mass": st.zero_mass, "launches": st.launches}
+
+
+def pw_plan_autotune(plan, trial_samples=0, stream=None) -> int:
+    """Time every threads-per-chain value on this device and keep the fastest
+    in the plan; returns it."""
+    chosen = C.c_int(0)
+    _check(load_library().pw_plan_autotune(plan, int(trial_samples), _stream_ptr(stream), C.byref(chosen)))
+    return chosen.value
 
 
 def pw_sample_static(plan, seed, first_sample, n_samples, out_bits, stream=None, want_stats=True):

@@ -556,3 +556,32 @@ def test_chip_noise_model_qaoa(pw):
     assert 0.5 * np.abs(emp - pdm).sum() < thr
     pw.pw_plan_destroy(plan)
     pw.pw_circuit_destroy(circ)
+
+
+def test_autotune_keeps_the_samples(pw):
+    """pw_plan_autotune picks a threads-per-chain value in 32..256 and stores it
+    in the plan; sampling afterwards still follows Alg. 1 on the same draws."""
+    import torch
+    spec = W.random_qaoa(12, 2, seed=77, with_h=True)
+    circ = _circ(pw, spec)
+    plan = pw.pw_plan_build(circ, chains_per_launch=1024)
+    chosen = pw.pw_plan_autotune(plan, 2048)
+    st = pw.pw_plan_stats(plan)
+    assert chosen in (32, 64, 128, 256) and st["threads_per_chain"] == chosen
+    N = 128
+    bits = torch.zeros((N, 1), dtype=torch.int64, device="cuda")
+    tr = torch.zeros((N, st["sampled_gates"], 4), dtype=torch.float64, device="cuda")
+    stats = pw.pw_sample(plan, 5, 0, N, bits, tr)
+    torch.cuda.synchronize()
+    got = pw.unpack_bits(bits.cpu().numpy(), spec.n)
+    ops = OC.qaoa_circuit(spec)
+    traces = [[] for _ in range(N)]
+    want, ost = OS.sample_sv(spec.n, ops, 5, list(range(N)), order=pw.pw_plan_exec_order(plan), traces=traces)
+    mism = int((~(want == got).all(axis=1)).sum())
+    assert mism <= max(stats["near_boundary"], ost.near_boundary)
+    trace = tr.cpu().numpy()
+    worst = max(pair_err(traces[k][spec.n + r][1], trace[k, r])
+                for k in range(N) if (want[k] == got[k]).all() for r in range(st["sampled_gates"]))
+    assert worst < 1e-5
+    pw.pw_plan_destroy(plan)
+    pw.pw_circuit_destroy(circ)
