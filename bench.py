@@ -3,10 +3,17 @@
 Workload (default): ideal QAOA p=2 MaxCut on the 6x6 grid (36 qubits), angles
 U[0, pi) from seed 2; one step = 10^5 exact samples drawn in launches of 4096
 chains (the sampler's whole hot path: every layer's contraction, readout and
-resampling). Prints one JSON line (see the design doc for the keys).
+resampling). Prints one JSON line: samples/s over the timed steps (device
+time, inputs resident), the roofline of the sampler kernel (algorithmic FP32
+flops per launch over its event time against the derived FP32 peak, DRAM
+bytes per launch from the ncu summary under profiles/), the FP64 oracle timed
+on the host cores, the end-to-end rate through the host-buffer API, the
+kernel launches of the timed region and the SM clocks sampled meanwhile.
+`--impl reference` times the oracle alone.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                   [--workload grid6x6|n12|heavyhex400|grid8x8noisy] [--precision fp32|fp64]
+                  [--samples S] [--no-cpu-baseline] [--no-autotune]
 """
 from __future__ import annotations
 
