@@ -1,0 +1,47 @@
+"""Pins of the gradient oracle: a one-qubit closed form and central finite
+differences of the state-vector amplitude."""
+import copy
+
+import numpy as np
+
+import workloads as W
+from oracle import circuit as OC
+from oracle import gradient as G
+from oracle import statevector as SV
+
+
+def _amp(spec, x):
+    psi = SV.run(spec.n, OC.qaoa_circuit(spec))
+    return psi[int(sum(int(b) << q for q, b in enumerate(x)))]
+
+
+def test_one_qubit_closed_form():
+    # |+>, exp(-i g h Z), exp(-i b X):  amp0 = (cos b e^{-igh} - i sin b e^{igh}) / sqrt 2
+    g, b, h = 0.37, 0.81, 1.3
+    spec = W.QaoaSpec(n=1, edges=np.zeros((0, 2), dtype=np.int64), weights=np.zeros(0), gammas=np.array([g]),
+                      betas=np.array([b]), h=np.array([h]), depol2=0.0, ad_gamma=0.0, name="one", extra={})
+    amp, grad = G.amp_and_grad(spec, np.array([[0], [1]], dtype=np.uint8))
+    e = np.exp(-1j * g * h)
+    want0 = (np.cos(b) * e - 1j * np.sin(b) / e) / np.sqrt(2)
+    want1 = (-1j * np.sin(b) * e + np.cos(b) / e) / np.sqrt(2)
+    assert np.allclose(amp, [want0, want1], atol=1e-14)
+    d_b0 = (-np.sin(b) * e - 1j * np.cos(b) / e) / np.sqrt(2)
+    d_g0 = (-1j * h * np.cos(b) * e + h * np.sin(b) / e) / np.sqrt(2)
+    assert abs(grad[0, 1] - d_b0) < 1e-14 and abs(grad[0, 0] - d_g0) < 1e-14
+
+
+def test_gradient_matches_central_differences():
+    spec = W.random_qaoa(7, 3, seed=21, with_h=True)
+    xs = W.random_bitstrings(5, spec.n, seed=22)
+    amp, grad = G.amp_and_grad(spec, xs)
+    for k, x in enumerate(xs):
+        assert abs(amp[k] - _amp(spec, x)) < 1e-13
+        for j in range(2 * spec.p):
+            hstep = 1e-5
+            sp, sm = copy.deepcopy(spec), copy.deepcopy(spec)
+            arr = "gammas" if j < spec.p else "betas"
+            l = j % spec.p
+            getattr(sp, arr)[l] += hstep
+            getattr(sm, arr)[l] -= hstep
+            fd = (_amp(sp, x) - _amp(sm, x)) / (2 * hstep)
+            assert abs(fd - grad[k, j]) < 1e-8 * max(1.0, abs(grad[k, j])), (k, j)
