@@ -197,6 +197,27 @@ int pw_sample_host(pw_plan* plan, uint64_t seed, uint64_t first_sample, uint64_t
 int pw_amplitudes(pw_plan* plan, int prefix_ops, uint64_t n_strings, const uint64_t* d_bits,
                   double* d_amp, void* stream);
 
+/* Derivatives of QAOA amplitudes with respect to the angles (not in the
+ * paper: an interface of this library built on the amplitude contraction of
+ * Sec. 2). For the noiseless circuit of pw_circuit_qaoa with the same
+ * arguments, writes, for each of the n_strings bitstrings x (device, packed
+ * like pw_sample's output):
+ *   d_amp  (nullable, device): 2 * n_strings doubles, amp(C, x) as (re, im);
+ *   d_grad (device): n_strings * 2p * 2 doubles; row k holds
+ *          d amp / d gammas[0..p-1] then d amp / d betas[0..p-1], each (re, im).
+ * Exact (parameter-shift rule): every angle enters through gates exp(-i t G)
+ * with G^2 = I, and d/dt exp(-i t G) = exp(-i (t + pi/2) G); each derivative is
+ * the weighted sum of the amplitudes of circuits with one gate advanced by a
+ * quarter turn, i.e. 2p(n_edges + n) contractions, plus p*n with fields h.
+ * opts: the plan options used for every contraction (precision, order, ...).
+ * Allocates and frees plans and an n_strings scratch vector; synchronises the
+ * stream before it returns. Errors of pw_plan_build / pw_amplitudes are
+ * passed on (a circuit the planner cannot take returns PW_ERR_UNSUPPORTED
+ * before any device work); p < 1 returns PW_ERR_ARG. */
+int pw_qaoa_amp_grad(int n, int n_edges, const int* edges, const double* w, const double* h, int p,
+                     const double* gammas, const double* betas, const pw_plan_opts* opts,
+                     uint64_t n_strings, const uint64_t* d_bits, double* d_amp, double* d_grad, void* stream);
+
 /* Allocation-free variant of pw_sample, for callers that cannot allocate
  * device memory: for example a process whose device memory is entirely
  * reserved by a framework's own memory pool, or code that must not allocate

@@ -79,3 +79,39 @@ def amp_and_grad(spec, bitstrings):
             psi = SV.apply(psi, n, o.qubits, o.mat)
         grads[:, p + l] = run_from(_apply_hm(psi, n), l + 1, 0)[idx] if l + 1 < p else _apply_hm(psi, n)[idx]
     return psi[idx], grads
+
+
+def amp_and_grad_tn(spec, bitstrings, columns=None):
+    """The same derivatives for circuits too wide for a state vector.
+
+    Each derivative is the sum over the layer's terms c G (c = w_e for
+    G = Z_u Z_v, h_j for Z_j, 1 for X_j) of c times the amplitude of the
+    circuit with the gate -i G inserted right after the term's gate, evaluated
+    by the variable-elimination oracle. columns: the derivative indices to
+    compute (gammas 0..p-1, then betas p..2p-1); the others stay zero.
+    """
+    from . import tn as TN
+    n, p = spec.n, spec.p
+    ops = C.qaoa_circuit(spec)
+    assert spec.depol2 == 0 and spec.ad_gamma == 0, "gradients of the noiseless circuit"
+    cols = range(2 * p) if columns is None else columns
+    per_layer = len(spec.edges) + (n if spec.h is not None else 0) + n
+    grads = np.zeros((len(bitstrings), 2 * p), dtype=complex)
+    for col in cols:
+        l, is_beta = col % p, col >= p
+        first = n + l * per_layer
+        for t in range(per_layer):
+            i = first + t
+            mixer = t >= per_layer - n
+            if mixer != is_beta:
+                continue
+            if mixer:
+                coef, G = 1.0, PAULI_X
+            elif t < len(spec.edges):
+                coef, G = float(spec.weights[t]), np.kron(PAULI_Z, PAULI_Z)
+            else:
+                coef, G = float(spec.h[t - len(spec.edges)]), PAULI_Z
+            ins = ops[:i + 1] + [C.gate(ops[i].qubits, -1j * G)] + ops[i + 1:]
+            for k, x in enumerate(bitstrings):
+                grads[k, col] += coef * TN.amplitudes(n, ins, x)
+    return grads

@@ -75,6 +75,8 @@ def load_library():
         "pw_plan_autotune": (C.c_int, [vp, C.c_uint64, vp, C.POINTER(C.c_int)]),
         "pw_sample_host": (C.c_int, [vp, C.c_uint64, C.c_uint64, C.c_uint64, vp, vp, C.POINTER(RunStats)]),
         "pw_amplitudes": (C.c_int, [vp, C.c_int, C.c_uint64, vp, vp, vp]),
+        "pw_qaoa_amp_grad": (C.c_int, [C.c_int, C.c_int, ip, dp, dp, C.c_int, dp, dp, C.POINTER(PlanOpts),
+                                       C.c_uint64, vp, vp, vp, vp]),
         "pw_sample_static": (C.c_int, [vp, C.c_uint64, C.c_uint64, C.c_uint64, vp, vp, C.POINTER(RunStats)]),
         "pw_last_error": (C.c_char_p, []),
     }
@@ -237,6 +239,26 @@ def pw_amplitudes(plan, prefix_ops, bits, amp_out, stream=None):
     """bits: torch CUDA int64 [n_strings, words]; amp_out: torch CUDA float64 [n_strings, 2]."""
     _check(load_library().pw_amplitudes(plan, int(prefix_ops), int(bits.shape[0]), C.c_void_p(bits.data_ptr()),
                                         C.c_void_p(amp_out.data_ptr()), _stream_ptr(stream)))
+
+
+def pw_qaoa_amp_grad(n, edges, weights, h, p, gammas, betas, bits, grad_out, amp_out=None, precision=PW_PREC_FP32,
+                     order=PW_ORDER_AUTO, stream=None):
+    """Exact d amp / d (gammas, betas) of the noiseless QAOA circuit.
+
+    bits: torch CUDA int64 [n_strings, words]; grad_out: torch CUDA float64
+    [n_strings, 2p, 2] (gammas first); amp_out: None or float64 [n_strings, 2].
+    """
+    e, ep = _iarr(edges)
+    w, wp = _darr(weights)
+    g, gp = _darr(gammas)
+    b, bp = _darr(betas)
+    hh, hp = _darr(h) if h is not None else (None, None)
+    o = PlanOpts()
+    o.precision, o.order = precision, order
+    _check(load_library().pw_qaoa_amp_grad(int(n), len(e) // 2, ep, wp, hp, int(p), gp, bp, C.byref(o),
+                                           int(bits.shape[0]), C.c_void_p(bits.data_ptr()),
+                                           C.c_void_p(amp_out.data_ptr()) if amp_out is not None else None,
+                                           C.c_void_p(grad_out.data_ptr()), _stream_ptr(stream)))
 
 
 # ------------------------------------------------------------ bit packing

@@ -45,3 +45,13 @@ def test_gradient_matches_central_differences():
             getattr(sm, arr)[l] -= hstep
             fd = (_amp(sp, x) - _amp(sm, x)) / (2 * hstep)
             assert abs(fd - grad[k, j]) < 1e-8 * max(1.0, abs(grad[k, j])), (k, j)
+
+
+def test_elimination_gradient_matches_state_vector_gradient():
+    spec = W.random_qaoa(8, 2, seed=23, with_h=True)
+    xs = W.random_bitstrings(3, spec.n, seed=24)
+    _, want = G.amp_and_grad(spec, xs)
+    got = G.amp_and_grad_tn(spec, xs)
+    assert np.abs(got - want).max() < 1e-13
+    part = G.amp_and_grad_tn(spec, xs, columns=[3])
+    assert np.abs(part[:, 3] - want[:, 3]).max() < 1e-13 and not part[:, :3].any()
