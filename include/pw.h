@@ -218,6 +218,23 @@ int pw_qaoa_amp_grad(int n, int n_edges, const int* edges, const double* w, cons
                      const double* gammas, const double* betas, const pw_plan_opts* opts,
                      uint64_t n_strings, const uint64_t* d_bits, double* d_amp, double* d_grad, void* stream);
 
+/* Score-function estimate of the gradient of the expected cost (not in the
+ * paper; built on pw_qaoa_amp_grad). d_bits (device, packed like pw_sample's
+ * output) holds n_samples >= 1 bitstrings drawn from p(x) = |amp(C, x)|^2 of
+ * the noiseless QAOA circuit, e.g. by pw_sample on the same circuit. With the
+ * diagonal cost C(x) = sum_e w_e z_u z_v + sum_j h_j z_j, z = 1 - 2x (the
+ * energy of the cost Hamiltonian), and the score d log p = 2 Re(conj(amp)
+ * d amp) / |amp|^2, writes d_out (device, 1 + 2p doubles): the sample mean of
+ * C, then N/(N-1) (mean(C score) - mean(C) mean(score)) for gammas[0..p-1]
+ * and betas[0..p-1] (the sample-mean baseline, unbiased; the plain mean of
+ * C score when N = 1). Reductions run in FP64 in a fixed order, so the result
+ * is deterministic. Allocates and frees scratch of about (2p + 1) * 16 bytes
+ * per sample, synchronises the stream; errors as pw_qaoa_amp_grad, and
+ * PW_ERR_ARG for n_samples == 0. */
+int pw_qaoa_cost_grad(int n, int n_edges, const int* edges, const double* w, const double* h, int p,
+                      const double* gammas, const double* betas, const pw_plan_opts* opts,
+                      uint64_t n_samples, const uint64_t* d_bits, double* d_out, void* stream);
+
 /* Allocation-free variant of pw_sample, for callers that cannot allocate
  * device memory: for example a process whose device memory is entirely
  * reserved by a framework's own memory pool, or code that must not allocate

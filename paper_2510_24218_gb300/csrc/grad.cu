@@ -154,3 +154,136 @@ extern "C" int pw_qaoa_amp_grad(int n, int n_edges, const int* edges, const doub
     if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return grad_cuda_fail(e, "cudaStreamSynchronize");
     return PW_OK;
 }
+
+// ------------------------------------------- score-function cost gradient
+// For samples x_1..x_N drawn from p(x) = |amp(x)|^2 and the diagonal cost
+// C(x) = <x|H_C|x> = sum_e w_e z_u z_v + sum_j h_j z_j (z = 1 - 2 x), the
+// gradient of E[C] is E[C(x) d log p(x)] with d log p = 2 Re(conj(amp) d amp) /
+// |amp|^2 (the score). With the sample-mean baseline the unbiased estimate is
+//   N/(N-1) * (mean(C * score) - mean(C) * mean(score)).
+namespace {
+
+constexpr int kCostThreads = 256;
+
+// One thread per sample; a block's sums of C, score_j and C * score_j go to
+// partial[block][1 + 4p] (fixed-order tree reductions: the result does not
+// depend on scheduling).
+__global__ void cost_score_partials(const uint64_t* __restrict__ bits, int words, const double2* __restrict__ amp,
+                                   const double2* __restrict__ grad, int ncol, const int* __restrict__ edges,
+                                   const double* __restrict__ w, int n_edges, const double* __restrict__ h, int n,
+                                   uint64_t count, double* __restrict__ partial) {
+    extern __shared__ double red[];   // [1 + 2 ncol][kCostThreads]
+    const int nv = 1 + 2 * ncol;
+    const uint64_t k = blockIdx.x * (uint64_t)kCostThreads + threadIdx.x;
+    double c = 0.0;
+    double inv_p = 0.0;
+    double2 a = make_double2(0.0, 0.0);
+    if (k < count) {
+        const uint64_t* x = bits + k * words;
+        auto z = [&](int q) { return ((x[q >> 6] >> (q & 63)) & 1ull) ? -1.0 : 1.0; };
+        for (int e = 0; e < n_edges; ++e) c = fma(w[e], z(edges[2 * e]) * z(edges[2 * e + 1]), c);
+        if (h)
+            for (int j = 0; j < n; ++j) c = fma(h[j], z(j), c);
+        a = amp[k];
+        const double pr = a.x * a.x + a.y * a.y;
+        inv_p = pr > 0.0 ? 1.0 / pr : 0.0;   // a string of zero probability is never drawn
+    }
+    red[threadIdx.x] = k < count ? c : 0.0;
+    for (int j = 0; j < ncol; ++j) {
+        double s = 0.0;
+        if (k < count) {
+            const double2 g = grad[k * ncol + j];
+            s = 2.0 * (a.x * g.x + a.y * g.y) * inv_p;
+        }
+        red[(1 + j) * kCostThreads + threadIdx.x] = s;
+        red[(1 + ncol + j) * kCostThreads + threadIdx.x] = k < count ? c * s : 0.0;
+    }
+    __syncthreads();
+    for (int half = kCostThreads / 2; half > 0; half >>= 1) {
+        if (threadIdx.x < half)
+            for (int v = 0; v < nv; ++v) red[v * kCostThreads + threadIdx.x] += red[v * kCostThreads + threadIdx.x + half];
+        __syncthreads();
+    }
+    if (threadIdx.x < nv) partial[blockIdx.x * (uint64_t)nv + threadIdx.x] = red[threadIdx.x * kCostThreads];
+}
+
+// out[0] = mean C; out[1 + j] = the baselined score-function estimate.
+__global__ void cost_score_finish(const double* __restrict__ partial, unsigned blocks, int ncol, uint64_t count,
+                                  double* __restrict__ out) {
+    const int nv = 1 + 2 * ncol;
+    const double inv_n = 1.0 / (double)count;
+    double sum_c = 0.0;
+    for (unsigned b = 0; b < blocks; ++b) sum_c += partial[b * (uint64_t)nv];
+    for (int j = threadIdx.x; j < ncol; j += blockDim.x) {
+        double s = 0.0, cs = 0.0;
+        for (unsigned b = 0; b < blocks; ++b) {
+            s += partial[b * (uint64_t)nv + 1 + j];
+            cs += partial[b * (uint64_t)nv + 1 + ncol + j];
+        }
+        const double mc = sum_c * inv_n;
+        out[1 + j] = count > 1 ? ((double)count / (double)(count - 1)) * (cs * inv_n - mc * (s * inv_n)) : cs;
+    }
+    if (threadIdx.x == 0) out[0] = sum_c * inv_n;
+}
+
+struct DevBuf {
+    void* p = nullptr;
+    ~DevBuf() { cudaFree(p); }
+};
+
+}  // namespace
+
+extern "C" int pw_qaoa_cost_grad(int n, int n_edges, const int* edges, const double* w, const double* h, int p,
+                                 const double* gammas, const double* betas, const pw_plan_opts* opts,
+                                 uint64_t n_samples, const uint64_t* d_bits, double* d_out, void* stream) {
+    if (p < 1) return pw::set_error(PW_ERR_ARG, "p must be >= 1");
+    if (n_samples == 0) return pw::set_error(PW_ERR_ARG, "n_samples must be >= 1");
+    if (!d_bits || !d_out || (n_edges > 0 && (!edges || !w))) return pw::set_error(PW_ERR_ARG, "null argument");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int ncol = 2 * p;
+    const unsigned blocks = (unsigned)((n_samples + kCostThreads - 1) / kCostThreads);
+    const size_t nv = 1 + 2 * (size_t)ncol;
+    const size_t smem = nv * kCostThreads * sizeof(double);
+    if (smem > 227 * 1024) return pw::set_error(PW_ERR_TOO_LARGE, "too many angles for one reduction block");
+    const size_t amp_b = n_samples * sizeof(double2), grad_b = n_samples * ncol * sizeof(double2);
+    const size_t part_b = (size_t)blocks * nv * sizeof(double);
+    const size_t edge_b = (size_t)n_edges * 2 * sizeof(int), w_b = (size_t)n_edges * sizeof(double);
+    const size_t h_b = h ? (size_t)n * sizeof(double) : 0;
+    auto up = [](size_t b) { return (b + 255) & ~size_t(255); };
+    DevBuf buf;
+    cudaError_t e = cudaMalloc(&buf.p, up(amp_b) + up(grad_b) + up(part_b) + up(edge_b) + up(w_b) + up(h_b));
+    if (e != cudaSuccess) return grad_cuda_fail(e, "cudaMalloc(cost gradient scratch)");
+    struct SyncOnExit {   // destroyed before the scratch: nothing is freed under running copies or kernels
+        cudaStream_t s;
+        ~SyncOnExit() { cudaStreamSynchronize(s); }
+    } sync_on_exit{st};
+    char* base = static_cast<char*>(buf.p);
+    double2* d_amp = reinterpret_cast<double2*>(base);
+    double2* d_grad = reinterpret_cast<double2*>(base + up(amp_b));
+    double* d_part = reinterpret_cast<double*>(base + up(amp_b) + up(grad_b));
+    int* d_edges = reinterpret_cast<int*>(base + up(amp_b) + up(grad_b) + up(part_b));
+    double* d_w = reinterpret_cast<double*>(base + up(amp_b) + up(grad_b) + up(part_b) + up(edge_b));
+    double* d_h = h ? reinterpret_cast<double*>(base + up(amp_b) + up(grad_b) + up(part_b) + up(edge_b) + up(w_b))
+                    : nullptr;
+    if (n_edges > 0) {
+        if ((e = cudaMemcpyAsync(d_edges, edges, edge_b, cudaMemcpyHostToDevice, st)) != cudaSuccess ||
+            (e = cudaMemcpyAsync(d_w, w, w_b, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+            return grad_cuda_fail(e, "cudaMemcpyAsync(graph)");
+    }
+    if (h && (e = cudaMemcpyAsync(d_h, h, h_b, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+        return grad_cuda_fail(e, "cudaMemcpyAsync(fields)");
+    int rc = pw_qaoa_amp_grad(n, n_edges, edges, w, h, p, gammas, betas, opts, n_samples, d_bits,
+                              reinterpret_cast<double*>(d_amp), reinterpret_cast<double*>(d_grad), stream);
+    if (rc) return rc;
+    if (smem > 48 * 1024 &&
+        (e = cudaFuncSetAttribute(cost_score_partials, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
+            cudaSuccess)
+        return grad_cuda_fail(e, "cudaFuncSetAttribute");
+    cost_score_partials<<<blocks, kCostThreads, smem, st>>>(d_bits, (n + 63) / 64, d_amp, d_grad, ncol, d_edges, d_w,
+                                                            n_edges, d_h, n, n_samples, d_part);
+    if ((e = cudaGetLastError()) != cudaSuccess) return grad_cuda_fail(e, "cost_score_partials launch");
+    cost_score_finish<<<1, 64, 0, st>>>(d_part, blocks, ncol, n_samples, d_out);
+    if ((e = cudaGetLastError()) != cudaSuccess) return grad_cuda_fail(e, "cost_score_finish launch");
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return grad_cuda_fail(e, "cudaStreamSynchronize");
+    return PW_OK;
+}

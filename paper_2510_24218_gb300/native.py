@@ -77,6 +77,8 @@ def load_library():
         "pw_amplitudes": (C.c_int, [vp, C.c_int, C.c_uint64, vp, vp, vp]),
         "pw_qaoa_amp_grad": (C.c_int, [C.c_int, C.c_int, ip, dp, dp, C.c_int, dp, dp, C.POINTER(PlanOpts),
                                        C.c_uint64, vp, vp, vp, vp]),
+        "pw_qaoa_cost_grad": (C.c_int, [C.c_int, C.c_int, ip, dp, dp, C.c_int, dp, dp, C.POINTER(PlanOpts),
+                                        C.c_uint64, vp, vp, vp]),
         "pw_sample_static": (C.c_int, [vp, C.c_uint64, C.c_uint64, C.c_uint64, vp, vp, C.POINTER(RunStats)]),
         "pw_last_error": (C.c_char_p, []),
     }
@@ -259,6 +261,25 @@ def pw_qaoa_amp_grad(n, edges, weights, h, p, gammas, betas, bits, grad_out, amp
                                            int(bits.shape[0]), C.c_void_p(bits.data_ptr()),
                                            C.c_void_p(amp_out.data_ptr()) if amp_out is not None else None,
                                            C.c_void_p(grad_out.data_ptr()), _stream_ptr(stream)))
+
+
+def pw_qaoa_cost_grad(n, edges, weights, h, p, gammas, betas, bits, out, precision=PW_PREC_FP32, order=PW_ORDER_AUTO,
+                      stream=None):
+    """Score-function estimate of d E[C] / d (gammas, betas) from sampled bits.
+
+    bits: torch CUDA int64 [n_samples, words]; out: torch CUDA float64 [1 + 2p]
+    (mean cost, then the gammas' and the betas' derivatives).
+    """
+    e, ep = _iarr(edges)
+    w, wp = _darr(weights)
+    g, gp = _darr(gammas)
+    b, bp = _darr(betas)
+    hh, hp = _darr(h) if h is not None else (None, None)
+    o = PlanOpts()
+    o.precision, o.order = precision, order
+    _check(load_library().pw_qaoa_cost_grad(int(n), len(e) // 2, ep, wp, hp, int(p), gp, bp, C.byref(o),
+                                            int(bits.shape[0]), C.c_void_p(bits.data_ptr()),
+                                            C.c_void_p(out.data_ptr()), _stream_ptr(stream)))
 
 
 # ------------------------------------------------------------ bit packing

@@ -72,3 +72,68 @@ def test_gradient_edge_cases(pw):
     _, got = _grad(pw, spec, xs, 1)
     _, want = G.amp_and_grad(spec, xs)
     assert np.abs(got - want).max() <= 1e-11 * np.abs(want).max()
+
+
+def test_autograd_function_matches_oracle_gradient(pw):
+    """The torch.autograd binding: a real loss of the amplitudes back-propagates
+    the oracle's derivatives, and gradcheck's finite differences agree."""
+    import torch
+    from paper_2510_24218_gb300.autograd import qaoa_amplitudes
+    spec = W.random_qaoa(10, 2, seed=36, with_h=True)
+    xs = W.random_bitstrings(6, spec.n, seed=37)
+    bits = torch.from_numpy(pw.pack_bits(xs).view(np.int64)).cuda()
+    gam = torch.tensor(spec.gammas, dtype=torch.float64, requires_grad=True)
+    bet = torch.tensor(spec.betas, dtype=torch.float64, requires_grad=True)
+    c = torch.from_numpy(np.random.default_rng(38).normal(size=(6, 2))).cuda()
+    loss = (qaoa_amplitudes(gam, bet, spec.n, spec.edges, spec.weights, spec.h, bits) * c).sum()
+    loss.backward()
+    _, want = G.amp_and_grad(spec, xs)
+    cc = c.cpu().numpy()
+    want_d = (cc[:, :1] * want.real + cc[:, 1:] * want.imag).sum(axis=0)
+    got = np.concatenate([gam.grad.numpy(), bet.grad.numpy()])
+    assert np.abs(got - want_d).max() <= 1e-11 * np.abs(want_d).max()
+    f = lambda g_, b_: qaoa_amplitudes(g_, b_, spec.n, spec.edges, spec.weights, spec.h, bits)  # noqa: E731
+    assert torch.autograd.gradcheck(f, (gam.detach().requires_grad_(), bet.detach().requires_grad_()),
+                                    eps=1e-6, atol=1e-7, rtol=1e-5)
+
+
+def _closed_form_cost(spec, g, b):
+    from oracle import closed_form as CF
+    return float(np.dot(spec.weights, CF.zz_p1(spec.n, spec.edges, spec.weights, g, b)))
+
+
+def test_score_function_cost_gradient_against_p1_closed_form(pw):
+    """Samples of a 20-qubit 3-regular p = 1 circuit from the GPU sampler feed
+    pw_qaoa_cost_grad; its mean cost and its gradient estimate agree with the
+    closed-form p = 1 expectation (and its central differences) within five
+    standard errors, and with the same estimator formed on the host from
+    pw_qaoa_amp_grad to 1e-10."""
+    import torch
+    from tests.test_gpu_parity import run_gpu
+    spec = W.random_qaoa(20, 1, seed=39)
+    N = 20000
+    g = run_gpu(pw, spec, N, seed=40, precision=1, trace=False)
+    xs = g["bits"]
+    bits = torch.from_numpy(pw.pack_bits(xs).view(np.int64)).cuda()
+    out = torch.zeros(3, dtype=torch.float64, device="cuda")
+    pw.pw_qaoa_cost_grad(spec.n, spec.edges, spec.weights, None, 1, spec.gammas, spec.betas, bits, out,
+                         precision=pw.PW_PREC_FP64)
+    got = out.cpu().numpy()
+    # host formation of the same estimator from the amplitude derivatives
+    amp, grad = _grad(pw, spec, xs, 1)
+    z = 1.0 - 2.0 * xs.astype(np.float64)
+    cost = (spec.weights * z[:, spec.edges[:, 0]] * z[:, spec.edges[:, 1]]).sum(axis=1)
+    score = 2.0 * (np.conj(amp)[:, None] * grad).real / (np.abs(amp) ** 2)[:, None]
+    est = N / (N - 1) * ((cost[:, None] * score).mean(axis=0) - cost.mean() * score.mean(axis=0))
+    assert abs(got[0] - cost.mean()) <= 1e-10 * np.abs(cost).max()
+    assert np.abs(got[1:] - est).max() <= 1e-9 * np.abs(est).max()
+    # statistics against the closed form
+    ga, be = float(spec.gammas[0]), float(spec.betas[0])
+    exact_c = _closed_form_cost(spec, ga, be)
+    assert abs(cost.mean() - exact_c) <= 5 * cost.std() / np.sqrt(N)
+    hstep = 1e-6
+    d_exact = [(_closed_form_cost(spec, ga + hstep, be) - _closed_form_cost(spec, ga - hstep, be)) / (2 * hstep),
+               (_closed_form_cost(spec, ga, be + hstep) - _closed_form_cost(spec, ga, be - hstep)) / (2 * hstep)]
+    for j in range(2):
+        se = ((cost - cost.mean()) * score[:, j]).std() / np.sqrt(N)
+        assert abs(got[1 + j] - d_exact[j]) <= 5 * se, (j, got[1 + j], d_exact[j], se)

@@ -55,3 +55,19 @@ def test_elimination_gradient_matches_state_vector_gradient():
     assert np.abs(got - want).max() < 1e-13
     part = G.amp_and_grad_tn(spec, xs, columns=[3])
     assert np.abs(part[:, 3] - want[:, 3]).max() < 1e-13 and not part[:, :3].any()
+
+
+def test_expected_cost_gradient_matches_p1_closed_form():
+    """sum_x C(x) 2 Re(conj(amp) d amp) over all 2^n strings is d E[C]; at
+    p = 1 it must equal central differences of the closed-form correlators."""
+    from oracle import closed_form as CF
+    spec = W.random_qaoa(10, 1, seed=39)
+    xs = np.array([[(i >> q) & 1 for q in range(spec.n)] for i in range(1 << spec.n)], dtype=np.uint8)
+    amp, grad = G.amp_and_grad(spec, xs)
+    z = 1.0 - 2.0 * xs
+    cost = (spec.weights * z[:, spec.edges[:, 0]] * z[:, spec.edges[:, 1]]).sum(axis=1)
+    d = (cost[:, None] * 2.0 * (np.conj(amp)[:, None] * grad).real).sum(axis=0)
+    f = lambda g, b: float(np.dot(spec.weights, CF.zz_p1(spec.n, spec.edges, spec.weights, g, b)))  # noqa: E731
+    g0, b0, h = float(spec.gammas[0]), float(spec.betas[0]), 1e-6
+    want = [(f(g0 + h, b0) - f(g0 - h, b0)) / (2 * h), (f(g0, b0 + h) - f(g0, b0 - h)) / (2 * h)]
+    assert np.allclose(d, want, atol=1e-7, rtol=0)
