@@ -11,8 +11,14 @@ on the host cores, the end-to-end rate through the host-buffer API, the
 kernel launches of the timed region and the SM clocks sampled meanwhile.
 `--impl reference` times the oracle alone.
 
+`--workload grad3reg` measures the QAOA amplitude derivatives instead: the
+seeded p=3 random 3-regular instances (n in [20, 48]) whose frontier fits on
+chip, K=64 bitstrings per instance drawn by its own sampler, one step = the
+exact d amp / d(gamma, beta) of every instance (pw_qaoa_amp_grad); the value
+is amplitude gradients (2p-vectors) per second.
+
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload grid6x6|n12|heavyhex400|grid8x8noisy] [--precision fp32|fp64]
+                  [--workload grid6x6|n12|heavyhex400|grid8x8noisy|grad3reg] [--precision fp32|fp64]
                   [--samples S] [--no-cpu-baseline] [--no-autotune]
 """
 from __future__ import annotations
@@ -39,7 +45,9 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # FP64 (non-tensor) rate of the part: the nominal 1.25 TFLOP/s
 FP64_PEAK_TFLOPS = 1.25
 # arithmetic of each workload's configuration (the 12-qubit one is complex128)
-DEFAULT_PRECISION = {"grid6x6": "fp32", "n12": "fp64", "heavyhex400": "fp32", "grid8x8noisy": "fp32"}
+DEFAULT_PRECISION = {"grid6x6": "fp32", "n12": "fp64", "heavyhex400": "fp32", "grid8x8noisy": "fp32",
+                     "grad3reg": "fp32"}
+GRAD_K = 64   # bitstrings per instance of the gradient workload
 
 
 def workload(name):
@@ -50,6 +58,9 @@ def workload(name):
         return W.maxcut_3reg_n12(), 10000, 256, "qaoa_p1_3reg_n12 (ideal, 10^4 samples, B=256)"
     if name == "heavyhex400":
         return W.heavy_hex_400_p1(), 100000, 16384, "qaoa_p1_heavyhex400 (400 qubits, ideal, 10^5 samples, B=16384)"
+    if name == "grad3reg":
+        return (None, GRAD_K, 0, "qaoa_p3_3reg_gradients (instances of n in [20, 48] whose frontier fits on chip, "
+                                 "K=64 bitstrings each, d amp/d(gamma, beta))")
     if name == "grid8x8noisy":
         return (W.grid_8x8_p2_noisy(), 100000, 8192,
                 "qaoa_p2_grid8x8_noisy (64 qubits, depol 1e-3, AD 1e-3, 10^5 samples, B=8192)")
@@ -255,6 +266,125 @@ def run_ours(args, rank, world):
                 e2e=e2e_value, h2d=h2d, d2h=n_samples * words * 8, wall=t_wall)
 
 
+# ---------------------------------------------------------- gradient leg
+
+def grad_instances(pw, prec):
+    """The seeded p=3 3-regular instances whose plan fits the device limits."""
+    import workloads as W
+    out = []
+    for spec in W.gradient_instances():
+        c = pw.pw_circuit_qaoa(spec.n, spec.edges, spec.weights, None, spec.p, spec.gammas, spec.betas)
+        try:
+            pw.pw_plan_destroy(pw.pw_plan_build(c, precision=prec))
+            out.append(spec)
+        except pw.PwError:
+            pass
+        finally:
+            pw.pw_circuit_destroy(c)
+    return out
+
+
+def _grad_oracle_worker(args):
+    names, seed, budget = args
+    import workloads as W
+    from oracle import gradient as G
+    by_name = {s.name: s for s in W.gradient_instances()}
+    t0 = time.perf_counter()
+    rows = 0
+    for j, name in enumerate(names):
+        spec = by_name[name]
+        G.amp_and_grad_tn(spec, W.random_bitstrings(1, spec.n, seed=seed + j))
+        rows += 1
+        if time.perf_counter() - t0 > budget:
+            break
+    return rows, time.perf_counter() - t0
+
+
+def grad_oracle_rate(names, budget_s=20.0, seed=1):
+    """Amplitude gradients/s of the FP64 oracle (generator insertion, each term
+    by variable elimination) on the host cores: worker w takes the instances
+    names[w], names[w + cores], ... one bitstring each until its budget is
+    spent."""
+    cores = max(1, min(os.cpu_count() or 1, 16))
+    ctx = mp.get_context("spawn")
+    jobs = [(names[w::cores] or names[:1], seed + 1000 * w, budget_s) for w in range(cores)]
+    with ctx.Pool(cores) as pool:
+        res = pool.map(_grad_oracle_worker, jobs)
+    done = sum(r[0] for r in res)
+    return done / max(r[1] for r in res), cores, done
+
+
+def run_grad(args, rank, world):
+    import numpy as np
+    import torch
+
+    import paper_2510_24218_gb300 as pw
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    prec = pw.PW_PREC_FP64 if args.precision == "fp64" else pw.PW_PREC_FP32
+    specs = grad_instances(pw, prec)
+    stream = torch.cuda.current_stream(dev)
+    K = GRAD_K
+    bits, grads, amps = [], [], []
+    launches_per_step = 0
+    for i, spec in enumerate(specs):
+        # the instance's own sampler draws its K bitstrings (inputs of the step)
+        c = pw.pw_circuit_qaoa(spec.n, spec.edges, spec.weights, None, spec.p, spec.gammas, spec.betas)
+        pl = pw.pw_plan_build(c, precision=prec)
+        b = torch.empty((K, (spec.n + 63) // 64), dtype=torch.int64, device=dev)
+        pw.pw_sample(pl, args.seed + rank, i * K, K, b, None, stream, want_stats=False)
+        pw.pw_plan_destroy(pl)
+        pw.pw_circuit_destroy(c)
+        bits.append(b)
+        grads.append(torch.empty((K, 2 * spec.p, 2), dtype=torch.float64, device=dev))
+        amps.append(torch.empty((K, 2), dtype=torch.float64, device=dev))
+        terms = spec.p * (len(spec.edges) + spec.n)
+        launches_per_step += 1 + 2 * terms     # the amplitudes, then one contraction + one accumulation per term
+
+    def step(bs, gs, as_):
+        for spec, b, g, a in zip(specs, bs, gs, as_):
+            pw.pw_qaoa_amp_grad(spec.n, spec.edges, spec.weights, None, spec.p, spec.gammas, spec.betas, b, g,
+                                amp_out=a, precision=prec, stream=stream)
+
+    for _ in range(args.warmup):
+        step(bits, grads, amps)
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize(dev)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clk_path = os.path.join(tempfile.gettempdir(), f"pw_clocks_{os.getpid()}.csv")
+    with ClockSampler(clk_path) as clk:
+        for i in range(args.steps):
+            ev[i][0].record(stream)
+            step(bits, grads, amps)
+            ev[i][1].record(stream)
+        torch.cuda.synchronize(dev)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize(dev)
+    ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in ev), world, dev)
+    value = len(specs) * K * args.steps * world / (ms / 1e3)
+
+    # e2e: bitstrings from pinned host memory, derivatives back to host memory
+    h_bits = [b.cpu().pin_memory() for b in bits]
+    h_grads = [torch.empty(g.shape, dtype=g.dtype).pin_memory() for g in grads]
+    t0 = time.perf_counter()
+    d_bits = [hb.to(dev, non_blocking=True) for hb in h_bits]
+    step(d_bits, grads, amps)
+    for hg, g in zip(h_grads, grads):
+        hg.copy_(g, non_blocking=True)
+    torch.cuda.synchronize(dev)
+    e2e_s = time.perf_counter() - t0
+    h2d = sum(hb.numel() * 8 for hb in h_bits)
+    d2h = sum(hg.numel() * 8 for hg in h_grads)
+    ns = [s.n for s in specs]
+    return dict(value=value, ms=ms, launches=launches_per_step * args.steps, clocks=clk.summary(dev.index),
+                e2e=len(specs) * K * world / e2e_s, h2d=h2d, d2h=d2h, n_instances=len(specs),
+                n_range=[min(ns), max(ns)], finite=bool(all(torch.isfinite(g).all().item() for g in grads)))
+
+
 KERNEL_SOURCES = ("paper_2510_24218_gb300/csrc/sampler.cu", "paper_2510_24218_gb300/csrc/pw_internal.h",
                   "paper_2510_24218_gb300/csrc/smem_layout.h", "paper_2510_24218_gb300/csrc/planner.cpp")
 PROFILE_OF = {"grid6x6": "pw_chain_kernel_grid6x6_p2.md", "grid8x8noisy": "pw_chain_kernel_grid8x8_p2_noisy.md"}
@@ -329,6 +459,8 @@ def main():
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
     spec, n_samples, B, desc = workload(args.workload)
+    if args.workload == "grad3reg":
+        return main_grad(args, rank, world, desc)
 
     if args.impl == "reference":
         # the reference arm of this build is the FP64 CPU oracle, on host cores
@@ -384,6 +516,59 @@ def main():
             "clocks": r["clocks"],
         }
         print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main_grad(args, rank, world, desc):
+    metric = "exact QAOA amplitude gradients/s (d amp/d(gamma, beta), p=3) on 1 GB300"
+    import paper_2510_24218_gb300 as pw
+    prec = pw.PW_PREC_FP64 if args.precision == "fp64" else pw.PW_PREC_FP32
+    # the workload's instance set (host planning only, no device call)
+    names = [s.name for s in grad_instances(pw, prec)]
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        rate, cores, done = grad_oracle_rate(names, budget_s=max(5.0, args.cpu_budget / 2))
+        print(json.dumps({"impl": "reference", "metric": metric, "value": rate, "unit": "gradients/s",
+                          "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+                          "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                          "data": "synthetic", "config": {"workload": desc},
+                          "cpu_baseline": {"value": rate, "unit": "gradients/s", "cores": cores, "kind": "oracle",
+                                           "sample": f"{done} gradients (one bitstring each) of the same "
+                                                     "instances, FP64 generator insertion by elimination"},
+                          "e2e": {"value": rate, "unit": "gradients/s", "h2d_bytes_per_step": 0,
+                                  "d2h_bytes_per_step": 0}}))
+        return
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        rate, cores, done = grad_oracle_rate(names, budget_s=args.cpu_budget)
+        cpu = {"value": rate, "unit": "gradients/s", "cores": cores, "kind": "oracle",
+               "sample": f"{done} gradients (one bitstring each) of the same instances, FP64 generator "
+                         f"insertion by elimination, ~{args.cpu_budget:.0f} s"}
+    import torch
+    if world > 1:
+        torch.distributed.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    r = run_grad(args, rank, world)
+    if rank == 0:
+        print(json.dumps({
+            "metric": metric, "value": r["value"], "unit": "gradients/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": r["ms"] / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f64",
+            "data": "synthetic",
+            "config": {"workload": desc, "instances": r["n_instances"], "n_range": r["n_range"],
+                       "bitstrings_per_instance": GRAD_K, "precision": args.precision,
+                       "l2": "inputs are a few KB per instance; each contraction re-reads its plan tables",
+                       "parallelism": f"replicas x{world}", "all_finite": r["finite"]},
+            "roofline": {"bound": "alu", "achieved": None, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": None,
+                         "traffic": None, "kernel": "pw_chain_kernel (amplitude mode)",
+                         "note": "host-bound: every derivative term plans and uploads one shifted circuit"},
+            "cpu_baseline": cpu,
+            "e2e": {"value": r["e2e"], "unit": "gradients/s", "h2d_bytes_per_step": r["h2d"],
+                    "d2h_bytes_per_step": r["d2h"]},
+            "gpu_launches": int(r["launches"]),
+            "clocks": r["clocks"],
+        }))
     if world > 1:
         torch.distributed.destroy_process_group()
 

@@ -19,6 +19,7 @@
 
 #include <algorithm>
 #include <string>
+#include <thread>
 #include <utility>
 #include <vector>
 
@@ -119,36 +120,91 @@ extern "C" int pw_qaoa_amp_grad(int n, int n_edges, const int* edges, const doub
     const uint64_t want = (n_strings + 255) / 256;
     const unsigned blocks = (unsigned)std::min<uint64_t>(want, (uint64_t)std::max(nsm, 1) * 8);
 
-    // Depth-2 pipeline: the next shifted circuit is planned on the host while
-    // the previous one's contraction runs; a plan is destroyed only after the
-    // event recorded behind its work has completed.
-    pw_circuit shifted;
-    shifted.n = base.c->n;
-    PlanGuard prev;
+    // The shifted circuits are planned in chunks by a pool of host threads;
+    // chunk c + 1 is planned while chunk c's contractions run on the device,
+    // and a chunk's plans are destroyed only after the event recorded behind
+    // its work has completed.
+    struct Term {
+        int op, col;
+        bool mixer;
+        double coef;
+    };
+    std::vector<Term> terms;
+    for (int l = 0; l < p; ++l)
+        for (int t = 0; t < per_layer; ++t) {
+            const bool mixer = t >= per_layer - n;
+            const double coef = mixer ? 1.0 : t < n_edges ? w[t] : h[t - n_edges];
+            if (coef != 0.0) terms.push_back({n + l * per_layer + t, mixer ? p + l : l, mixer, coef});
+        }
+    const int n_terms = (int)terms.size();
+    const int hw = (int)std::max(1u, std::thread::hardware_concurrency());
+    const int chunk = std::min(n_terms, 64);
+    const int workers = std::max(1, std::min({hw, 16, chunk}));
+    struct Chunk {
+        std::vector<pw_plan*> plans;
+        ~Chunk() {
+            for (pw_plan* q : plans) pw_plan_destroy(q);
+        }
+    };
+    auto plan_chunk = [&](int first_term, Chunk& out, std::string& err) -> int {
+        const int cnt = std::min(chunk, n_terms - first_term);
+        out.plans.assign(cnt, nullptr);
+        std::vector<int> codes(cnt, 0);
+        std::vector<std::string> msgs(cnt);
+        auto work = [&](int wid) {
+            pw_circuit shifted;
+            shifted.n = base.c->n;
+            for (int i = wid; i < cnt; i += workers) {
+                const Term& tm = terms[first_term + i];
+                shifted.ops = base.c->ops;
+                advance_quarter_turn(shifted.ops[tm.op], tm.mixer);
+                try {
+                    codes[i] = pw_plan_build(&shifted, opts, &out.plans[i]);
+                } catch (...) {
+                    codes[i] = pw::set_error(PW_ERR_OOM, "allocation failed while planning a shifted circuit");
+                }
+                if (codes[i]) msgs[i] = pw_last_error();
+            }
+        };
+        std::vector<std::thread> pool;
+        for (int wid = 1; wid < std::min(workers, cnt); ++wid) pool.emplace_back(work, wid);
+        work(0);
+        for (auto& th : pool) th.join();
+        for (int i = 0; i < cnt; ++i)
+            if (codes[i]) {
+                err = msgs[i];
+                return codes[i];
+            }
+        return PW_OK;
+    };
+
+    Chunk chunks[2];
     struct SyncOnExit {   // destroyed first: no plan or scratch is freed under running work
         cudaStream_t s;
         ~SyncOnExit() { cudaStreamSynchronize(s); }
     } sync_on_exit{st};
-    for (int l = 0; l < p; ++l) {
-        const int first = n + l * per_layer;
-        for (int t = 0; t < per_layer; ++t) {
-            const bool mixer = t >= per_layer - n;
-            const double coef = mixer ? 1.0 : t < n_edges ? w[t] : h[t - n_edges];
-            if (coef == 0.0) continue;
-            shifted.ops = base.c->ops;
-            advance_quarter_turn(shifted.ops[first + t], mixer);
-            PlanGuard cur;
-            if ((rc = pw_plan_build(&shifted, opts, &cur.p))) return rc;
-            if (prev.p && (e = cudaEventSynchronize(sc.done)) != cudaSuccess)
-                return grad_cuda_fail(e, "cudaEventSynchronize");
-            if ((rc = pw_amplitudes(cur.p, n_ops, n_strings, d_bits, reinterpret_cast<double*>(sc.amp), stream)))
+    std::string err;
+    if (n_terms > 0 && (rc = plan_chunk(0, chunks[0], err))) return pw::set_error(rc, err);
+    for (int c0 = 0, ci = 0; c0 < n_terms; c0 += chunk, ci ^= 1) {
+        Chunk& cur = chunks[ci];
+        for (int i = 0; i < (int)cur.plans.size(); ++i) {
+            const Term& tm = terms[c0 + i];
+            if ((rc = pw_amplitudes(cur.plans[i], n_ops, n_strings, d_bits, reinterpret_cast<double*>(sc.amp),
+                                    stream)))
                 return rc;
-            axpy_column<<<blocks, 256, 0, st>>>(sc.amp, coef, reinterpret_cast<double2*>(d_grad), ncol,
-                                                mixer ? p + l : l, n_strings);
+            axpy_column<<<blocks, 256, 0, st>>>(sc.amp, tm.coef, reinterpret_cast<double2*>(d_grad), ncol, tm.col,
+                                                n_strings);
             if ((e = cudaGetLastError()) != cudaSuccess) return grad_cuda_fail(e, "axpy_column launch");
-            if ((e = cudaEventRecord(sc.done, st)) != cudaSuccess) return grad_cuda_fail(e, "cudaEventRecord");
-            std::swap(prev.p, cur.p);   // cur now holds the plan whose work has finished
         }
+        if ((e = cudaEventRecord(sc.done, st)) != cudaSuccess) return grad_cuda_fail(e, "cudaEventRecord");
+        // plan the next chunk meanwhile, then release this one
+        Chunk& nxt = chunks[ci ^ 1];
+        for (pw_plan* q : nxt.plans) pw_plan_destroy(q);
+        nxt.plans.clear();
+        if (c0 + chunk < n_terms && (rc = plan_chunk(c0 + chunk, nxt, err))) return pw::set_error(rc, err);
+        if ((e = cudaEventSynchronize(sc.done)) != cudaSuccess) return grad_cuda_fail(e, "cudaEventSynchronize");
+        for (pw_plan* q : cur.plans) pw_plan_destroy(q);
+        cur.plans.clear();
     }
     // the scratch and the last plan are freed on return: wait for their work
     if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return grad_cuda_fail(e, "cudaStreamSynchronize");
