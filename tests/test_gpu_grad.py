@@ -137,3 +137,35 @@ def test_score_function_cost_gradient_against_p1_closed_form(pw):
     for j in range(2):
         se = ((cost - cost.mean()) * score[:, j]).std() / np.sqrt(N)
         assert abs(got[1 + j] - d_exact[j]) <= 5 * se, (j, got[1 + j], d_exact[j], se)
+
+
+def test_gradient_cluster_instance_in_bench_configuration(pw):
+    """The gradient workload's launch configuration: the first seeded p = 3
+    3-regular instance whose FP32 plan runs on a 2-CTA cluster, 64 bitstrings
+    drawn by its own sampler; two of them checked against the elimination
+    oracle on every derivative, to 1e-4 of the largest (FP32 amplitudes summed
+    over 3(|E| + n) terms), and every row finite."""
+    import torch
+    spec = None
+    for s in W.gradient_instances():
+        c = pw.pw_circuit_qaoa(s.n, s.edges, s.weights, None, s.p, s.gammas, s.betas)
+        try:
+            pl = pw.pw_plan_build(c)
+        except pw.PwError:
+            pw.pw_circuit_destroy(c)
+            continue
+        st = pw.pw_plan_stats(pl)
+        if st["ctas_per_chain"] == 2 and s.n <= 22:
+            spec = s
+            bits = torch.empty((64, 1), dtype=torch.int64, device="cuda")
+            pw.pw_sample(pl, 11, 0, 64, bits, None)
+        pw.pw_plan_destroy(pl)
+        pw.pw_circuit_destroy(c)
+        if spec is not None:
+            break
+    assert spec is not None
+    xs = pw.unpack_bits(bits.cpu().numpy(), spec.n)
+    _, grad = _grad(pw, spec, xs, 0)
+    assert np.isfinite(grad).all()
+    want = G.amp_and_grad_tn(spec, xs[[0, 37]])
+    assert np.abs(grad[[0, 37]] - want).max() <= 1e-4 * np.abs(want).max()
