@@ -228,6 +228,23 @@ def test_noisy_distribution_against_density_matrix(pw):
     assert 0.5 * np.abs(emp - p).sum() < thr
 
 
+def test_noisy_distribution_against_trajectories(pw):
+    """The same check against the second, differently derived noisy oracle:
+    the branch-weighted average of standard quantum trajectories."""
+    from oracle import trajectory as TR
+    spec = W.random_qaoa(3, 2, seed=55, with_h=True, depol2=0.3, ad_gamma=0.4)
+    spec.edges = spec.edges[:1]
+    spec.weights = spec.weights[:1]
+    N = 40000
+    g = run_gpu(pw, spec, N, seed=63, trace=False)
+    p = TR.exact_distribution(spec.n, OC.qaoa_circuit(spec))
+    idx = (g["bits"].astype(np.int64) << np.arange(spec.n)).sum(axis=1)
+    emp = np.bincount(idx, minlength=1 << spec.n) / N
+    rng = np.random.default_rng(2)
+    thr = np.quantile([0.5 * np.abs(rng.multinomial(N, p) / N - p).sum() for _ in range(200)], 0.99)
+    assert 0.5 * np.abs(emp - p).sum() < thr
+
+
 # -------------------------------------------------------------- amplitudes
 
 def test_amplitudes_api_against_state_vector(pw):
