@@ -230,3 +230,34 @@ def test_ops_inside_a_layer_move_out_exactly(pw):
     pw.pw_plan_destroy(plan)
     pw.pw_circuit_destroy(c)
     pw.pw_circuit_destroy(c2)
+
+
+def test_gradient_calls_validate_before_device_work(pw):
+    """The gradient entry points check their arguments and plan the circuit
+    before any CUDA call: no strings is a no-op, p < 1, missing buffers and
+    an empty sample are errors (host-only paths)."""
+    import ctypes as C
+    from paper_2510_24218_gb300 import native as N
+    lib = pw.load_library()
+    spec = W.random_qaoa(6, 2, seed=81)
+    e = np.ascontiguousarray(spec.edges.astype(np.int32).ravel())
+    w = np.ascontiguousarray(spec.weights)
+    g = np.ascontiguousarray(spec.gammas)
+    b = np.ascontiguousarray(spec.betas)
+    ip, dp = C.POINTER(C.c_int), C.POINTER(C.c_double)
+    args = (spec.n, len(spec.edges), e.ctypes.data_as(ip), w.ctypes.data_as(dp), None)
+    o = N.PlanOpts()
+    assert lib.pw_qaoa_amp_grad(*args, 2, g.ctypes.data_as(dp), b.ctypes.data_as(dp), C.byref(o), 0, None, None,
+                                None, None) == 0
+    assert lib.pw_qaoa_amp_grad(*args, 0, g.ctypes.data_as(dp), b.ctypes.data_as(dp), C.byref(o), 0, None, None,
+                                None, None) == -1
+    assert lib.pw_qaoa_amp_grad(*args, 2, g.ctypes.data_as(dp), b.ctypes.data_as(dp), C.byref(o), 4, None, None,
+                                None, None) == -1
+    assert lib.pw_qaoa_cost_grad(*args, 2, g.ctypes.data_as(dp), b.ctypes.data_as(dp), C.byref(o), 0, None, None,
+                                 None) == -1
+    assert "n_samples" in pw.pw_last_error()
+    # a structure the planner rejects is reported before any device work
+    bad = np.ascontiguousarray(np.array([0, 0], dtype=np.int32))
+    assert lib.pw_qaoa_amp_grad(spec.n, 1, bad.ctypes.data_as(ip), w.ctypes.data_as(dp), None, 2,
+                                g.ctypes.data_as(dp), b.ctypes.data_as(dp), C.byref(o), 0, None, None, None,
+                                None) < 0
