@@ -389,7 +389,8 @@ def run_grad(args, rank, world):
 
 KERNEL_SOURCES = ("paper_2510_24218_gb300/csrc/sampler.cu", "paper_2510_24218_gb300/csrc/pw_internal.h",
                   "paper_2510_24218_gb300/csrc/smem_layout.h", "paper_2510_24218_gb300/csrc/planner.cpp")
-PROFILE_OF = {"grid6x6": "pw_chain_kernel_grid6x6_p2.md", "grid8x8noisy": "pw_chain_kernel_grid8x8_p2_noisy.md"}
+PROFILE_OF = {"grid6x6": "pw_chain_kernel_grid6x6_p2.md", "grid8x8noisy": "pw_chain_kernel_grid8x8_p2_noisy.md",
+              "heavyhex400": "pw_chain_kernel_heavyhex400_p1.md"}
 
 
 def kernel_sources_sha256():
