@@ -169,3 +169,37 @@ def test_gradient_cluster_instance_in_bench_configuration(pw):
     assert np.isfinite(grad).all()
     want = G.amp_and_grad_tn(spec, xs[[0, 37]])
     assert np.abs(grad[[0, 37]] - want).max() <= 1e-4 * np.abs(want).max()
+
+
+def test_cost_gradient_with_fields_against_exact_expectation(pw):
+    """With fields h the cost gains sum_j h_j z_j: the kernel's estimate equals
+    the host-formed one, and it is within five standard errors of the exact
+    d E[C] from the state-vector oracle (sum over all 2^n strings)."""
+    import torch
+    from tests.test_gpu_parity import run_gpu
+    spec = W.random_qaoa(10, 2, seed=41, with_h=True)
+    N = 8000
+    xs = run_gpu(pw, spec, N, seed=42, precision=1, trace=False)["bits"]
+    bits = torch.from_numpy(pw.pack_bits(xs).view(np.int64)).cuda()
+    out = torch.zeros(1 + 2 * spec.p, dtype=torch.float64, device="cuda")
+    pw.pw_qaoa_cost_grad(spec.n, spec.edges, spec.weights, spec.h, spec.p, spec.gammas, spec.betas, bits, out,
+                         precision=pw.PW_PREC_FP64)
+    got = out.cpu().numpy()
+
+    def cost_of(x):
+        z = 1.0 - 2.0 * x.astype(np.float64)
+        return (spec.weights * z[:, spec.edges[:, 0]] * z[:, spec.edges[:, 1]]).sum(axis=1) + z @ spec.h
+
+    amp, grad = _grad(pw, spec, xs, 1)
+    cost = cost_of(xs)
+    score = 2.0 * (np.conj(amp)[:, None] * grad).real / (np.abs(amp) ** 2)[:, None]
+    est = N / (N - 1) * ((cost[:, None] * score).mean(axis=0) - cost.mean() * score.mean(axis=0))
+    assert abs(got[0] - cost.mean()) <= 1e-10 * np.abs(cost).max()
+    assert np.abs(got[1:] - est).max() <= 1e-9 * np.abs(est).max()
+    allx = np.array([[(i >> q) & 1 for q in range(spec.n)] for i in range(1 << spec.n)], dtype=np.uint8)
+    a_all, g_all = G.amp_and_grad(spec, allx)
+    c_all = cost_of(allx)
+    exact = (c_all[:, None] * 2.0 * (np.conj(a_all)[:, None] * g_all).real).sum(axis=0)
+    for j in range(2 * spec.p):
+        se = ((cost - cost.mean()) * score[:, j]).std() / np.sqrt(N)
+        assert abs(got[1 + j] - exact[j]) <= 5 * se, (j, got[1 + j], exact[j], se)
