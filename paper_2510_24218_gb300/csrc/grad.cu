@@ -66,14 +66,35 @@ struct PlanGuard {
     ~PlanGuard() { pw_plan_destroy(p); }
 };
 
-struct Scratch {
-    double2* amp = nullptr;
+// One concurrent lane of derivative terms: a non-blocking stream with its own
+// amplitude scratch and derivative accumulator (lanes are summed in a fixed
+// order at the end, so the result does not depend on their scheduling).
+struct Lane {
+    cudaStream_t s = nullptr;
     cudaEvent_t done = nullptr;
-    ~Scratch() {
+    double2* amp = nullptr;   // n_strings
+    double2* acc = nullptr;   // n_strings * ncol
+    ~Lane() {
+        if (s) cudaStreamSynchronize(s);
         if (done) cudaEventDestroy(done);
+        if (s) cudaStreamDestroy(s);
         cudaFree(amp);
+        cudaFree(acc);
     }
 };
+
+// grad[i] = sum over lanes l (in order) of acc_l[i], i < count (complex).
+__global__ void sum_lanes(const double2* const* __restrict__ acc, int lanes, double2* __restrict__ grad,
+                         uint64_t count) {
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < count; i += (uint64_t)gridDim.x * blockDim.x) {
+        double2 g = acc[0][i];
+        for (int l = 1; l < lanes; ++l) {
+            g.x += acc[l][i].x;
+            g.y += acc[l][i].y;
+        }
+        grad[i] = g;
+    }
+}
 
 struct CircuitGuard {
     pw_circuit* c = nullptr;
@@ -106,24 +127,41 @@ extern "C" int pw_qaoa_amp_grad(int n, int n_edges, const int* edges, const doub
         cudaError_t e = cudaStreamSynchronize(st);   // before the plan's tables are freed
         if (e != cudaSuccess) return grad_cuda_fail(e, "cudaStreamSynchronize");
     }
-    cudaError_t e = cudaMemsetAsync(d_grad, 0, n_strings * ncol * 2 * sizeof(double), st);
-    if (e != cudaSuccess) return grad_cuda_fail(e, "cudaMemsetAsync(grad)");
-    Scratch sc;
-    if ((e = cudaMalloc(&sc.amp, n_strings * sizeof(double2))) != cudaSuccess)
-        return grad_cuda_fail(e, "cudaMalloc(grad scratch)");
-    if ((e = cudaEventCreateWithFlags(&sc.done, cudaEventDisableTiming)) != cudaSuccess)
-        return grad_cuda_fail(e, "cudaEventCreate");
-
     int dev = 0, nsm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     const uint64_t want = (n_strings + 255) / 256;
     const unsigned blocks = (unsigned)std::min<uint64_t>(want, (uint64_t)std::max(nsm, 1) * 8);
+    cudaError_t e;
+
+    // Terms run on kLanes non-blocking streams, so that the contractions of
+    // different shifted circuits overlap (a 64-chain launch on one CTA per
+    // chain fills less than half of the GPU) and the synchronous plan uploads
+    // do not wait for them. Every lane waits for the caller's stream first.
+    constexpr int kLanes = 4;
+    Lane lanes[kLanes];
+    cudaEvent_t ready = nullptr;
+    if ((e = cudaEventCreateWithFlags(&ready, cudaEventDisableTiming)) != cudaSuccess)
+        return grad_cuda_fail(e, "cudaEventCreate");
+    struct EventGuard {
+        cudaEvent_t ev;
+        ~EventGuard() { cudaEventDestroy(ev); }
+    } ready_guard{ready};
+    if ((e = cudaEventRecord(ready, st)) != cudaSuccess) return grad_cuda_fail(e, "cudaEventRecord");
+    for (Lane& ln : lanes) {
+        if ((e = cudaStreamCreateWithFlags(&ln.s, cudaStreamNonBlocking)) != cudaSuccess ||
+            (e = cudaEventCreateWithFlags(&ln.done, cudaEventDisableTiming)) != cudaSuccess ||
+            (e = cudaMalloc(&ln.amp, n_strings * sizeof(double2))) != cudaSuccess ||
+            (e = cudaMalloc(&ln.acc, n_strings * ncol * sizeof(double2))) != cudaSuccess)
+            return grad_cuda_fail(e, "gradient lane set-up");
+        if ((e = cudaStreamWaitEvent(ln.s, ready, 0)) != cudaSuccess ||
+            (e = cudaMemsetAsync(ln.acc, 0, n_strings * ncol * sizeof(double2), ln.s)) != cudaSuccess)
+            return grad_cuda_fail(e, "gradient lane set-up");
+    }
 
     // The shifted circuits are planned in chunks by a pool of host threads;
     // chunk c + 1 is planned while chunk c's contractions run on the device,
-    // and a chunk's plans are destroyed only after the event recorded behind
-    // its work has completed.
+    // and a chunk's plans are destroyed only after every lane has finished it.
     struct Term {
         int op, col;
         bool mixer;
@@ -177,36 +215,69 @@ extern "C" int pw_qaoa_amp_grad(int n, int n_edges, const int* edges, const doub
             }
         return PW_OK;
     };
+    auto wait_lanes = [&]() -> cudaError_t {
+        for (Lane& ln : lanes) {
+            cudaError_t r = cudaEventRecord(ln.done, ln.s);
+            if (r == cudaSuccess) r = cudaEventSynchronize(ln.done);
+            if (r != cudaSuccess) return r;
+        }
+        return cudaSuccess;
+    };
 
     Chunk chunks[2];
-    struct SyncOnExit {   // destroyed first: no plan or scratch is freed under running work
-        cudaStream_t s;
-        ~SyncOnExit() { cudaStreamSynchronize(s); }
-    } sync_on_exit{st};
+    struct LaneSync {   // declared after the chunks, so destroyed first: no plan
+        Lane* l;        // is freed while a lane may still read it
+        ~LaneSync() {
+            for (int i = 0; i < kLanes; ++i)
+                if (l[i].s) cudaStreamSynchronize(l[i].s);
+        }
+    } lane_sync{lanes};
     std::string err;
     if (n_terms > 0 && (rc = plan_chunk(0, chunks[0], err))) return pw::set_error(rc, err);
     for (int c0 = 0, ci = 0; c0 < n_terms; c0 += chunk, ci ^= 1) {
         Chunk& cur = chunks[ci];
         for (int i = 0; i < (int)cur.plans.size(); ++i) {
             const Term& tm = terms[c0 + i];
-            if ((rc = pw_amplitudes(cur.plans[i], n_ops, n_strings, d_bits, reinterpret_cast<double*>(sc.amp),
-                                    stream)))
+            Lane& ln = lanes[(c0 + i) % kLanes];
+            if ((rc = pw_amplitudes(cur.plans[i], n_ops, n_strings, d_bits, reinterpret_cast<double*>(ln.amp), ln.s))) {
+                wait_lanes();
                 return rc;
-            axpy_column<<<blocks, 256, 0, st>>>(sc.amp, tm.coef, reinterpret_cast<double2*>(d_grad), ncol, tm.col,
-                                                n_strings);
-            if ((e = cudaGetLastError()) != cudaSuccess) return grad_cuda_fail(e, "axpy_column launch");
+            }
+            axpy_column<<<blocks, 256, 0, ln.s>>>(ln.amp, tm.coef, ln.acc, ncol, tm.col, n_strings);
+            if ((e = cudaGetLastError()) != cudaSuccess) {
+                wait_lanes();
+                return grad_cuda_fail(e, "axpy_column launch");
+            }
         }
-        if ((e = cudaEventRecord(sc.done, st)) != cudaSuccess) return grad_cuda_fail(e, "cudaEventRecord");
         // plan the next chunk meanwhile, then release this one
         Chunk& nxt = chunks[ci ^ 1];
-        for (pw_plan* q : nxt.plans) pw_plan_destroy(q);
-        nxt.plans.clear();
-        if (c0 + chunk < n_terms && (rc = plan_chunk(c0 + chunk, nxt, err))) return pw::set_error(rc, err);
-        if ((e = cudaEventSynchronize(sc.done)) != cudaSuccess) return grad_cuda_fail(e, "cudaEventSynchronize");
+        if (c0 + chunk < n_terms && (rc = plan_chunk(c0 + chunk, nxt, err))) {
+            wait_lanes();
+            return pw::set_error(rc, err);
+        }
+        if ((e = wait_lanes()) != cudaSuccess) return grad_cuda_fail(e, "gradient lane wait");
         for (pw_plan* q : cur.plans) pw_plan_destroy(q);
         cur.plans.clear();
     }
-    // the scratch and the last plan are freed on return: wait for their work
+    // d_grad = the lanes' accumulators summed in lane order, on the caller's stream
+    const double2* acc_ptrs[kLanes];
+    for (int l = 0; l < kLanes; ++l) acc_ptrs[l] = lanes[l].acc;
+    const double2** d_ptrs = nullptr;
+    if ((e = cudaMalloc(&d_ptrs, sizeof(acc_ptrs))) != cudaSuccess) return grad_cuda_fail(e, "cudaMalloc");
+    struct PtrFree {
+        const double2** q;
+        ~PtrFree() { cudaFree(q); }
+    } ptr_free{d_ptrs};
+    if ((e = cudaMemcpy(d_ptrs, acc_ptrs, sizeof(acc_ptrs), cudaMemcpyHostToDevice)) != cudaSuccess)
+        return grad_cuda_fail(e, "cudaMemcpy");
+    for (Lane& ln : lanes) {
+        if ((e = cudaEventRecord(ln.done, ln.s)) != cudaSuccess || (e = cudaStreamWaitEvent(st, ln.done, 0)) != cudaSuccess)
+            return grad_cuda_fail(e, "gradient lane join");
+    }
+    const uint64_t total = n_strings * ncol;
+    const unsigned sblocks = (unsigned)std::min<uint64_t>((total + 255) / 256, (uint64_t)std::max(nsm, 1) * 8);
+    sum_lanes<<<sblocks, 256, 0, st>>>(d_ptrs, kLanes, reinterpret_cast<double2*>(d_grad), total);
+    if ((e = cudaGetLastError()) != cudaSuccess) return grad_cuda_fail(e, "sum_lanes launch");
     if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return grad_cuda_fail(e, "cudaStreamSynchronize");
     return PW_OK;
 }
