@@ -138,7 +138,7 @@ extern "C" int pw_qaoa_amp_grad(int n, int n_edges, const int* edges, const doub
     // different shifted circuits overlap (a 64-chain launch on one CTA per
     // chain fills less than half of the GPU) and the synchronous plan uploads
     // do not wait for them. Every lane waits for the caller's stream first.
-    constexpr int kLanes = 4;
+    constexpr int kLanes = 8;
     Lane lanes[kLanes];
     cudaEvent_t ready = nullptr;
     if ((e = cudaEventCreateWithFlags(&ready, cudaEventDisableTiming)) != cudaSuccess)
