@@ -1331,7 +1331,11 @@ int ensure_device_plan(pw_plan* plan) {
     std::vector<unsigned char> blob = make_blob(plan->hp, plan->off);
     void* d = nullptr;
     if ((e = cudaMalloc(&d, blob.size())) != cudaSuccess) return cuda_fail(e, "cudaMalloc(plan)");
-    if ((e = cudaMemcpy(d, blob.data(), blob.size(), cudaMemcpyHostToDevice)) != cudaSuccess) {
+    // cudaMemcpy from pageable memory returns once the source is staged; the
+    // copy itself is ordered on the legacy stream only. Wait for it, so that a
+    // launch on any stream (also a non-blocking one) reads complete tables.
+    if ((e = cudaMemcpy(d, blob.data(), blob.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(cudaStreamLegacy)) != cudaSuccess) {
         cudaFree(d);
         return cuda_fail(e, "cudaMemcpy(plan)");
     }

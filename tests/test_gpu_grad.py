@@ -203,3 +203,25 @@ def test_cost_gradient_with_fields_against_exact_expectation(pw):
     for j in range(2 * spec.p):
         se = ((cost - cost.mean()) * score[:, j]).std() / np.sqrt(N)
         assert abs(got[1 + j] - exact[j]) <= 5 * se, (j, got[1 + j], exact[j], se)
+
+
+def test_gradient_is_deterministic_across_calls(pw):
+    """The derivative terms run on concurrent streams with fresh plans each
+    call; four calls give bit-identical FP64 rows (each plan's tables are
+    complete before any stream reads them, and the lanes are summed in a fixed
+    order), equal to the oracle."""
+    import torch
+    spec = W.random_qaoa(16, 1, seed=43)
+    N = 20000
+    xs = W.random_bitstrings(N, spec.n, seed=44)
+    bits = torch.from_numpy(pw.pack_bits(xs).view(np.int64)).cuda()
+    runs = []
+    for _ in range(4):
+        g = torch.full((N, 2, 2), np.nan, dtype=torch.float64, device="cuda")
+        pw.pw_qaoa_amp_grad(spec.n, spec.edges, spec.weights, None, 1, spec.gammas, spec.betas, bits, g,
+                            precision=pw.PW_PREC_FP64)
+        runs.append(g.cpu().numpy())
+    assert all(np.array_equal(runs[0], r) for r in runs[1:])
+    _, want = G.amp_and_grad(spec, xs[:500])
+    got = runs[0][:500, :, 0] + 1j * runs[0][:500, :, 1]
+    assert np.abs(got - want).max() <= 1e-11 * np.abs(want).max()

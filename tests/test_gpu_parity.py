@@ -228,6 +228,28 @@ def test_noisy_distribution_against_density_matrix(pw):
     assert 0.5 * np.abs(emp - p).sum() < thr
 
 
+def test_first_upload_then_non_blocking_stream(pw):
+    """A fresh plan's first call on a non-blocking stream reads complete
+    tables: the samples equal those of the same plan drawn on the default
+    stream afterwards."""
+    import torch
+    spec = W.grid_6x6_p2()
+    circ = _circ(pw, spec)
+    words = 1
+    for rep in range(3):
+        plan = pw.pw_plan_build(circ, chains_per_launch=4096)
+        side = torch.cuda.Stream()   # torch creates its streams non-blocking
+        a = torch.empty((4096, words), dtype=torch.int64, device="cuda")
+        b = torch.empty((4096, words), dtype=torch.int64, device="cuda")
+        pw.pw_sample(plan, 5 + rep, 0, 4096, a, None, side, want_stats=False)
+        side.synchronize()
+        pw.pw_sample(plan, 5 + rep, 0, 4096, b, None, None, want_stats=False)
+        torch.cuda.synchronize()
+        assert torch.equal(a, b)
+        pw.pw_plan_destroy(plan)
+    pw.pw_circuit_destroy(circ)
+
+
 def test_noisy_distribution_against_trajectories(pw):
     """The same check against the second, differently derived noisy oracle:
     the branch-weighted average of standard quantum trajectories."""
