@@ -208,7 +208,7 @@ int pw_amplitudes(pw_plan* plan, int prefix_ops, uint64_t n_strings, const uint6
  * Exact (parameter-shift rule): every angle enters through gates exp(-i t G)
  * with G^2 = I, and d/dt exp(-i t G) = exp(-i (t + pi/2) G); each derivative is
  * the weighted sum of the amplitudes of circuits with one gate advanced by a
- * quarter turn, i.e. 2p(n_edges + n) contractions, plus p*n with fields h.
+ * quarter turn, i.e. p(n_edges + n) contractions, plus p*n with fields h.
  * opts: the plan options used for every contraction (precision, order, ...).
  * Allocates and frees plans and an n_strings scratch vector; synchronises the
  * stream before it returns. Errors of pw_plan_build / pw_amplitudes are

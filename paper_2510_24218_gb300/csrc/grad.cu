@@ -14,7 +14,7 @@
 // contracted by the pilot-wave amplitude path; the replaced matrix is the
 // original one with rows swapped and entries multiplied by +-i, exact in
 // floating point. This is not the paper's method (it gives no gradients); it
-// reuses the amplitude contraction 2p(|E| + 2n) times (n without fields).
+// reuses the amplitude contraction p(|E| + n) times, p(|E| + 2n) with fields h.
 #include <cuda_runtime.h>
 
 #include <algorithm>
