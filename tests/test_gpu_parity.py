@@ -316,6 +316,27 @@ def test_heavy_hex_400_zz_closed_form(pw):
     assert np.max(np.abs(zs)) < 5.0, np.max(np.abs(zs))
 
 
+def test_max_qubits_4096_path_zz_closed_form(pw):
+    """The largest circuit a plan takes: 4096 qubits (64 words per sample), a
+    weighted path at p = 1. Each of the 4095 edge means of z_u z_v is within
+    five standard errors of the closed form, and their squared z-scores
+    average about one (no systematic bias)."""
+    n = 4096
+    rng = np.random.default_rng(91)
+    e = np.array([(i, i + 1) for i in range(n - 1)], dtype=np.int64)
+    spec = W.QaoaSpec(n=n, edges=e, weights=rng.normal(size=n - 1), gammas=np.array([0.45]),
+                      betas=np.array([0.35]), h=None, depol2=0.0, ad_gamma=0.0, name="path4096", extra={})
+    N = 8192
+    g = run_gpu(pw, spec, N, seed=92, trace=False)
+    assert g["bits"].shape == (N, n)
+    z = 1 - 2 * g["bits"].astype(np.int64)
+    cf = CF.zz_p1(spec.n, spec.edges, spec.weights, spec.gammas[0], spec.betas[0])
+    zz = (z[:, e[:, 0]] * z[:, e[:, 1]]).mean(axis=0)
+    zs = (zz - cf) / np.sqrt(np.maximum(1e-12, (1 - cf ** 2) / N))
+    assert np.max(np.abs(zs)) < 5.0, np.max(np.abs(zs))
+    assert np.mean(zs ** 2) < 1.2, np.mean(zs ** 2)
+
+
 def test_heavy_hex_400_amplitudes_against_elimination(pw):
     """400 qubits: FP64 amplitudes of random strings (full circuit) against the
     elimination oracle, and the FP64 sampler's candidate pairs along one
