@@ -70,6 +70,9 @@ struct PlanGuard {
 // amplitude scratch and derivative accumulator (lanes are summed in a fixed
 // order at the end, so the result does not depend on their scheduling).
 struct Lane {
+    Lane() = default;
+    Lane(const Lane&) = delete;
+    Lane& operator=(const Lane&) = delete;
     cudaStream_t s = nullptr;
     cudaEvent_t done = nullptr;
     double2* amp = nullptr;   // n_strings
@@ -95,6 +98,9 @@ __global__ void sum_lanes(const double2* const* __restrict__ acc, int lanes, dou
         grad[i] = g;
     }
 }
+
+constexpr int kMaxLanes = 16;
+constexpr int kRoundPerLane = 16;
 
 struct CircuitGuard {
     pw_circuit* c = nullptr;
@@ -134,34 +140,13 @@ extern "C" int pw_qaoa_amp_grad(int n, int n_edges, const int* edges, const doub
     const unsigned blocks = (unsigned)std::min<uint64_t>(want, (uint64_t)std::max(nsm, 1) * 8);
     cudaError_t e;
 
-    // Terms run on kLanes non-blocking streams, so that the contractions of
-    // different shifted circuits overlap (a 64-chain launch on one CTA per
-    // chain fills less than half of the GPU) and the synchronous plan uploads
-    // do not wait for them. Every lane waits for the caller's stream first.
-    constexpr int kLanes = 8;
-    Lane lanes[kLanes];
-    cudaEvent_t ready = nullptr;
-    if ((e = cudaEventCreateWithFlags(&ready, cudaEventDisableTiming)) != cudaSuccess)
-        return grad_cuda_fail(e, "cudaEventCreate");
-    struct EventGuard {
-        cudaEvent_t ev;
-        ~EventGuard() { cudaEventDestroy(ev); }
-    } ready_guard{ready};
-    if ((e = cudaEventRecord(ready, st)) != cudaSuccess) return grad_cuda_fail(e, "cudaEventRecord");
-    for (Lane& ln : lanes) {
-        if ((e = cudaStreamCreateWithFlags(&ln.s, cudaStreamNonBlocking)) != cudaSuccess ||
-            (e = cudaEventCreateWithFlags(&ln.done, cudaEventDisableTiming)) != cudaSuccess ||
-            (e = cudaMalloc(&ln.amp, n_strings * sizeof(double2))) != cudaSuccess ||
-            (e = cudaMalloc(&ln.acc, n_strings * ncol * sizeof(double2))) != cudaSuccess)
-            return grad_cuda_fail(e, "gradient lane set-up");
-        if ((e = cudaStreamWaitEvent(ln.s, ready, 0)) != cudaSuccess ||
-            (e = cudaMemsetAsync(ln.acc, 0, n_strings * ncol * sizeof(double2), ln.s)) != cudaSuccess)
-            return grad_cuda_fail(e, "gradient lane set-up");
-    }
-
-    // The shifted circuits are planned in chunks by a pool of host threads;
-    // chunk c + 1 is planned while chunk c's contractions run on the device,
-    // and a chunk's plans are destroyed only after every lane has finished it.
+    // The derivative terms are spread over lanes: lane l takes terms l, l + L,
+    // l + 2L, ... in order, on its own host thread (planning the shifted
+    // circuit, uploading its tables, launching its contraction and the
+    // accumulation) and its own non-blocking stream with its own amplitude
+    // scratch and FP64 accumulator. Contractions of different terms overlap on
+    // the device and the host work runs in parallel; the lanes are summed in a
+    // fixed order at the end, so the result does not depend on scheduling.
     struct Term {
         int op, col;
         bool mixer;
@@ -176,99 +161,96 @@ extern "C" int pw_qaoa_amp_grad(int n, int n_edges, const int* edges, const doub
         }
     const int n_terms = (int)terms.size();
     const int hw = (int)std::max(1u, std::thread::hardware_concurrency());
-    const int chunk = std::min(n_terms, 64);
-    const int workers = std::max(1, std::min({hw, 16, chunk}));
-    struct Chunk {
-        std::vector<pw_plan*> plans;
-        ~Chunk() {
-            for (pw_plan* q : plans) pw_plan_destroy(q);
-        }
-    };
-    auto plan_chunk = [&](int first_term, Chunk& out, std::string& err) -> int {
-        const int cnt = std::min(chunk, n_terms - first_term);
-        out.plans.assign(cnt, nullptr);
-        std::vector<int> codes(cnt, 0);
-        std::vector<std::string> msgs(cnt);
-        auto work = [&](int wid) {
-            pw_circuit shifted;
-            shifted.n = base.c->n;
-            for (int i = wid; i < cnt; i += workers) {
-                const Term& tm = terms[first_term + i];
-                shifted.ops = base.c->ops;
-                advance_quarter_turn(shifted.ops[tm.op], tm.mixer);
-                try {
-                    codes[i] = pw_plan_build(&shifted, opts, &out.plans[i]);
-                } catch (...) {
-                    codes[i] = pw::set_error(PW_ERR_OOM, "allocation failed while planning a shifted circuit");
-                }
-                if (codes[i]) msgs[i] = pw_last_error();
-            }
-        };
-        std::vector<std::thread> pool;
-        for (int wid = 1; wid < std::min(workers, cnt); ++wid) pool.emplace_back(work, wid);
-        work(0);
-        for (auto& th : pool) th.join();
-        for (int i = 0; i < cnt; ++i)
-            if (codes[i]) {
-                err = msgs[i];
-                return codes[i];
-            }
-        return PW_OK;
-    };
-    auto wait_lanes = [&]() -> cudaError_t {
-        for (Lane& ln : lanes) {
-            cudaError_t r = cudaEventRecord(ln.done, ln.s);
-            if (r == cudaSuccess) r = cudaEventSynchronize(ln.done);
-            if (r != cudaSuccess) return r;
-        }
-        return cudaSuccess;
-    };
+    const int n_lanes = std::max(1, std::min({kMaxLanes, hw, n_terms}));
 
-    Chunk chunks[2];
-    struct LaneSync {   // declared after the chunks, so destroyed first: no plan
-        Lane* l;        // is freed while a lane may still read it
-        ~LaneSync() {
-            for (int i = 0; i < kLanes; ++i)
-                if (l[i].s) cudaStreamSynchronize(l[i].s);
-        }
-    } lane_sync{lanes};
-    std::string err;
-    if (n_terms > 0 && (rc = plan_chunk(0, chunks[0], err))) return pw::set_error(rc, err);
-    for (int c0 = 0, ci = 0; c0 < n_terms; c0 += chunk, ci ^= 1) {
-        Chunk& cur = chunks[ci];
-        for (int i = 0; i < (int)cur.plans.size(); ++i) {
-            const Term& tm = terms[c0 + i];
-            Lane& ln = lanes[(c0 + i) % kLanes];
-            if ((rc = pw_amplitudes(cur.plans[i], n_ops, n_strings, d_bits, reinterpret_cast<double*>(ln.amp), ln.s))) {
-                wait_lanes();
-                return rc;
-            }
-            axpy_column<<<blocks, 256, 0, ln.s>>>(ln.amp, tm.coef, ln.acc, ncol, tm.col, n_strings);
-            if ((e = cudaGetLastError()) != cudaSuccess) {
-                wait_lanes();
-                return grad_cuda_fail(e, "axpy_column launch");
-            }
-        }
-        // plan the next chunk meanwhile, then release this one
-        Chunk& nxt = chunks[ci ^ 1];
-        if (c0 + chunk < n_terms && (rc = plan_chunk(c0 + chunk, nxt, err))) {
-            wait_lanes();
-            return pw::set_error(rc, err);
-        }
-        if ((e = wait_lanes()) != cudaSuccess) return grad_cuda_fail(e, "gradient lane wait");
-        for (pw_plan* q : cur.plans) pw_plan_destroy(q);
-        cur.plans.clear();
+    cudaEvent_t ready = nullptr;
+    if ((e = cudaEventCreateWithFlags(&ready, cudaEventDisableTiming)) != cudaSuccess)
+        return grad_cuda_fail(e, "cudaEventCreate");
+    struct EventGuard {
+        cudaEvent_t ev;
+        ~EventGuard() { cudaEventDestroy(ev); }
+    } ready_guard{ready};
+    if ((e = cudaEventRecord(ready, st)) != cudaSuccess) return grad_cuda_fail(e, "cudaEventRecord");
+    std::vector<Lane> lanes(n_lanes);
+    for (Lane& ln : lanes) {
+        if ((e = cudaStreamCreateWithFlags(&ln.s, cudaStreamNonBlocking)) != cudaSuccess ||
+            (e = cudaEventCreateWithFlags(&ln.done, cudaEventDisableTiming)) != cudaSuccess ||
+            (e = cudaMalloc(&ln.amp, n_strings * sizeof(double2))) != cudaSuccess ||
+            (e = cudaMalloc(&ln.acc, n_strings * ncol * sizeof(double2))) != cudaSuccess)
+            return grad_cuda_fail(e, "gradient lane set-up");
+        if ((e = cudaStreamWaitEvent(ln.s, ready, 0)) != cudaSuccess ||
+            (e = cudaMemsetAsync(ln.acc, 0, n_strings * ncol * sizeof(double2), ln.s)) != cudaSuccess)
+            return grad_cuda_fail(e, "gradient lane set-up");
     }
+
+    // A round's plans stay alive until every lane has finished the round
+    // (freeing device memory synchronises the whole device, which would stall
+    // the other lanes); a round holds at most kRoundPerLane terms per lane.
+    std::vector<pw_plan*> plans(n_terms, nullptr);
+    struct PlansGuard {
+        std::vector<pw_plan*>& v;
+        std::vector<Lane>& lanes;
+        void release(int b, int e) {
+            for (Lane& ln : lanes)
+                if (ln.s) cudaStreamSynchronize(ln.s);
+            for (int i = b; i < e; ++i) {
+                pw_plan_destroy(v[i]);
+                v[i] = nullptr;
+            }
+        }
+        ~PlansGuard() { release(0, (int)v.size()); }
+    } plans_guard{plans, lanes};
+    std::vector<int> codes(n_lanes, 0);
+    std::vector<std::string> msgs(n_lanes);
+    auto run_lane = [&](int l, int b, int e_) {
+        Lane& ln = lanes[l];
+        pw_circuit shifted;
+        shifted.n = base.c->n;
+        for (int i = b + l; i < e_ && !codes[l]; i += n_lanes) {
+            const Term& tm = terms[i];
+            shifted.ops = base.c->ops;
+            advance_quarter_turn(shifted.ops[tm.op], tm.mixer);
+            int r;
+            try {
+                r = pw_plan_build(&shifted, opts, &plans[i]);
+            } catch (...) {
+                r = pw::set_error(PW_ERR_OOM, "allocation failed while planning a shifted circuit");
+            }
+            if (!r) r = pw_amplitudes(plans[i], n_ops, n_strings, d_bits, reinterpret_cast<double*>(ln.amp), ln.s);
+            if (!r) {
+                axpy_column<<<blocks, 256, 0, ln.s>>>(ln.amp, tm.coef, ln.acc, ncol, tm.col, n_strings);
+                const cudaError_t le = cudaGetLastError();
+                if (le != cudaSuccess) r = grad_cuda_fail(le, "axpy_column launch");
+            }
+            if (r) {
+                codes[l] = r;
+                msgs[l] = pw_last_error();
+            }
+        }
+    };
+    const int round = n_lanes * kRoundPerLane;
+    for (int b = 0; b < n_terms; b += round) {
+        const int e_ = std::min(n_terms, b + round);
+        std::vector<std::thread> pool;
+        for (int l = 1; l < n_lanes; ++l) pool.emplace_back(run_lane, l, b, e_);
+        run_lane(0, b, e_);
+        for (auto& th : pool) th.join();
+        for (int l = 0; l < n_lanes; ++l)
+            if (codes[l]) return pw::set_error(codes[l], msgs[l]);
+        plans_guard.release(b, e_);
+    }
+
     // d_grad = the lanes' accumulators summed in lane order, on the caller's stream
-    const double2* acc_ptrs[kLanes];
-    for (int l = 0; l < kLanes; ++l) acc_ptrs[l] = lanes[l].acc;
+    std::vector<const double2*> acc_ptrs(n_lanes);
+    for (int l = 0; l < n_lanes; ++l) acc_ptrs[l] = lanes[l].acc;
     const double2** d_ptrs = nullptr;
-    if ((e = cudaMalloc(&d_ptrs, sizeof(acc_ptrs))) != cudaSuccess) return grad_cuda_fail(e, "cudaMalloc");
+    if ((e = cudaMalloc(&d_ptrs, n_lanes * sizeof(double2*))) != cudaSuccess) return grad_cuda_fail(e, "cudaMalloc");
     struct PtrFree {
         const double2** q;
         ~PtrFree() { cudaFree(q); }
     } ptr_free{d_ptrs};
-    if ((e = cudaMemcpy(d_ptrs, acc_ptrs, sizeof(acc_ptrs), cudaMemcpyHostToDevice)) != cudaSuccess)
+    if ((e = cudaMemcpy(d_ptrs, acc_ptrs.data(), n_lanes * sizeof(double2*), cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(cudaStreamLegacy)) != cudaSuccess)
         return grad_cuda_fail(e, "cudaMemcpy");
     for (Lane& ln : lanes) {
         if ((e = cudaEventRecord(ln.done, ln.s)) != cudaSuccess || (e = cudaStreamWaitEvent(st, ln.done, 0)) != cudaSuccess)
@@ -276,7 +258,7 @@ extern "C" int pw_qaoa_amp_grad(int n, int n_edges, const int* edges, const doub
     }
     const uint64_t total = n_strings * ncol;
     const unsigned sblocks = (unsigned)std::min<uint64_t>((total + 255) / 256, (uint64_t)std::max(nsm, 1) * 8);
-    sum_lanes<<<sblocks, 256, 0, st>>>(d_ptrs, kLanes, reinterpret_cast<double2*>(d_grad), total);
+    sum_lanes<<<sblocks, 256, 0, st>>>(d_ptrs, n_lanes, reinterpret_cast<double2*>(d_grad), total);
     if ((e = cudaGetLastError()) != cudaSuccess) return grad_cuda_fail(e, "sum_lanes launch");
     if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return grad_cuda_fail(e, "cudaStreamSynchronize");
     return PW_OK;
