@@ -569,8 +569,8 @@ def main_grad(args, rank, world, desc):
             "roofline": {"bound": "alu", "achieved": None, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": None,
                          "traffic": None, "kernel": "pw_chain_kernel (amplitude mode)",
                          "note": "no flop count of the amplitude mode is exported; the step is the amplitude "
-                                 "contractions (64 chains, one per derivative term, four or more in flight) plus "
-                                 "host planning and plan uploads"},
+                                 "contractions (64 chains, one per derivative term, up to 16 lanes in flight), "
+                                 "planned and uploaded by one host thread per lane"},
             "cpu_baseline": cpu,
             "e2e": {"value": r["e2e"], "unit": "gradients/s", "h2d_bytes_per_step": r["h2d"],
                     "d2h_bytes_per_step": r["d2h"]},
