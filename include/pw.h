@@ -218,6 +218,31 @@ int pw_qaoa_amp_grad(int n, int n_edges, const int* edges, const double* w, cons
                      const double* gammas, const double* betas, const pw_plan_opts* opts,
                      uint64_t n_strings, const uint64_t* d_bits, double* d_amp, double* d_grad, void* stream);
 
+/* Derivatives of amplitudes of a parameterised noiseless circuit (not in the
+ * paper; built on the amplitude contraction of Sec. 2). Operation i of c
+ * depends on parameter param_of_op[i] in 0..n_params-1, or on none (-1);
+ * param_of_op has one entry per operation (pw_circuit_num_ops). dmats holds,
+ * for every operation with a parameter, in operation order, the derivative of
+ * its matrix with respect to that parameter (2^m x 2^m complex, row-major,
+ * interleaved (re, im), as in pw_circuit_add_gate). By the product rule
+ *   d amp(x) / d theta_k = sum over operations i with param_of_op[i] = k of
+ *                          amp(c with operation i's matrix replaced by dmats_i, x);
+ * each replaced circuit must still be one the planner accepts (a diagonal gate
+ * with a diagonal derivative, a one-qubit gate with a one-qubit derivative),
+ * else the planner's error is returned. Writes d_amp (nullable, device,
+ * 2 * n_strings doubles: amp(c, x)) and d_grad (device, n_strings * n_params * 2
+ * doubles; row k holds d amp / d theta_0..n_params-1, each (re, im)); a
+ * parameter no operation depends on gets zeros. Bitstrings d_bits as in
+ * pw_amplitudes. Exact up to rounding; the rows are deterministic. Allocates
+ * and frees plans and scratch, synchronises the stream before it returns.
+ * Errors: PW_ERR_ARG (null pointers, n_params < 1, an entry out of range, a
+ * channel with a parameter), PW_ERR_NUMERIC (non-finite derivative entry),
+ * and those of pw_plan_build / pw_amplitudes (a noisy circuit is
+ * PW_ERR_UNSUPPORTED). */
+int pw_amp_grad(const pw_circuit* c, int n_params, const int* param_of_op, const double* dmats,
+                const pw_plan_opts* opts, uint64_t n_strings, const uint64_t* d_bits, double* d_amp,
+                double* d_grad, void* stream);
+
 /* Score-function estimate of the gradient of the expected cost (not in the
  * paper; built on pw_qaoa_amp_grad). d_bits (device, packed like pw_sample's
  * output) holds n_samples >= 1 bitstrings drawn from p(x) = |amp(C, x)|^2 of

@@ -115,3 +115,25 @@ def amp_and_grad_tn(spec, bitstrings, columns=None):
             for k, x in enumerate(bitstrings):
                 grads[k, col] += coef * TN.amplitudes(n, ins, x)
     return grads
+
+
+def amp_grad_product_rule(n, ops, param_of_op, dmats, n_params, bitstrings):
+    """d amp / d theta_k of a parameterised gate list by the product rule.
+
+    Operation i depends on parameter param_of_op[i] (or -1); dmats lists the
+    derivative matrices of the parameterised operations in operation order.
+    d amp / d theta_k = sum over i with param_of_op[i] = k of the amplitude of
+    the list with operation i's matrix replaced by its derivative (state
+    vector, FP64). Returns grad [K, n_params] complex.
+    """
+    idx = np.asarray([int(sum(int(b) << q for q, b in enumerate(x))) for x in bitstrings])
+    grads = np.zeros((len(idx), n_params), dtype=complex)
+    j = 0
+    for i, k in enumerate(param_of_op):
+        if k < 0:
+            continue
+        repl = list(ops)
+        repl[i] = C.gate(ops[i].qubits, dmats[j])
+        j += 1
+        grads[:, k] += SV.run(n, repl)[idx]
+    return grads

@@ -1,23 +1,24 @@
-// Exact derivatives of QAOA amplitudes with respect to the angles, by the
-// parameter-shift rule for amplitudes.
+// Exact derivatives of amplitudes with respect to circuit parameters.
 //
-// Every angle enters the QAOA circuit of App. D through gates exp(-i t G) with
-// an involutory generator G (G^2 = I: Z_u Z_v, Z_j, X_j). For such a gate
-// d/dt exp(-i t G) = -i G exp(-i t G) = exp(-i (t + pi/2) G), so
+// By the product rule, if each gate A_i depends on at most one parameter
+// theta_k(i), then d amp(x) / d theta_k = sum over the gates i of parameter k
+// of the amplitude (Sec. 2) of the circuit with A_i replaced by dA_i / d theta_k
+// (pw_amp_grad: the caller gives dA_i). A replaced diagonal gate stays
+// diagonal and a one-qubit gate stays a one-qubit gate, so each such circuit is
+// planned and contracted by the pilot-wave amplitude path like the original.
 //
-//   d amp(x) / d gamma_l = sum_e w_e amp_{e,l}(x) + sum_j h_j amp_{j,l}(x),
-//   d amp(x) / d beta_l  = sum_j amp'_{j,l}(x),
-//
-// where each amp_* is the amplitude (Sec. 2) of the same circuit with the one
-// gate replaced by -i G times itself (its angle advanced by pi/2). Those
-// circuits have the structure of the original, so each is planned and
-// contracted by the pilot-wave amplitude path; the replaced matrix is the
-// original one with rows swapped and entries multiplied by +-i, exact in
-// floating point. This is not the paper's method (it gives no gradients); it
-// reuses the amplitude contraction p(|E| + n) times, p(|E| + 2n) with fields h.
+// For the QAOA circuit of App. D (pw_qaoa_amp_grad) every angle enters through
+// gates exp(-i t G) with an involutory generator G (Z_u Z_v, Z_j, X_j) and t
+// proportional to the angle with coefficient w_e, h_j or 1; the derivative
+// matrix is that coefficient times -i G A = exp(-i (t + pi/2) G) (the gate
+// advanced by a quarter turn, the parameter-shift rule for amplitudes), formed
+// exactly by swapping rows and multiplying by +-i, with the coefficient applied
+// to the amplitude in FP64. The QAOA gradient takes p(|E| + n) contractions,
+// p(|E| + 2n) with fields h. Gradients are not part of the paper's method.
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <string>
 #include <thread>
 #include <utility>
@@ -46,19 +47,20 @@ __global__ void axpy_column(const double2* __restrict__ amp, double coef, double
 }
 
 // -i G A for the gate's generator G on its own local index (bit i = qubit i).
-void advance_quarter_turn(pw::Op& op, bool x_generator) {
+std::vector<cd> quarter_turn(const pw::Op& op, bool x_generator) {
     const int d = op.dim();
-    std::vector<cd> A(op.mats.begin(), op.mats.begin() + d * d);
+    std::vector<cd> out((size_t)d * d);
     const cd mi(0.0, -1.0);
     for (int r = 0; r < d; ++r)
         for (int c = 0; c < d; ++c) {
             if (x_generator) {   // -i X A: row r of the result is row r^1 of A
-                op.mats[r * d + c] = mi * A[(r ^ 1) * d + c];
+                out[r * d + c] = mi * op.mats[(r ^ 1) * d + c];
             } else {             // -i Z..Z A: sign (-1)^(parity of r)
                 const bool odd = __builtin_popcount((unsigned)r) & 1;
-                op.mats[r * d + c] = (odd ? -mi : mi) * A[r * d + c];
+                out[r * d + c] = (odd ? -mi : mi) * op.mats[r * d + c];
             }
         }
+    return out;
 }
 
 struct PlanGuard {
@@ -107,32 +109,31 @@ struct CircuitGuard {
     ~CircuitGuard() { pw_circuit_destroy(c); }
 };
 
-}  // namespace
+// One derivative term: the circuit with op `op`'s matrix replaced by `mat`,
+// whose amplitude times `coef` adds to derivative column `col`.
+struct Term {
+    int op, col;
+    double coef;
+    std::vector<cd> mat;
+};
 
-extern "C" int pw_qaoa_amp_grad(int n, int n_edges, const int* edges, const double* w, const double* h, int p,
-                                const double* gammas, const double* betas, const pw_plan_opts* opts,
-                                uint64_t n_strings, const uint64_t* d_bits, double* d_amp, double* d_grad,
-                                void* stream) {
-    if (p < 1) return pw::set_error(PW_ERR_ARG, "p must be >= 1");
-    if (n_strings && (!d_bits || !d_grad)) return pw::set_error(PW_ERR_ARG, "null argument");
-    CircuitGuard base;
-    int rc = pw_circuit_qaoa(n, n_edges, edges, w, h, p, gammas, betas, 0.0, 0.0, &base.c);
-    if (rc) return rc;
-    const int n_ops = (int)base.c->ops.size();
-    const int per_layer = n_edges + (h ? n : 0) + n;
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
-    const int ncol = 2 * p;
+// amp(C, x) of the circuit into d_amp (nullable). Plans it first, so that an
+// unsupported structure is reported before any device work.
+int base_amplitudes(const pw_circuit* base, const pw_plan_opts* opts, uint64_t n_strings, const uint64_t* d_bits,
+                    double* d_amp, cudaStream_t st) {
+    PlanGuard pl;
+    int rc = pw_plan_build(base, opts, &pl.p);
+    if (rc || n_strings == 0) return rc;
+    if (d_amp && (rc = pw_amplitudes(pl.p, (int)base->ops.size(), n_strings, d_bits, d_amp, st))) return rc;
+    const cudaError_t e = cudaStreamSynchronize(st);   // before the plan's tables are freed
+    return e == cudaSuccess ? PW_OK : grad_cuda_fail(e, "cudaStreamSynchronize");
+}
 
-    // the unshifted amplitudes (plans the circuit first: an unsupported
-    // structure is reported before any device work)
-    {
-        PlanGuard pl;
-        if ((rc = pw_plan_build(base.c, opts, &pl.p))) return rc;
-        if (n_strings == 0) return PW_OK;
-        if (d_amp && (rc = pw_amplitudes(pl.p, n_ops, n_strings, d_bits, d_amp, stream))) return rc;
-        cudaError_t e = cudaStreamSynchronize(st);   // before the plan's tables are freed
-        if (e != cudaSuccess) return grad_cuda_fail(e, "cudaStreamSynchronize");
-    }
+// d_grad[k][col] = sum over the terms of that column of coef * amp(term's circuit, x_k),
+// for n_strings strings and ncol columns (complex, row-major).
+int run_terms(const pw_circuit* base, const std::vector<Term>& terms, int ncol, const pw_plan_opts* opts,
+              uint64_t n_strings, const uint64_t* d_bits, double* d_grad, cudaStream_t st) {
+    const int n_ops = (int)base->ops.size();
     int dev = 0, nsm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
@@ -140,25 +141,13 @@ extern "C" int pw_qaoa_amp_grad(int n, int n_edges, const int* edges, const doub
     const unsigned blocks = (unsigned)std::min<uint64_t>(want, (uint64_t)std::max(nsm, 1) * 8);
     cudaError_t e;
 
-    // The derivative terms are spread over lanes: lane l takes terms l, l + L,
+    // The terms are spread over lanes: lane l takes terms l, l + L,
     // l + 2L, ... in order, on its own host thread (planning the shifted
     // circuit, uploading its tables, launching its contraction and the
     // accumulation) and its own non-blocking stream with its own amplitude
     // scratch and FP64 accumulator. Contractions of different terms overlap on
     // the device and the host work runs in parallel; the lanes are summed in a
     // fixed order at the end, so the result does not depend on scheduling.
-    struct Term {
-        int op, col;
-        bool mixer;
-        double coef;
-    };
-    std::vector<Term> terms;
-    for (int l = 0; l < p; ++l)
-        for (int t = 0; t < per_layer; ++t) {
-            const bool mixer = t >= per_layer - n;
-            const double coef = mixer ? 1.0 : t < n_edges ? w[t] : h[t - n_edges];
-            if (coef != 0.0) terms.push_back({n + l * per_layer + t, mixer ? p + l : l, mixer, coef});
-        }
     const int n_terms = (int)terms.size();
     const int hw = (int)std::max(1u, std::thread::hardware_concurrency());
     const int n_lanes = std::max(1, std::min({kMaxLanes, hw, n_terms}));
@@ -205,16 +194,16 @@ extern "C" int pw_qaoa_amp_grad(int n, int n_edges, const int* edges, const doub
     auto run_lane = [&](int l, int b, int e_) {
         Lane& ln = lanes[l];
         pw_circuit shifted;
-        shifted.n = base.c->n;
+        shifted.n = base->n;
         for (int i = b + l; i < e_ && !codes[l]; i += n_lanes) {
             const Term& tm = terms[i];
-            shifted.ops = base.c->ops;
-            advance_quarter_turn(shifted.ops[tm.op], tm.mixer);
+            shifted.ops = base->ops;
+            shifted.ops[tm.op].mats = tm.mat;
             int r;
             try {
                 r = pw_plan_build(&shifted, opts, &plans[i]);
             } catch (...) {
-                r = pw::set_error(PW_ERR_OOM, "allocation failed while planning a shifted circuit");
+                r = pw::set_error(PW_ERR_OOM, "allocation failed while planning a derivative term");
             }
             if (!r) r = pw_amplitudes(plans[i], n_ops, n_strings, d_bits, reinterpret_cast<double*>(ln.amp), ln.s);
             if (!r) {
@@ -262,6 +251,64 @@ extern "C" int pw_qaoa_amp_grad(int n, int n_edges, const int* edges, const doub
     if ((e = cudaGetLastError()) != cudaSuccess) return grad_cuda_fail(e, "sum_lanes launch");
     if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return grad_cuda_fail(e, "cudaStreamSynchronize");
     return PW_OK;
+}
+
+
+}  // namespace
+
+extern "C" int pw_qaoa_amp_grad(int n, int n_edges, const int* edges, const double* w, const double* h, int p,
+                                const double* gammas, const double* betas, const pw_plan_opts* opts,
+                                uint64_t n_strings, const uint64_t* d_bits, double* d_amp, double* d_grad,
+                                void* stream) {
+    if (p < 1) return pw::set_error(PW_ERR_ARG, "p must be >= 1");
+    if (n_strings && (!d_bits || !d_grad)) return pw::set_error(PW_ERR_ARG, "null argument");
+    CircuitGuard base;
+    int rc = pw_circuit_qaoa(n, n_edges, edges, w, h, p, gammas, betas, 0.0, 0.0, &base.c);
+    if (rc) return rc;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if ((rc = base_amplitudes(base.c, opts, n_strings, d_bits, d_amp, st)) || n_strings == 0) return rc;
+    // per layer: the edges' RZZ (generator Z_u Z_v, weight w_e), the fields' RZ
+    // (Z_j, h_j), the mixers' RX (X_j, 1)
+    const int per_layer = n_edges + (h ? n : 0) + n;
+    std::vector<Term> terms;
+    for (int l = 0; l < p; ++l)
+        for (int t = 0; t < per_layer; ++t) {
+            const bool mixer = t >= per_layer - n;
+            const double coef = mixer ? 1.0 : t < n_edges ? w[t] : h[t - n_edges];
+            const int op = n + l * per_layer + t;
+            if (coef != 0.0) terms.push_back({op, mixer ? p + l : l, coef, quarter_turn(base.c->ops[op], mixer)});
+        }
+    return run_terms(base.c, terms, 2 * p, opts, n_strings, d_bits, d_grad, st);
+}
+
+extern "C" int pw_amp_grad(const pw_circuit* c, int n_params, const int* param_of_op, const double* dmats,
+                           const pw_plan_opts* opts, uint64_t n_strings, const uint64_t* d_bits, double* d_amp,
+                           double* d_grad, void* stream) {
+    if (!c || !param_of_op) return pw::set_error(PW_ERR_ARG, "null argument");
+    if (n_params < 1) return pw::set_error(PW_ERR_ARG, "n_params must be >= 1");
+    if (n_strings && (!d_bits || !d_grad)) return pw::set_error(PW_ERR_ARG, "null argument");
+    std::vector<Term> terms;
+    size_t at = 0;
+    for (int i = 0; i < (int)c->ops.size(); ++i) {
+        const int k = param_of_op[i];
+        if (k < -1 || k >= n_params) return pw::set_error(PW_ERR_ARG, "param_of_op entry out of range");
+        if (k < 0) continue;
+        const pw::Op& op = c->ops[i];
+        if (op.kind != pw::OP_GATE) return pw::set_error(PW_ERR_ARG, "a parameterised operation must be a gate");
+        if (!dmats) return pw::set_error(PW_ERR_ARG, "null argument");
+        const int d = op.dim();
+        Term tm{i, k, 1.0, std::vector<cd>((size_t)d * d)};
+        for (int j = 0; j < d * d; ++j, ++at) {
+            tm.mat[j] = cd(dmats[2 * at], dmats[2 * at + 1]);
+            if (!std::isfinite(tm.mat[j].real()) || !std::isfinite(tm.mat[j].imag()))
+                return pw::set_error(PW_ERR_NUMERIC, "non-finite derivative entry");
+        }
+        terms.push_back(std::move(tm));
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int rc = base_amplitudes(c, opts, n_strings, d_bits, d_amp, st);
+    if (rc || n_strings == 0) return rc;
+    return run_terms(c, terms, n_params, opts, n_strings, d_bits, d_grad, st);
 }
 
 // ------------------------------------------- score-function cost gradient

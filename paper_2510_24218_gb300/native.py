@@ -77,6 +77,7 @@ def load_library():
         "pw_amplitudes": (C.c_int, [vp, C.c_int, C.c_uint64, vp, vp, vp]),
         "pw_qaoa_amp_grad": (C.c_int, [C.c_int, C.c_int, ip, dp, dp, C.c_int, dp, dp, C.POINTER(PlanOpts),
                                        C.c_uint64, vp, vp, vp, vp]),
+        "pw_amp_grad": (C.c_int, [vp, C.c_int, ip, dp, C.POINTER(PlanOpts), C.c_uint64, vp, vp, vp, vp]),
         "pw_qaoa_cost_grad": (C.c_int, [C.c_int, C.c_int, ip, dp, dp, C.c_int, dp, dp, C.POINTER(PlanOpts),
                                         C.c_uint64, vp, vp, vp]),
         "pw_sample_static": (C.c_int, [vp, C.c_uint64, C.c_uint64, C.c_uint64, vp, vp, C.POINTER(RunStats)]),
@@ -261,6 +262,29 @@ def pw_qaoa_amp_grad(n, edges, weights, h, p, gammas, betas, bits, grad_out, amp
                                            int(bits.shape[0]), C.c_void_p(bits.data_ptr()),
                                            C.c_void_p(amp_out.data_ptr()) if amp_out is not None else None,
                                            C.c_void_p(grad_out.data_ptr()), _stream_ptr(stream)))
+
+
+def pw_amp_grad(circ, n_params, param_of_op, dmats, bits, grad_out, amp_out=None, precision=PW_PREC_FP32,
+                order=PW_ORDER_AUTO, stream=None):
+    """Exact d amp / d theta of a parameterised circuit (product rule).
+
+    param_of_op: int [n_ops] (-1 = no parameter); dmats: the derivative matrices
+    of the parameterised operations in operation order (a list of 2^m x 2^m
+    complex arrays); bits: torch CUDA int64 [n_strings, words]; grad_out: torch
+    CUDA float64 [n_strings, n_params, 2]; amp_out: None or float64 [n_strings, 2].
+    """
+    q, qp = _iarr(param_of_op)
+    flat = [np.asarray(D, dtype=np.complex128).ravel() for D in dmats]
+    if flat:
+        d, dp_ = _cplx(np.concatenate(flat))
+    else:
+        d, dp_ = None, None
+    o = PlanOpts()
+    o.precision, o.order = precision, order
+    _check(load_library().pw_amp_grad(circ, int(n_params), qp, dp_, C.byref(o), int(bits.shape[0]),
+                                      C.c_void_p(bits.data_ptr()),
+                                      C.c_void_p(amp_out.data_ptr()) if amp_out is not None else None,
+                                      C.c_void_p(grad_out.data_ptr()), _stream_ptr(stream)))
 
 
 def pw_qaoa_cost_grad(n, edges, weights, h, p, gammas, betas, bits, out, precision=PW_PREC_FP32, order=PW_ORDER_AUTO,

@@ -225,3 +225,80 @@ def test_gradient_is_deterministic_across_calls(pw):
     _, want = G.amp_and_grad(spec, xs[:500])
     got = runs[0][:500, :, 0] + 1j * runs[0][:500, :, 1]
     assert np.abs(got - want).max() <= 1e-11 * np.abs(want).max()
+
+
+def _build_param_circuit(pw, n, ops):
+    circ = pw.pw_circuit_create(n)
+    for o in ops:
+        pw.pw_circuit_add_gate(circ, o.qubits, o.mat)
+    return circ
+
+
+@pytest.mark.parametrize("prec,tol", [(1, 1e-11), (0, 2e-5)])
+def test_general_parameterised_gradient_against_product_rule_oracle(pw, prec, tol):
+    """pw_amp_grad on a circuit with one parameter per layer on its RZZ gates
+    and one per RY mixer (26 parameters, 12 qubits, p = 2) against the oracle's
+    product rule on the state vector; a parameter nothing depends on is zero."""
+    import torch
+    from tests.test_oracle_gradient import parameterised_circuit
+    rng = np.random.default_rng(45)
+    n, p = 12, 2
+    spec = W.random_qaoa(n, 1, seed=46)
+    theta = rng.uniform(0, np.pi, size=p + p * n)
+    ops, param, dm = parameterised_circuit(n, spec.edges, spec.weights, theta, p)
+    circ = _build_param_circuit(pw, n, ops)
+    xs = W.random_bitstrings(24, n, seed=47)
+    bits = torch.from_numpy(pw.pack_bits(xs).view(np.int64)).cuda()
+    n_params = len(theta) + 1
+    grad = torch.full((24, n_params, 2), np.nan, dtype=torch.float64, device="cuda")
+    amp = torch.zeros((24, 2), dtype=torch.float64, device="cuda")
+    pw.pw_amp_grad(circ, n_params, param, dm, bits, grad, amp_out=amp, precision=prec)
+    pw.pw_circuit_destroy(circ)
+    g = grad.cpu().numpy()
+    g = g[..., 0] + 1j * g[..., 1]
+    want = G.amp_grad_product_rule(n, ops, param, dm, n_params, xs)
+    assert np.abs(g - want).max() <= tol * np.abs(want).max()
+    assert not g[:, -1].any()
+    a = amp.cpu().numpy()
+    from oracle import statevector as SV
+    psi = SV.run(n, ops)
+    idx = [int(sum(int(b) << q for q, b in enumerate(x))) for x in xs]
+    assert np.abs(a[:, 0] + 1j * a[:, 1] - psi[idx]).max() <= tol * np.abs(psi[idx]).max()
+
+
+def test_general_gradient_equals_qaoa_gradient(pw):
+    """The QAOA circuit written as a parameterised circuit (the gammas on the
+    RZZ and RZ gates, the betas on the RX gates, derivatives -i coef G A) gives
+    the rows of pw_qaoa_amp_grad."""
+    import torch
+    from oracle import circuit as OC
+    spec = W.random_qaoa(10, 2, seed=48, with_h=True)
+    ops = OC.qaoa_circuit(spec)
+    n, p = spec.n, spec.p
+    Z2 = np.diag([1.0, -1.0, -1.0, 1.0]).astype(complex)
+    Z1 = np.diag([1.0, -1.0]).astype(complex)
+    X1 = np.array([[0, 1], [1, 0]], dtype=complex)
+    param, dm = [-1] * n, []
+    pos = n
+    for l in range(p):
+        for w in spec.weights:
+            param.append(l)
+            dm.append(-1j * w * Z2 @ ops[pos].mat)
+            pos += 1
+        for j in range(n):
+            param.append(l)
+            dm.append(-1j * spec.h[j] * Z1 @ ops[pos].mat)
+            pos += 1
+        for j in range(n):
+            param.append(p + l)
+            dm.append(-1j * X1 @ ops[pos].mat)
+            pos += 1
+    circ = _build_param_circuit(pw, n, ops)
+    xs = W.random_bitstrings(16, n, seed=49)
+    bits = torch.from_numpy(pw.pack_bits(xs).view(np.int64)).cuda()
+    g1 = torch.zeros((16, 2 * p, 2), dtype=torch.float64, device="cuda")
+    pw.pw_amp_grad(circ, 2 * p, param, dm, bits, g1, precision=pw.PW_PREC_FP64)
+    pw.pw_circuit_destroy(circ)
+    _, g2 = _grad(pw, spec, xs, 1)
+    a = g1.cpu().numpy()
+    assert np.abs(a[..., 0] + 1j * a[..., 1] - g2).max() <= 1e-12 * np.abs(g2).max()

@@ -261,3 +261,31 @@ def test_gradient_calls_validate_before_device_work(pw):
     assert lib.pw_qaoa_amp_grad(spec.n, 1, bad.ctypes.data_as(ip), w.ctypes.data_as(dp), None, 2,
                                 g.ctypes.data_as(dp), b.ctypes.data_as(dp), C.byref(o), 0, None, None, None,
                                 None) < 0
+
+
+def test_general_gradient_validates_its_arguments(pw):
+    """pw_amp_grad rejects bad parameter maps and parameterised channels on
+    the host, before any device work."""
+    import ctypes as C
+    from paper_2510_24218_gb300 import native as N
+    from oracle import circuit as OC
+    lib = pw.load_library()
+    spec = W.random_qaoa(4, 1, seed=82, depol2=0.1)
+    ops = OC.qaoa_circuit(spec)
+    circ = pw.pw_circuit_qaoa(spec.n, spec.edges, spec.weights, None, 1, spec.gammas, spec.betas, spec.depol2)
+    n_ops = pw.pw_circuit_num_ops(circ)
+    o = N.PlanOpts()
+    ip, dp = C.POINTER(C.c_int), C.POINTER(C.c_double)
+    d = np.zeros(2 * 16 * n_ops)
+    def call(param, n_params=2):
+        q = np.ascontiguousarray(np.asarray(param, dtype=np.int32))
+        return lib.pw_amp_grad(circ, n_params, q.ctypes.data_as(ip), d.ctypes.data_as(dp), C.byref(o), 0, None,
+                               None, None, None)
+    assert call([-1] * n_ops) == 0
+    assert call([-1] * n_ops, n_params=0) == -1
+    assert call([5] + [-1] * (n_ops - 1)) == -1
+    kraus_at = next(i for i, op in enumerate(ops) if op.kind == "kraus")
+    bad = [-1] * n_ops
+    bad[kraus_at] = 0
+    assert call(bad) == -1 and "must be a gate" in pw.pw_last_error()
+    pw.pw_circuit_destroy(circ)

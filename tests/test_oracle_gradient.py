@@ -71,3 +71,53 @@ def test_expected_cost_gradient_matches_p1_closed_form():
     g0, b0, h = float(spec.gammas[0]), float(spec.betas[0]), 1e-6
     want = [(f(g0 + h, b0) - f(g0 - h, b0)) / (2 * h), (f(g0, b0 + h) - f(g0, b0 - h)) / (2 * h)]
     assert np.allclose(d, want, atol=1e-7, rtol=0)
+
+
+def ry_mat(phi):
+    c, s = np.cos(phi / 2), np.sin(phi / 2)
+    return np.array([[c, -s], [s, c]], dtype=complex)
+
+
+def d_ry_mat(phi):
+    c, s = np.cos(phi / 2), np.sin(phi / 2)
+    return 0.5 * np.array([[-s, -c], [c, -s]], dtype=complex)
+
+
+def parameterised_circuit(n, edges, weights, theta, p):
+    """H layer, then per layer l: RZZ(theta[l] w_e) on every edge and
+    RY(theta[p + l n + j]) on every qubit j. Returns (ops, param_of_op, dmats)."""
+    Z2 = np.diag([1.0, -1.0, -1.0, 1.0]).astype(complex)
+    ops = [OC.gate((q,), OC.h_mat()) for q in range(n)]
+    param, dm = [-1] * n, []
+    for l in range(p):
+        for (u, v), w in zip(edges, weights):
+            A = OC.rzz_mat(theta[l] * w)
+            ops.append(OC.gate((int(u), int(v)), A))
+            param.append(l)
+            dm.append(w * (-0.5j) * Z2 @ A)
+        for j in range(n):
+            k = p + l * n + j
+            ops.append(OC.gate((j,), ry_mat(theta[k])))
+            param.append(k)
+            dm.append(d_ry_mat(theta[k]))
+    return ops, param, dm
+
+
+def test_product_rule_gradient_matches_central_differences():
+    rng = np.random.default_rng(25)
+    n, p = 6, 2
+    edges = np.array([(i, (i + 1) % n) for i in range(n)])
+    weights = rng.normal(size=n)
+    theta = rng.uniform(0, np.pi, size=p + p * n)
+    xs = W.random_bitstrings(4, n, seed=26)
+    ops, param, dm = parameterised_circuit(n, edges, weights, theta, p)
+    got = G.amp_grad_product_rule(n, ops, param, dm, len(theta), xs)
+    idx = [int(sum(int(b) << q for q, b in enumerate(x))) for x in xs]
+    h = 1e-5
+    for k in range(len(theta)):
+        tp, tm = theta.copy(), theta.copy()
+        tp[k] += h
+        tm[k] -= h
+        fp = SV.run(n, parameterised_circuit(n, edges, weights, tp, p)[0])[idx]
+        fm = SV.run(n, parameterised_circuit(n, edges, weights, tm, p)[0])[idx]
+        assert np.abs((fp - fm) / (2 * h) - got[:, k]).max() < 1e-8, k
