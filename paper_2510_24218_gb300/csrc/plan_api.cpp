@@ -4,6 +4,7 @@
 #include <algorithm>
 #include <cstring>
 #include <new>
+#include <utility>
 
 #include "pw_internal.h"
 #include "smem_layout.h"
@@ -35,6 +36,47 @@ int choose_threads(HostPlan& hp, int requested) {
     return (int)pw2;
 }
 
+// A two-qubit gate A = SWAP D with D diagonal (SWAP, iSWAP, fSim(pi/2, phi)):
+// A[r][c] != 0 exactly when r is c with its two bits exchanged.
+bool swap_class(const Op& op) {
+    if (op.kind != OP_GATE || op.qubits.size() != 2) return false;
+    for (int r = 0; r < 4; ++r)
+        for (int c = 0; c < 4; ++c) {
+            const int sc = ((c & 1) << 1) | (c >> 1);
+            if ((op.mats[r * 4 + c] != cd(0.0, 0.0)) != (r == sc)) return false;
+        }
+    return true;
+}
+
+// Monomial gates move the chain deterministically (Alg. 1); a SWAP-class gate
+// on (a, b) exchanges the contents of two qubits, A|x_a x_b> = D(x)|x_b x_a>.
+// Following the qubits' contents on wires instead: the gate becomes its phase
+// D on the current wires of (a, b), after which a's content is on b's old wire
+// and vice versa, and every later operation acts on the wires its qubits'
+// contents are on. Operation positions (the draws' ids) stay the same.
+// Returns false (out untouched) when the circuit has no such gate.
+bool relabel_swaps(const pw_circuit* c, pw_circuit& out, std::vector<int>& wire_of) {
+    bool any = false;
+    for (const Op& op : c->ops) any = any || swap_class(op);
+    if (!any) return false;
+    out.n = c->n;
+    out.ops = c->ops;
+    wire_of.resize(c->n);
+    for (int q = 0; q < c->n; ++q) wire_of[q] = q;
+    for (Op& op : out.ops) {
+        const bool sw = swap_class(op);
+        const int a = op.qubits.size() > 0 ? op.qubits[0] : -1, b = op.qubits.size() > 1 ? op.qubits[1] : -1;
+        for (int& q : op.qubits) q = wire_of[q];
+        if (sw) {
+            std::vector<cd> D(16, cd(0.0, 0.0));
+            for (int x = 0; x < 4; ++x) D[x * 4 + x] = op.mats[(((x & 1) << 1) | (x >> 1)) * 4 + x];
+            op.mats = D;
+            std::swap(wire_of[a], wire_of[b]);
+        }
+    }
+    return true;
+}
+
 }  // namespace
 
 extern "C" {
@@ -48,7 +90,15 @@ int pw_plan_build(const pw_circuit* c, const pw_plan_opts* opts, pw_plan** out) 
     if (!plan) return set_error(PW_ERR_OOM, "allocation failed");
     int rc;
     try {
-        rc = build_plan(c, o, plan->hp);
+        pw_circuit relabelled;
+        const bool moved = relabel_swaps(c, relabelled, plan->out_wire);
+        bool noisy = false;
+        for (const Op& op : c->ops) noisy = noisy || op.kind == OP_KRAUS;
+        // (with channels, Alg. 2's frame stays on the qubits while the
+        // relabelling would carry it with the wires: same distribution, other
+        // draws; not offered)
+        rc = moved && noisy ? set_error(PW_ERR_UNSUPPORTED, "SWAP-class gates in noisy circuits are not supported")
+                            : build_plan(moved ? &relabelled : c, o, plan->hp);
     } catch (const std::bad_alloc&) {
         rc = set_error(PW_ERR_OOM, "allocation failed while planning");
     }
@@ -136,13 +186,14 @@ int pw_plan_exec_order(const pw_plan* plan, int* order) {
 
 void pw_plan_destroy(pw_plan* plan) {
     if (!plan) return;
-    if (plan->d_blob || plan->d_counters || plan->d_stage) {
+    if (plan->d_blob || plan->d_counters || plan->d_stage || plan->d_out_wire) {
         int cur = -1;
         cudaGetDevice(&cur);
         if (plan->device >= 0 && plan->device != cur) cudaSetDevice(plan->device);
         if (plan->d_blob) cudaFree(plan->d_blob);
         if (plan->d_counters) cudaFree(plan->d_counters);
         if (plan->d_stage) cudaFree(plan->d_stage);
+        if (plan->d_out_wire) cudaFree(plan->d_out_wire);
         if (plan->device >= 0 && plan->device != cur && cur >= 0) cudaSetDevice(cur);
     }
     delete plan;

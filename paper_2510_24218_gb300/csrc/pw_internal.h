@@ -274,4 +274,14 @@ struct pw_plan {
     unsigned long long* d_counters = nullptr;
     void* d_stage = nullptr;       // staging for pw_sample_host
     size_t stage_bytes = 0;
+    // SWAP-class gates are planned as relabellings of the qubit wires: output
+    // bit q is the bit of wire out_wire[q] (empty: the identity)
+    std::vector<int> out_wire;
+    int* d_out_wire = nullptr;
 };
+
+namespace pw {
+// Reorder the packed output rows of a plan with relabelled wires in place
+// (stream: a cudaStream_t).
+int permute_output(pw_plan* plan, uint64_t* d_bits, uint64_t n_samples, void* stream);
+}  // namespace pw

@@ -1546,6 +1546,10 @@ int pw_sample(pw_plan* plan, uint64_t seed, uint64_t first_sample, uint64_t n_sa
     uint64_t launches = 0;
     rc = run(plan, kp, st, &launches);
     if (rc) return rc;
+    if (!plan->out_wire.empty()) {   // wires back to qubits (SWAP-class gates)
+        if ((rc = permute_output(plan, d_out_bits, n_samples, st))) return rc;
+        ++launches;
+    }
     if (stats) {
         unsigned long long h[4] = {0, 0, 0, 0};
         e = cudaMemcpyAsync(h, plan->d_counters, sizeof(h), cudaMemcpyDeviceToHost, st);
@@ -1653,6 +1657,8 @@ int pw_amplitudes(pw_plan* plan, int prefix_ops, uint64_t n_strings, const uint6
     if (!plan || ((!d_bits || !d_amp) && n_strings)) return set_error(PW_ERR_ARG, "null argument");
     const HostPlan& hp = plan->hp;
     if (hp.noisy) return set_error(PW_ERR_UNSUPPORTED, "amplitudes are defined for noiseless circuits only");
+    if (!plan->out_wire.empty())
+        return set_error(PW_ERR_UNSUPPORTED, "amplitudes of circuits with SWAP-class gates are not supported");
     if (prefix_ops < 1 || prefix_ops > (int)hp.exec_order.size()) return set_error(PW_ERR_ARG, "prefix_ops out of range");
     const int op = hp.exec_order[prefix_ops - 1];
     if (hp.exec_layer[op] < 1)
@@ -1764,6 +1770,8 @@ extern "C" int pw_sample_static(const pw_plan* plan, uint64_t seed, uint64_t fir
     const HostPlan& hp = plan->hp;
     if (hp.ctas_per_chain > 1)
         return set_error(PW_ERR_UNSUPPORTED, "pw_sample_static runs plans of one CTA per chain only");
+    if (!plan->out_wire.empty())
+        return set_error(PW_ERR_UNSUPPORTED, "pw_sample_static does not run circuits with SWAP-class gates");
     DevPlanOffsets off{};
     const std::vector<unsigned char> blob = make_blob(hp, off);
     if (blob.size() > kStaticScratchBytes - kStaticCounterBytes)

@@ -645,3 +645,53 @@ def test_autotune_keeps_the_samples(pw):
     assert worst < 1e-5
     pw.pw_plan_destroy(plan)
     pw.pw_circuit_destroy(circ)
+
+
+def _swap_class(rng):
+    """SWAP times a random diagonal of phases (SWAP, iSWAP and fSim(pi/2, phi)
+    are of this form)."""
+    S = np.eye(4)[[0, 2, 1, 3]].astype(complex)
+    return S @ np.diag(np.exp(1j * rng.uniform(0, 2 * np.pi, 4)))
+
+
+@pytest.mark.parametrize("n,rows,p,seed", [(8, 2, 2, 15), (9, 3, 2, 16)])
+def test_swap_class_gates_against_alg1(pw, n, rows, p, seed):
+    """Two-qubit SWAP-class gates (a swap of two qubits' contents times
+    phases) between the sections, planned as relabellings of the wires: bits
+    equal to Alg. 1 on the original gate list (the swaps as deterministic
+    moves) and candidate pairs within 1e-5."""
+    import torch
+    rng = np.random.default_rng(seed + 100)
+    edges = [(a, b) for a, b in W.grid_edges(rows, n // rows)]
+    ops = _general_circuit(n, edges, p, seed)
+    sec = len(edges) + len(range(0, n, 3))
+    pos1 = n + sec                      # end of layer 1's diagonal section
+    pos2 = n + (sec + n) + sec          # end of layer 2's diagonal section
+    ops = (ops[:n] + [OC.gate((0, n - 1), _swap_class(rng))] + ops[n:pos1] +
+           [OC.gate((1, 2), OC.iswap_mat()), OC.gate((5, 3), _swap_class(rng))] + ops[pos1:pos2] +
+           [OC.gate((2, n - 2), _swap_class(rng))] + ops[pos2:])
+    circ = pw.pw_circuit_create(n)
+    for o in ops:
+        pw.pw_circuit_add_gate(circ, list(o.qubits), o.mat)
+    plan = pw.pw_plan_build(circ)
+    st = pw.pw_plan_stats(plan)
+    N = 64
+    bits = torch.zeros((N, 1), dtype=torch.int64, device="cuda")
+    tr = torch.zeros((N, st["sampled_gates"], 4), dtype=torch.float64, device="cuda")
+    stats = pw.pw_sample(plan, 23, 0, N, bits, tr)
+    torch.cuda.synchronize()
+    order = pw.pw_plan_exec_order(plan)
+    assert sorted(order) == list(range(len(ops)))
+    with pytest.raises(pw.PwError):
+        pw.pw_amplitudes(plan, len(ops), bits, torch.zeros((N, 2), dtype=torch.float64, device="cuda"))
+    pw.pw_plan_destroy(plan)
+    pw.pw_circuit_destroy(circ)
+    got = pw.unpack_bits(bits.cpu().numpy(), n)
+    trace = tr.cpu().numpy()
+    traces = [[] for _ in range(N)]
+    want, ost = OS.sample_sv(n, ops, 23, list(range(N)), order=order, traces=traces)
+    mism = int((~(want == got).all(axis=1)).sum())
+    assert mism <= max(stats["near_boundary"], ost.near_boundary)
+    worst = max(pair_err(traces[k][n + r][1], trace[k, r])
+                for k in range(N) if (want[k] == got[k]).all() for r in range(st["sampled_gates"]))
+    assert worst < 1e-5

@@ -289,3 +289,41 @@ def test_general_gradient_validates_its_arguments(pw):
     bad[kraus_at] = 0
     assert call(bad) == -1 and "must be a gate" in pw.pw_last_error()
     pw.pw_circuit_destroy(circ)
+
+
+def test_swap_class_gates_plan_or_fail_cleanly(pw):
+    """SWAP-class two-qubit gates between sections plan (the exported order is
+    a permutation of every operation); in a noisy circuit, or placed where a
+    wire would get two gates of one layer, they are refused."""
+    from oracle import circuit as OC
+    S = np.eye(4)[[0, 2, 1, 3]].astype(complex)
+    spec = W.random_qaoa(6, 2, seed=83)
+    ops = OC.qaoa_circuit(spec)
+    n = spec.n
+    pos = n + len(spec.edges)          # after layer 1's cost gates, before its mixers
+
+    def plan_of(oplist):
+        c = pw.pw_circuit_create(n)
+        for o in oplist:
+            if o.kind == "gate":
+                pw.pw_circuit_add_gate(c, list(o.qubits), o.mat)
+            else:
+                pw.pw_circuit_add_kraus(c, list(o.qubits), o.mats)
+        try:
+            p = pw.pw_plan_build(c)
+            order = pw.pw_plan_exec_order(p)
+            pw.pw_plan_destroy(p)
+            return order
+        finally:
+            pw.pw_circuit_destroy(c)
+
+    good = ops[:pos] + [OC.gate((0, 3), S)] + ops[pos:]
+    assert sorted(plan_of(good)) == list(range(len(good)))
+    # inside layer 1's mixers, after qubit 0's mixer and before qubit 3's
+    bad = ops[:pos + 1] + [OC.gate((0, 3), S)] + ops[pos + 1:]
+    with pytest.raises(pw.PwError):
+        plan_of(bad)
+    noisy = W.random_qaoa(6, 2, seed=83, depol2=0.1)
+    nops = OC.qaoa_circuit(noisy)
+    with pytest.raises(pw.PwError, match="SWAP-class"):
+        plan_of(nops[:n] + [OC.gate((0, 3), S)] + nops[n:])
