@@ -145,7 +145,12 @@ void pw_circuit_destroy(pw_circuit* c);
  * channels; channels may also follow the last layer. A diagonal gate or
  * channel placed inside a layer is accepted when it commutes out of it: all
  * its qubits already had their gate of that layer (it moves after the layer)
- * or none did (it moves before). Anything else returns PW_ERR_UNSUPPORTED.
+ * or none did (it moves before). A two-qubit gate of the form SWAP x diagonal
+ * (exact zero pattern: SWAP, iSWAP, fSim(pi/2, phi)) is accepted in noiseless
+ * circuits: it exchanges two qubits' contents (a deterministic move, Alg. 1),
+ * planned by relabelling the qubit wires, with the output bits permuted back;
+ * pw_amplitudes and pw_sample_static refuse such plans (PW_ERR_UNSUPPORTED).
+ * Anything else returns PW_ERR_UNSUPPORTED.
  * The plan fixes the order of the commuting one-qubit gates inside each layer
  * and of the moved operations (see pw_plan_exec_order). */
 int pw_plan_build(const pw_circuit* c, const pw_plan_opts* opts, pw_plan** out);
