@@ -330,10 +330,12 @@ def run_grad(args, rank, world):
     K = GRAD_K
     bits, grads, amps = [], [], []
     launches_per_step = 0
+    flops_per_step = 0.0
     for i, spec in enumerate(specs):
         # the instance's own sampler draws its K bitstrings (inputs of the step)
         c = pw.pw_circuit_qaoa(spec.n, spec.edges, spec.weights, None, spec.p, spec.gammas, spec.betas)
         pl = pw.pw_plan_build(c, precision=prec)
+        amp_flops = pw.pw_plan_stats(pl)["flops_per_amplitude"]
         b = torch.empty((K, (spec.n + 63) // 64), dtype=torch.int64, device=dev)
         pw.pw_sample(pl, args.seed + rank, i * K, K, b, None, stream, want_stats=False)
         pw.pw_plan_destroy(pl)
@@ -344,6 +346,8 @@ def run_grad(args, rank, world):
         terms = spec.p * (len(spec.edges) + spec.n)
         # the amplitudes, one contraction + one accumulation per term, the final sum of the lanes
         launches_per_step += 2 + 2 * terms
+        # algorithmic flops: every shifted circuit has the plan structure of the original
+        flops_per_step += (1 + terms) * K * amp_flops
 
     def step(bs, gs, as_):
         for spec, b, g, a in zip(specs, bs, gs, as_):
@@ -383,7 +387,9 @@ def run_grad(args, rank, world):
     h2d = sum(hb.numel() * 8 for hb in h_bits)
     d2h = sum(hg.numel() * 8 for hg in h_grads)
     ns = [s.n for s in specs]
+    achieved = flops_per_step * args.steps / (ms / 1e3) / 1e12
     return dict(value=value, ms=ms, launches=launches_per_step * args.steps, clocks=clk.summary(dev.index),
+                achieved=achieved, flops_per_step=flops_per_step,
                 e2e=len(specs) * K * world / e2e_s, h2d=h2d, d2h=d2h, n_instances=len(specs),
                 n_range=[min(ns), max(ns)], finite=bool(all(torch.isfinite(g).all().item() for g in grads)))
 
@@ -566,11 +572,15 @@ def main_grad(args, rank, world, desc):
                        "bitstrings_per_instance": GRAD_K, "precision": args.precision,
                        "l2": "inputs are a few KB per instance; each contraction re-reads its plan tables",
                        "parallelism": f"replicas x{world}", "all_finite": r["finite"]},
-            "roofline": {"bound": "alu", "achieved": None, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": None,
+            "roofline": {"bound": "alu", "achieved": r["achieved"],
+                         "peak": FP32_PEAK_TFLOPS if args.precision == "fp32" else FP64_PEAK_TFLOPS,
+                         "unit": "TFLOP/s",
+                         "frac": r["achieved"] / (FP32_PEAK_TFLOPS if args.precision == "fp32" else FP64_PEAK_TFLOPS),
                          "traffic": None, "kernel": "pw_chain_kernel (amplitude mode)",
-                         "note": "no flop count of the amplitude mode is exported; the step is the amplitude "
-                                 "contractions (64 chains, one per derivative term, up to 16 lanes in flight), "
-                                 "planned and uploaded by one host thread per lane"},
+                         "flops_per_step": r["flops_per_step"],
+                         "note": "step-level: the algorithmic flops of every contraction of the step over the step's "
+                                 "time (the contractions of up to 16 lanes overlap, so no per-launch time is taken); "
+                                 "host planning and uploads run in parallel with them"},
             "cpu_baseline": cpu,
             "e2e": {"value": r["e2e"], "unit": "gradients/s", "h2d_bytes_per_step": r["h2d"],
                     "d2h_bytes_per_step": r["d2h"]},

@@ -95,6 +95,7 @@ typedef struct {
     double amps_per_sample;    /* amplitudes evaluated per sample */
     double device_bytes;       /* bytes of plan tables copied to the device on first use */
     int ctas_per_chain;        /* > 1: one chain per thread-block cluster of that many CTAs */
+    double flops_per_amplitude;   /* real flops of pw_amplitudes of the whole circuit, per string */
 } pw_plan_stats_t;
 
 /* Counters of one pw_sample call. */

@@ -168,6 +168,7 @@ int pw_plan_stats(const pw_plan* plan, pw_plan_stats_t* s) {
     s->noisy = hp.noisy ? 1 : 0;
     s->flops_per_sample = hp.flops_per_sample;
     s->amps_per_sample = hp.amps_per_sample;
+    s->flops_per_amplitude = hp.flops_per_amplitude;
     s->device_bytes = (double)plan_device_bytes(hp);
     // shared memory of the kernel's layout
     const SmemLayout L = make_layout(hp, hp.precision == PW_PREC_FP64 ? 16 : 8);

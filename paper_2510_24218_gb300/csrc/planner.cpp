@@ -1119,6 +1119,24 @@ int build_plan(const pw_circuit* c, const pw_plan_opts& opts, HostPlan& hp) {
         }
     }
     hp.flops_per_sample = flops;
+    // the amplitude of the whole circuit contracts only the last layer's
+    // forward sweep, up to the block of the last gate
+    {
+        int kend = K - 1;
+        for (auto it = hp.exec_order.rbegin(); it != hp.exec_order.rend(); ++it)
+            if (hp.exec_layer[*it] == P) {
+                kend = hp.exec_block[*it];
+                break;
+            }
+        const double NF = std::ldexp(1.0, S * P);
+        double a = 0.0;
+        for (int k = 0; k <= kend && k < K; ++k) {
+            const DevBlockRange& br = hp.block_ranges[(size_t)P * K + k];
+            for (int i = br.fwd_st; i < br.fwd_st + br.fwd_nst; ++i) a += stage_flops(hp.stages[i]) * NF;
+            a += 8.0 * NF;
+        }
+        hp.flops_per_amplitude = a;
+    }
     hp.amps_per_sample = 2.0 * trace_row;
     hp.hdr.n = n;
     hp.hdr.P = P;

@@ -247,6 +247,7 @@ struct HostPlan {
     int W = 0, W_low = 0;                 // at the deepest layer
     double flops_per_sample = 0.0;
     double amps_per_sample = 0.0;
+    double flops_per_amplitude = 0.0;   // pw_amplitudes of the whole circuit
     int precision = PW_PREC_FP32;
     int threads_per_chain = 0;
     int chains_per_cta = 1;

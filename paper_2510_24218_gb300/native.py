@@ -42,7 +42,7 @@ class PlanStats(C.Structure):
                 ("sampled_gates", C.c_int), ("threads_per_chain", C.c_int), ("chains_per_cta", C.c_int),
                 ("smem_bytes_per_cta", C.c_int), ("noisy", C.c_int), ("flops_per_sample", C.c_double),
                 ("amps_per_sample", C.c_double),
-                ("device_bytes", C.c_double), ("ctas_per_chain", C.c_int)]
+                ("device_bytes", C.c_double), ("ctas_per_chain", C.c_int), ("flops_per_amplitude", C.c_double)]
 
 
 class RunStats(C.Structure):
