@@ -150,7 +150,9 @@ void pw_circuit_destroy(pw_circuit* c);
  * (exact zero pattern: SWAP, iSWAP, fSim(pi/2, phi)) is accepted in noiseless
  * circuits: it exchanges two qubits' contents (a deterministic move, Alg. 1),
  * planned by relabelling the qubit wires, with the output bits permuted back;
- * pw_amplitudes and pw_sample_static refuse such plans (PW_ERR_UNSUPPORTED).
+ * for such plans pw_amplitudes takes only the whole circuit (it then also
+ * allocates a reordered copy of the strings and synchronises the stream) and
+ * pw_sample_static refuses them (PW_ERR_UNSUPPORTED).
  * Anything else returns PW_ERR_UNSUPPORTED.
  * The plan fixes the order of the commuting one-qubit gates inside each layer
  * and of the moved operations (see pw_plan_exec_order). */

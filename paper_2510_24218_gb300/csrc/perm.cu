@@ -5,6 +5,7 @@
 
 #include <algorithm>
 #include <string>
+#include <vector>
 
 #include "pw_internal.h"
 
@@ -36,6 +37,31 @@ int perm_fail(cudaError_t e, const char* what) {
     return pw::set_error(PW_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
 }
 
+// A device copy of a host map (waits for the copy itself: pageable source).
+int upload_map(const std::vector<int>& map, int** out) {
+    int* d = nullptr;
+    cudaError_t e;
+    if ((e = cudaMalloc(&d, sizeof(int) * map.size())) != cudaSuccess) return perm_fail(e, "cudaMalloc(wire map)");
+    if ((e = cudaMemcpy(d, map.data(), sizeof(int) * map.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(cudaStreamLegacy)) != cudaSuccess) {
+        cudaFree(d);
+        return perm_fail(e, "cudaMemcpy(wire map)");
+    }
+    *out = d;
+    return PW_OK;
+}
+
+int launch_permute(uint64_t* d_bits, const int* d_map, int n, uint64_t count, cudaStream_t st) {
+    int dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const uint64_t want = (count + 127) / 128;
+    const unsigned blocks = (unsigned)std::min<uint64_t>(want, (uint64_t)(nsm > 0 ? nsm : 1) * 16);
+    permute_rows<<<blocks, 128, 0, st>>>(d_bits, d_map, n, (n + 63) / 64, count);
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? PW_OK : perm_fail(e, "permute_rows launch");
+}
+
 }  // namespace
 
 namespace pw {
@@ -43,29 +69,27 @@ namespace pw {
 int permute_output(pw_plan* plan, uint64_t* d_bits, uint64_t n_samples, void* stream) {
     const int n = (int)plan->out_wire.size();
     if (n == 0 || n_samples == 0) return PW_OK;
-    const int words = (n + 63) / 64;
-    if (words > kMaxWords) return set_error(PW_ERR_TOO_LARGE, "more than 4096 qubits");
-    cudaError_t e;
-    if (!plan->d_out_wire) {
-        int* d = nullptr;
-        if ((e = cudaMalloc(&d, sizeof(int) * n)) != cudaSuccess) return perm_fail(e, "cudaMalloc(wire map)");
-        // (pageable source: wait for the copy itself, not only for its staging)
-        if ((e = cudaMemcpy(d, plan->out_wire.data(), sizeof(int) * n, cudaMemcpyHostToDevice)) != cudaSuccess ||
-            (e = cudaStreamSynchronize(cudaStreamLegacy)) != cudaSuccess) {
-            cudaFree(d);
-            return perm_fail(e, "cudaMemcpy(wire map)");
-        }
-        plan->d_out_wire = d;
+    if ((n + 63) / 64 > kMaxWords) return set_error(PW_ERR_TOO_LARGE, "more than 4096 qubits");
+    int rc;
+    if (!plan->d_out_wire && (rc = upload_map(plan->out_wire, &plan->d_out_wire))) return rc;
+    return launch_permute(d_bits, plan->d_out_wire, n, n_samples, static_cast<cudaStream_t>(stream));
+}
+
+int permute_input(pw_plan* plan, const uint64_t* d_src, uint64_t* d_dst, uint64_t n_strings, void* stream) {
+    const int n = (int)plan->out_wire.size();
+    if (n == 0 || n_strings == 0) return PW_OK;
+    if ((n + 63) / 64 > kMaxWords) return set_error(PW_ERR_TOO_LARGE, "more than 4096 qubits");
+    int rc;
+    if (!plan->d_in_wire) {
+        std::vector<int> inv(n);
+        for (int q = 0; q < n; ++q) inv[plan->out_wire[q]] = q;   // wire out_wire[q] holds qubit q
+        if ((rc = upload_map(inv, &plan->d_in_wire))) return rc;
     }
-    int dev = 0, nsm = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    const uint64_t want = (n_samples + 127) / 128;
-    const unsigned blocks = (unsigned)std::min<uint64_t>(want, (uint64_t)(nsm > 0 ? nsm : 1) * 16);
-    permute_rows<<<blocks, 128, 0, static_cast<cudaStream_t>(stream)>>>(d_bits, plan->d_out_wire, n, words,
-                                                                          n_samples);
-    if ((e = cudaGetLastError()) != cudaSuccess) return perm_fail(e, "permute_rows launch");
-    return PW_OK;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const cudaError_t e = cudaMemcpyAsync(d_dst, d_src, n_strings * ((n + 63) / 64) * sizeof(uint64_t),
+                                          cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) return perm_fail(e, "cudaMemcpyAsync(rows)");
+    return launch_permute(d_dst, plan->d_in_wire, n, n_strings, st);
 }
 
 }  // namespace pw

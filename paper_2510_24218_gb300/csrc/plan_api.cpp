@@ -187,7 +187,7 @@ int pw_plan_exec_order(const pw_plan* plan, int* order) {
 
 void pw_plan_destroy(pw_plan* plan) {
     if (!plan) return;
-    if (plan->d_blob || plan->d_counters || plan->d_stage || plan->d_out_wire) {
+    if (plan->d_blob || plan->d_counters || plan->d_stage || plan->d_out_wire || plan->d_in_wire) {
         int cur = -1;
         cudaGetDevice(&cur);
         if (plan->device >= 0 && plan->device != cur) cudaSetDevice(plan->device);
@@ -195,6 +195,7 @@ void pw_plan_destroy(pw_plan* plan) {
         if (plan->d_counters) cudaFree(plan->d_counters);
         if (plan->d_stage) cudaFree(plan->d_stage);
         if (plan->d_out_wire) cudaFree(plan->d_out_wire);
+        if (plan->d_in_wire) cudaFree(plan->d_in_wire);
         if (plan->device >= 0 && plan->device != cur && cur >= 0) cudaSetDevice(cur);
     }
     delete plan;

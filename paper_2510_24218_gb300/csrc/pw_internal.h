@@ -279,10 +279,13 @@ struct pw_plan {
     // bit q is the bit of wire out_wire[q] (empty: the identity)
     std::vector<int> out_wire;
     int* d_out_wire = nullptr;
+    int* d_in_wire = nullptr;   // the inverse map: wire w holds qubit d_in_wire[w]
 };
 
 namespace pw {
 // Reorder the packed output rows of a plan with relabelled wires in place
 // (stream: a cudaStream_t).
 int permute_output(pw_plan* plan, uint64_t* d_bits, uint64_t n_samples, void* stream);
+// Copy qubit-ordered packed rows to wire order (dst: n_strings rows).
+int permute_input(pw_plan* plan, const uint64_t* d_src, uint64_t* d_dst, uint64_t n_strings, void* stream);
 }  // namespace pw

@@ -1657,8 +1657,10 @@ int pw_amplitudes(pw_plan* plan, int prefix_ops, uint64_t n_strings, const uint6
     if (!plan || ((!d_bits || !d_amp) && n_strings)) return set_error(PW_ERR_ARG, "null argument");
     const HostPlan& hp = plan->hp;
     if (hp.noisy) return set_error(PW_ERR_UNSUPPORTED, "amplitudes are defined for noiseless circuits only");
-    if (!plan->out_wire.empty())
-        return set_error(PW_ERR_UNSUPPORTED, "amplitudes of circuits with SWAP-class gates are not supported");
+    const bool relabelled = !plan->out_wire.empty();
+    if (relabelled && prefix_ops != (int)hp.exec_order.size())
+        return set_error(PW_ERR_UNSUPPORTED,
+                         "with SWAP-class gates only the amplitudes of the whole circuit are supported");
     if (prefix_ops < 1 || prefix_ops > (int)hp.exec_order.size()) return set_error(PW_ERR_ARG, "prefix_ops out of range");
     const int op = hp.exec_order[prefix_ops - 1];
     if (hp.exec_layer[op] < 1)
@@ -1678,7 +1680,20 @@ int pw_amplitudes(pw_plan* plan, int prefix_ops, uint64_t n_strings, const uint6
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     cudaError_t e = cudaMemsetAsync(plan->d_counters, 0, 4 * sizeof(unsigned long long), st);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
-    return run(plan, kp, st, nullptr);
+    if (!relabelled) return run(plan, kp, st, nullptr);
+    // the kernel reads the bits per wire: reorder a copy of the strings
+    uint64_t* d_wire_bits = nullptr;
+    if ((e = cudaMalloc(&d_wire_bits, n_strings * hp.hdr.words * sizeof(uint64_t))) != cudaSuccess)
+        return cuda_fail(e, "cudaMalloc(wire-ordered strings)");
+    rc = permute_input(plan, d_bits, d_wire_bits, n_strings, st);
+    if (!rc) {
+        kp.in_bits = d_wire_bits;
+        rc = run(plan, kp, st, nullptr);
+    }
+    e = cudaStreamSynchronize(st);   // before the copy is freed
+    cudaFree(d_wire_bits);
+    if (!rc && e != cudaSuccess) rc = cuda_fail(e, "cudaStreamSynchronize");
+    return rc;
 }
 
 }  // extern "C"

@@ -302,3 +302,30 @@ def test_general_gradient_equals_qaoa_gradient(pw):
     _, g2 = _grad(pw, spec, xs, 1)
     a = g1.cpu().numpy()
     assert np.abs(a[..., 0] + 1j * a[..., 1] - g2).max() <= 1e-12 * np.abs(g2).max()
+
+
+def test_general_gradient_with_swap_class_gates(pw):
+    """pw_amp_grad on a parameterised circuit with SWAP-class gates between
+    its sections (planned as wire relabellings) against the product rule on
+    the state vector, FP64."""
+    import torch
+    from oracle import circuit as OC
+    from tests.test_oracle_gradient import parameterised_circuit
+    rng = np.random.default_rng(50)
+    n, p = 8, 2
+    spec = W.random_qaoa(n, 1, seed=51)
+    theta = rng.uniform(0, np.pi, size=p + p * n)
+    ops, param, dm = parameterised_circuit(n, spec.edges, spec.weights, theta, p)
+    pos = n + len(spec.edges)          # after layer 1's RZZ gates, before its RY gates
+    S = np.eye(4)[[0, 2, 1, 3]].astype(complex)
+    ops = ops[:pos] + [OC.gate((0, 5), S), OC.gate((2, 3), OC.iswap_mat())] + ops[pos:]
+    param = param[:pos] + [-1, -1] + param[pos:]
+    circ = _build_param_circuit(pw, n, ops)
+    xs = W.random_bitstrings(12, n, seed=52)
+    bits = torch.from_numpy(pw.pack_bits(xs).view(np.int64)).cuda()
+    grad = torch.zeros((12, len(theta), 2), dtype=torch.float64, device="cuda")
+    pw.pw_amp_grad(circ, len(theta), param, dm, bits, grad, precision=pw.PW_PREC_FP64)
+    pw.pw_circuit_destroy(circ)
+    g = grad.cpu().numpy()
+    want = G.amp_grad_product_rule(n, ops, param, dm, len(theta), xs)
+    assert np.abs(g[..., 0] + 1j * g[..., 1] - want).max() <= 1e-11 * np.abs(want).max()

@@ -682,8 +682,18 @@ def test_swap_class_gates_against_alg1(pw, n, rows, p, seed):
     torch.cuda.synchronize()
     order = pw.pw_plan_exec_order(plan)
     assert sorted(order) == list(range(len(ops)))
+    # whole-circuit amplitudes of random strings (FP32 plan) against the state
+    # vector; a shorter prefix is refused
+    xs = W.random_bitstrings(32, n, seed=seed + 200)
+    d_x = torch.from_numpy(pw.pack_bits(xs).view(np.int64)).cuda()
+    amp = torch.zeros((32, 2), dtype=torch.float64, device="cuda")
+    pw.pw_amplitudes(plan, len(ops), d_x, amp)
+    psi = SV.run(n, ops)
+    want_a = psi[[int(sum(int(b) << q for q, b in enumerate(x))) for x in xs]]
+    got_a = amp.cpu().numpy()
+    assert np.abs(got_a[:, 0] + 1j * got_a[:, 1] - want_a).max() <= 1e-5 * np.abs(psi).max()
     with pytest.raises(pw.PwError):
-        pw.pw_amplitudes(plan, len(ops), bits, torch.zeros((N, 2), dtype=torch.float64, device="cuda"))
+        pw.pw_amplitudes(plan, len(ops) - n, d_x, amp)
     pw.pw_plan_destroy(plan)
     pw.pw_circuit_destroy(circ)
     got = pw.unpack_bits(bits.cpu().numpy(), n)
