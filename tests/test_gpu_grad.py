@@ -329,3 +329,32 @@ def test_general_gradient_with_swap_class_gates(pw):
     g = grad.cpu().numpy()
     want = G.amp_grad_product_rule(n, ops, param, dm, len(theta), xs)
     assert np.abs(g[..., 0] + 1j * g[..., 1] - want).max() <= 1e-11 * np.abs(want).max()
+
+
+def test_autograd_general_circuit(pw):
+    """The autograd binding of pw_amp_grad: a real loss of the amplitudes of a
+    parameterised circuit back-propagates the product-rule derivatives, and
+    gradcheck's finite differences agree."""
+    import torch
+    from paper_2510_24218_gb300.autograd import circuit_amplitudes
+    from tests.test_oracle_gradient import parameterised_circuit
+    rng = np.random.default_rng(53)
+    n, p = 8, 2
+    spec = W.random_qaoa(n, 1, seed=54)
+
+    def build(th):
+        ops, param, dm = parameterised_circuit(n, spec.edges, spec.weights, th, p)
+        return [(list(o.qubits), o.mat) for o in ops], param, dm
+
+    theta = torch.tensor(rng.uniform(0, np.pi, size=p + p * n), dtype=torch.float64, requires_grad=True)
+    xs = W.random_bitstrings(5, n, seed=55)
+    bits = torch.from_numpy(pw.pack_bits(xs).view(np.int64)).cuda()
+    c = torch.from_numpy(rng.normal(size=(5, 2))).cuda()
+    (circuit_amplitudes(theta, build, n, bits) * c).sum().backward()
+    ops, param, dm = parameterised_circuit(n, spec.edges, spec.weights, theta.detach().numpy(), p)
+    want = G.amp_grad_product_rule(n, ops, param, dm, theta.numel(), xs)
+    cc = c.cpu().numpy()
+    want_d = (cc[:, :1] * want.real + cc[:, 1:] * want.imag).sum(axis=0)
+    assert np.abs(theta.grad.numpy() - want_d).max() <= 1e-11 * np.abs(want_d).max()
+    f = lambda t: circuit_amplitudes(t, build, n, bits)  # noqa: E731
+    assert torch.autograd.gradcheck(f, (theta.detach().requires_grad_(),), eps=1e-6, atol=1e-7, rtol=1e-5)
