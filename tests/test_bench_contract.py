@@ -1,0 +1,35 @@
+"""bench.py's reference arm runs on the host (the FP64 oracle): its JSON line
+keeps the contract's keys, for the sampling and the gradient workloads."""
+import json
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _run(*args):
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--cpu-budget", "2",
+                        *args], capture_output=True, text=True, timeout=600, cwd=ROOT)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1, r.stdout
+    return json.loads(lines[0])
+
+
+@pytest.mark.parametrize("workload,unit", [("n12", "samples/s"), ("grad3reg", "gradients/s")])
+def test_reference_arm_line(workload, unit):
+    if workload == "grad3reg":
+        import paper_2510_24218_gb300 as mod
+        from paper_2510_24218_gb300 import build as B
+        if not os.path.exists(mod.library_path()):
+            B.build()
+    d = _run("--workload", workload)
+    assert d["impl"] == "reference" and d["unit"] == unit and d["value"] > 0
+    for key in ("metric", "n_gpus", "steps", "warmup", "higher_is_better", "scaling", "vs_baseline", "dtype",
+                "data", "config", "cpu_baseline", "e2e"):
+        assert key in d, key
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]
