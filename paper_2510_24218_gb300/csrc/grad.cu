@@ -150,7 +150,10 @@ int run_terms(const pw_circuit* base, const std::vector<Term>& terms, int ncol, 
     // fixed order at the end, so the result does not depend on scheduling.
     const int n_terms = (int)terms.size();
     const int hw = (int)std::max(1u, std::thread::hardware_concurrency());
-    const int n_lanes = std::max(1, std::min({kMaxLanes, hw, n_terms}));
+    // each lane holds n_strings * (ncol + 1) complex values: at most 1 GiB for all lanes
+    const uint64_t lane_bytes = n_strings * (uint64_t)(ncol + 1) * sizeof(double2);
+    const int by_memory = (int)std::max<uint64_t>(1, std::min<uint64_t>(kMaxLanes, (uint64_t(1) << 30) / lane_bytes));
+    const int n_lanes = std::max(1, std::min({kMaxLanes, hw, n_terms, by_memory}));
 
     cudaEvent_t ready = nullptr;
     if ((e = cudaEventCreateWithFlags(&ready, cudaEventDisableTiming)) != cudaSuccess)
