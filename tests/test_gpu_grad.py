@@ -358,3 +358,45 @@ def test_autograd_general_circuit(pw):
     assert np.abs(theta.grad.numpy() - want_d).max() <= 1e-11 * np.abs(want_d).max()
     f = lambda t: circuit_amplitudes(t, build, n, bits)  # noqa: E731
     assert torch.autograd.gradcheck(f, (theta.detach().requires_grad_(),), eps=1e-6, atol=1e-7, rtol=1e-5)
+
+
+def test_gradient_wide_instances_against_elimination_differences(pw):
+    """Four of the seeded p = 3 instances with n > 26 (beyond a state vector),
+    FP32 plans as in the gradient workload: every derivative of two strings
+    drawn by each instance's sampler against central differences (h = 1e-4) of
+    the FP64 elimination oracle's amplitude, to 2e-4 of the largest."""
+    import copy
+    import torch
+    from oracle import circuit as OC
+    from oracle import tn as TN
+    picked = []
+    for s in W.gradient_instances():
+        if s.n <= 26:
+            continue
+        c = pw.pw_circuit_qaoa(s.n, s.edges, s.weights, None, s.p, s.gammas, s.betas)
+        try:
+            pl = pw.pw_plan_build(c)
+        except pw.PwError:
+            pw.pw_circuit_destroy(c)
+            continue
+        bits = torch.empty((2, 1), dtype=torch.int64, device="cuda")
+        pw.pw_sample(pl, 13, 0, 2, bits, None)
+        pw.pw_plan_destroy(pl)
+        pw.pw_circuit_destroy(c)
+        picked.append((s, pw.unpack_bits(bits.cpu().numpy(), s.n)))
+        if len(picked) == 4:
+            break
+    assert len(picked) == 4
+    h = 1e-4
+    for spec, xs in picked:
+        _, grad = _grad(pw, spec, xs, 0)
+        fd = np.zeros_like(grad)
+        for j in range(2 * spec.p):
+            sp, sm = copy.deepcopy(spec), copy.deepcopy(spec)
+            arr = "gammas" if j < spec.p else "betas"
+            getattr(sp, arr)[j % spec.p] += h
+            getattr(sm, arr)[j % spec.p] -= h
+            ops_p, ops_m = OC.qaoa_circuit(sp), OC.qaoa_circuit(sm)
+            for k, x in enumerate(xs):
+                fd[k, j] = (TN.amplitudes(spec.n, ops_p, x) - TN.amplitudes(spec.n, ops_m, x)) / (2 * h)
+        assert np.abs(grad - fd).max() <= 2e-4 * np.abs(fd).max(), spec.name
