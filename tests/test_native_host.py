@@ -327,3 +327,9 @@ def test_swap_class_gates_plan_or_fail_cleanly(pw):
     nops = OC.qaoa_circuit(noisy)
     with pytest.raises(pw.PwError, match="SWAP-class"):
         plan_of(nops[:n] + [OC.gate((0, 3), S)] + nops[n:])
+
+
+def test_binding_has_every_declared_call(pw):
+    """The Python binding offers every call of the C ABI under its own name."""
+    missing = [name for name in _declared_functions() if not hasattr(pw, name)]
+    assert not missing, missing
