@@ -705,3 +705,28 @@ def test_swap_class_gates_against_alg1(pw, n, rows, p, seed):
     worst = max(pair_err(traces[k][n + r][1], trace[k, r])
                 for k in range(N) if (want[k] == got[k]).all() for r in range(st["sampled_gates"]))
     assert worst < 1e-5
+
+
+def test_sampling_step_replays_as_a_cuda_graph(pw):
+    """A step of pw_sample (several launches of a 4096-chain plan and the
+    counter reset) captured once into a CUDA graph and replayed gives the
+    samples of a direct call (after the plan's first, uploading call)."""
+    import torch
+    spec = W.grid_6x6_p2()
+    circ = _circ(pw, spec)
+    plan = pw.pw_plan_build(circ, chains_per_launch=4096)
+    N = 10000
+    s = torch.cuda.Stream()
+    direct = torch.empty((N, 1), dtype=torch.int64, device="cuda")
+    replay = torch.zeros((N, 1), dtype=torch.int64, device="cuda")
+    with torch.cuda.stream(s):
+        pw.pw_sample(plan, 31, 0, N, direct, None, s, want_stats=False)
+    s.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s, capture_error_mode="relaxed"):
+        pw.pw_sample(plan, 31, 0, N, replay, None, s, want_stats=False)
+    g.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(direct, replay)
+    pw.pw_plan_destroy(plan)
+    pw.pw_circuit_destroy(circ)
