@@ -175,7 +175,9 @@ void pw_plan_destroy(pw_plan* plan);
  *   sampled gate, where C_t is the executed prefix including that gate.
  * stream: a cudaStream_t (NULL = legacy default stream). The call is
  * asynchronous with respect to the host unless stats != NULL, in which case it
- * synchronises the stream to read the counters. */
+ * synchronises the stream to read the counters. The first call of a plan on a
+ * device uploads its tables (synchronously); later calls with stats == NULL
+ * only enqueue work on the stream and can be captured into a CUDA graph. */
 int pw_sample(pw_plan* plan, uint64_t seed, uint64_t first_sample, uint64_t n_samples,
               uint64_t* d_out_bits, double* d_trace, void* stream, pw_run_stats_t* stats);
 
