@@ -182,3 +182,50 @@ def test_lsm_noise_leaves_network_shape_unchanged():
                 D = MX if (C.is_diagonal(MX) and not C.is_diagonal(M)) else M
                 added.append(C.is_diagonal(D))
     assert all(added)
+
+
+def _with_swaps(rng, n):
+    spec = W.random_qaoa(n, 2, seed=int(rng.integers(1000)), with_h=True)
+    ops = C.qaoa_circuit(spec)
+    S_ = np.eye(4)[[0, 2, 1, 3]].astype(complex)
+    pos = n + len(spec.edges) + n       # end of layer 1's diagonal section
+    return ops[:n] + [C.gate((0, n - 1), C.iswap_mat())] + ops[n:pos] + \
+        [C.gate((1, 2), S_ @ np.diag(np.exp(1j * rng.uniform(0, 6.3, 4))))] + ops[pos:]
+
+
+def test_markov_condition_with_swap_class_gates():
+    # Eq. (1) at every gate also across SWAP-class (monomial two-qubit) gates
+    rng = np.random.default_rng(17)
+    ops = _with_swaps(rng, 4)
+    chain, exact = S.exact_chain_distributions(4, ops)
+    for a, b in zip(chain, exact):
+        assert np.max(np.abs(a - b)) < 1e-12
+
+
+def test_wire_relabelling_identity():
+    """The identity the planner uses for SWAP-class gates A = SWAP D: replacing
+    each by its phase D on the current wires of its qubits, moving the qubits'
+    contents between wires and acting with every later operation on the wires
+    its qubits' contents are on gives the original state with qubit q read
+    from wire wire_of[q]."""
+    rng = np.random.default_rng(18)
+    n = 5
+    ops = _with_swaps(rng, n)
+    wire_of = list(range(n))
+    relabelled = []
+    for op in ops:
+        A = op.mat
+        qs = tuple(wire_of[q] for q in op.qubits)
+        if len(op.qubits) == 2 and C.is_monomial(A) and not C.is_diagonal(A) and \
+                all(A[((x & 1) << 1) | (x >> 1), x] != 0 for x in range(4)):
+            D = np.diag([A[((x & 1) << 1) | (x >> 1), x] for x in range(4)])
+            relabelled.append(C.gate(qs, D))
+            a, b = op.qubits
+            wire_of[a], wire_of[b] = wire_of[b], wire_of[a]
+        else:
+            relabelled.append(C.gate(qs, A))
+    psi = SV.run(n, ops)
+    phi = SV.run(n, relabelled)
+    for x in range(1 << n):
+        w = sum(((x >> q) & 1) << wire_of[q] for q in range(n))
+        assert abs(psi[x] - phi[w]) < 1e-13
