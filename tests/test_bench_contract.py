@@ -33,3 +33,15 @@ def test_reference_arm_line(workload, unit):
         assert key in d, key
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]
+
+
+def test_profiled_traffic_follows_the_kernel_sources(monkeypatch):
+    """roofline.traffic comes from a profile summary only while the kernel
+    sources hash to the captured value and the launch has the captured size."""
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.profiled_traffic("grid6x6", 4096) is not None
+    assert bench.profiled_traffic("grid6x6", 4095) is None
+    assert bench.profiled_traffic("n12", 256) is None            # no FP32 summary mapped
+    monkeypatch.setattr(bench, "kernel_sources_sha256", lambda: "0" * 64)
+    assert bench.profiled_traffic("grid6x6", 4096) is None
