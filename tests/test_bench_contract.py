@@ -40,7 +40,10 @@ def test_profiled_traffic_follows_the_kernel_sources(monkeypatch):
     sources hash to the captured value and the launch has the captured size."""
     sys.path.insert(0, ROOT)
     import bench
-    assert bench.profiled_traffic("grid6x6", 4096) is not None
+    text = open(os.path.join(ROOT, "profiles", bench.PROFILE_OF["grid6x6"])).read()
+    captured = text.split("kernel-sources-sha256:")[1].split()[0]
+    monkeypatch.setattr(bench, "kernel_sources_sha256", lambda: captured)
+    assert bench.profiled_traffic("grid6x6", 4096) > 0
     assert bench.profiled_traffic("grid6x6", 4095) is None
     assert bench.profiled_traffic("n12", 256) is None            # no FP32 summary mapped
     monkeypatch.setattr(bench, "kernel_sources_sha256", lambda: "0" * 64)
