@@ -1,15 +1,19 @@
 """Benchmark: exact samples/s of the pilot-wave sampler on one GB300.
 
-Workload (default): ideal QAOA p=2 MaxCut on the 6x6 grid (36 qubits), angles
-U[0, pi) from seed 2; one step = 10^5 exact samples drawn in launches of 4096
-chains (the sampler's whole hot path: every layer's contraction, readout and
-resampling). Prints one JSON line: samples/s over the timed steps (device
-time, inputs resident), the roofline of the sampler kernel (algorithmic FP32
-flops per launch over its event time against the derived FP32 peak, DRAM
-bytes per launch from the ncu summary under profiles/), the FP64 oracle timed
-on the host cores, the end-to-end rate through the host-buffer API, the
-kernel launches of the timed region and the SM clocks sampled meanwhile.
-`--impl reference` times the oracle alone.
+Workload (default): noisy QAOA p=2 on the 8x8 grid (64 qubits), two-qubit
+depolarizing 1e-3 after every RZZ and amplitude damping 1e-3 on every qubit
+after every mixer layer, angles U[0, pi) from seed 3; one step = 10^5 exact
+samples drawn in launches of 8192 chains (the sampler's whole hot path: every
+layer's Kraus draws, contraction, readout and resampling). Prints one JSON
+line: samples/s over the timed steps (device time, inputs resident), the
+roofline of the sampler kernel (algorithmic FP32 flops per launch over its
+event time against the FP32 FMA rate measured on the device by
+pw_device_fma_rate, DRAM bytes per launch from the ncu summary under
+profiles/), the FP64 oracle timed on the host cores, the end-to-end rate
+through the host-buffer API, the kernel launches of the timed region and the
+SM clocks sampled meanwhile. `--impl reference` times the oracle alone: each
+of its steps is a bounded sample of the same workload (one chain per host
+core), run for real, warm-up steps included.
 
 `--workload grad3reg` measures the QAOA amplitude derivatives instead: the
 seeded p=3 random 3-regular instances (n in [20, 48]) whose frontier fits on
@@ -18,7 +22,7 @@ exact d amp / d(gamma, beta) of every instance (pw_qaoa_amp_grad); the value
 is amplitude gradients (2p-vectors) per second.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload grid6x6|n12|heavyhex400|grid8x8noisy|grad3reg] [--precision fp32|fp64]
+                  [--workload grid8x8noisy|grid6x6|n12|heavyhex400|grad3reg] [--precision fp32|fp64]
                   [--samples S] [--no-cpu-baseline] [--no-autotune] [--grad-instances N]
 """
 from __future__ import annotations
@@ -40,10 +44,6 @@ if ROOT not in sys.path:
 
 METRIC = "exact samples/s on 1 GB300 (mixed vs plain FP32, same accuracy); TC % of peak"
 
-# FP32 FMA peak of the part: 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
-# FP64 (non-tensor) rate of the part: the nominal 1.25 TFLOP/s
-FP64_PEAK_TFLOPS = 1.25
 # arithmetic of each workload's configuration (the 12-qubit one is complex128)
 DEFAULT_PRECISION = {"grid6x6": "fp32", "n12": "fp64", "heavyhex400": "fp32", "grid8x8noisy": "fp32",
                      "grad3reg": "fp32"}
@@ -104,6 +104,50 @@ def oracle_rate(name, budget_s=20.0, seed=1):
     done = sum(r[0] for r in res)
     busy = max(r[1] for r in res)
     return done / busy, cores, done, wall
+
+
+def _oracle_chain(args):
+    name, seed, sid = args
+    from oracle import circuit as OC
+    from oracle import sampler as OS
+    spec = workload(name)[0]
+    ops = OC.qaoa_circuit(spec)
+    if spec.depol2 > 0 or spec.ad_gamma > 0:
+        OS.noisy_sample(spec.n, ops, seed, sid, backend="tn" if spec.n > 16 else "sv")
+    elif spec.n <= 16:
+        OS.sample_sv(spec.n, ops, seed, [sid])
+    else:
+        OS.sample_tn(spec.n, ops, seed, sid)
+    return 1
+
+
+def oracle_steps(name, warmup, steps, seed):
+    """The oracle as the reference arm: warmup + steps steps, each a bounded
+    sample of the workload (one chain per host core, in a spawned pool); the
+    rate is the chains of the timed steps over their wall time."""
+    cores = max(1, min(os.cpu_count() or 1, 16))
+    ctx = mp.get_context("spawn")
+    timed, wall = 0, 0.0
+    with ctx.Pool(cores) as pool:
+        for k in range(warmup + steps):
+            ids = [(name, seed, k * cores + i) for i in range(cores)]
+            t0 = time.perf_counter()
+            done = sum(pool.map(_oracle_chain, ids))
+            dt = time.perf_counter() - t0
+            if k >= warmup:
+                timed += done
+                wall += dt
+    return timed / wall, cores, timed, wall / max(1, steps) * 1e3
+
+
+def workload_config(args, world):
+    """The `config` of the bench line: the workload alone, identical in both arms."""
+    spec, n_samples, B, desc = workload(args.workload)
+    if args.samples:
+        n_samples = args.samples
+    return {"workload": desc, "samples_per_step": n_samples, "chains_per_launch": B, "precision": args.precision,
+            "l2": "flushed (256 MB write) before every timed step",
+            "parallelism": f"replicas x{world} (disjoint sample ranges)"}
 
 
 # ------------------------------------------------------------------- clocks
@@ -209,6 +253,9 @@ def run_ours(args, rank, world):
         return pw.pw_sample(plan, args.seed, first + i * n_samples, n_samples, out, None, stream, want_stats=stats)
 
     launches_per_step = (n_samples + B - 1) // B
+    # the roofline's denominator: the FMA rate of this device's CUDA cores,
+    # measured by the library's probe kernel (not a nominal figure)
+    peak = pw.pw_device_fma_rate(prec, stream)
     near = 0
     for i in range(args.warmup):
         near += step(i, stats=True)["near_boundary"]
@@ -262,7 +309,7 @@ def run_ours(args, rank, world):
     pw.pw_plan_destroy(plan)
     pw.pw_circuit_destroy(circ)
     return dict(value=value, ms=ms, launches=launches, near=near, pst=pst, desc=desc, n_samples=n_samples, B=B,
-                achieved=achieved, per_launch_ms=per_launch_ms, flops_per_launch=flops_per_launch, clocks=clocks,
+                achieved=achieved, peak=peak, per_launch_ms=per_launch_ms, flops_per_launch=flops_per_launch, clocks=clocks,
                 e2e=e2e_value, h2d=h2d, d2h=n_samples * words * 8, wall=t_wall)
 
 
@@ -354,6 +401,7 @@ def run_grad(args, rank, world):
             pw.pw_qaoa_amp_grad(spec.n, spec.edges, spec.weights, None, spec.p, spec.gammas, spec.betas, b, g,
                                 amp_out=a, precision=prec, stream=stream)
 
+    peak = pw.pw_device_fma_rate(prec, stream)
     for _ in range(args.warmup):
         step(bits, grads, amps)
     torch.cuda.synchronize(dev)
@@ -389,7 +437,7 @@ def run_grad(args, rank, world):
     ns = [s.n for s in specs]
     achieved = flops_per_step * args.steps / (ms / 1e3) / 1e12
     return dict(value=value, ms=ms, launches=launches_per_step * args.steps, clocks=clk.summary(dev.index),
-                achieved=achieved, flops_per_step=flops_per_step,
+                achieved=achieved, flops_per_step=flops_per_step, peak=peak,
                 e2e=len(specs) * K * world / e2e_s, h2d=h2d, d2h=d2h, n_instances=len(specs),
                 n_range=[min(ns), max(ns)], finite=bool(all(torch.isfinite(g).all().item() for g in grads)))
 
@@ -453,7 +501,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="grid6x6")
+    ap.add_argument("--workload", default="grid8x8noisy")
     ap.add_argument("--precision", default=None, choices=["fp32", "fp64"],
                     help="default: the workload's own (fp64 for n12, fp32 otherwise)")
     ap.add_argument("--seed", type=int, default=20251203)
@@ -478,13 +526,16 @@ def main():
         # the reference arm of this build is the FP64 CPU oracle, on host cores
         if rank != 0:
             return
-        rate, cores, done, wall = oracle_rate(args.workload, budget_s=max(5.0, args.cpu_budget / 2))
+        rate, cores, timed, ms_step = oracle_steps(args.workload, args.warmup, args.steps, args.seed)
         line = {"impl": "reference", "metric": METRIC, "value": rate, "unit": "samples/s", "n_gpus": args.gpus,
-                "steps": args.steps, "warmup": args.warmup, "ms_per_step": n_samples / rate * 1e3,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-                "data": "synthetic", "config": {"workload": desc, "samples_per_step": n_samples},
+                "data": "synthetic", "config": workload_config(args, 1),
+                "chains_timed": timed, "extrapolated": False,
                 "cpu_baseline": {"value": rate, "unit": "samples/s", "cores": cores, "kind": "oracle",
-                                 "sample": f"{done} chains of the same workload (naive Alg. 1/2, FP64)"},
+                                 "sample": f"each step is a bounded sample of the workload: {cores} chains, one per "
+                                           f"host core (naive Alg. 1/2, FP64); {timed} chains over the "
+                                           f"{args.steps} timed steps"},
                 "e2e": {"value": rate, "unit": "samples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
         print(json.dumps(line))
         return
@@ -502,25 +553,23 @@ def main():
         torch.distributed.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     r = run_ours(args, rank, world)
     if rank == 0:
-        peak = FP32_PEAK_TFLOPS if args.precision == "fp32" else FP64_PEAK_TFLOPS
+        peak = r["peak"]
         line = {
             "metric": METRIC, "value": r["value"], "unit": "samples/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": r["ms"] / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f64",
             "data": "synthetic",
-            "config": {"workload": r["desc"], "samples_per_step": r["n_samples"], "chains_per_launch": r["B"],
-                       "precision": args.precision, "l2": "flushed (256 MB write) before every timed step",
-                       "parallelism": f"replicas x{world} (disjoint sample ranges)",
-                       "amplitudes_per_s": r["value"] * r["pst"]["amps_per_sample"],
-                       "plan": {k: r["pst"][k] for k in ("n_slots", "width_bits", "n_blocks", "threads_per_chain",
-                                                         "chains_per_cta", "flops_per_sample")},
-                       "near_boundary_draws_in_warmup": int(r["near"])},
+            "config": workload_config(args, world),
+            "details": {"amplitudes_per_s": r["value"] * r["pst"]["amps_per_sample"],
+                        "plan": {k: r["pst"][k] for k in ("n_slots", "width_bits", "n_blocks", "threads_per_chain",
+                                                          "chains_per_cta", "ctas_per_chain", "flops_per_sample")},
+                        "near_boundary_draws_in_warmup": int(r["near"])},
             "roofline": {"bound": "alu", "achieved": r["achieved"], "peak": peak, "unit": "TFLOP/s",
                          "frac": (r["achieved"] / peak) if peak else None,
                          "traffic": profiled_traffic(args.workload, r["B"]) if args.precision == "fp32" else None,
                          "kernel": "pw_chain_kernel<float>" if args.precision == "fp32" else "pw_chain_kernel<double>",
-                         "peak_note": ("FP32 FMA peak derived: 152 SMs x 128 lanes x 2 x 2.07 GHz" if args.precision == "fp32"
-                                       else "nominal FP64 (non-tensor) rate, 1.25 TFLOP/s")},
+                         "peak_note": f"of measured: {args.precision.upper()} FMA rate of this device's CUDA cores "
+                                      "(pw_device_fma_rate probe, best of five ~30 ms launches)"},
             "cpu_baseline": cpu,
             "e2e": {"value": r["e2e"], "unit": "samples/s", "h2d_bytes_per_step": r["h2d"],
                     "d2h_bytes_per_step": r["d2h"]},
@@ -572,10 +621,10 @@ def main_grad(args, rank, world, desc):
                        "bitstrings_per_instance": GRAD_K, "precision": args.precision,
                        "l2": "inputs are a few KB per instance; each contraction re-reads its plan tables",
                        "parallelism": f"replicas x{world}", "all_finite": r["finite"]},
-            "roofline": {"bound": "alu", "achieved": r["achieved"],
-                         "peak": FP32_PEAK_TFLOPS if args.precision == "fp32" else FP64_PEAK_TFLOPS,
-                         "unit": "TFLOP/s",
-                         "frac": r["achieved"] / (FP32_PEAK_TFLOPS if args.precision == "fp32" else FP64_PEAK_TFLOPS),
+            "roofline": {"bound": "alu", "achieved": r["achieved"], "peak": r["peak"], "unit": "TFLOP/s",
+                         "frac": r["achieved"] / r["peak"],
+                         "peak_note": f"of measured: {args.precision.upper()} FMA rate of this device's CUDA cores "
+                                      "(pw_device_fma_rate probe)",
                          "traffic": None, "kernel": "pw_chain_kernel (amplitude mode)",
                          "flops_per_step": r["flops_per_step"],
                          "note": "step-level: the algorithmic flops of every contraction of the step over the step's "

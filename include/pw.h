@@ -290,6 +290,15 @@ int pw_qaoa_cost_grad(int n, int n_edges, const int* edges, const double* w, con
 int pw_sample_static(const pw_plan* plan, uint64_t seed, uint64_t first_sample, uint64_t n_samples,
                      uint64_t* d_out_bits, void* stream, pw_run_stats_t* stats);
 
+/* Measured arithmetic rate of the current device's CUDA cores (not in the
+ * paper: the denominator of the roofline fractions of the SIMT contraction
+ * kernels). Runs a probe kernel of independent fused multiply-add chains in
+ * FP32 (precision = PW_PREC_FP32) or FP64 (PW_PREC_FP64) on every SM for
+ * about 30 ms, five times after a calibration, on stream (NULL = legacy), and
+ * writes the best rate in TFLOP/s (2 flops per FMA) to *tflops. Synchronises
+ * the stream; allocates nothing. */
+int pw_device_fma_rate(int precision, void* stream, double* tflops);
+
 /* Thread-local message describing the last failure of this thread. */
 const char* pw_last_error(void);
 

@@ -196,6 +196,14 @@ int run_terms(const pw_circuit* base, const std::vector<Term>& terms, int ncol, 
     std::vector<std::string> msgs(n_lanes);
     auto run_lane = [&](int l, int b, int e_) {
         Lane& ln = lanes[l];
+        // the runtime keeps the current device per host thread: a new lane
+        // thread starts on device 0, while the plans, streams and scratch
+        // of this call belong to the caller's device
+        if (const cudaError_t de = cudaSetDevice(dev); de != cudaSuccess) {
+            codes[l] = grad_cuda_fail(de, "cudaSetDevice");
+            msgs[l] = pw_last_error();
+            return;
+        }
         pw_circuit shifted;
         shifted.n = base->n;
         for (int i = b + l; i < e_ && !codes[l]; i += n_lanes) {

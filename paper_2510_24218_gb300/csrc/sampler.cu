@@ -1363,7 +1363,18 @@ static int carveout_percent(int dev, int resident, size_t smem) {
     return (int)std::min<size_t>(100, (need * 100 + (size_t)maxsm - 1) / (size_t)maxsm);
 }
 
+// cudaFuncSetAttribute changes process-wide attributes of a kernel (its
+// dynamic shared-memory limit, its carveout preference): every sequence of
+// setting them, querying the occupancy they give and launching holds this
+// lock, so that concurrent callers (the gradient lanes, other threads) cannot
+// lower a limit between another caller's setting and its launch.
+std::mutex& launch_mutex() {
+    static std::mutex mu;
+    return mu;
+}
+
 template <typename R> int launch(pw_plan* plan, KParams& kp, cudaStream_t st, uint64_t* launches) {
+    std::lock_guard<std::mutex> attr_lock(launch_mutex());
     const HostPlan& hp = plan->hp;
     const size_t csz = 2 * sizeof(R);
     kp.sm = make_layout(hp, csz);
@@ -1731,6 +1742,7 @@ int static_scratch(int dev, unsigned char** out) {
 }
 
 template <typename R> int launch_static(const HostPlan& hp, int dev, KParams& kp, cudaStream_t st, uint64_t* launches) {
+    std::lock_guard<std::mutex> attr_lock(launch_mutex());
     kp.sm = make_layout(hp, 2 * sizeof(R));
     kp.tpc = hp.threads_per_chain;
     if (kp.sm.group_bytes > 227 * 1024) return set_error(PW_ERR_TOO_LARGE, "per-chain shared memory exceeds 227 KB");

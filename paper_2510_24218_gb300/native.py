@@ -81,6 +81,7 @@ def load_library():
         "pw_qaoa_cost_grad": (C.c_int, [C.c_int, C.c_int, ip, dp, dp, C.c_int, dp, dp, C.POINTER(PlanOpts),
                                         C.c_uint64, vp, vp, vp]),
         "pw_sample_static": (C.c_int, [vp, C.c_uint64, C.c_uint64, C.c_uint64, vp, vp, C.POINTER(RunStats)]),
+        "pw_device_fma_rate": (C.c_int, [C.c_int, vp, dp]),
         "pw_last_error": (C.c_char_p, []),
     }
     for name, (res, args) in sig.items():
@@ -225,6 +226,13 @@ def pw_sample_static(plan, seed, first_sample, n_samples, out_bits, stream=None,
                                            C.c_void_p(out_bits.data_ptr()), _stream_ptr(stream),
                                            C.byref(st) if want_stats else None))
     return {"near_boundary": st.near_boundary, "zero_mass": st.zero_mass, "launches": st.launches}
+
+
+def pw_device_fma_rate(precision=PW_PREC_FP32, stream=None) -> float:
+    """Measured FP32 or FP64 FMA rate of the current device's CUDA cores, TFLOP/s."""
+    r = C.c_double(0.0)
+    _check(load_library().pw_device_fma_rate(int(precision), _stream_ptr(stream), C.byref(r)))
+    return r.value
 
 
 def pw_sample_host(plan, seed, first_sample, n_samples, out_bits: np.ndarray, trace: np.ndarray | None = None):

@@ -26,13 +26,22 @@ def test_reference_arm_line(workload, unit):
         from paper_2510_24218_gb300 import build as B
         if not os.path.exists(mod.library_path()):
             B.build()
-    d = _run("--workload", workload)
+    d = _run("--workload", workload, "--steps", "2", "--warmup", "1")
     assert d["impl"] == "reference" and d["unit"] == unit and d["value"] > 0
+    assert d["steps"] == 2 and d["warmup"] == 1
     for key in ("metric", "n_gpus", "steps", "warmup", "higher_is_better", "scaling", "vs_baseline", "dtype",
                 "data", "config", "cpu_baseline", "e2e"):
         assert key in d, key
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]
+    if workload == "n12":
+        # the steps were run (a bounded sample each), and the config is the GPU arm's
+        sys.path.insert(0, ROOT)
+        import argparse
+        import bench
+        assert d["chains_timed"] >= 2 and d["extrapolated"] is False
+        ns = argparse.Namespace(workload="n12", samples=0, precision="fp64")
+        assert d["config"] == bench.workload_config(ns, 1)
 
 
 def test_profiled_traffic_follows_the_kernel_sources(monkeypatch):
