@@ -290,6 +290,47 @@ int pw_qaoa_cost_grad(int n, int n_edges, const int* edges, const double* w, con
 int pw_sample_static(const pw_plan* plan, uint64_t seed, uint64_t first_sample, uint64_t n_samples,
                      uint64_t* d_out_bits, void* stream, pw_run_stats_t* stats);
 
+/* ----------------------------------------------------- dense sweep passes */
+
+/* Arithmetic of a dense pass (pw_dense_apply, and the wide engine of
+ * pw_plan_opts.engine). */
+#define PW_GEMM_FP32 0     /* FP32 CUDA cores (SIMT), the plain-FP32 arm */
+#define PW_GEMM_BF16 1     /* tensor cores: BF16 operands (one term), FP32 accumulation */
+#define PW_GEMM_SPLIT2 2   /* tensor cores: operands split into two BF16 terms, 3 products */
+#define PW_GEMM_SPLIT3 3   /* tensor cores: three BF16 terms (the 24-bit FP32 significand), 6 products */
+
+/* Index bits of a dense pass. Tensor entry i (complex) has index bits
+ * b_0 .. b_{W-1}; the pass acts on the k tile bits. */
+typedef struct {
+    int width_bits;      /* W: each tensor holds 2^W complex entries, tile_bits + 7 <= W <= 40 */
+    int tile_bits;       /* k: 5 or 6 */
+    int tile_pos[8];     /* operator index bit j is tensor index bit tile_pos[j] */
+    int row_pos[7];      /* seven more distinct bits: the 128 rows of one GEMM tile (put
+                            the lowest free bits here: consecutive rows, consecutive
+                            addresses) */
+    int swizzled;        /* 1: entry i is stored at position i ^ ((i >> 4) & 15) */
+    int n_diag;          /* diagonal factors applied after the operator, 0..4 */
+    int diag_bits[4];    /* bits read by factor d, 0..5 */
+    int diag_pos[4][5];  /* factor d's table index bit b is tensor index bit diag_pos[d][b] */
+    int reserved[8];
+} pw_dense_desc;
+
+/* One dense pass of the sweep contraction (Sec. 2; the per-gate contraction's
+ * big steps as GEMMs, not in the paper): for each of n_tensors tensors x
+ * (device, 2^W complex FP32 entries each, interleaved (re, im), updated in
+ * place) with its operator Op (device d_ops: 2^k x 2^k complex FP32 per
+ * tensor, row-major, Op[t'][t]) and its diagonal tables (device d_diag:
+ * n_diag x 32 complex FP32 per tensor; nullable when n_diag = 0):
+ *   x'[i] = prod_d D_d[bits of i at diag_pos[d]] * sum_t Op[t'(i)][t] x[i with tile bits = t],
+ * t'(i) being i's tile bits. gemm picks the arithmetic (PW_GEMM_*): the
+ * tensor-core kinds run tcgen05 MMAs with FP32 accumulation in tensor memory,
+ * the operator and the tensor entries split into BF16 terms. Allocates and
+ * frees an operator image and an error flag, synchronises the stream.
+ * PW_ERR_ARG for invalid bit sets, PW_ERR_TIMEOUT if a bounded wait of the
+ * tensor-core kernel ran out. */
+int pw_dense_apply(int gemm, const pw_dense_desc* desc, uint64_t n_tensors, float* d_tensors,
+                   const float* d_ops, const float* d_diag, void* stream);
+
 /* Measured arithmetic rate of the current device's CUDA cores (not in the
  * paper: the denominator of the roofline fractions of the SIMT contraction
  * kernels). Runs a probe kernel of independent fused multiply-add chains in

@@ -1,0 +1,644 @@
+// Dense passes of the sweep contraction on an HBM-resident frontier.
+//
+// A pass of the plan's sweep (Sec. 2: the amplitudes amp(C_t, y) are
+// contractions of the circuit's tensor network) applies a product of 2x2
+// matrices on a few index bits of a chain's frontier tensor and of diagonal
+// factors. Composed over k tile bits it is one dense 2^k x 2^k complex
+// operator Op (per chain) followed by diagonal factors that also read other
+// bits. With the tensor of 2^W entries in HBM, the pass is a GEMM:
+//   rows    = the 2^(W-k) settings of the other bits (M, in tiles of 128),
+//   columns = the 2^k settings of the tile bits (K in, N out),
+// y[row, t'] = D(row, t') * sum_t x[row, t] Op[t'][t], complex, in place.
+// Complex numbers enter the real GEMM as 2x2 real blocks: row entries
+// interleave (re, im) and the operator becomes Bre[2t'+c'][2t+c] =
+// [[Re, -Im], [Im, Re]] of Op[t'][t], so K = N = 2^(k+1) reals.
+//
+// Two arms run the same pass:
+//   * dense_tc_kernel: 5th-generation tensor cores (tcgen05.mma, kind::f16,
+//     BF16 operands, FP32 accumulators in tensor memory). FP32 operands are
+//     split into NP BF16 terms x = x_0 + x_1 (+ x_2) (8 significant bits
+//     each) and the products of total order below NP are accumulated: one
+//     product for NP = 1 (plain BF16), three for NP = 2, six for NP = 3
+//     (inputs represented to 24 bits, the FP32 significand). One warp issues
+//     the MMAs, four producer warps gather the A tiles (rows of 2^k entries at
+//     scattered index bits) and write the BF16 terms into shared memory in the
+//     128-byte-swizzled K-major layout, four epilogue warps read the
+//     accumulators back (tcgen05.ld) and scatter the rows to HBM. The B
+//     operand (one per chain) is brought into shared memory by TMA
+//     (cp.async.bulk) from a pre-split image built once per call.
+//   * dense_simt_kernel: the same GEMM on FP32 CUDA cores (the plain-FP32
+//     comparison arm).
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cstring>
+#include <mutex>
+#include <string>
+
+#include "dense.h"
+#include "pw_internal.h"
+
+namespace pw {
+namespace {
+
+constexpr long long kWaitCycles = 4000000000ll;   // bounded waits: about 2 s at 2 GHz
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.release.cta.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.acquire.cta.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Wait for the phase of the given parity to complete; false (and the CTA's
+// abort flag set) when it did not within kWaitCycles, or when another role
+// of the CTA gave up already.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity)) {
+        if (*abort_flag) return false;
+        if (clock64() - t0 > kWaitCycles) {
+            *abort_flag = 1;
+            return false;
+        }
+    }
+    return true;
+}
+
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+
+// Shared-memory matrix descriptor: 128-byte swizzle, K-major, 8-row groups
+// 1024 bytes apart (stride byte offset), fixed field 0b001 at bit 46.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
+    uint64_t d = (uint64_t)((addr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)(16u >> 4) << 16;      // leading byte offset (unused for swizzled K-major)
+    d |= (uint64_t)(1024u >> 4) << 32;    // stride byte offset
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)2 << 61;               // SWIZZLE_128B
+    return d;
+}
+
+// Instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B, both
+// K-major, M = 128, N = n.
+__device__ __forceinline__ uint32_t idesc_bf16(int n) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+}
+
+__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accum) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+        ::"r"(d_tmem), "l"(a), "l"(b), "r"(idesc), "r"(accum)
+        : "memory");
+}
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+// 32 lanes x 32 columns of 32-bit accumulators (lane = this warp's quarter of
+// the 128 rows, register j = column col + j).
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr)
+        : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+// Bulk copy global -> shared (TMA engine, no tensor map: a contiguous image),
+// completion counted in bytes on an mbarrier.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
+// The BF16 terms of x (round to nearest at every step): x = t0 + t1 (+ t2)
+// exactly for NP = 3 (the 24 significant bits of an FP32 value), to about
+// 2^-17 |x| for NP = 2.
+template <int NP> __device__ __forceinline__ void split_bf16(float x, __nv_bfloat16 (&t)[NP]) {
+    t[0] = __float2bfloat16_rn(x);
+    if constexpr (NP >= 2) {
+        const float r1 = x - __bfloat162float(t[0]);
+        t[1] = __float2bfloat16_rn(r1);
+        if constexpr (NP >= 3) t[2] = __float2bfloat16_rn(r1 - __bfloat162float(t[1]));
+    }
+}
+
+// Word j of every term plane: the BF16 terms of (re, im) side by side (re in
+// the low half: k index 2j before 2j + 1).
+template <int NP> __device__ __forceinline__ void pack_terms(float re, float im, uint32_t (&h)[NP][4], int j) {
+    __nv_bfloat16 tr[NP], ti[NP];
+    split_bf16<NP>(re, tr);
+    split_bf16<NP>(im, ti);
+#pragma unroll
+    for (int q = 0; q < NP; ++q)
+        h[q][j] = (uint32_t)__bfloat16_as_ushort(tr[q]) | ((uint32_t)__bfloat16_as_ushort(ti[q]) << 16);
+}
+
+// Byte offset of the 16-byte chunk c (8 BF16 values, k index 8c..8c+7 of the
+// 64 in one 128-byte row segment) of row r in a K-major, 128-byte-swizzled
+// operand of `rows` rows: K blocks of 64 values are rows x 128 bytes apart.
+__device__ __forceinline__ uint32_t sw128_chunk(int rows, int r, int kb, int c) {
+    return (uint32_t)(kb * rows * 128 + r * 128 + ((c ^ (r & 7)) << 4));
+}
+
+__device__ __forceinline__ int64_t phys_index(int64_t i, int swz) {
+    return swz ? (i ^ ((i >> 4) & 15)) : i;
+}
+
+__device__ __forceinline__ float2 cmulf(float2 a, float2 b) {
+    return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+
+// Diagonal factors of the pass at logical index i of tensor `tens`.
+__device__ __forceinline__ float2 diag_factor(const DenseArgs& a, uint64_t tens, int64_t i) {
+    float2 f = make_float2(1.f, 0.f);
+    for (int d = 0; d < a.ndiag; ++d) {
+        int e = 0;
+        for (int b = 0; b < a.diag_nb[d]; ++b) e |= (int)((i >> a.diag_pos[d][b]) & 1) << b;
+        f = cmulf(f, a.diag[(tens * a.ndiag + d) * 32 + e]);
+    }
+    return f;
+}
+
+__device__ __forceinline__ int64_t outer_offset(const DenseArgs& a, uint64_t o) {
+    int64_t off = 0;
+    for (int b = 0; b < a.nouter; ++b) off |= (int64_t)((o >> b) & 1) << a.outer_pos[b];
+    return off;
+}
+
+// ------------------------------------------------------------------ tcgen05
+template <int KT, int NP> struct TcCfg {
+    static constexpr int TE = 1 << KT;          // complex entries per row
+    static constexpr int KR = 2 * TE;           // real K = N
+    static constexpr int PLANE_A = 128 * KR * 2;
+    static constexpr int PLANE_B = KR * KR * 2;
+    static constexpr int NPROD = NP == 1 ? 1 : NP == 2 ? 3 : 6;
+    static constexpr int SA = (NP * PLANE_B + 2 * NP * PLANE_A) <= 200 * 1024 ? 2 : 1;   // A stages
+    static constexpr int TMEM_COLS = 2 * KR;    // two accumulators
+    static constexpr size_t SMEM = (size_t)NP * PLANE_B + (size_t)SA * NP * PLANE_A + 2048;
+};
+
+template <int KT, int NP>
+__global__ void __launch_bounds__(288, 1) dense_tc_kernel(const DenseArgs a, const unsigned char* __restrict__ bimg) {
+    using Cfg = TcCfg<KT, NP>;
+    constexpr int TE = Cfg::TE, KR = Cfg::KR, SA = Cfg::SA;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char* smem = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    unsigned char* sB = smem;                                   // NP planes of B
+    unsigned char* sA = smem + NP * Cfg::PLANE_B;               // SA stages x NP planes of A
+    uint64_t* bars = reinterpret_cast<uint64_t*>(sA + SA * NP * Cfg::PLANE_A);
+    uint64_t* a_full = bars;            // [SA] producers -> MMA (128 arrivals)
+    uint64_t* a_empty = bars + SA;      // [SA] MMA commit -> producers
+    uint64_t* acc_full = bars + 2 * SA; // [2] MMA commit -> epilogue
+    uint64_t* acc_empty = bars + 2 * SA + 2;   // [2] epilogue (128 arrivals) -> MMA
+    uint64_t* b_full = bars + 2 * SA + 4;      // B image landed (TMA bytes)
+    int* misc = reinterpret_cast<int*>(bars + 2 * SA + 5);
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(misc);     // written by tcgen05.alloc
+    volatile int* abort_flag = misc + 1;                         // a bounded wait ran out
+    int* rowoff = misc + 4;                                      // [128] index bits of tile row r
+    int* coloff = rowoff + 128;                                  // [TE] index bits of operator column t
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const uint64_t tiles_per = (uint64_t)1 << (a.W - KT - 7);
+    const uint64_t total = a.ntens * tiles_per;
+    const uint64_t per = (total + gridDim.x - 1) / gridDim.x;
+    const uint64_t t_begin = (uint64_t)blockIdx.x * per;
+    const uint64_t t_end = t_begin + per < total ? t_begin + per : total;
+    const int64_t N = (int64_t)1 << a.W;
+
+    if (tid < 128) {
+        int o = 0;
+        for (int b = 0; b < 7; ++b) o |= ((tid >> b) & 1) << a.row_pos[b];
+        rowoff[tid] = o;
+    }
+    if (tid < TE) {
+        int o = 0;
+        for (int b = 0; b < KT; ++b) o |= ((tid >> b) & 1) << a.tile_pos[b];
+        coloff[tid] = o;
+    }
+    if (tid == 0) {
+        for (int s = 0; s < SA; ++s) {
+            mbar_init(&a_full[s], 128);
+            mbar_init(&a_empty[s], 1);
+        }
+        for (int s = 0; s < 2; ++s) {
+            mbar_init(&acc_full[s], 1);
+            mbar_init(&acc_empty[s], 128);
+        }
+        mbar_init(b_full, 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 8) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"((uint32_t)Cfg::TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp >= 4 && warp < 8) {
+        // ---------------------------------------------------------- producers
+        const int pt = tid - 128;              // 0..127: row of the A tile
+        uint64_t cur = ~0ull;                  // tensor whose B image is loaded
+        uint32_t b_phase = 0;
+        for (uint64_t t = t_begin; t < t_end; ++t) {
+            const uint64_t it = t - t_begin;
+            const int s = (int)(it % SA);
+            const uint64_t tens = t / tiles_per, o = t % tiles_per;
+            if (tens != cur) {
+                // every MMA of the previous tile is complete before B changes
+                if (it > 0 && !mbar_wait(&a_empty[(it - 1) % SA], (uint32_t)(((it - 1) / SA) & 1), abort_flag)) break;
+                if (pt == 0) {
+                    mbar_expect_tx(b_full, (uint32_t)(NP * Cfg::PLANE_B));
+                    bulk_g2s(sB, bimg + tens * (size_t)(NP * Cfg::PLANE_B), (uint32_t)(NP * Cfg::PLANE_B), b_full);
+                }
+                if (!mbar_wait(b_full, b_phase, abort_flag)) break;
+                b_phase ^= 1;
+                cur = tens;
+            }
+            if (it >= (uint64_t)SA && !mbar_wait(&a_empty[s], (uint32_t)(((it / SA) - 1) & 1), abort_flag)) break;
+            const float2* src = a.L + tens * (uint64_t)N;
+            const int64_t base = outer_offset(a, o) | rowoff[pt];
+            unsigned char* stage = sA + (size_t)s * NP * Cfg::PLANE_A;
+#pragma unroll 1
+            for (int g0 = 0; g0 < TE / 4; g0 += 4) {
+                float2 v[16];
+#pragma unroll
+                for (int j = 0; j < 16; ++j) v[j] = src[phys_index(base | coloff[g0 * 4 + j], a.swz)];
+#pragma unroll
+                for (int gg = 0; gg < 4; ++gg) {
+                    const int g = g0 + gg;   // complex entries 4g..4g+3 = reals 8g..8g+7
+                    uint32_t h[NP][4];
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) pack_terms<NP>(v[gg * 4 + j].x, v[gg * 4 + j].y, h, j);
+                    const uint32_t off = sw128_chunk(128, pt, g >> 3, g & 7);
+#pragma unroll
+                    for (int q = 0; q < NP; ++q)
+                        *reinterpret_cast<uint4*>(stage + q * Cfg::PLANE_A + off) = make_uint4(h[q][0], h[q][1], h[q][2], h[q][3]);
+                }
+            }
+            fence_async_smem();
+            mbar_arrive(&a_full[s]);
+        }
+    } else if (warp == 8) {
+        // -------------------------------------------------------------- MMA
+        const uint32_t idesc = idesc_bf16(KR);
+        for (uint64_t t = t_begin; t < t_end; ++t) {
+            const uint64_t it = t - t_begin;
+            const int s = (int)(it % SA), ab = (int)(it & 1);
+            if (!mbar_wait(&a_full[s], (uint32_t)((it / SA) & 1), abort_flag)) break;
+            if (it >= 2 && !mbar_wait(&acc_empty[ab], (uint32_t)(((it >> 1) - 1) & 1), abort_flag)) break;
+            tc_fence_after();
+            if (lane == 0) {
+                const uint32_t a0 = smem_u32(sA + (size_t)s * NP * Cfg::PLANE_A), b0 = smem_u32(sB);
+                const uint32_t d = tmem + (uint32_t)(ab * KR);
+                int first = 1;
+#pragma unroll
+                for (int pr = 0; pr < Cfg::NPROD; ++pr) {
+                    // products of total order < NP, smallest first: the last three
+                    // are those of NP = 2, the last one that of NP = 1
+                    constexpr int PA[6] = {2, 1, 0, 1, 0, 0}, PB[6] = {0, 1, 2, 0, 1, 0};
+                    constexpr int off = NP == 1 ? 5 : NP == 2 ? 3 : 0;
+                    const int pa = PA[off + pr], pb = PB[off + pr];
+#pragma unroll
+                    for (int ks = 0; ks < KR / 16; ++ks) {
+                        const uint32_t koff = (uint32_t)((ks >> 2) * 128 * 128 + (ks & 3) * 32);
+                        const uint32_t kofb = (uint32_t)((ks >> 2) * KR * 128 + (ks & 3) * 32);
+                        umma_bf16(d, smem_desc(a0 + pa * Cfg::PLANE_A + koff), smem_desc(b0 + pb * Cfg::PLANE_B + kofb),
+                                  idesc, first ? 0u : 1u);
+                        first = 0;
+                    }
+                }
+                umma_commit(&a_empty[s]);
+                umma_commit(&acc_full[ab]);
+            }
+            __syncwarp();
+        }
+        // the last commits complete before tensor memory is released
+        const uint64_t n = t_end > t_begin ? t_end - t_begin : 0;
+        if (n > 0) mbar_wait(&a_empty[(n - 1) % SA], (uint32_t)(((n - 1) / SA) & 1), abort_flag);
+    } else {
+        // --------------------------------------------------------- epilogue
+        const int r = tid;   // row of the tile = accumulator lane (warp w reads lanes 32w..32w+31)
+        for (uint64_t t = t_begin; t < t_end; ++t) {
+            const uint64_t it = t - t_begin;
+            const int ab = (int)(it & 1);
+            if (!mbar_wait(&acc_full[ab], (uint32_t)((it >> 1) & 1), abort_flag)) break;
+            tc_fence_after();
+            const uint64_t tens = t / tiles_per, o = t % tiles_per;
+            float2* dst = a.L + tens * (uint64_t)N;
+            const int64_t base = outer_offset(a, o) | rowoff[r];
+#pragma unroll 1
+            for (int c = 0; c < KR / 32; ++c) {
+                float v[32];
+                tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(ab * KR + c * 32), v);
+                if (c == KR / 32 - 1) {
+                    tc_fence_before();
+                    mbar_arrive(&acc_empty[ab]);
+                }
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    const int64_t i = base | coloff[c * 16 + j];
+                    float2 y = make_float2(v[2 * j], v[2 * j + 1]);
+                    if (a.ndiag) y = cmulf(y, diag_factor(a, tens, i));
+                    dst[phys_index(i, a.swz)] = y;
+                }
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 8) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)Cfg::TMEM_COLS)
+                     : "memory");
+    }
+    if (tid == 0 && *abort_flag) atomicExch(a.err, 1);
+}
+
+// The B operand image of every tensor: NP BF16 planes of the real block form
+// of its operator, K-major and 128-byte swizzled exactly as the MMA reads them
+// from shared memory (one thread per 16-byte chunk).
+template <int KT, int NP>
+__global__ void dense_bimage_kernel(const float2* __restrict__ ops, uint64_t ntens, unsigned char* __restrict__ img) {
+    using Cfg = TcCfg<KT, NP>;
+    constexpr int TE = Cfg::TE, KR = Cfg::KR;
+    const uint64_t chunks = ntens * (uint64_t)KR * (KR / 8);
+    for (uint64_t u = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; u < chunks; u += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t tens = u / ((uint64_t)KR * (KR / 8));
+        const int rem = (int)(u % ((uint64_t)KR * (KR / 8)));
+        const int n = rem / (KR / 8), g = rem % (KR / 8);   // output real n, chunk g (reals 8g..8g+7)
+        const int tp = n >> 1, cp = n & 1;
+        const float2* op = ops + tens * (uint64_t)TE * TE + (uint64_t)tp * TE;
+        uint32_t h[NP][4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const float2 w = op[4 * g + j];   // Op[t'][t], t = 4g + j
+            // row (t', cp) of [[Re, -Im], [Im, Re]] against input (t, re) and (t, im)
+            pack_terms<NP>(cp == 0 ? w.x : w.y, cp == 0 ? -w.y : w.x, h, j);
+        }
+        unsigned char* base = img + tens * (size_t)(NP * Cfg::PLANE_B);
+        const uint32_t off = sw128_chunk(KR, n, g >> 3, g & 7);
+#pragma unroll
+        for (int q = 0; q < NP; ++q)
+            *reinterpret_cast<uint4*>(base + q * Cfg::PLANE_B + off) = make_uint4(h[q][0], h[q][1], h[q][2], h[q][3]);
+    }
+}
+
+// --------------------------------------------------------------------- SIMT
+// One CTA per tile of 128 rows: the rows and the operator in shared memory,
+// every thread an 8 x 4 block of complex outputs, FP32 fused multiply-adds.
+template <int KT>
+__global__ void __launch_bounds__(256) dense_simt_kernel(const DenseArgs a) {
+    constexpr int TE = 1 << KT;
+    constexpr int RB = 8, CB = TE / 16;   // rows and columns per thread (16 x 16 threads)
+    extern __shared__ __align__(16) unsigned char smem_simt[];
+    float2* sX = reinterpret_cast<float2*>(smem_simt);   // [TE][128]: x[row][t] at t * 128 + row
+    float2* sO = sX + TE * 128;                         // [TE][TE]: Op[t'][t] at t * TE + t'
+    __shared__ int rowoff[128], coloff[64];
+    const int tid = threadIdx.x;
+    const uint64_t tiles_per = (uint64_t)1 << (a.W - KT - 7);
+    const uint64_t total = a.ntens * tiles_per;
+    const int64_t N = (int64_t)1 << a.W;
+    if (tid < 128) {
+        int o = 0;
+        for (int b = 0; b < 7; ++b) o |= ((tid >> b) & 1) << a.row_pos[b];
+        rowoff[tid] = o;
+    }
+    if (tid < TE) {
+        int o = 0;
+        for (int b = 0; b < KT; ++b) o |= ((tid >> b) & 1) << a.tile_pos[b];
+        coloff[tid] = o;
+    }
+    uint64_t cur = ~0ull;
+    const int tx = tid & 15, ty = tid >> 4;
+    for (uint64_t t = blockIdx.x; t < total; t += gridDim.x) {
+        const uint64_t tens = t / tiles_per, o = t % tiles_per;
+        __syncthreads();
+        if (tens != cur) {
+            const float2* op = a.ops + tens * (uint64_t)TE * TE;
+            for (int e = tid; e < TE * TE; e += 256) {
+                const int tp = e / TE, ti = e % TE;
+                sO[ti * TE + tp] = op[e];
+            }
+            cur = tens;
+        }
+        float2* L = a.L + tens * (uint64_t)N;
+        const int64_t ob = outer_offset(a, o);
+        for (int e = tid; e < TE * 128; e += 256) {
+            const int r = e & 127, c = e >> 7;
+            sX[c * 128 + r] = L[phys_index(ob | rowoff[r] | coloff[c], a.swz)];
+        }
+        __syncthreads();
+        float2 acc[RB][CB];
+#pragma unroll
+        for (int i = 0; i < RB; ++i)
+#pragma unroll
+            for (int j = 0; j < CB; ++j) acc[i][j] = make_float2(0.f, 0.f);
+#pragma unroll 4
+        for (int c = 0; c < TE; ++c) {
+            float2 x[RB], w[CB];
+#pragma unroll
+            for (int i = 0; i < RB; ++i) x[i] = sX[c * 128 + ty * RB + i];
+#pragma unroll
+            for (int j = 0; j < CB; ++j) w[j] = sO[c * TE + tx * CB + j];
+#pragma unroll
+            for (int i = 0; i < RB; ++i)
+#pragma unroll
+                for (int j = 0; j < CB; ++j) {
+                    acc[i][j].x = fmaf(x[i].x, w[j].x, fmaf(-x[i].y, w[j].y, acc[i][j].x));
+                    acc[i][j].y = fmaf(x[i].x, w[j].y, fmaf(x[i].y, w[j].x, acc[i][j].y));
+                }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < RB; ++i)
+#pragma unroll
+            for (int j = 0; j < CB; ++j) sX[(tx * CB + j) * 128 + ty * RB + i] = acc[i][j];
+        __syncthreads();
+        for (int e = tid; e < TE * 128; e += 256) {
+            const int r = e & 127, c = e >> 7;
+            const int64_t i = ob | rowoff[r] | coloff[c];
+            float2 y = sX[c * 128 + r];
+            if (a.ndiag) y = cmulf(y, diag_factor(a, tens, i));
+            L[phys_index(i, a.swz)] = y;
+        }
+    }
+}
+
+int dense_fail(cudaError_t e, const char* what) {
+    return set_error(PW_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+std::mutex& dense_mutex() {
+    static std::mutex mu;
+    return mu;
+}
+
+template <int KT, int NP> int launch_tc(const DenseArgs& a, unsigned char* bimg, int nsm, cudaStream_t st) {
+    using Cfg = TcCfg<KT, NP>;
+    const uint64_t chunks = a.ntens * (uint64_t)Cfg::KR * (Cfg::KR / 8);
+    const unsigned gb = (unsigned)std::min<uint64_t>((chunks + 255) / 256, (uint64_t)nsm * 16);
+    dense_bimage_kernel<KT, NP><<<gb, 256, 0, st>>>(a.ops, a.ntens, bimg);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return dense_fail(e, "dense B-image launch");
+    auto kern = dense_tc_kernel<KT, NP>;
+    {
+        std::lock_guard<std::mutex> lk(dense_mutex());
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::SMEM);
+    }
+    if (e != cudaSuccess) return dense_fail(e, "cudaFuncSetAttribute(dense tc)");
+    const uint64_t tiles = a.ntens << (a.W - KT - 7);
+    const unsigned grid = (unsigned)std::min<uint64_t>(tiles, (uint64_t)nsm);
+    kern<<<grid, 288, Cfg::SMEM, st>>>(a, bimg);
+    e = cudaGetLastError();
+    return e == cudaSuccess ? PW_OK : dense_fail(e, "dense tc launch");
+}
+
+template <int KT> int launch_simt(const DenseArgs& a, int nsm, cudaStream_t st) {
+    constexpr int TE = 1 << KT;
+    const size_t smem = (size_t)(TE * 128 + TE * TE) * sizeof(float2);
+    auto kern = dense_simt_kernel<KT>;
+    cudaError_t e;
+    {
+        std::lock_guard<std::mutex> lk(dense_mutex());
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    }
+    if (e != cudaSuccess) return dense_fail(e, "cudaFuncSetAttribute(dense simt)");
+    const uint64_t tiles = a.ntens << (a.W - KT - 7);
+    const unsigned grid = (unsigned)std::min<uint64_t>(tiles, (uint64_t)nsm * 2);
+    kern<<<grid, 256, smem, st>>>(a);
+    e = cudaGetLastError();
+    return e == cudaSuccess ? PW_OK : dense_fail(e, "dense simt launch");
+}
+
+}  // namespace
+
+size_t dense_bimage_bytes(int gemm, int k) {
+    const int np = gemm == PW_GEMM_BF16 ? 1 : gemm == PW_GEMM_SPLIT2 ? 2 : gemm == PW_GEMM_SPLIT3 ? 3 : 0;
+    const size_t kr = (size_t)2 << k;
+    return np * kr * kr * 2;
+}
+
+int dense_run(int gemm, const DenseArgs& a, unsigned char* bimg, cudaStream_t st) {
+    int dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    nsm = std::max(nsm, 1);
+    if (a.ntens == 0) return PW_OK;
+    if (gemm == PW_GEMM_FP32) return a.k == 5 ? launch_simt<5>(a, nsm, st) : launch_simt<6>(a, nsm, st);
+    if (gemm == PW_GEMM_BF16) return a.k == 5 ? launch_tc<5, 1>(a, bimg, nsm, st) : launch_tc<6, 1>(a, bimg, nsm, st);
+    if (gemm == PW_GEMM_SPLIT2) return a.k == 5 ? launch_tc<5, 2>(a, bimg, nsm, st) : launch_tc<6, 2>(a, bimg, nsm, st);
+    return a.k == 5 ? launch_tc<5, 3>(a, bimg, nsm, st) : launch_tc<6, 3>(a, bimg, nsm, st);
+}
+
+}  // namespace pw
+
+using namespace pw;
+
+extern "C" int pw_dense_apply(int gemm, const pw_dense_desc* desc, uint64_t n_tensors, float* d_tensors,
+                              const float* d_ops, const float* d_diag, void* stream) {
+    if (!desc) return set_error(PW_ERR_ARG, "null descriptor");
+    if (gemm < PW_GEMM_FP32 || gemm > PW_GEMM_SPLIT3) return set_error(PW_ERR_ARG, "unknown gemm kind");
+    const pw_dense_desc& d = *desc;
+    if (d.tile_bits != 5 && d.tile_bits != 6) return set_error(PW_ERR_ARG, "tile_bits must be 5 or 6");
+    if (d.width_bits < d.tile_bits + 7 || d.width_bits > 40)
+        return set_error(PW_ERR_ARG, "width_bits must be in [tile_bits + 7, 40]");
+    if (d.n_diag < 0 || d.n_diag > 4) return set_error(PW_ERR_ARG, "n_diag must be in 0..4");
+    if (n_tensors && (!d_tensors || !d_ops || (d.n_diag && !d_diag))) return set_error(PW_ERR_ARG, "null buffer");
+    DenseArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.W = d.width_bits;
+    a.k = d.tile_bits;
+    a.swz = d.swizzled ? 1 : 0;
+    // the tile and row bits: distinct, in range; the others are the outer bits
+    uint64_t used = 0;
+    auto take = [&](int b) {
+        if (b < 0 || b >= a.W || ((used >> b) & 1)) return false;
+        used |= 1ull << b;
+        return true;
+    };
+    for (int j = 0; j < a.k; ++j) {
+        if (!take(d.tile_pos[j])) return set_error(PW_ERR_ARG, "tile_pos: bits must be distinct and < width_bits");
+        a.tile_pos[j] = d.tile_pos[j];
+    }
+    for (int j = 0; j < 7; ++j) {
+        if (!take(d.row_pos[j])) return set_error(PW_ERR_ARG, "row_pos: bits must be distinct, < width_bits, not tile bits");
+        a.row_pos[j] = d.row_pos[j];
+    }
+    for (int b = 0; b < a.W; ++b)
+        if (!((used >> b) & 1)) a.outer_pos[a.nouter++] = b;
+    a.ndiag = d.n_diag;
+    for (int i = 0; i < a.ndiag; ++i) {
+        if (d.diag_bits[i] < 0 || d.diag_bits[i] > 5) return set_error(PW_ERR_ARG, "diag_bits must be in 0..5");
+        a.diag_nb[i] = d.diag_bits[i];
+        for (int b = 0; b < a.diag_nb[i]; ++b) {
+            if (d.diag_pos[i][b] < 0 || d.diag_pos[i][b] >= a.W) return set_error(PW_ERR_ARG, "diag_pos out of range");
+            a.diag_pos[i][b] = d.diag_pos[i][b];
+        }
+    }
+    if (n_tensors == 0) return PW_OK;
+    a.L = reinterpret_cast<float2*>(d_tensors);
+    a.ops = reinterpret_cast<const float2*>(d_ops);
+    a.diag = reinterpret_cast<const float2*>(d_diag);
+    a.ntens = n_tensors;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t e;
+    int* d_err = nullptr;
+    unsigned char* bimg = nullptr;
+    const size_t img = dense_bimage_bytes(gemm, a.k) * n_tensors;
+    if ((e = cudaMalloc(&d_err, sizeof(int))) != cudaSuccess) return dense_fail(e, "cudaMalloc(flag)");
+    if (img && (e = cudaMalloc(&bimg, img)) != cudaSuccess) {
+        cudaFree(d_err);
+        return dense_fail(e, "cudaMalloc(operator image)");
+    }
+    a.err = d_err;
+    int rc = PW_OK;
+    if ((e = cudaMemsetAsync(d_err, 0, sizeof(int), st)) != cudaSuccess) rc = dense_fail(e, "cudaMemsetAsync");
+    if (!rc) rc = dense_run(gemm, a, bimg, st);
+    int h_err = 0;
+    if (!rc && (e = cudaMemcpyAsync(&h_err, d_err, sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+        rc = dense_fail(e, "reading the error flag");
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess && !rc) rc = dense_fail(e, "cudaStreamSynchronize");
+    cudaFree(bimg);
+    cudaFree(d_err);
+    if (!rc && h_err) rc = set_error(PW_ERR_TIMEOUT, "a bounded wait of the tensor-core pass ran out");
+    return rc;
+}

@@ -1,0 +1,37 @@
+// Dense passes of the sweep on HBM-resident tensors (dense.cu): the kernel
+// arguments and the host entry shared by the pass call of the C ABI and the
+// wide sampler.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+
+namespace pw {
+
+struct DenseArgs {
+    float2* L;             // ntens tensors of 2^W complex entries, updated in place
+    const float2* ops;     // ntens operators of 2^k x 2^k entries, Op[t'][t] at t' * 2^k + t
+    const float2* diag;    // ntens x ndiag x 32 diagonal-factor tables
+    uint64_t ntens;
+    int W, k;
+    int swz;               // 1: entry i stored at i ^ ((i >> 4) & 15)
+    int tile_pos[8];       // operator index bit j <-> tensor index bit tile_pos[j]
+    int row_pos[7];        // the index bits numbering the 128 rows of a GEMM tile
+    int outer_pos[40];     // the other index bits, numbering the tiles of a tensor
+    int nouter;
+    int ndiag;
+    int diag_nb[4];
+    int diag_pos[4][5];
+    int* err;              // device flag: a bounded wait ran out
+};
+
+// Bytes of the operator image of one tensor for the tensor-core arm (0 for
+// the SIMT arm).
+size_t dense_bimage_bytes(int gemm, int k);
+
+// Enqueue one pass on stream st (bimg: ntens * dense_bimage_bytes scratch).
+int dense_run(int gemm, const DenseArgs& a, unsigned char* bimg, cudaStream_t st);
+
+}  // namespace pw

@@ -45,6 +45,18 @@ class PlanStats(C.Structure):
                 ("device_bytes", C.c_double), ("ctas_per_chain", C.c_int), ("flops_per_amplitude", C.c_double)]
 
 
+PW_GEMM_FP32 = 0
+PW_GEMM_BF16 = 1
+PW_GEMM_SPLIT2 = 2
+PW_GEMM_SPLIT3 = 3
+
+
+class DenseDesc(C.Structure):
+    _fields_ = [("width_bits", C.c_int), ("tile_bits", C.c_int), ("tile_pos", C.c_int * 8), ("row_pos", C.c_int * 7),
+                ("swizzled", C.c_int), ("n_diag", C.c_int), ("diag_bits", C.c_int * 4),
+                ("diag_pos", (C.c_int * 5) * 4), ("reserved", C.c_int * 8)]
+
+
 class RunStats(C.Structure):
     _fields_ = [("near_boundary", C.c_uint64), ("zero_mass", C.c_uint64), ("launches", C.c_uint64)]
 
@@ -82,6 +94,7 @@ def load_library():
                                         C.c_uint64, vp, vp, vp]),
         "pw_sample_static": (C.c_int, [vp, C.c_uint64, C.c_uint64, C.c_uint64, vp, vp, C.POINTER(RunStats)]),
         "pw_device_fma_rate": (C.c_int, [C.c_int, vp, dp]),
+        "pw_dense_apply": (C.c_int, [C.c_int, C.POINTER(DenseDesc), C.c_uint64, vp, vp, vp, vp]),
         "pw_last_error": (C.c_char_p, []),
     }
     for name, (res, args) in sig.items():
@@ -233,6 +246,34 @@ def pw_device_fma_rate(precision=PW_PREC_FP32, stream=None) -> float:
     r = C.c_double(0.0)
     _check(load_library().pw_device_fma_rate(int(precision), _stream_ptr(stream), C.byref(r)))
     return r.value
+
+
+def make_dense_desc(width_bits, tile_pos, row_pos, swizzled=0, diag_pos=()):
+    """pw_dense_desc from bit lists (diag_pos: one list of bits per factor)."""
+    d = DenseDesc()
+    d.width_bits = int(width_bits)
+    d.tile_bits = len(tile_pos)
+    for j, b in enumerate(tile_pos):
+        d.tile_pos[j] = int(b)
+    for j, b in enumerate(row_pos):
+        d.row_pos[j] = int(b)
+    d.swizzled = int(swizzled)
+    d.n_diag = len(diag_pos)
+    for i, bits in enumerate(diag_pos):
+        d.diag_bits[i] = len(bits)
+        for j, b in enumerate(bits):
+            d.diag_pos[i][j] = int(b)
+    return d
+
+
+def pw_dense_apply(gemm, desc, n_tensors, tensors, ops, diag=None, stream=None):
+    """tensors: torch CUDA complex64 [n, 2^W] (in place); ops: complex64 [n, 2^k, 2^k];
+    diag: complex64 [n, n_diag, 32] or None."""
+    _check(load_library().pw_dense_apply(int(gemm), C.byref(desc), int(n_tensors),
+                                         C.c_void_p(tensors.data_ptr()) if tensors is not None else None,
+                                         C.c_void_p(ops.data_ptr()) if ops is not None else None,
+                                         C.c_void_p(diag.data_ptr()) if diag is not None else None,
+                                         _stream_ptr(stream)))
 
 
 def pw_sample_host(plan, seed, first_sample, n_samples, out_bits: np.ndarray, trace: np.ndarray | None = None):
