@@ -302,7 +302,7 @@ int pw_sample_static(const pw_plan* plan, uint64_t seed, uint64_t first_sample, 
 /* Index bits of a dense pass. Tensor entry i (complex) has index bits
  * b_0 .. b_{W-1}; the pass acts on the k tile bits. */
 typedef struct {
-    int width_bits;      /* W: each tensor holds 2^W complex entries, tile_bits + 7 <= W <= 40 */
+    int width_bits;      /* W: each tensor holds 2^W complex entries, tile_bits + 7 <= W <= 31 */
     int tile_bits;       /* k: 5 or 6 */
     int tile_pos[8];     /* operator index bit j is tensor index bit tile_pos[j] */
     int row_pos[7];      /* seven more distinct bits: the 128 rows of one GEMM tile (put

@@ -174,23 +174,8 @@ __device__ __forceinline__ uint32_t sw128_chunk(int rows, int r, int kb, int c) 
     return (uint32_t)(kb * rows * 128 + r * 128 + ((c ^ (r & 7)) << 4));
 }
 
-__device__ __forceinline__ int64_t phys_index(int64_t i, int swz) {
-    return swz ? (i ^ ((i >> 4) & 15)) : i;
-}
-
 __device__ __forceinline__ float2 cmulf(float2 a, float2 b) {
     return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
-}
-
-// Diagonal factors of the pass at logical index i of tensor `tens`.
-__device__ __forceinline__ float2 diag_factor(const DenseArgs& a, uint64_t tens, int64_t i) {
-    float2 f = make_float2(1.f, 0.f);
-    for (int d = 0; d < a.ndiag; ++d) {
-        int e = 0;
-        for (int b = 0; b < a.diag_nb[d]; ++b) e |= (int)((i >> a.diag_pos[d][b]) & 1) << b;
-        f = cmulf(f, a.diag[(tens * a.ndiag + d) * 32 + e]);
-    }
-    return f;
 }
 
 __device__ __forceinline__ int64_t outer_offset(const DenseArgs& a, uint64_t o) {
@@ -208,19 +193,64 @@ template <int KT, int NP> struct TcCfg {
     static constexpr int NPROD = NP == 1 ? 1 : NP == 2 ? 3 : 6;
     static constexpr int SA = (NP * PLANE_B + 2 * NP * PLANE_A) <= 200 * 1024 ? 2 : 1;   // A stages
     static constexpr int TMEM_COLS = 2 * KR;    // two accumulators
-    static constexpr size_t SMEM = (size_t)NP * PLANE_B + (size_t)SA * NP * PLANE_A + 2048;
+    static constexpr size_t SMEM = (size_t)NP * PLANE_B + (size_t)SA * NP * PLANE_A + 4096;
+    static constexpr int THREADS = 416;         // 4 epilogue warps, 8 producer warps, 1 MMA warp
 };
 
+// Per-CTA index tables of a pass. The storage position of logical index i
+// is linear over XOR in i's bits (the swizzle XORs bits 4..7 into bits 0..3),
+// and the tile row, the tile column and the tile's outer bits set disjoint
+// bits of i; so position = pout ^ prow[r] ^ pcol[t], and likewise the table
+// index of every diagonal factor (one byte per factor, packed) =
+// dout ^ drow[r] ^ dcol[t].
+struct PassTables {
+    int prow[128], drow[128];
+    int pcol[64], dcol[64];
+};
+
+__device__ __forceinline__ int64_t swz64(int64_t i, int swz) { return swz ? (i ^ ((i >> 4) & 15)) : i; }
+
+__device__ __forceinline__ int diag_index_bits(const DenseArgs& a, int64_t i) {
+    int e = 0;
+    for (int d = 0; d < a.ndiag; ++d)
+        for (int b = 0; b < a.diag_nb[d]; ++b) e |= (int)((i >> a.diag_pos[d][b]) & 1) << (8 * d + b);
+    return e;
+}
+
+__device__ void fill_pass_tables(const DenseArgs& a, PassTables* T, int tid, int nthreads) {
+    for (int r = tid; r < 128; r += nthreads) {
+        int64_t o = 0;
+        for (int b = 0; b < 7; ++b) o |= (int64_t)((r >> b) & 1) << a.row_pos[b];
+        T->prow[r] = (int)swz64(o, a.swz);
+        T->drow[r] = diag_index_bits(a, o);
+    }
+    for (int t = tid; t < (1 << a.k); t += nthreads) {
+        int64_t o = 0;
+        for (int b = 0; b < a.k; ++b) o |= (int64_t)((t >> b) & 1) << a.tile_pos[b];
+        T->pcol[t] = (int)swz64(o, a.swz);
+        T->dcol[t] = diag_index_bits(a, o);
+    }
+}
+
+// The diagonal factors at packed table indices e (tables of this tensor in
+// shared memory, 32 entries per factor).
+__device__ __forceinline__ float2 diag_product(const float2* tab, int ndiag, int e) {
+    float2 f = tab[e & 31];
+    for (int d = 1; d < ndiag; ++d) f = cmulf(f, tab[32 * d + ((e >> (8 * d)) & 31)]);
+    return f;
+}
+
 template <int KT, int NP>
-__global__ void __launch_bounds__(288, 1) dense_tc_kernel(const DenseArgs a, const unsigned char* __restrict__ bimg) {
+__global__ void __launch_bounds__(416, 1) dense_tc_kernel(const DenseArgs a, const unsigned char* __restrict__ bimg) {
     using Cfg = TcCfg<KT, NP>;
     constexpr int TE = Cfg::TE, KR = Cfg::KR, SA = Cfg::SA;
+    constexpr int PCOLS = TE / 2;   // columns of one producer thread
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* smem = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     unsigned char* sB = smem;                                   // NP planes of B
     unsigned char* sA = smem + NP * Cfg::PLANE_B;               // SA stages x NP planes of A
     uint64_t* bars = reinterpret_cast<uint64_t*>(sA + SA * NP * Cfg::PLANE_A);
-    uint64_t* a_full = bars;            // [SA] producers -> MMA (128 arrivals)
+    uint64_t* a_full = bars;            // [SA] producers -> MMA (256 arrivals)
     uint64_t* a_empty = bars + SA;      // [SA] MMA commit -> producers
     uint64_t* acc_full = bars + 2 * SA; // [2] MMA commit -> epilogue
     uint64_t* acc_empty = bars + 2 * SA + 2;   // [2] epilogue (128 arrivals) -> MMA
@@ -228,8 +258,8 @@ __global__ void __launch_bounds__(288, 1) dense_tc_kernel(const DenseArgs a, con
     int* misc = reinterpret_cast<int*>(bars + 2 * SA + 5);
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(misc);     // written by tcgen05.alloc
     volatile int* abort_flag = misc + 1;                         // a bounded wait ran out
-    int* rowoff = misc + 4;                                      // [128] index bits of tile row r
-    int* coloff = rowoff + 128;                                  // [TE] index bits of operator column t
+    PassTables* T = reinterpret_cast<PassTables*>(misc + 4);
+    float2* stab = reinterpret_cast<float2*>(T + 1);             // [4][32] diagonal tables of the current tensor
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const uint64_t tiles_per = (uint64_t)1 << (a.W - KT - 7);
@@ -239,19 +269,10 @@ __global__ void __launch_bounds__(288, 1) dense_tc_kernel(const DenseArgs a, con
     const uint64_t t_end = t_begin + per < total ? t_begin + per : total;
     const int64_t N = (int64_t)1 << a.W;
 
-    if (tid < 128) {
-        int o = 0;
-        for (int b = 0; b < 7; ++b) o |= ((tid >> b) & 1) << a.row_pos[b];
-        rowoff[tid] = o;
-    }
-    if (tid < TE) {
-        int o = 0;
-        for (int b = 0; b < KT; ++b) o |= ((tid >> b) & 1) << a.tile_pos[b];
-        coloff[tid] = o;
-    }
+    fill_pass_tables(a, T, tid, Cfg::THREADS);
     if (tid == 0) {
         for (int s = 0; s < SA; ++s) {
-            mbar_init(&a_full[s], 128);
+            mbar_init(&a_full[s], 256);
             mbar_init(&a_empty[s], 1);
         }
         for (int s = 0; s < 2; ++s) {
@@ -262,7 +283,7 @@ __global__ void __launch_bounds__(288, 1) dense_tc_kernel(const DenseArgs a, con
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == 8) {
+    if (warp == 12) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
                      "r"((uint32_t)Cfg::TMEM_COLS)
                      : "memory");
@@ -273,9 +294,11 @@ __global__ void __launch_bounds__(288, 1) dense_tc_kernel(const DenseArgs a, con
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
 
-    if (warp >= 4 && warp < 8) {
+    if (warp >= 4 && warp < 12) {
         // ---------------------------------------------------------- producers
-        const int pt = tid - 128;              // 0..127: row of the A tile
+        // thread (r, h): row r of the A tile, columns h*TE/2 .. h*TE/2 + TE/2 - 1;
+        // consecutive lanes take consecutive rows (the low free index bits)
+        const int pt = tid - 128, r = pt & 127, c0 = (pt >> 7) * PCOLS;
         uint64_t cur = ~0ull;                  // tensor whose B image is loaded
         uint32_t b_phase = 0;
         for (uint64_t t = t_begin; t < t_end; ++t) {
@@ -294,30 +317,28 @@ __global__ void __launch_bounds__(288, 1) dense_tc_kernel(const DenseArgs a, con
                 cur = tens;
             }
             if (it >= (uint64_t)SA && !mbar_wait(&a_empty[s], (uint32_t)(((it / SA) - 1) & 1), abort_flag)) break;
+            // (positions combine by XOR: the swizzle mixes the bits of the parts)
             const float2* src = a.L + tens * (uint64_t)N;
-            const int64_t base = outer_offset(a, o) | rowoff[pt];
+            const int64_t pr = swz64(outer_offset(a, o), a.swz) ^ T->prow[r];
             unsigned char* stage = sA + (size_t)s * NP * Cfg::PLANE_A;
-#pragma unroll 1
-            for (int g0 = 0; g0 < TE / 4; g0 += 4) {
-                float2 v[16];
+            float2 v[PCOLS];
 #pragma unroll
-                for (int j = 0; j < 16; ++j) v[j] = src[phys_index(base | coloff[g0 * 4 + j], a.swz)];
+            for (int j = 0; j < PCOLS; ++j) v[j] = src[pr ^ T->pcol[c0 + j]];
 #pragma unroll
-                for (int gg = 0; gg < 4; ++gg) {
-                    const int g = g0 + gg;   // complex entries 4g..4g+3 = reals 8g..8g+7
-                    uint32_t h[NP][4];
+            for (int gg = 0; gg < PCOLS / 4; ++gg) {
+                const int g = c0 / 4 + gg;   // complex entries 4g..4g+3 = reals 8g..8g+7
+                uint32_t h[NP][4];
 #pragma unroll
-                    for (int j = 0; j < 4; ++j) pack_terms<NP>(v[gg * 4 + j].x, v[gg * 4 + j].y, h, j);
-                    const uint32_t off = sw128_chunk(128, pt, g >> 3, g & 7);
+                for (int j = 0; j < 4; ++j) pack_terms<NP>(v[gg * 4 + j].x, v[gg * 4 + j].y, h, j);
+                const uint32_t off = sw128_chunk(128, r, g >> 3, g & 7);
 #pragma unroll
-                    for (int q = 0; q < NP; ++q)
-                        *reinterpret_cast<uint4*>(stage + q * Cfg::PLANE_A + off) = make_uint4(h[q][0], h[q][1], h[q][2], h[q][3]);
-                }
+                for (int q = 0; q < NP; ++q)
+                    *reinterpret_cast<uint4*>(stage + q * Cfg::PLANE_A + off) = make_uint4(h[q][0], h[q][1], h[q][2], h[q][3]);
             }
             fence_async_smem();
             mbar_arrive(&a_full[s]);
         }
-    } else if (warp == 8) {
+    } else if (warp == 12) {
         // -------------------------------------------------------------- MMA
         const uint32_t idesc = idesc_bf16(KR);
         for (uint64_t t = t_begin; t < t_end; ++t) {
@@ -357,14 +378,24 @@ __global__ void __launch_bounds__(288, 1) dense_tc_kernel(const DenseArgs a, con
     } else {
         // --------------------------------------------------------- epilogue
         const int r = tid;   // row of the tile = accumulator lane (warp w reads lanes 32w..32w+31)
+        uint64_t cur = ~0ull;
         for (uint64_t t = t_begin; t < t_end; ++t) {
             const uint64_t it = t - t_begin;
             const int ab = (int)(it & 1);
+            const uint64_t tens = t / tiles_per, o = t % tiles_per;
+            if (a.ndiag && tens != cur) {
+                // this tensor's diagonal tables (the four epilogue warps: named barrier 1)
+                asm volatile("bar.sync 1, 128;" ::: "memory");
+                for (int e = r; e < a.ndiag * 32; e += 128) stab[e] = a.diag[tens * a.ndiag * 32 + e];
+                asm volatile("bar.sync 1, 128;" ::: "memory");
+                cur = tens;
+            }
             if (!mbar_wait(&acc_full[ab], (uint32_t)((it >> 1) & 1), abort_flag)) break;
             tc_fence_after();
-            const uint64_t tens = t / tiles_per, o = t % tiles_per;
+            const int64_t ob = outer_offset(a, o);
             float2* dst = a.L + tens * (uint64_t)N;
-            const int64_t base = outer_offset(a, o) | rowoff[r];
+            const int64_t pr = swz64(ob, a.swz) ^ T->prow[r];
+            const int dr = diag_index_bits(a, ob) ^ T->drow[r];
 #pragma unroll 1
             for (int c = 0; c < KR / 32; ++c) {
                 float v[32];
@@ -375,17 +406,17 @@ __global__ void __launch_bounds__(288, 1) dense_tc_kernel(const DenseArgs a, con
                 }
 #pragma unroll
                 for (int j = 0; j < 16; ++j) {
-                    const int64_t i = base | coloff[c * 16 + j];
+                    const int col = c * 16 + j;
                     float2 y = make_float2(v[2 * j], v[2 * j + 1]);
-                    if (a.ndiag) y = cmulf(y, diag_factor(a, tens, i));
-                    dst[phys_index(i, a.swz)] = y;
+                    if (a.ndiag) y = cmulf(y, diag_product(stab, a.ndiag, dr ^ T->dcol[col]));
+                    dst[pr ^ T->pcol[col]] = y;
                 }
             }
         }
     }
     tc_fence_before();
     __syncthreads();
-    if (warp == 8) {
+    if (warp == 12) {
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)Cfg::TMEM_COLS)
                      : "memory");
@@ -431,22 +462,14 @@ __global__ void __launch_bounds__(256) dense_simt_kernel(const DenseArgs a) {
     constexpr int RB = 8, CB = TE / 16;   // rows and columns per thread (16 x 16 threads)
     extern __shared__ __align__(16) unsigned char smem_simt[];
     float2* sX = reinterpret_cast<float2*>(smem_simt);   // [TE][128]: x[row][t] at t * 128 + row
-    float2* sO = sX + TE * 128;                         // [TE][TE]: Op[t'][t] at t * TE + t'
-    __shared__ int rowoff[128], coloff[64];
+    float2* sO = sX + TE * 128;                          // [TE][TE]: Op[t'][t] at t * TE + t'
+    __shared__ PassTables T;
+    __shared__ float2 stab[4 * 32];
     const int tid = threadIdx.x;
     const uint64_t tiles_per = (uint64_t)1 << (a.W - KT - 7);
     const uint64_t total = a.ntens * tiles_per;
     const int64_t N = (int64_t)1 << a.W;
-    if (tid < 128) {
-        int o = 0;
-        for (int b = 0; b < 7; ++b) o |= ((tid >> b) & 1) << a.row_pos[b];
-        rowoff[tid] = o;
-    }
-    if (tid < TE) {
-        int o = 0;
-        for (int b = 0; b < KT; ++b) o |= ((tid >> b) & 1) << a.tile_pos[b];
-        coloff[tid] = o;
-    }
+    fill_pass_tables(a, &T, tid, 256);
     uint64_t cur = ~0ull;
     const int tx = tid & 15, ty = tid >> 4;
     for (uint64_t t = blockIdx.x; t < total; t += gridDim.x) {
@@ -458,13 +481,16 @@ __global__ void __launch_bounds__(256) dense_simt_kernel(const DenseArgs a) {
                 const int tp = e / TE, ti = e % TE;
                 sO[ti * TE + tp] = op[e];
             }
+            for (int e = tid; e < a.ndiag * 32; e += 256) stab[e] = a.diag[tens * a.ndiag * 32 + e];
             cur = tens;
         }
-        float2* L = a.L + tens * (uint64_t)N;
         const int64_t ob = outer_offset(a, o);
+        float2* L = a.L + tens * (uint64_t)N;
+        const int64_t pob = swz64(ob, a.swz);
+        const int dob = diag_index_bits(a, ob);
         for (int e = tid; e < TE * 128; e += 256) {
             const int r = e & 127, c = e >> 7;
-            sX[c * 128 + r] = L[phys_index(ob | rowoff[r] | coloff[c], a.swz)];
+            sX[c * 128 + r] = L[pob ^ T.prow[r] ^ T.pcol[c]];
         }
         __syncthreads();
         float2 acc[RB][CB];
@@ -495,10 +521,9 @@ __global__ void __launch_bounds__(256) dense_simt_kernel(const DenseArgs a) {
         __syncthreads();
         for (int e = tid; e < TE * 128; e += 256) {
             const int r = e & 127, c = e >> 7;
-            const int64_t i = ob | rowoff[r] | coloff[c];
             float2 y = sX[c * 128 + r];
-            if (a.ndiag) y = cmulf(y, diag_factor(a, tens, i));
-            L[phys_index(i, a.swz)] = y;
+            if (a.ndiag) y = cmulf(y, diag_product(stab, a.ndiag, dob ^ T.drow[r] ^ T.dcol[c]));
+            L[pob ^ T.prow[r] ^ T.pcol[c]] = y;
         }
     }
 }
@@ -527,7 +552,7 @@ template <int KT, int NP> int launch_tc(const DenseArgs& a, unsigned char* bimg,
     if (e != cudaSuccess) return dense_fail(e, "cudaFuncSetAttribute(dense tc)");
     const uint64_t tiles = a.ntens << (a.W - KT - 7);
     const unsigned grid = (unsigned)std::min<uint64_t>(tiles, (uint64_t)nsm);
-    kern<<<grid, 288, Cfg::SMEM, st>>>(a, bimg);
+    kern<<<grid, Cfg::THREADS, Cfg::SMEM, st>>>(a, bimg);
     e = cudaGetLastError();
     return e == cudaSuccess ? PW_OK : dense_fail(e, "dense tc launch");
 }
@@ -579,8 +604,8 @@ extern "C" int pw_dense_apply(int gemm, const pw_dense_desc* desc, uint64_t n_te
     if (gemm < PW_GEMM_FP32 || gemm > PW_GEMM_SPLIT3) return set_error(PW_ERR_ARG, "unknown gemm kind");
     const pw_dense_desc& d = *desc;
     if (d.tile_bits != 5 && d.tile_bits != 6) return set_error(PW_ERR_ARG, "tile_bits must be 5 or 6");
-    if (d.width_bits < d.tile_bits + 7 || d.width_bits > 40)
-        return set_error(PW_ERR_ARG, "width_bits must be in [tile_bits + 7, 40]");
+    if (d.width_bits < d.tile_bits + 7 || d.width_bits > 31)
+        return set_error(PW_ERR_ARG, "width_bits must be in [tile_bits + 7, 31]");
     if (d.n_diag < 0 || d.n_diag > 4) return set_error(PW_ERR_ARG, "n_diag must be in 0..4");
     if (n_tensors && (!d_tensors || !d_ops || (d.n_diag && !d_diag))) return set_error(PW_ERR_ARG, "null buffer");
     DenseArgs a;

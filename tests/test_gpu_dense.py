@@ -86,3 +86,30 @@ def test_dense_pass_many_tiles_and_identity(gemm):
     pw.pw_dense_apply(gemm, desc, n_t, d_x, d_op, None)
     got = d_x.cpu().numpy()
     assert np.abs(got - x).max() <= 1e-7 * np.abs(x).max()
+
+
+@pytest.mark.parametrize("gemm", [0, 3, 1])
+def test_dense_pass_any_bit_roles(gemm):
+    """Row bits above the outer bits and tile bits among the swizzled low
+    bits: positions combine the three parts by XOR, whatever bits they hold."""
+    import torch
+    import paper_2510_24218_gb300 as pw
+    rng = np.random.default_rng(31 + gemm)
+    k, W, n_t = 6, 17, 3
+    tile = [3, 0, 9, 1, 8, 2]
+    row = [10, 11, 12, 13, 14, 15, 16]
+    diag_pos = [[4, 5, 0], [6, 7, 13, 9]]
+    x = (rng.standard_normal((n_t, 1 << W)) + 1j * rng.standard_normal((n_t, 1 << W))) / np.sqrt(2)
+    ops = (rng.standard_normal((n_t, 1 << k, 1 << k)) + 1j * rng.standard_normal((n_t, 1 << k, 1 << k))) / np.sqrt(2 << k)
+    diag = np.exp(1j * rng.uniform(0, 2 * np.pi, (n_t, 2, 32)))
+    phys = _swz(np.arange(1 << W))
+    stored = np.empty_like(x)
+    stored[:, phys] = x
+    d_x = torch.from_numpy(stored.astype(np.complex64)).cuda()
+    pw.pw_dense_apply(gemm, pw.make_dense_desc(W, tile, row, 1, diag_pos), n_t, d_x,
+                      torch.from_numpy(ops.astype(np.complex64)).cuda(), torch.from_numpy(diag.astype(np.complex64)).cuda())
+    got = d_x.cpu().numpy().astype(np.complex128)[:, phys]
+    for b in range(n_t):
+        want = _reference(W, tile, diag_pos, x[b].astype(np.complex64).astype(complex),
+                          ops[b].astype(np.complex64).astype(complex), diag[b].astype(np.complex64).astype(complex))
+        assert np.linalg.norm(got[b] - want) / np.linalg.norm(want) < TOL[gemm]
