@@ -57,6 +57,17 @@ extern "C" {
 #define PW_ORDER_AUTO 0          /* search sweep orders, keep the narrowest */
 #define PW_ORDER_NATURAL 1       /* sweep qubits in index order */
 
+#define PW_ENGINE_AUTO 0         /* on-chip frontier when it fits, else the HBM engine */
+#define PW_ENGINE_ONCHIP 1       /* frontier in shared memory (one CTA or a cluster per chain) */
+#define PW_ENGINE_HBM 2          /* frontier in HBM; wide layers' passes are dense GEMMs */
+
+/* Arithmetic of a dense pass (pw_dense_apply, and the HBM engine's passes). */
+#define PW_GEMM_SPLIT3 0   /* tensor cores: operands split into three BF16 terms (the 24-bit
+                              FP32 significand), 6 products, FP32 accumulation (the default) */
+#define PW_GEMM_SPLIT2 1   /* tensor cores: two BF16 terms (16 bits), 3 products */
+#define PW_GEMM_BF16 2     /* tensor cores: BF16 operands (one term) */
+#define PW_GEMM_FP32 3     /* FP32 CUDA cores (SIMT), the plain-FP32 arm */
+
 typedef struct pw_circuit pw_circuit;
 typedef struct pw_plan pw_plan;
 
@@ -72,7 +83,13 @@ typedef struct {
     int ctas_per_chain;     /* 0 -> auto (a thread-block cluster only when one CTA's
                                shared memory cannot hold the frontier); 2, 4 or 8
                                force that split of the frontier over a cluster */
-    int reserved[6];
+    int engine;             /* PW_ENGINE_AUTO (default): the on-chip engine, or the HBM
+                               engine when the frontier exceeds 2^17 entries (FP32 plans);
+                               PW_ENGINE_HBM forces the HBM engine (FP32 plans only) */
+    int gemm;               /* HBM engine: arithmetic of the dense passes, PW_GEMM_*
+                               (default PW_GEMM_SPLIT3: tensor cores at FP32-equivalent
+                               input precision) */
+    int reserved[4];
 } pw_plan_opts;
 
 /* Shape and cost of a plan (pw_plan_stats). */
@@ -96,6 +113,12 @@ typedef struct {
     double device_bytes;       /* bytes of plan tables copied to the device on first use */
     int ctas_per_chain;        /* > 1: one chain per thread-block cluster of that many CTAs */
     double flops_per_amplitude;   /* real flops of pw_amplitudes of the whole circuit, per string */
+    int engine;                /* PW_ENGINE_ONCHIP or PW_ENGINE_HBM */
+    int gemm;                  /* HBM engine: PW_GEMM_* of its dense passes */
+    int dense_tile_bits;       /* HBM engine: tile bits k of the widest layer's dense passes */
+    double dense_passes_per_sample;   /* HBM engine: dense GEMM passes per chain */
+    double dense_flops_per_sample;    /* HBM engine: real flops of those passes per chain
+                                         (2^W x 2^k complex multiply-adds each, 8 flops) */
 } pw_plan_stats_t;
 
 /* Counters of one pw_sample call. */
@@ -291,13 +314,6 @@ int pw_sample_static(const pw_plan* plan, uint64_t seed, uint64_t first_sample, 
                      uint64_t* d_out_bits, void* stream, pw_run_stats_t* stats);
 
 /* ----------------------------------------------------- dense sweep passes */
-
-/* Arithmetic of a dense pass (pw_dense_apply, and the wide engine of
- * pw_plan_opts.engine). */
-#define PW_GEMM_FP32 0     /* FP32 CUDA cores (SIMT), the plain-FP32 arm */
-#define PW_GEMM_BF16 1     /* tensor cores: BF16 operands (one term), FP32 accumulation */
-#define PW_GEMM_SPLIT2 2   /* tensor cores: operands split into two BF16 terms, 3 products */
-#define PW_GEMM_SPLIT3 3   /* tensor cores: three BF16 terms (the 24-bit FP32 significand), 6 products */
 
 /* Index bits of a dense pass. Tensor entry i (complex) has index bits
  * b_0 .. b_{W-1}; the pass acts on the k tile bits. */

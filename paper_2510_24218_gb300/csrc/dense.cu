@@ -386,7 +386,7 @@ __global__ void __launch_bounds__(416, 1) dense_tc_kernel(const DenseArgs a, con
             if (a.ndiag && tens != cur) {
                 // this tensor's diagonal tables (the four epilogue warps: named barrier 1)
                 asm volatile("bar.sync 1, 128;" ::: "memory");
-                for (int e = r; e < a.ndiag * 32; e += 128) stab[e] = a.diag[tens * a.ndiag * 32 + e];
+                for (int e = r; e < a.ndiag * 32; e += 128) stab[e] = a.diag[tens * (uint64_t)a.diag_stride + e];
                 asm volatile("bar.sync 1, 128;" ::: "memory");
                 cur = tens;
             }
@@ -481,7 +481,7 @@ __global__ void __launch_bounds__(256) dense_simt_kernel(const DenseArgs a) {
                 const int tp = e / TE, ti = e % TE;
                 sO[ti * TE + tp] = op[e];
             }
-            for (int e = tid; e < a.ndiag * 32; e += 256) stab[e] = a.diag[tens * a.ndiag * 32 + e];
+            for (int e = tid; e < a.ndiag * 32; e += 256) stab[e] = a.diag[tens * (uint64_t)a.diag_stride + e];
             cur = tens;
         }
         const int64_t ob = outer_offset(a, o);
@@ -601,7 +601,8 @@ using namespace pw;
 extern "C" int pw_dense_apply(int gemm, const pw_dense_desc* desc, uint64_t n_tensors, float* d_tensors,
                               const float* d_ops, const float* d_diag, void* stream) {
     if (!desc) return set_error(PW_ERR_ARG, "null descriptor");
-    if (gemm < PW_GEMM_FP32 || gemm > PW_GEMM_SPLIT3) return set_error(PW_ERR_ARG, "unknown gemm kind");
+    if (gemm != PW_GEMM_FP32 && gemm != PW_GEMM_BF16 && gemm != PW_GEMM_SPLIT2 && gemm != PW_GEMM_SPLIT3)
+        return set_error(PW_ERR_ARG, "unknown gemm kind");
     const pw_dense_desc& d = *desc;
     if (d.tile_bits != 5 && d.tile_bits != 6) return set_error(PW_ERR_ARG, "tile_bits must be 5 or 6");
     if (d.width_bits < d.tile_bits + 7 || d.width_bits > 31)
@@ -631,6 +632,7 @@ extern "C" int pw_dense_apply(int gemm, const pw_dense_desc* desc, uint64_t n_te
     for (int b = 0; b < a.W; ++b)
         if (!((used >> b) & 1)) a.outer_pos[a.nouter++] = b;
     a.ndiag = d.n_diag;
+    a.diag_stride = 32 * d.n_diag;
     for (int i = 0; i < a.ndiag; ++i) {
         if (d.diag_bits[i] < 0 || d.diag_bits[i] > 5) return set_error(PW_ERR_ARG, "diag_bits must be in 0..5");
         a.diag_nb[i] = d.diag_bits[i];

@@ -13,7 +13,8 @@ namespace pw {
 struct DenseArgs {
     float2* L;             // ntens tensors of 2^W complex entries, updated in place
     const float2* ops;     // ntens operators of 2^k x 2^k entries, Op[t'][t] at t' * 2^k + t
-    const float2* diag;    // ntens x ndiag x 32 diagonal-factor tables
+    const float2* diag;    // per tensor diag_stride entries: ndiag tables of 32
+    int diag_stride;
     uint64_t ntens;
     int W, k;
     int swz;               // 1: entry i stored at i ^ ((i >> 4) & 15)

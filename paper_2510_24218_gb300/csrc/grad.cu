@@ -153,7 +153,17 @@ int run_terms(const pw_circuit* base, const std::vector<Term>& terms, int ncol, 
     // each lane holds n_strings * (ncol + 1) complex values: at most 1 GiB for all lanes
     const uint64_t lane_bytes = n_strings * (uint64_t)(ncol + 1) * sizeof(double2);
     const int by_memory = (int)std::max<uint64_t>(1, std::min<uint64_t>(kMaxLanes, (uint64_t(1) << 30) / lane_bytes));
-    const int n_lanes = std::max(1, std::min({kMaxLanes, hw, n_terms, by_memory}));
+    // plans on the HBM engine hold frontier buffers of up to 16 GB each: their
+    // terms run one after another, each plan released after its term
+    bool hbm = false;
+    {
+        pw_plan* probe = nullptr;
+        if (pw_plan_build(base, opts, &probe) == PW_OK) {
+            hbm = probe->hp.engine == 1;
+            pw_plan_destroy(probe);
+        }
+    }
+    const int n_lanes = hbm ? 1 : std::max(1, std::min({kMaxLanes, hw, n_terms, by_memory}));
 
     cudaEvent_t ready = nullptr;
     if ((e = cudaEventCreateWithFlags(&ready, cudaEventDisableTiming)) != cudaSuccess)
@@ -228,7 +238,7 @@ int run_terms(const pw_circuit* base, const std::vector<Term>& terms, int ncol, 
             }
         }
     };
-    const int round = n_lanes * kRoundPerLane;
+    const int round = hbm ? 1 : n_lanes * kRoundPerLane;
     for (int b = 0; b < n_terms; b += round) {
         const int e_ = std::min(n_terms, b + round);
         std::vector<std::thread> pool;

@@ -106,7 +106,8 @@ int pw_plan_build(const pw_circuit* c, const pw_plan_opts* opts, pw_plan** out) 
         delete plan;
         return rc;
     }
-    int tpc = choose_threads(plan->hp, o.threads_per_chain);
+    // (the HBM engine streams frontiers from HBM in its readouts: 256 threads per chain)
+    int tpc = plan->hp.engine == 1 && o.threads_per_chain <= 0 ? 256 : choose_threads(plan->hp, o.threads_per_chain);
     if (tpc < 0) {
         delete plan;
         return set_error(PW_ERR_ARG, "threads_per_chain must be a power of two in 32..256");
@@ -123,7 +124,11 @@ int pw_plan_build(const pw_circuit* c, const pw_plan_opts* opts, pw_plan** out) 
             delete plan;
             return set_error(PW_ERR_ARG, "ctas_per_chain must be 0, 2, 4 or 8");
         }
-        if ((forced > 1 || make_layout(hp, csz).group_bytes > 200 * 1024) && hp.hdr.P >= 1) {
+        if (hp.engine == 1 && forced > 1) {
+            delete plan;
+            return set_error(PW_ERR_ARG, "ctas_per_chain applies to the on-chip engine only");
+        }
+        if (hp.engine == 0 && (forced > 1 || make_layout(hp, csz).group_bytes > 200 * 1024) && hp.hdr.P >= 1) {
             int wloc = hp.precision == PW_PREC_FP64 ? 13 : 14;
             if (forced > 1) wloc = hp.W - (forced == 2 ? 1 : forced == 4 ? 2 : 3);
             const int c = hp.W - wloc;
@@ -176,6 +181,11 @@ int pw_plan_stats(const pw_plan* plan, pw_plan_stats_t* s) {
     s->ctas_per_chain = hp.ctas_per_chain;
     s->chains_per_cta = gpc;
     s->smem_bytes_per_cta = L.group_bytes * gpc;
+    s->engine = hp.engine == 1 ? PW_ENGINE_HBM : PW_ENGINE_ONCHIP;
+    s->gemm = hp.gemm;
+    s->dense_tile_bits = hp.dense_k;
+    s->dense_passes_per_sample = hp.dense_passes_per_sample;
+    s->dense_flops_per_sample = hp.dense_flops_per_sample;
     return PW_OK;
 }
 
@@ -187,7 +197,7 @@ int pw_plan_exec_order(const pw_plan* plan, int* order) {
 
 void pw_plan_destroy(pw_plan* plan) {
     if (!plan) return;
-    if (plan->d_blob || plan->d_counters || plan->d_stage || plan->d_out_wire || plan->d_in_wire) {
+    if (plan->d_blob || plan->d_counters || plan->d_stage || plan->d_out_wire || plan->d_in_wire || plan->d_dense) {
         int cur = -1;
         cudaGetDevice(&cur);
         if (plan->device >= 0 && plan->device != cur) cudaSetDevice(plan->device);
@@ -196,6 +206,7 @@ void pw_plan_destroy(pw_plan* plan) {
         if (plan->d_stage) cudaFree(plan->d_stage);
         if (plan->d_out_wire) cudaFree(plan->d_out_wire);
         if (plan->d_in_wire) cudaFree(plan->d_in_wire);
+        if (plan->d_dense) cudaFree(plan->d_dense);
         if (plan->device >= 0 && plan->device != cur && cur >= 0) cudaSetDevice(cur);
     }
     delete plan;

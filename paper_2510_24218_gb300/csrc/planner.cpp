@@ -433,6 +433,123 @@ int fuse_range(HostPlan& hp, int b, int e, int* nst_out) {
     return tab;
 }
 
+// Group the micro-ops [b, e) of a forward block program of a dense layer into
+// dense passes (executed as GEMMs on the HBM-resident frontier): the 2x2
+// matrices of a pass act on at most kd distinct bits, its tile (padded to
+// exactly kd bits with free high bits: the operator is the identity on them);
+// diagonal factors whose bits all lie in the tile are composed into the
+// pass's dense operator in program order; diagonal factors that also read
+// other bits are deferred to the pass's epilogue, which is exact because they
+// commute with every later matrix of the pass that does not act on one of
+// their bits (a matrix that would ends the pass first). At most four deferred
+// factors, each over at most five bits, per pass. Stage tables are laid out
+// as in fuse_range (a matrix 4 entries, a diagonal 2^bits).
+int fuse_dense(HostPlan& hp, int b, int e, int kd, int W, int* nst_out) {
+    int tab = 0;
+    int i = b;
+    const int st0 = (int)hp.stages.size();
+    auto uniq_bits = [&](const DevMicroOp& o) {
+        std::vector<int> u;
+        for (int j = 0; j < o.nbits; ++j)
+            if (std::find(u.begin(), u.end(), (int)o.bits[j]) == u.end()) u.push_back(o.bits[j]);
+        return u;
+    };
+    while (i < e) {
+        DevFused f{};
+        f.st_begin = (int)hp.stages.size();
+        std::vector<int> tiles;
+        std::vector<std::vector<int>> sbits;   // per stage: diagonal bits
+        std::vector<char> sepi;                // per stage: deferred to the epilogue
+        int n_epi = 0;
+        while (i < e) {
+            const DevMicroOp& o = hp.micro[i];
+            const int nst = (int)sbits.size();
+            if (nst == 250) break;
+            if (o.kind == MK_MAT1) {
+                const int bit = o.bits[0];
+                bool blocked = false;
+                for (int s2 = 0; s2 < nst; ++s2)
+                    if (sepi[s2] && std::find(sbits[s2].begin(), sbits[s2].end(), bit) != sbits[s2].end()) blocked = true;
+                if (blocked) break;
+                auto it = std::find(tiles.begin(), tiles.end(), bit);
+                int k;
+                if (it == tiles.end()) {
+                    if ((int)tiles.size() == kd) break;
+                    tiles.push_back(bit);
+                    k = (int)tiles.size() - 1;
+                } else {
+                    k = (int)(it - tiles.begin());
+                }
+                DevStage st{};
+                st.type = ST_MAT;
+                st.arg = (uint8_t)k;
+                st.op_begin = i;
+                st.op_end = i + 1;
+                const int rc = o.recipe;
+                st.form = rc == RC_EXPAND ? MF_EXPAND : (rc == RC_SUMOUT1 || rc == RC_SUMOUT_MIX) ? MF_ROW0 : MF_GENERAL;
+                hp.stages.push_back(st);
+                sbits.emplace_back();
+                sepi.push_back(0);
+                ++i;
+                continue;
+            }
+            const std::vector<int> X = uniq_bits(o);
+            bool inside = true;
+            for (int x : X) inside = inside && std::find(tiles.begin(), tiles.end(), x) != tiles.end();
+            // merge into the previous stage: a diagonal of the same kind, at most 5 bits
+            if (nst > 0 && hp.stages.back().type == ST_DIAG && (bool)sepi.back() == !inside) {
+                std::vector<int> u = sbits.back();
+                for (int x : X)
+                    if (std::find(u.begin(), u.end(), x) == u.end()) u.push_back(x);
+                if (u.size() <= 5) {
+                    sbits.back() = u;
+                    hp.stages.back().op_end = i + 1;
+                    ++i;
+                    continue;
+                }
+            }
+            if (!inside && n_epi == 4) break;
+            DevStage st{};
+            st.type = ST_DIAG;
+            st.op_begin = i;
+            st.op_end = i + 1;
+            st.epi = inside ? 0 : 1;
+            hp.stages.push_back(st);
+            sbits.push_back(X);
+            sepi.push_back(inside ? 0 : 1);
+            if (!inside) ++n_epi;
+            ++i;
+        }
+        // pad the tile with free high bits
+        for (int bit = W - 1; (int)tiles.size() < kd && bit >= 0; --bit)
+            if (std::find(tiles.begin(), tiles.end(), bit) == tiles.end()) tiles.push_back(bit);
+        f.ntb = (uint8_t)kd;
+        for (int k = 0; k < kd; ++k) f.tbits[k] = (uint8_t)tiles[k];
+        f.nst = (uint8_t)sbits.size();
+        for (int s2 = 0; s2 < f.nst; ++s2) {
+            DevStage& st = hp.stages[f.st_begin + s2];
+            for (int k = 0; k < 4; ++k) st.tpos[k] = 0xFF;
+            st.tab_off = tab;
+            if (st.type == ST_MAT) {
+                tab += 4;
+                continue;
+            }
+            const std::vector<int>& db = sbits[s2];
+            st.arg = (uint8_t)db.size();
+            for (size_t j = 0; j < db.size(); ++j) st.dbits[j] = (uint8_t)db[j];
+            tab += 1 << db.size();
+            for (int k = st.op_begin; k < st.op_end; ++k) {
+                DevMicroOp& o = hp.micro[k];
+                for (int j = 0; j < o.nbits; ++j)
+                    o.fpos[j] = (uint8_t)(std::find(db.begin(), db.end(), (int)o.bits[j]) - db.begin());
+            }
+        }
+        hp.fused.push_back(f);
+    }
+    *nst_out = (int)hp.stages.size() - st0;
+    return tab;
+}
+
 // ---------------------------------------------------------------------------
 // Host precompute of the tables of noiseless plans. Without channels the only
 // chain-dependent inputs of a stage's table are the current bits of at most a
@@ -904,9 +1021,29 @@ int build_plan(const pw_circuit* c, const pw_plan_opts& opts, HostPlan& hp) {
     }
     const int S = std::max(1, sw.nslots);
     std::vector<int> blk = sw.blk;
-    if (P >= 1 && S * P > 24)
+    // engine: the frontier in shared memory (one CTA or a cluster of up to 8
+    // holds 2^17 FP32 entries), or in HBM with the wide layers' forward passes
+    // run as dense GEMMs (FP32 plans)
+    if (opts.engine != PW_ENGINE_AUTO && opts.engine != PW_ENGINE_ONCHIP && opts.engine != PW_ENGINE_HBM)
+        return set_error(PW_ERR_ARG, "unknown engine");
+    if (opts.gemm != PW_GEMM_SPLIT3 && opts.gemm != PW_GEMM_SPLIT2 && opts.gemm != PW_GEMM_BF16 &&
+        opts.gemm != PW_GEMM_FP32)
+        return set_error(PW_ERR_ARG, "unknown gemm kind");
+    if (opts.engine == PW_ENGINE_HBM && hp.precision != PW_PREC_FP32)
+        return set_error(PW_ERR_UNSUPPORTED, "the HBM engine runs FP32 plans only");
+    const bool hbm = P >= 1 && hp.precision == PW_PREC_FP32 &&
+                     (opts.engine == PW_ENGINE_HBM || (opts.engine == PW_ENGINE_AUTO && S * P > 17));
+    hp.engine = hbm ? 1 : 0;
+    hp.gemm = opts.gemm;
+    if (P >= 1 && !hbm && S * P > 24)
         return set_error(PW_ERR_TOO_LARGE, "frontier tensor of 2^" + std::to_string(S * P) +
-                                               " entries per chain exceeds this plan family's limit (2^24)");
+                                               " entries per chain exceeds the on-chip engine's limit (2^24)");
+    if (P >= 1 && hbm && S * P > 30)
+        return set_error(PW_ERR_TOO_LARGE, "frontier tensor of 2^" + std::to_string(S * P) +
+                                               " entries per chain exceeds the HBM engine's limit (2^30)");
+    // dense layers: the forward frontier of layer m has 2^(S m) entries; its
+    // passes become GEMMs of 128-row tiles with 2^kd-entry rows
+    auto dense_k = [&](int m) { return !hbm ? 0 : S * m >= 14 ? 6 : S * m >= 12 ? 5 : 0; };
 
     auto gates_between = [&](int a, int b, int level) -> std::vector<int> {
         auto it = pair_gates.find({std::min(a, b), std::max(a, b), level});
@@ -998,7 +1135,8 @@ int build_plan(const pw_circuit* c, const pw_plan_opts& opts, HostPlan& hp) {
                 int mb = br.fwd_begin, me = (int)hp.micro.size();
                 br.fwd_begin = (int)hp.fused.size();
                 br.fwd_st = (int)hp.stages.size();
-                br.fwd_tab = fuse_range(hp, mb, me, &br.fwd_nst);
+                const int kd = dense_k(m);
+                br.fwd_tab = kd ? fuse_dense(hp, mb, me, kd, S * m, &br.fwd_nst) : fuse_range(hp, mb, me, &br.fwd_nst);
                 br.fwd_end = (int)hp.fused.size();
             }
             // backward (R_k -> R_{k-1}); not needed for k = 0
@@ -1119,6 +1257,22 @@ int build_plan(const pw_circuit* c, const pw_plan_opts& opts, HostPlan& hp) {
         }
     }
     hp.flops_per_sample = flops;
+    // dense passes: each a GEMM of 2^(S m) entries x 2^kd complex multiply-adds
+    hp.hdr.dense_mask = 0;
+    hp.hdr.dense_npass = 0;
+    for (int m = 1; m <= P; ++m) {
+        const int kd = dense_k(m);
+        if (!kd) continue;
+        hp.hdr.dense_mask |= 1 << m;
+        hp.dense_k = kd;
+        for (int k = 0; k < K; ++k) {
+            const DevBlockRange& br = hp.block_ranges[(size_t)m * K + k];
+            const int np = br.fwd_end - br.fwd_begin;
+            hp.hdr.dense_npass = std::max(hp.hdr.dense_npass, np);
+            hp.dense_passes_per_sample += np;
+            hp.dense_flops_per_sample += np * std::ldexp(8.0, S * m + kd);
+        }
+    }
     // the amplitude of the whole circuit contracts only the last layer's
     // forward sweep, up to the block of the last gate
     {

@@ -92,15 +92,16 @@ struct DevStage {
     uint8_t tpos[4];     // ST_DIAG: position in dbits of tile bit k, 0xFF if absent
     uint8_t ndep;        // precomputed table: chain bits it depends on (0..4); 0xFF: built at run time
     uint8_t form;        // ST_MAT: MatForm
+    uint8_t epi;         // dense pass: a diagonal factor applied after the pass's operator
     int32_t op_begin, op_end;   // constituent micro-ops
     int32_t tab_off;            // complex entries from the start of the block's table area
     int16_t dep[4];             // qubits whose current bits select the variant
     int32_t var_off;            // first entry of variant 0 in the precomputed tables
 };
 struct DevFused {
-    uint8_t ntb;         // tile bits (0..4)
-    uint8_t tbits[4];
-    uint8_t nst;         // stages (1..8)
+    uint8_t ntb;         // tile bits (0..4; a dense pass: 5 or 6)
+    uint8_t tbits[8];
+    uint8_t nst;         // stages (1..8; a dense pass: any number)
     uint8_t pad[2];
     int32_t st_begin;    // first DevStage
 };
@@ -193,6 +194,8 @@ struct DevPlanHeader {
     int32_t max_stages;        // max stages of one block program
     int32_t clean_tables;      // noisy plan whose variant tables assume Kraus pick 0 everywhere
     int32_t amp_exp;           // power of two of every amplitude left out of the tables
+    int32_t dense_mask;        // bit m: layer m's forward passes are dense GEMM passes (HBM frontier)
+    int32_t dense_npass;       // most dense passes of one forward block program
 };
 
 // Offsets (in bytes) of the arrays inside the device blob.
@@ -253,6 +256,11 @@ struct HostPlan {
     int chains_per_cta = 1;
     int chains_per_launch = 0;
     int ctas_per_chain = 1;               // > 1: one thread-block cluster per chain
+    int engine = 0;                       // 1: the frontier lives in HBM, dense layers run GEMM passes
+    int gemm = PW_GEMM_SPLIT3;            // arithmetic of the dense passes
+    int dense_k = 0;                      // tile bits of the widest dense layer's passes
+    double dense_flops_per_sample = 0.0;  // real flops of the dense passes (dense operators) per sample
+    double dense_passes_per_sample = 0.0;
     int wloc = 0;                         // log2 of the frontier entries per CTA then
     size_t smem_per_chain = 0;
     bool noisy = false;
@@ -280,6 +288,11 @@ struct pw_plan {
     std::vector<int> out_wire;
     int* d_out_wire = nullptr;
     int* d_in_wire = nullptr;   // the inverse map: wire w holds qubit d_in_wire[w]
+    // HBM engine (hp.engine == 1): frontiers, environments, saved chain states,
+    // dense operators, operator images, error flag, for dense_chains chains
+    void* d_dense = nullptr;
+    size_t dense_bytes = 0;
+    uint64_t dense_chains = 0;
 };
 
 namespace pw {

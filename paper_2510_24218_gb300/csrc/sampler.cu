@@ -22,6 +22,7 @@
 #include <cstring>
 #include <mutex>
 
+#include "dense.h"
 #include "pw_internal.h"
 #include "smem_layout.h"
 
@@ -110,10 +111,24 @@ struct KParams {
     int amp_layer, amp_block, amp_pos;
     int cr;             // CTAs (one thread-block cluster) per chain; 1: one group per chain
     int wloc;           // log2 of the frontier entries held by one CTA when cr > 1
+    // HBM engine (hdr.dense_mask != 0 or hbm = 1): the frontiers and the right
+    // environments live in HBM; a launch runs every chain from yield point
+    // y_from (-1: the start) to the next one, where it saves the chain state
+    int hbm;
+    int y_from;
+    int ybase[8];                 // first yield point of layer m
+    void* gL;                     // frontiers: chain c at layer m at gL + c * 2^(S m) entries
+    void* gR;                     // right environments: chain c at gR + c * strideR entries
+    uint64_t strideR;
+    unsigned char* gState;        // saved chain states, state_bytes each
+    int state_off, state_bytes;   // the saved part of a group's shared memory
+    void* gOps;                   // dense operators: pass i, chain c at (i * nch + c) * 2^(2k) entries
+    void* gDiag;                  // epilogue tables: (i * nch + c) * 4 * 32 entries
+    uint64_t nch;                 // chains the HBM buffers hold
 };
 
 enum { MODE_SAMPLE = 0, MODE_AMP = 1 };
-enum { CNT_NEAR = 0, CNT_ZERO = 1 };
+enum { CNT_NEAR = 0, CNT_ZERO = 1, CNT_DENSE = 2 };   // CNT_DENSE: a bounded wait of a dense pass ran out
 
 template <typename T> __device__ __forceinline__ const T* P_(const KParams& p, int64_t off) {
     return reinterpret_cast<const T*>(p.blob + off);
@@ -146,6 +161,7 @@ struct Grp {
 template <typename R> struct Chain {
     using C = typename CT<R>::T;
     C* L;         // frontier tensor, 2^W (top legs in the low S bits)
+    C* ob;        // HBM engine: the dense operator being composed (shared memory)
     C* Rt;        // right environments, K x 2^Wl
     int* Rexp;    // their power-of-two exponents
     C* rowdot;    // 2^S
@@ -1218,21 +1234,9 @@ __device__ void run_chain(const KParams& p, const Chain<R>& ch, int gid, int lt,
     G.sync();
 }
 
-// WIDE: the same kernel for CTAs of at most 64 threads with at most 5 of them
-// per SM (the chains that shared memory admits on the 6x6 grid): up to 204
-// registers per thread instead of 128, no occupancy lost when shared memory
-// is the limit.
-template <typename R, bool WIDE = false>
-__global__ void __launch_bounds__(WIDE ? 64 : 512, WIDE ? 5 : 1) pw_chain_kernel(const KParams p) {
+// The per-chain view of a group's shared memory.
+template <typename R> __device__ __forceinline__ Chain<R> make_chain(const KParams& p, unsigned char* g) {
     using C = typename CT<R>::T;
-    extern __shared__ __align__(16) unsigned char smem[];
-    // The launches of one sampling call take disjoint chains and read only the
-    // plan: the next one may start on the SMs this one no longer needs (it is
-    // launched as a programmatic dependent of this one; elsewhere a no-op).
-    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-    const int gid = threadIdx.x / p.tpc;
-    const int lt = threadIdx.x - gid * p.tpc;
-    unsigned char* g = smem + (size_t)gid * p.sm.group_bytes;
     Chain<R> ch;
     ch.L = reinterpret_cast<C*>(g + p.sm.L);
     ch.Rt = reinterpret_cast<C*>(g + p.sm.R);
@@ -1258,6 +1262,266 @@ __global__ void __launch_bounds__(WIDE ? 64 : 512, WIDE ? 5 : 1) pw_chain_kernel
     ch.pd = reinterpret_cast<double2*>(g + p.sm.pd);
     ch.rL = reinterpret_cast<C**>(g + p.sm.rlp);
     ch.cmax = reinterpret_cast<float*>(g + p.sm.cmax);
+    ch.ob = ch.L;
+    ch.rank = 0;
+    return ch;
+}
+
+// ------------------------------------------------------------ HBM engine
+// Dense operators of the passes of block program br (HBM engine): every pass
+// is the product of its stages restricted to its tile bits, Op[t'][t] over
+// the 2^k tile settings, composed in shared memory one column per thread
+// (columns are independent: no barrier between stages), then written to
+// HBM for the GEMM kernels; the stages deferred to the epilogue (diagonal
+// factors that read bits outside the tile) write their tables instead.
+__device__ void compose_dense(const KParams& p, const Chain<float>& ch, const Grp& G, const DevBlockRange& br,
+                              uint64_t chain) {
+    const DevFused* F = P_<DevFused>(p, p.off.fused);
+    const float2 one = make_float2(1.f, 0.f), zero = make_float2(0.f, 0.f);
+    float2* gops = static_cast<float2*>(p.gOps);
+    float2* gdiag = static_cast<float2*>(p.gDiag);
+    for (int fi = br.fwd_begin; fi < br.fwd_end; ++fi) {
+        const DevFused f = F[fi];
+        const int k = f.ntb, E = 1 << k;
+        const uint64_t slot = (uint64_t)(fi - br.fwd_begin) * p.nch + chain;
+        for (int c = G.lt; c < E; c += G.nt) {
+            float2* col = ch.ob + c;   // Op[r][c] at col[r * E]
+            for (int r = 0; r < E; ++r) col[r * E] = r == c ? one : zero;
+            for (int s2 = 0; s2 < f.nst; ++s2) {
+                const DevStage& st = ch.stg[f.st_begin - br.fwd_st + s2];
+                const float2* tab = ch.tab + st.tab_off;
+                if (st.type == ST_MAT) {
+                    const int bit = 1 << st.arg;
+                    const float2 m00 = tab[0], m01 = tab[1], m10 = tab[2], m11 = tab[3];
+                    for (int r0 = 0; r0 < E; ++r0) {
+                        if (r0 & bit) continue;
+                        const float2 x0 = col[r0 * E], x1 = col[(r0 | bit) * E];
+                        col[r0 * E] = cfma(m00, x0, cmul(m01, x1));
+                        col[(r0 | bit) * E] = cfma(m10, x0, cmul(m11, x1));
+                    }
+                } else if (!st.epi) {
+                    int tpos[5];   // tile index of each table bit
+                    for (int j = 0; j < st.arg; ++j) {
+                        tpos[j] = 0;
+                        for (int t = 0; t < k; ++t)
+                            if (f.tbits[t] == st.dbits[j]) tpos[j] = t;
+                    }
+                    for (int r = 0; r < E; ++r) {
+                        int e = 0;
+                        for (int j = 0; j < st.arg; ++j) e |= ((r >> tpos[j]) & 1) << j;
+                        col[r * E] = cmul(col[r * E], tab[e]);
+                    }
+                }
+            }
+            float2* dst = gops + (slot << (2 * k)) + c;
+            for (int r = 0; r < E; ++r) dst[(size_t)r * E] = col[r * E];
+        }
+        // the epilogue's tables, in stage order, 32 entries each
+        int d = 0;
+        for (int s2 = 0; s2 < f.nst; ++s2) {
+            const DevStage& st = ch.stg[f.st_begin - br.fwd_st + s2];
+            if (st.type != ST_DIAG || !st.epi) continue;
+            const float2* tab = ch.tab + st.tab_off;
+            for (int e = G.lt; e < 32; e += G.nt) gdiag[(slot * 4 + d) * 32 + e] = e < (1 << st.arg) ? tab[e] : zero;
+            ++d;
+        }
+        G.sync();   // (the next pass reuses the operator buffer)
+    }
+}
+
+// The chain program of the HBM engine: the same steps as run_chain, with the
+// frontier and the right environments in HBM and the forward passes of the
+// dense layers left to the GEMM kernels. A launch resumes every chain at
+// yield point p.y_from (restoring its saved state), runs it to the next yield
+// point (block k of a dense layer prepared: tables built, readout factors
+// staged, the block's dense operators written) and saves its state; the host
+// runs the block's passes and launches again. Yield points are numbered over
+// the dense layers' blocks in order (p.ybase[m] = the first of layer m).
+__device__ __forceinline__ void run_chain_hbm(const KParams& p, const Chain<float>& ch0, unsigned char* grp, int gid,
+                                           int lt, uint64_t chain) {
+    using R = float;
+    using C = float2;
+    const DevPlanHeader& h = p.hdr;
+    const int n = h.n, P = h.P, S = h.S, K = h.K;
+    const uint64_t sample_id = p.first + chain;
+    const C one = mk<R>(1, 0);
+    const DevBlockRange* BR = P_<DevBlockRange>(p, p.off.block_ranges);
+    const Grp G{lt, p.tpc, gid, p.tpc, false, false};
+    const bool exact = p.mode == MODE_AMP || p.trace != nullptr;
+    Chain<R> ch = ch0;
+    ch.Rt = static_cast<C*>(p.gR) + chain * p.strideR;
+    uint4* saved = reinterpret_cast<uint4*>(p.gState + chain * (uint64_t)p.state_bytes);
+    uint4* live = reinterpret_cast<uint4*>(grp + p.state_off);
+    const int y0 = p.y_from;
+
+    if (y0 >= 0) {
+        for (int i = lt; i < p.state_bytes / 16; i += p.tpc) live[i] = saved[i];
+        G.sync();
+    } else {
+        for (int q = lt; q < n; q += p.tpc) {
+            ch.x[q] = 0;
+            ch.s[q] = p.mode == MODE_AMP ? (uint8_t)((p.in_bits[chain * h.words + (q >> 6)] >> (q & 63)) & 1ull) : 0;
+        }
+        if (h.has_frame) {
+            for (int i = lt; i < (P + 1) * n; i += p.tpc) ch.xmix[i] = 0;
+            for (int i = lt; i < h.n_cost_gates; i += p.tpc) ch.gframe[i] = 0;
+        }
+        if (h.has_segfac) {
+            const bool starts_clean = h.has_frame && h.clean_tables && p.mode == MODE_SAMPLE;
+            const C* def = reinterpret_cast<const C*>(P_<unsigned char>(p, p.off.segdef_f));
+            for (int i = lt; i < n * (P + 1) * 2; i += p.tpc) ch.segfac[i] = starts_clean ? def[i] : one;
+        }
+        if (lt == 0) {
+            ch.misc[MISC_CLEAN] = 1;
+            ch.misc[MISC_DIRTY_EVENT] = 0;
+        }
+        if (p.mode == MODE_SAMPLE) {
+            const int32_t* rop = P_<int32_t>(p, p.off.row_opid);
+            for (int r = lt; r < h.n_sampled; r += p.tpc) {
+                const double u = draw_u(p.seed, sample_id, (uint32_t)rop[r], 0u);
+                ch.ud[r] = u;
+                ch.uf[r] = (float)u;
+            }
+            const int32_t* opid = P_<int32_t>(p, p.off.mix0_opid);
+            const int8_t* mono = P_<int8_t>(p, p.off.mix_mono);
+            const double* md = P_<double>(p, p.off.mix_d);
+            for (int q = lt; q < n; q += p.tpc) {
+                const double* A = md + (size_t)q * 8;
+                if (mono[q]) {
+                    ch.s[q] = (A[0] != 0.0 || A[1] != 0.0) ? 0 : 1;
+                    continue;
+                }
+                const double p0 = A[0] * A[0] + A[1] * A[1];
+                const double p1 = A[4] * A[4] + A[5] * A[5];
+                const double Pt = p0 + p1;
+                const double u = draw_u(p.seed, sample_id, (uint32_t)opid[q], 0u);
+                ch.s[q] = (u * Pt < p0) ? 0 : 1;
+                if (fabs(u * Pt - p0) < 1e-6 * Pt) atomicAdd(&p.counters[CNT_NEAR], 1ull);
+            }
+        }
+        G.sync();
+    }
+
+    const int mhi = p.mode == MODE_AMP ? p.amp_layer : P;
+    for (int m = 1; m <= mhi; ++m) {
+        const bool skip_layer = p.mode == MODE_AMP && m < p.amp_layer;
+        const bool dense = ((h.dense_mask >> m) & 1) && !skip_layer;
+        const int kend = p.mode == MODE_AMP ? p.amp_block : K - 1;
+        const int yb = p.ybase[m], ny = dense ? kend + 1 : 0;
+        // layers behind the resume point ran in earlier launches
+        if (y0 >= yb + ny && (ny > 0 || y0 >= yb)) continue;
+        const bool resume_here = ny > 0 && y0 >= yb;
+        const int Wl = S * (m - 1), W = S * m;
+        const int NL = 1 << Wl, N = 1 << W;
+        ch.L = static_cast<C*>(p.gL) + chain * ((uint64_t)1 << W);
+        const int kstop = p.mode == MODE_AMP ? p.amp_block : 0;
+        const int w32 = p.tpc < 32 ? p.tpc : 32;
+        auto phase_nt = [&](int e) { return e > 1024 ? p.tpc : (e >= 256 && p.tpc >= 256) ? 128 : w32; };
+        const int ntb = phase_nt(NL), ntf = dense ? p.tpc : phase_nt(N);
+        const Grp GB{lt, ntb, gid, p.tpc, ntb == 32 && p.tpc > 32, false};
+        const Grp GF{lt, ntf, gid, p.tpc, ntf == 32 && p.tpc > 32, false};
+        if (!resume_here) {
+            if (h.has_segfac || h.has_frame) {
+                cost_section<R>(p, ch, G, m, sample_id);
+                if (h.has_frame && !chain_clean<R>(p, ch))
+                    for (int q = lt; q < n; q += p.tpc) ch.xmix[m * n + q] = ch.x[q];
+            }
+            G.sync();
+            if (skip_layer) continue;
+            // backward sweep (right environments in HBM)
+            const bool skip_bwd = m == 1 && !exact;
+            if (skip_bwd && lt < GB.nt) {
+                for (int k = lt; k < K; k += GB.nt) {
+                    ch.Rt[k] = one;
+                    ch.Rexp[k] = 0;
+                }
+            }
+            if (!skip_bwd && lt < GB.nt) {
+                C* RK = ch.Rt + (size_t)(K - 1) * NL;
+                for (int i = lt; i < NL; i += GB.nt) RK[i] = one;
+                if (lt == 0) ch.Rexp[K - 1] = 0;
+                for (int k = K - 1; k > kstop; --k) {
+                    const DevBlockRange br = BR[(size_t)m * K + k];
+                    const C* src = ch.Rt + (size_t)k * NL;
+                    C* dst = ch.Rt + (size_t)(k - 1) * NL;
+                    build_tables<R>(p, ch, GB, br.bwd_st, br.bwd_nst, br.bwd_tab, 0, exact);
+                    GB.sync();
+                    for (int i = lt; i < NL; i += GB.nt) dst[i] = src[i];
+                    GB.sync();
+                    run_passes<R>(p, ch, GB, br.bwd_begin, br.bwd_end, br.bwd_st, dst, Wl);
+                    R mx = 0;
+                    for (int i = lt; i < NL; i += GB.nt) mx = rmax(mx, rmax(rabs(dst[i].x), rabs(dst[i].y)));
+                    mx = group_max<R>(ch, GB, mx);
+                    const int e = scale_exp<R>(mx);
+                    if (e != 0)
+                        for (int i = lt; i < NL; i += GB.nt) {
+                            dst[i].x = scl(dst[i].x, -e);
+                            dst[i].y = scl(dst[i].y, -e);
+                        }
+                    if (lt == 0) ch.Rexp[k - 1] = ch.Rexp[k] + e;
+                    GB.sync();
+                }
+            }
+            G.sync();
+            if (lt < GF.nt) {
+                for (int i = lt; i < N; i += GF.nt) ch.L[i] = mk<R>(i == 0 ? 1 : 0, 0);
+                if (lt == 0) {
+                    ch.misc[0] = 0;
+                    ch.misc[1] = 0;
+                }
+            }
+            G.sync();
+        }
+        if (lt < GF.nt) {
+            const int kstart = resume_here ? y0 - yb : 0;
+            for (int k = kstart; k <= kend; ++k) {
+                const DevBlockRange br = BR[(size_t)m * K + k];
+                if (!(resume_here && k == kstart)) {
+                    const int pend = ch.misc[1];
+                    build_tables<R>(p, ch, GF, br.fwd_st, br.fwd_nst, br.fwd_tab, pend, exact);
+                    build_fslot<R>(p, ch, GF, m, br);
+                    GF.sync();
+                    if (dense) {
+                        // yield: the GEMM kernels run this block's passes
+                        compose_dense(p, ch, GF, br, chain);
+                        for (int i = lt; i < p.state_bytes / 16; i += p.tpc) saved[i] = live[i];
+                        G.sync();
+                        return;
+                    }
+                    run_passes<R>(p, ch, GF, br.fwd_begin, br.fwd_end, br.fwd_st, ch.L, W);
+                }
+                readout_and_sample<R>(p, ch, GF, m, k, br, chain);
+            }
+        }
+        G.sync();
+    }
+    if (p.mode == MODE_AMP) return;
+    if (h.has_frame) cost_section<R>(p, ch, G, P + 1, sample_id);
+    G.sync();
+    for (int w = lt; w < h.words; w += p.tpc) {
+        uint64_t v = 0;
+        for (int b = 0; b < 64 && w * 64 + b < n; ++b) v |= (uint64_t)(ch.s[w * 64 + b] ^ ch.x[w * 64 + b]) << b;
+        p.out_bits[chain * h.words + w] = v;
+    }
+    G.sync();
+}
+
+// WIDE: the same kernel for CTAs of at most 64 threads with at most 5 of them
+// per SM (the chains that shared memory admits on the 6x6 grid): up to 204
+// registers per thread instead of 128, no occupancy lost when shared memory
+// is the limit.
+template <typename R, bool WIDE = false>
+__global__ void __launch_bounds__(WIDE ? 64 : 512, WIDE ? 5 : 1) pw_chain_kernel(const KParams p) {
+    using C = typename CT<R>::T;
+    extern __shared__ __align__(16) unsigned char smem[];
+    // The launches of one sampling call take disjoint chains and read only the
+    // plan: the next one may start on the SMs this one no longer needs (it is
+    // launched as a programmatic dependent of this one; elsewhere a no-op).
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    const int gid = threadIdx.x / p.tpc;
+    const int lt = threadIdx.x - gid * p.tpc;
+    unsigned char* g = smem + (size_t)gid * p.sm.group_bytes;
+    Chain<R> ch = make_chain<R>(p, g);
     if (p.cr > 1) {
         // one chain per cluster of p.cr CTAs (gpc == 1): every CTA keeps a copy
         // of the chain's small state and 1/cr of the frontier
@@ -1274,6 +1538,18 @@ __global__ void __launch_bounds__(WIDE ? 64 : 512, WIDE ? 5 : 1) pw_chain_kernel
     for (uint64_t chain = (uint64_t)blockIdx.x * p.gpc + gid; chain < p.count;
          chain += (uint64_t)gridDim.x * p.gpc)
         run_chain<R>(p, ch, gid, lt, chain);
+}
+
+// The HBM engine's chain kernel (FP32): one group of threads per chain, the
+// chain program of run_chain_hbm from one yield point to the next.
+__global__ void __launch_bounds__(512, 1) pw_chain_hbm_kernel(const KParams p) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int gid = threadIdx.x / p.tpc;
+    const int lt = threadIdx.x - gid * p.tpc;
+    unsigned char* g = smem + (size_t)gid * p.sm.group_bytes;
+    const Chain<float> ch = make_chain<float>(p, g);
+    for (uint64_t chain = (uint64_t)blockIdx.x * p.gpc + gid; chain < p.count; chain += (uint64_t)gridDim.x * p.gpc)
+        run_chain_hbm(p, ch, g, gid, lt, chain);
 }
 
 // ================================================================= host
@@ -1373,8 +1649,164 @@ std::mutex& launch_mutex() {
     return mu;
 }
 
+// Device buffers of the HBM engine for nch chains (kept by the plan and
+// reused; enlarged when a call needs more chains).
+struct HbmBuffers {
+    size_t L, R, state, ops, diag, bimg, total;
+};
+HbmBuffers hbm_sizes(const HostPlan& hp, const SmemLayout& sm, uint64_t nch) {
+    const int S = hp.hdr.S, P = std::max(hp.hdr.P, 1), K = std::max(hp.hdr.K, 1), k = std::max(hp.dense_k, 1);
+    HbmBuffers b{};
+    b.L = align16(nch * (sizeof(float2) << (S * P)));
+    b.R = align16(nch * (size_t)K * (sizeof(float2) << (S * (P - 1))));
+    b.state = align16(nch * (size_t)(sm.group_bytes - sm.R));
+    b.ops = align16((size_t)std::max(hp.hdr.dense_npass, 1) * nch * (sizeof(float2) << (2 * k)));
+    b.diag = align16((size_t)std::max(hp.hdr.dense_npass, 1) * nch * 4 * 32 * sizeof(float2));
+    b.bimg = align16(nch * dense_bimage_bytes(hp.gemm, k));
+    b.total = b.L + b.R + b.state + b.ops + b.diag + b.bimg;
+    return b;
+}
+
+// The HBM engine: launches of the chain kernel that run every chain of a
+// batch from one yield point to the next, with the dense passes of the
+// prepared block (GEMMs on the frontiers in HBM) in between.
+int launch_hbm(pw_plan* plan, KParams& kp, cudaStream_t st, uint64_t* launches) {
+    const HostPlan& hp = plan->hp;
+    const int S = hp.hdr.S, P = hp.hdr.P, K = hp.hdr.K;
+    kp.sm = make_layout(hp, sizeof(float2));
+    kp.tpc = hp.threads_per_chain;
+    kp.cr = 1;
+    kp.wloc = 0;
+    kp.hbm = 1;
+    if (kp.sm.group_bytes > 227 * 1024) return set_error(PW_ERR_TOO_LARGE, "per-chain shared memory exceeds 227 KB");
+    const int gpc = groups_per_cta(kp.tpc, kp.sm.group_bytes);
+    kp.gpc = gpc;
+    const int threads = kp.tpc * gpc;
+    const size_t smem = (size_t)kp.sm.group_bytes * gpc;
+    void (*kern)(const KParams) = pw_chain_hbm_kernel;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
+    cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    int dev = plan->device, nsm = 0, occ = 0;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, smem);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
+    occ = std::max(occ, 1);
+    // chains per batch: the plan's, else up to 8192 (and frontiers of at most 16 GB)
+    const uint64_t by_mem = std::max<uint64_t>(1, (uint64_t(16) << 30) / (sizeof(float2) << (S * P)));
+    const uint64_t per_launch = hp.chains_per_launch > 0 ? (uint64_t)hp.chains_per_launch
+                                                         : std::min<uint64_t>({kp.count, 8192, by_mem});
+    const HbmBuffers hb = hbm_sizes(hp, kp.sm, per_launch);
+    if (!plan->d_dense || plan->dense_chains < per_launch) {
+        if (plan->d_dense) cudaFree(plan->d_dense);
+        plan->d_dense = nullptr;
+        plan->dense_chains = 0;
+        if ((e = cudaMalloc(&plan->d_dense, hb.total)) != cudaSuccess)
+            return set_error(PW_ERR_OOM, std::string("HBM engine buffers (") + std::to_string(hb.total >> 20) +
+                                             " MiB): " + cudaGetErrorString(e));
+        plan->dense_bytes = hb.total;
+        plan->dense_chains = per_launch;
+    }
+    const uint64_t nch = plan->dense_chains;
+    const HbmBuffers ha = hbm_sizes(hp, kp.sm, nch);
+    unsigned char* base = static_cast<unsigned char*>(plan->d_dense);
+    kp.gL = base;
+    kp.gR = base + ha.L;
+    kp.gState = base + ha.L + ha.R;
+    kp.gOps = base + ha.L + ha.R + ha.state;
+    kp.gDiag = base + ha.L + ha.R + ha.state + ha.ops;
+    unsigned char* bimg = base + ha.L + ha.R + ha.state + ha.ops + ha.diag;
+    kp.strideR = (uint64_t)K << (S * std::max(P - 1, 0));
+    kp.state_off = kp.sm.R;
+    kp.state_bytes = kp.sm.group_bytes - kp.sm.R;
+    kp.nch = nch;
+    // yield points: every block of every dense layer that runs
+    const int mhi = kp.mode == MODE_AMP ? kp.amp_layer : P;
+    const int kend = kp.mode == MODE_AMP ? kp.amp_block : K - 1;
+    std::vector<std::pair<int, int>> yields;
+    for (int m = 1; m <= P && m < 8; ++m) {
+        kp.ybase[m] = (int)yields.size();
+        const bool dense = ((hp.hdr.dense_mask >> m) & 1) && m <= mhi && !(kp.mode == MODE_AMP && m < kp.amp_layer);
+        if (dense)
+            for (int k = 0; k <= kend; ++k) yields.push_back({m, k});
+    }
+    // the dense passes' arguments, per yield point
+    const DevBlockRange* BRs = hp.block_ranges.data();
+    const uint64_t total = kp.count, first0 = kp.first;
+    uint64_t* out0 = kp.out_bits;
+    double* tr0 = kp.trace;
+    const uint64_t* in0 = kp.in_bits;
+    double* amp0 = kp.amp_out;
+    for (uint64_t done = 0; done < total; done += per_launch) {
+        const uint64_t cnt = std::min(per_launch, total - done);
+        kp.count = cnt;
+        kp.first = first0 + done;
+        kp.out_bits = out0 ? out0 + done * hp.hdr.words : nullptr;
+        kp.trace = tr0 ? tr0 + done * (uint64_t)hp.hdr.n_sampled * 4 : nullptr;
+        kp.in_bits = in0 ? in0 + done * hp.hdr.words : nullptr;
+        kp.amp_out = amp0 ? amp0 + 2 * done : nullptr;
+        const int grid = (int)std::min<uint64_t>((cnt + gpc - 1) / gpc, (uint64_t)nsm * occ);
+        for (int y = -1; y < (int)yields.size(); ++y) {
+            if (y >= 0) {
+                const int m = yields[y].first, k = yields[y].second;
+                const DevBlockRange& br = BRs[(size_t)m * K + k];
+                for (int fi = br.fwd_begin; fi < br.fwd_end; ++fi) {
+                    const DevFused& f = hp.fused[fi];
+                    const int pi = fi - br.fwd_begin;
+                    DenseArgs a;
+                    std::memset(&a, 0, sizeof(a));
+                    a.L = static_cast<float2*>(kp.gL);
+                    a.ntens = cnt;
+                    a.W = S * m;
+                    a.k = f.ntb;
+                    a.swz = 1;
+                    uint64_t used = 0;
+                    for (int j = 0; j < a.k; ++j) {
+                        a.tile_pos[j] = f.tbits[j];
+                        used |= 1ull << f.tbits[j];
+                    }
+                    for (int b = 0, r = 0; b < a.W && r < 7; ++b)
+                        if (!((used >> b) & 1)) {
+                            a.row_pos[r++] = b;
+                            used |= 1ull << b;
+                        }
+                    for (int b = 0; b < a.W; ++b)
+                        if (!((used >> b) & 1)) a.outer_pos[a.nouter++] = b;
+                    for (int s2 = 0; s2 < f.nst; ++s2) {
+                        const DevStage& sg = hp.stages[f.st_begin + s2];
+                        if (sg.type != ST_DIAG || !sg.epi) continue;
+                        a.diag_nb[a.ndiag] = sg.arg;
+                        for (int j = 0; j < sg.arg; ++j) a.diag_pos[a.ndiag][j] = sg.dbits[j];
+                        ++a.ndiag;
+                    }
+                    a.ops = static_cast<const float2*>(kp.gOps) + (((uint64_t)pi * nch) << (2 * a.k));
+                    a.diag = static_cast<const float2*>(kp.gDiag) + (uint64_t)pi * nch * 4 * 32;
+                    a.diag_stride = 4 * 32;
+                    a.err = reinterpret_cast<int*>(kp.counters + CNT_DENSE);
+                    const int rc = dense_run(hp.gemm, a, bimg, st);
+                    if (rc) return rc;
+                    if (launches) *launches += hp.gemm == PW_GEMM_FP32 ? 1 : 2;
+                }
+            }
+            kp.y_from = y;
+            cudaLaunchConfig_t cfg = {};
+            cfg.gridDim = dim3((unsigned)grid);
+            cfg.blockDim = dim3((unsigned)threads);
+            cfg.dynamicSmemBytes = smem;
+            cfg.stream = st;
+            e = cudaLaunchKernelEx(&cfg, kern, kp);
+            if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
+            if (launches) ++*launches;
+        }
+    }
+    return PW_OK;
+}
+
 template <typename R> int launch(pw_plan* plan, KParams& kp, cudaStream_t st, uint64_t* launches) {
     std::lock_guard<std::mutex> attr_lock(launch_mutex());
+    if constexpr (sizeof(R) == 4) {
+        if (plan->hp.engine == 1) return launch_hbm(plan, kp, st, launches);
+    }
     const HostPlan& hp = plan->hp;
     const size_t csz = 2 * sizeof(R);
     kp.sm = make_layout(hp, csz);
@@ -1569,6 +2001,7 @@ int pw_sample(pw_plan* plan, uint64_t seed, uint64_t first_sample, uint64_t n_sa
         stats->near_boundary = h[CNT_NEAR];
         stats->zero_mass = h[CNT_ZERO];
         stats->launches = launches;
+        if (h[CNT_DENSE]) return set_error(PW_ERR_TIMEOUT, "a bounded wait of a tensor-core pass ran out");
     }
     return PW_OK;
 }
@@ -1578,7 +2011,7 @@ int pw_plan_autotune(pw_plan* plan, uint64_t trial_samples, void* stream, int* c
     HostPlan& hp = plan->hp;
     const int keep = hp.threads_per_chain;
     if (chosen) *chosen = keep;
-    if (hp.ctas_per_chain > 1) return PW_OK;   // a cluster's CTAs keep their 512 threads
+    if (hp.ctas_per_chain > 1 || hp.engine == 1) return PW_OK;   // clusters and the HBM engine keep their shape
     int rc = ensure_device_plan(plan);
     if (rc) return rc;
     const uint64_t cpl = hp.chains_per_launch > 0 ? (uint64_t)hp.chains_per_launch : 4096;
@@ -1795,8 +2228,8 @@ extern "C" int pw_sample_static(const pw_plan* plan, uint64_t seed, uint64_t fir
     if (stats) std::memset(stats, 0, sizeof(*stats));
     if (n_samples == 0) return PW_OK;
     const HostPlan& hp = plan->hp;
-    if (hp.ctas_per_chain > 1)
-        return set_error(PW_ERR_UNSUPPORTED, "pw_sample_static runs plans of one CTA per chain only");
+    if (hp.ctas_per_chain > 1 || hp.engine == 1)
+        return set_error(PW_ERR_UNSUPPORTED, "pw_sample_static runs on-chip plans of one CTA per chain only");
     if (!plan->out_wire.empty())
         return set_error(PW_ERR_UNSUPPORTED, "pw_sample_static does not run circuits with SWAP-class gates");
     DevPlanOffsets off{};

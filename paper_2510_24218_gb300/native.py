@@ -33,7 +33,7 @@ class PwError(RuntimeError):
 class PlanOpts(C.Structure):
     _fields_ = [("precision", C.c_int), ("order", C.c_int), ("max_block", C.c_int),
                 ("threads_per_chain", C.c_int), ("chains_per_launch", C.c_int),
-                ("ctas_per_chain", C.c_int), ("reserved", C.c_int * 6)]
+                ("ctas_per_chain", C.c_int), ("engine", C.c_int), ("gemm", C.c_int), ("reserved", C.c_int * 4)]
 
 
 class PlanStats(C.Structure):
@@ -42,13 +42,18 @@ class PlanStats(C.Structure):
                 ("sampled_gates", C.c_int), ("threads_per_chain", C.c_int), ("chains_per_cta", C.c_int),
                 ("smem_bytes_per_cta", C.c_int), ("noisy", C.c_int), ("flops_per_sample", C.c_double),
                 ("amps_per_sample", C.c_double),
-                ("device_bytes", C.c_double), ("ctas_per_chain", C.c_int), ("flops_per_amplitude", C.c_double)]
+                ("device_bytes", C.c_double), ("ctas_per_chain", C.c_int), ("flops_per_amplitude", C.c_double),
+                ("engine", C.c_int), ("gemm", C.c_int), ("dense_tile_bits", C.c_int),
+                ("dense_passes_per_sample", C.c_double), ("dense_flops_per_sample", C.c_double)]
 
 
-PW_GEMM_FP32 = 0
-PW_GEMM_BF16 = 1
-PW_GEMM_SPLIT2 = 2
-PW_GEMM_SPLIT3 = 3
+PW_GEMM_SPLIT3 = 0
+PW_GEMM_SPLIT2 = 1
+PW_GEMM_BF16 = 2
+PW_GEMM_FP32 = 3
+PW_ENGINE_AUTO = 0
+PW_ENGINE_ONCHIP = 1
+PW_ENGINE_HBM = 2
 
 
 class DenseDesc(C.Structure):
@@ -184,11 +189,12 @@ def pw_circuit_destroy(circ):
 # --------------------------------------------------------------------- plan
 
 def pw_plan_build(circ, precision=PW_PREC_FP32, order=PW_ORDER_AUTO, max_block=0, threads_per_chain=0,
-                  chains_per_launch=0, ctas_per_chain=0):
+                  chains_per_launch=0, ctas_per_chain=0, engine=PW_ENGINE_AUTO, gemm=PW_GEMM_SPLIT3):
     o = PlanOpts()
     o.precision, o.order, o.max_block = precision, order, max_block
     o.threads_per_chain, o.chains_per_launch = threads_per_chain, chains_per_launch
     o.ctas_per_chain = ctas_per_chain
+    o.engine, o.gemm = engine, gemm
     h = C.c_void_p()
     _check(load_library().pw_plan_build(circ, C.byref(o), C.byref(h)))
     return h

@@ -13,7 +13,8 @@ pytestmark = pytest.mark.gpu
 # relative error of every tensor, ||y - y_ref|| / ||y_ref||: FP32-level for the
 # FP32 arm and the three-term split (24-bit inputs, products to 2^-24), about
 # 2^-17 per input term for the two-term split, 2^-9 for plain BF16
-TOL = {0: 2e-6, 3: 2e-6, 2: 4e-5, 1: 1.5e-2}
+FP32, BF16, SPLIT2, SPLIT3 = 3, 2, 1, 0   # PW_GEMM_* of include/pw.h
+TOL = {FP32: 2e-6, SPLIT3: 2e-6, SPLIT2: 4e-5, BF16: 1.5e-2}
 
 
 def _swz(i):
@@ -41,7 +42,7 @@ def _reference(W, tile, diag_pos, x, op, diag):
     return y
 
 
-@pytest.mark.parametrize("gemm", [0, 3, 2, 1])
+@pytest.mark.parametrize("gemm", [FP32, SPLIT3, SPLIT2, BF16])
 @pytest.mark.parametrize("k", [5, 6])
 @pytest.mark.parametrize("swizzled", [0, 1])
 def test_dense_pass_matches_the_oracle(gemm, k, swizzled):
@@ -69,7 +70,7 @@ def test_dense_pass_matches_the_oracle(gemm, k, swizzled):
         assert err < TOL[gemm], (gemm, k, swizzled, b, err)
 
 
-@pytest.mark.parametrize("gemm", [0, 3])
+@pytest.mark.parametrize("gemm", [FP32, SPLIT3])
 def test_dense_pass_many_tiles_and_identity(gemm):
     """An identity operator with no diagonal leaves 131 tensors of 2^14
     entries as they are (to FP32 rounding of the split), over many tiles per
@@ -88,7 +89,7 @@ def test_dense_pass_many_tiles_and_identity(gemm):
     assert np.abs(got - x).max() <= 1e-7 * np.abs(x).max()
 
 
-@pytest.mark.parametrize("gemm", [0, 3, 1])
+@pytest.mark.parametrize("gemm", [FP32, SPLIT3, BF16])
 def test_dense_pass_any_bit_roles(gemm):
     """Row bits above the outer bits and tile bits among the swizzled low
     bits: positions combine the three parts by XOR, whatever bits they hold."""
