@@ -193,7 +193,7 @@ template <int KT, int NP> struct TcCfg {
     static constexpr int NPROD = NP == 1 ? 1 : NP == 2 ? 3 : 6;
     static constexpr int SA = (NP * PLANE_B + 2 * NP * PLANE_A) <= 200 * 1024 ? 2 : 1;   // A stages
     static constexpr int TMEM_COLS = 2 * KR;    // two accumulators
-    static constexpr size_t SMEM = (size_t)NP * PLANE_B + (size_t)SA * NP * PLANE_A + 4096;
+    static constexpr size_t SMEM = (size_t)NP * PLANE_B + (size_t)SA * NP * PLANE_A + 6144;
     static constexpr int THREADS = 416;         // 4 epilogue warps, 8 producer warps, 1 MMA warp
 };
 
@@ -206,6 +206,11 @@ template <int KT, int NP> struct TcCfg {
 struct PassTables {
     int prow[128], drow[128];
     int pcol[64], dcol[64];
+    // the tile's 2^(k+7) entries in index order: entry e has the tile's
+    // (row and column) bits in ascending position, e's low 6 bits giving the
+    // lowest six of them; positions and (row | column << 8) of both halves
+    int plo[64], rtlo[64];
+    int phi[128], rthi[128];
 };
 
 __device__ __forceinline__ int64_t swz64(int64_t i, int swz) { return swz ? (i ^ ((i >> 4) & 15)) : i; }
@@ -218,6 +223,41 @@ __device__ __forceinline__ int diag_index_bits(const DenseArgs& a, int64_t i) {
 }
 
 __device__ void fill_pass_tables(const DenseArgs& a, PassTables* T, int tid, int nthreads) {
+    {
+        // the tile's bits in ascending order, with their row / column role
+        int pos[13], role[13], nb = 0;   // role: row bit j (j), or column bit j (16 + j)
+        for (int b = 0; b < a.W && nb < a.k + 7; ++b) {
+            for (int j = 0; j < 7; ++j)
+                if (a.row_pos[j] == b) {
+                    pos[nb] = b;
+                    role[nb++] = j;
+                }
+            for (int j = 0; j < a.k; ++j)
+                if (a.tile_pos[j] == b) {
+                    pos[nb] = b;
+                    role[nb++] = 16 + j;
+                }
+        }
+        for (int u = tid; u < 64 + (1 << (a.k + 1)); u += nthreads) {
+            const bool lo = u < 64;
+            const int e = lo ? u : u - 64, b0 = lo ? 0 : 6, nbits = lo ? 6 : a.k + 1;
+            int64_t off = 0;
+            int rt = 0;
+            for (int i = 0; i < nbits; ++i)
+                if ((e >> i) & 1) {
+                    off |= (int64_t)1 << pos[b0 + i];
+                    const int ro = role[b0 + i];
+                    rt |= ro < 16 ? 1 << ro : 1 << (8 + ro - 16);
+                }
+            if (lo) {
+                T->plo[e] = (int)swz64(off, a.swz);
+                T->rtlo[e] = rt;
+            } else {
+                T->phi[e] = (int)swz64(off, a.swz);
+                T->rthi[e] = rt;
+            }
+        }
+    }
     for (int r = tid; r < 128; r += nthreads) {
         int64_t o = 0;
         for (int b = 0; b < 7; ++b) o |= (int64_t)((r >> b) & 1) << a.row_pos[b];
@@ -296,9 +336,11 @@ __global__ void __launch_bounds__(416, 1) dense_tc_kernel(const DenseArgs a, con
 
     if (warp >= 4 && warp < 12) {
         // ---------------------------------------------------------- producers
-        // thread (r, h): row r of the A tile, columns h*TE/2 .. h*TE/2 + TE/2 - 1;
-        // consecutive lanes take consecutive rows (the low free index bits)
-        const int pt = tid - 128, r = pt & 127, c0 = (pt >> 7) * PCOLS;
+        // thread pt loads the tile's entries e = pt + 256 j in index order: the
+        // lanes of a warp cover the tile's lowest index bits (its lowest 5,
+        // which are the tensor's lowest 5 since the row bits are the lowest
+        // free ones), so every warp load reads whole 128-byte lines
+        const int pt = tid - 128;
         uint64_t cur = ~0ull;                  // tensor whose B image is loaded
         uint32_t b_phase = 0;
         for (uint64_t t = t_begin; t < t_end; ++t) {
@@ -319,21 +361,22 @@ __global__ void __launch_bounds__(416, 1) dense_tc_kernel(const DenseArgs a, con
             if (it >= (uint64_t)SA && !mbar_wait(&a_empty[s], (uint32_t)(((it / SA) - 1) & 1), abort_flag)) break;
             // (positions combine by XOR: the swizzle mixes the bits of the parts)
             const float2* src = a.L + tens * (uint64_t)N;
-            const int64_t pr = swz64(outer_offset(a, o), a.swz) ^ T->prow[r];
+            const int64_t pr = swz64(outer_offset(a, o), a.swz) ^ T->plo[pt & 63];
+            const int rtl = T->rtlo[pt & 63];
             unsigned char* stage = sA + (size_t)s * NP * Cfg::PLANE_A;
             float2 v[PCOLS];
 #pragma unroll
-            for (int j = 0; j < PCOLS; ++j) v[j] = src[pr ^ T->pcol[c0 + j]];
+            for (int j = 0; j < PCOLS; ++j) v[j] = src[pr ^ T->phi[(pt >> 6) + 4 * j]];
 #pragma unroll
-            for (int gg = 0; gg < PCOLS / 4; ++gg) {
-                const int g = c0 / 4 + gg;   // complex entries 4g..4g+3 = reals 8g..8g+7
+            for (int j = 0; j < PCOLS; ++j) {
+                const int rt = rtl | T->rthi[(pt >> 6) + 4 * j];
+                const int r = rt & 255, c = rt >> 8;   // row, operator column (complex entry)
                 uint32_t h[NP][4];
+                pack_terms<NP>(v[j].x, v[j].y, h, 0);
+                // the 4-byte (re, im) pair of entry c in its 16-byte chunk (c >> 2) & 7
+                const uint32_t off = sw128_chunk(128, r, c >> 5, (c >> 2) & 7) + (uint32_t)((c & 3) << 2);
 #pragma unroll
-                for (int j = 0; j < 4; ++j) pack_terms<NP>(v[gg * 4 + j].x, v[gg * 4 + j].y, h, j);
-                const uint32_t off = sw128_chunk(128, r, g >> 3, g & 7);
-#pragma unroll
-                for (int q = 0; q < NP; ++q)
-                    *reinterpret_cast<uint4*>(stage + q * Cfg::PLANE_A + off) = make_uint4(h[q][0], h[q][1], h[q][2], h[q][3]);
+                for (int q = 0; q < NP; ++q) *reinterpret_cast<uint32_t*>(stage + q * Cfg::PLANE_A + off) = h[q][0];
             }
             fence_async_smem();
             mbar_arrive(&a_full[s]);

@@ -494,6 +494,23 @@ int fuse_dense(HostPlan& hp, int b, int e, int kd, int W, int* nst_out) {
                 continue;
             }
             const std::vector<int> X = uniq_bits(o);
+            // a factor reading bits outside the tile takes them into the tile
+            // while it has room (they would otherwise be padding): it is then
+            // composed into the operator, and later matrices on those bits
+            // can join the pass
+            {
+                std::vector<int> add;
+                for (int x : X)
+                    if (std::find(tiles.begin(), tiles.end(), x) == tiles.end()) add.push_back(x);
+                if (!add.empty() && (int)(tiles.size() + add.size()) <= kd) {
+                    bool free_bits = true;   // (no deferred factor may read a bit the tile takes)
+                    for (int s2 = 0; s2 < nst; ++s2)
+                        if (sepi[s2])
+                            for (int x : add)
+                                if (std::find(sbits[s2].begin(), sbits[s2].end(), x) != sbits[s2].end()) free_bits = false;
+                    if (free_bits) tiles.insert(tiles.end(), add.begin(), add.end());
+                }
+            }
             bool inside = true;
             for (int x : X) inside = inside && std::find(tiles.begin(), tiles.end(), x) != tiles.end();
             // merge into the previous stage: a diagonal of the same kind, at most 5 bits

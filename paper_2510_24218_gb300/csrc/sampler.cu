@@ -1270,52 +1270,57 @@ template <typename R> __device__ __forceinline__ Chain<R> make_chain(const KPara
 // ------------------------------------------------------------ HBM engine
 // Dense operators of the passes of block program br (HBM engine): every pass
 // is the product of its stages restricted to its tile bits, Op[t'][t] over
-// the 2^k tile settings, composed in shared memory one column per thread
-// (columns are independent: no barrier between stages), then written to
-// HBM for the GEMM kernels; the stages deferred to the epilogue (diagonal
-// factors that read bits outside the tile) write their tables instead.
+// the 2^k tile settings, composed in shared memory stage by stage over all
+// the group's threads (a 2x2 stage updates 2^(k-1) row pairs of every
+// column, a diagonal one scales every entry), then written to HBM for the
+// GEMM kernels; the stages deferred to the epilogue (diagonal factors that
+// read bits outside the tile) write their tables instead.
 __device__ void compose_dense(const KParams& p, const Chain<float>& ch, const Grp& G, const DevBlockRange& br,
                               uint64_t chain) {
     const DevFused* F = P_<DevFused>(p, p.off.fused);
     const float2 one = make_float2(1.f, 0.f), zero = make_float2(0.f, 0.f);
     float2* gops = static_cast<float2*>(p.gOps);
     float2* gdiag = static_cast<float2*>(p.gDiag);
+    float2* ob = ch.ob;   // Op[r][c] at ob[r * E + c]
     for (int fi = br.fwd_begin; fi < br.fwd_end; ++fi) {
         const DevFused f = F[fi];
         const int k = f.ntb, E = 1 << k;
         const uint64_t slot = (uint64_t)(fi - br.fwd_begin) * p.nch + chain;
-        for (int c = G.lt; c < E; c += G.nt) {
-            float2* col = ch.ob + c;   // Op[r][c] at col[r * E]
-            for (int r = 0; r < E; ++r) col[r * E] = r == c ? one : zero;
-            for (int s2 = 0; s2 < f.nst; ++s2) {
-                const DevStage& st = ch.stg[f.st_begin - br.fwd_st + s2];
-                const float2* tab = ch.tab + st.tab_off;
-                if (st.type == ST_MAT) {
-                    const int bit = 1 << st.arg;
-                    const float2 m00 = tab[0], m01 = tab[1], m10 = tab[2], m11 = tab[3];
-                    for (int r0 = 0; r0 < E; ++r0) {
-                        if (r0 & bit) continue;
-                        const float2 x0 = col[r0 * E], x1 = col[(r0 | bit) * E];
-                        col[r0 * E] = cfma(m00, x0, cmul(m01, x1));
-                        col[(r0 | bit) * E] = cfma(m10, x0, cmul(m11, x1));
-                    }
-                } else if (!st.epi) {
-                    int tpos[5];   // tile index of each table bit
-                    for (int j = 0; j < st.arg; ++j) {
-                        tpos[j] = 0;
-                        for (int t = 0; t < k; ++t)
-                            if (f.tbits[t] == st.dbits[j]) tpos[j] = t;
-                    }
-                    for (int r = 0; r < E; ++r) {
-                        int e = 0;
-                        for (int j = 0; j < st.arg; ++j) e |= ((r >> tpos[j]) & 1) << j;
-                        col[r * E] = cmul(col[r * E], tab[e]);
-                    }
+        for (int i = G.lt; i < E * E; i += G.nt) ob[i] = (i >> k) == (i & (E - 1)) ? one : zero;
+        G.sync();
+        for (int s2 = 0; s2 < f.nst; ++s2) {
+            const DevStage& st = ch.stg[f.st_begin - br.fwd_st + s2];
+            const float2* tab = ch.tab + st.tab_off;
+            if (st.type == ST_MAT) {
+                const int a = st.arg;
+                const float2 m00 = tab[0], m01 = tab[1], m10 = tab[2], m11 = tab[3];
+                for (int w = G.lt; w < (E >> 1) * E; w += G.nt) {
+                    const int c = w & (E - 1), hr = w >> k;   // column, row pair
+                    const int r0 = ((hr >> a) << (a + 1)) | (hr & ((1 << a) - 1)), r1 = r0 | (1 << a);
+                    const float2 x0 = ob[r0 * E + c], x1 = ob[r1 * E + c];
+                    ob[r0 * E + c] = cfma(m00, x0, cmul(m01, x1));
+                    ob[r1 * E + c] = cfma(m10, x0, cmul(m11, x1));
                 }
+            } else if (!st.epi) {
+                int tpos[5];   // tile index of each table bit
+                for (int j = 0; j < st.arg; ++j) {
+                    tpos[j] = 0;
+                    for (int t = 0; t < k; ++t)
+                        if (f.tbits[t] == st.dbits[j]) tpos[j] = t;
+                }
+                for (int i = G.lt; i < E * E; i += G.nt) {
+                    const int r = i >> k;
+                    int e = 0;
+                    for (int j = 0; j < st.arg; ++j) e |= ((r >> tpos[j]) & 1) << j;
+                    ob[i] = cmul(ob[i], tab[e]);
+                }
+            } else {
+                continue;   // deferred to the epilogue: no barrier needed
             }
-            float2* dst = gops + (slot << (2 * k)) + c;
-            for (int r = 0; r < E; ++r) dst[(size_t)r * E] = col[r * E];
+            G.sync();
         }
+        float2* dst = gops + (slot << (2 * k));
+        for (int i = G.lt; i < E * E; i += G.nt) dst[i] = ob[i];
         // the epilogue's tables, in stage order, 32 entries each
         int d = 0;
         for (int s2 = 0; s2 < f.nst; ++s2) {
