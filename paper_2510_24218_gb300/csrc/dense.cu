@@ -358,15 +358,17 @@ __global__ void __launch_bounds__(416, 1) dense_tc_kernel(const DenseArgs a, con
                 b_phase ^= 1;
                 cur = tens;
             }
-            if (it >= (uint64_t)SA && !mbar_wait(&a_empty[s], (uint32_t)(((it / SA) - 1) & 1), abort_flag)) break;
             // (positions combine by XOR: the swizzle mixes the bits of the parts)
             const float2* src = a.L + tens * (uint64_t)N;
             const int64_t pr = swz64(outer_offset(a, o), a.swz) ^ T->plo[pt & 63];
             const int rtl = T->rtlo[pt & 63];
             unsigned char* stage = sA + (size_t)s * NP * Cfg::PLANE_A;
+            // the loads are in flight while the stage is still being read by
+            // the previous tile's MMAs (a register stage in front of the shared one)
             float2 v[PCOLS];
 #pragma unroll
             for (int j = 0; j < PCOLS; ++j) v[j] = src[pr ^ T->phi[(pt >> 6) + 4 * j]];
+            if (it >= (uint64_t)SA && !mbar_wait(&a_empty[s], (uint32_t)(((it / SA) - 1) & 1), abort_flag)) break;
 #pragma unroll
             for (int j = 0; j < PCOLS; ++j) {
                 const int rt = rtl | T->rthi[(pt >> 6) + 4 * j];
