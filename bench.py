@@ -47,6 +47,23 @@ METRIC = "exact samples/s on 1 GB300 (mixed vs plain FP32, same accuracy); TC % 
 # arithmetic of each workload's configuration (the 12-qubit one is complex128)
 DEFAULT_PRECISION = {"grid6x6": "fp32", "n12": "fp64", "heavyhex400": "fp32", "grid8x8noisy": "fp32",
                      "grad3reg": "fp32"}
+# engine of each workload: the 64-qubit noisy grid's 2^16-entry frontiers run
+# on the HBM engine (dense passes on the tensor cores), the others on chip
+DEFAULT_ENGINE = {"grid8x8noisy": "hbm"}
+GEMMS = {"split3": 0, "split2": 1, "bf16": 2, "fp32": 3}   # PW_GEMM_*
+ENGINES = {"auto": 0, "onchip": 1, "hbm": 2}                # PW_ENGINE_*
+
+
+def measured_peaks():
+    """HBM GB/s and dense BF16 TFLOP/s measured on the GB300s (the
+    driver writes MEASURED_PEAKS.json), else the stated fallback."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), float(d["bf16_tflops"]), "of measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, 1900.0, "of fallback"
 GRAD_K = 64   # bitstrings per instance of the gradient workload
 
 
@@ -145,7 +162,10 @@ def workload_config(args, world):
     spec, n_samples, B, desc = workload(args.workload)
     if args.samples:
         n_samples = args.samples
+    engine = getattr(args, "engine", None) or (DEFAULT_ENGINE.get(args.workload, "onchip")
+                                               if args.precision == "fp32" else "onchip")
     return {"workload": desc, "samples_per_step": n_samples, "chains_per_launch": B, "precision": args.precision,
+            "engine": engine, "gemm": getattr(args, "gemm", "split3") if engine == "hbm" else None,
             "l2": "flushed (256 MB write) before every timed step",
             "parallelism": f"replicas x{world} (disjoint sample ranges)"}
 
@@ -238,7 +258,8 @@ def run_ours(args, rank, world):
     prec = pw.PW_PREC_FP64 if args.precision == "fp64" else pw.PW_PREC_FP32
     circ = pw.pw_circuit_qaoa(spec.n, spec.edges, spec.weights, spec.h, spec.p, spec.gammas, spec.betas,
                               spec.depol2, spec.ad_gamma)
-    plan = pw.pw_plan_build(circ, precision=prec, chains_per_launch=B)
+    eng, gemm = ENGINES[args.engine], GEMMS[args.gemm]
+    plan = pw.pw_plan_build(circ, precision=prec, chains_per_launch=B, engine=eng, gemm=gemm)
     tuned = pw.pw_plan_autotune(plan, 0, torch.cuda.current_stream(dev)) if args.autotune else 0
     pst = pw.pw_plan_stats(plan)
     # the end-to-end leg builds its plans with the tuned shape (single-CTA plans)
@@ -249,8 +270,11 @@ def run_ours(args, rank, world):
     stream = torch.cuda.current_stream(dev)
     first = replica_first(rank, n_samples, args.warmup, args.steps)
 
-    def step(i, stats=False):
-        return pw.pw_sample(plan, args.seed, first + i * n_samples, n_samples, out, None, stream, want_stats=stats)
+    hbm = pst["engine"] == ENGINES["hbm"]
+
+    def step(i, stats=False, pl=None):
+        return pw.pw_sample(pl or plan, args.seed, first + i * n_samples, n_samples, out, None, stream,
+                            want_stats=stats)
 
     launches_per_step = (n_samples + B - 1) // B
     # the roofline's denominator: the FMA rate of this device's CUDA cores,
@@ -265,15 +289,23 @@ def run_ours(args, rank, world):
     torch.cuda.synchronize(dev)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     launches = 0
+    dense = {"passes": 0, "ms": 0.0, "bytes": 0.0, "flops": 0.0}
     clk_path = os.path.join(tempfile.gettempdir(), f"pw_clocks_{os.getpid()}.csv")
     with ClockSampler(clk_path) as clk:
         t_wall = time.perf_counter()
         for i in range(args.steps):
             flush.zero_()
             ev[i][0].record(stream)
-            step(args.warmup + i)
+            # the HBM engine's dense passes are timed by the library with CUDA
+            # events around each GEMM kernel, on this stream (stats requested)
+            st = step(args.warmup + i, stats=hbm)
             ev[i][1].record(stream)
-            launches += launches_per_step
+            if hbm:
+                launches += st["launches"]
+                for k in dense:
+                    dense[k] += st["dense_" + k]
+            else:
+                launches += launches_per_step
         torch.cuda.synchronize(dev)
         t_wall = time.perf_counter() - t_wall
     if world > 1:
@@ -283,6 +315,27 @@ def run_ours(args, rank, world):
     ms = max_over_ranks(ms, world, dev)
     total = n_samples * args.steps * world
     value = total / (ms / 1e3)
+
+    def rate_of(engine, gemm_kind, steps=2):
+        """samples/s of the same workload on another engine or arithmetic
+        (warm-up call, then `steps` timed steps): the comparison arms."""
+        p2 = pw.pw_plan_build(circ, precision=prec, chains_per_launch=B, engine=engine, gemm=gemm_kind)
+        try:
+            step(0, pl=p2)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for i in range(steps):
+                step(1 + i, pl=p2)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            return n_samples * steps / (e0.elapsed_time(e1) / 1e3)
+        finally:
+            pw.pw_plan_destroy(p2)
+
+    arms = {}
+    if hbm and rank == 0 and not args.no_arms:
+        arms["fp32_simt_same_plan"] = rate_of(ENGINES["hbm"], GEMMS["fp32"])
+        arms["onchip_engine"] = rate_of(ENGINES["onchip"], 0)
     per_launch_ms = ms / max(1, launches)
     # roofline of the sampler kernel: algorithmic flops of one launch / launch time
     flops_per_launch = pst["flops_per_sample"] * (n_samples / max(1, launches / args.steps))
@@ -298,7 +351,8 @@ def run_ours(args, rank, world):
         t0 = time.perf_counter()
         c2 = pw.pw_circuit_qaoa(spec.n, spec.edges, spec.weights, spec.h, spec.p, spec.gammas, spec.betas,
                                 spec.depol2, spec.ad_gamma)
-        p2 = pw.pw_plan_build(c2, precision=prec, chains_per_launch=B, threads_per_chain=e2e_tpc)
+        p2 = pw.pw_plan_build(c2, precision=prec, chains_per_launch=B, threads_per_chain=e2e_tpc, engine=eng,
+                              gemm=gemm)
         pw.pw_sample_host(p2, args.seed, first + i * n_samples, n_samples, host_out)
         pw.pw_plan_destroy(p2)
         pw.pw_circuit_destroy(c2)
@@ -309,7 +363,7 @@ def run_ours(args, rank, world):
     pw.pw_plan_destroy(plan)
     pw.pw_circuit_destroy(circ)
     return dict(value=value, ms=ms, launches=launches, near=near, pst=pst, desc=desc, n_samples=n_samples, B=B,
-                achieved=achieved, peak=peak, per_launch_ms=per_launch_ms, flops_per_launch=flops_per_launch, clocks=clocks,
+                achieved=achieved, peak=peak, hbm=hbm, dense=dense, arms=arms, per_launch_ms=per_launch_ms, flops_per_launch=flops_per_launch, clocks=clocks,
                 e2e=e2e_value, h2d=h2d, d2h=n_samples * words * 8, wall=t_wall)
 
 
@@ -497,6 +551,38 @@ def _plan_blob_bytes(pw, plan):
     return int(pw.pw_plan_stats(plan)["device_bytes"])
 
 
+def roofline_of(args, r, fma_peak):
+    """Roofline of the dominant kernel. HBM engine: the dense GEMM pass
+    (dense_tc_kernel / dense_simt_kernel), its algorithmic bytes (every
+    frontier entry read and written once) over its event-timed duration
+    against the measured HBM copy rate, with its tensor-pipe rate against the
+    measured BF16 peak beside it. On-chip engine: the sampler kernel's
+    algorithmic FP32 flops over its time against the measured FMA rate."""
+    if r["hbm"]:
+        hbm_gbs, bf16_tf, note = measured_peaks()
+        d = r["dense"]
+        gbs = d["bytes"] / (d["ms"] / 1e3) / 1e9 if d["ms"] else None
+        tcf = d["flops"] / (d["ms"] / 1e3) / 1e12 if d["ms"] else None
+        tc = args.gemm != "fp32"
+        return {"bound": "hbm", "achieved": gbs, "peak": hbm_gbs, "unit": "GB/s",
+                "frac": gbs / hbm_gbs if gbs else None,
+                "traffic": profiled_traffic(args.workload + "_hbm", r["B"]),
+                "kernel": "dense_tc_kernel<6,3>" if args.gemm == "split3" else
+                          ("dense_simt_kernel<6>" if not tc else f"dense_tc_kernel ({args.gemm})"),
+                "launches_timed": d["passes"], "algorithmic_bytes_per_launch": d["bytes"] / max(1, d["passes"]),
+                "avg_launch_ms": d["ms"] / max(1, d["passes"]),
+                "peak_note": f"{note} HBM copy rate (MEASURED_PEAKS.json)",
+                "tensor": ({"achieved": tcf, "peak": bf16_tf, "unit": "TFLOP/s", "frac": tcf / bf16_tf if tcf else None,
+                            "note": f"issued BF16 MMA flops of the dense passes (2^W x 2^k complex multiply-adds x "
+                                    f"the split's products) over their time, {note} dense BF16 peak"} if tc else None)}
+    return {"bound": "alu", "achieved": r["achieved"], "peak": fma_peak, "unit": "TFLOP/s",
+            "frac": (r["achieved"] / fma_peak) if fma_peak else None,
+            "traffic": profiled_traffic(args.workload, r["B"]) if args.precision == "fp32" else None,
+            "kernel": "pw_chain_kernel<float>" if args.precision == "fp32" else "pw_chain_kernel<double>",
+            "peak_note": f"of measured: {args.precision.upper()} FMA rate of this device's CUDA cores "
+                         "(pw_device_fma_rate probe, best of five ~30 ms launches)"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -514,9 +600,16 @@ def main():
                     help="grad3reg: time only the first N fitting instances (profiling)")
     ap.add_argument("--no-autotune", dest="autotune", action="store_false",
                     help="keep the plan's own threads per chain (default: tune it before the warm-up)")
+    ap.add_argument("--engine", default=None, choices=list(ENGINES),
+                    help="default: the workload's own (hbm for grid8x8noisy, onchip otherwise)")
+    ap.add_argument("--gemm", default="split3", choices=list(GEMMS),
+                    help="HBM engine: arithmetic of the dense passes (default split3: tensor cores, FP32-equivalent)")
+    ap.add_argument("--no-arms", action="store_true", help="skip the comparison arms (FP32 SIMT, on-chip engine)")
     args = ap.parse_args()
     if args.precision is None:
         args.precision = DEFAULT_PRECISION.get(args.workload, "fp32")
+    if args.engine is None:
+        args.engine = DEFAULT_ENGINE.get(args.workload, "onchip") if args.precision == "fp32" else "onchip"
 
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
@@ -563,15 +656,16 @@ def main():
             "data": "synthetic",
             "config": workload_config(args, world),
             "details": {"amplitudes_per_s": r["value"] * r["pst"]["amps_per_sample"],
+                        "engine": args.engine, "gemm": args.gemm if r["hbm"] else None,
                         "plan": {k: r["pst"][k] for k in ("n_slots", "width_bits", "n_blocks", "threads_per_chain",
-                                                          "chains_per_cta", "ctas_per_chain", "flops_per_sample")},
-                        "near_boundary_draws_in_warmup": int(r["near"])},
-            "roofline": {"bound": "alu", "achieved": r["achieved"], "peak": peak, "unit": "TFLOP/s",
-                         "frac": (r["achieved"] / peak) if peak else None,
-                         "traffic": profiled_traffic(args.workload, r["B"]) if args.precision == "fp32" else None,
-                         "kernel": "pw_chain_kernel<float>" if args.precision == "fp32" else "pw_chain_kernel<double>",
-                         "peak_note": f"of measured: {args.precision.upper()} FMA rate of this device's CUDA cores "
-                                      "(pw_device_fma_rate probe, best of five ~30 ms launches)"},
+                                                          "chains_per_cta", "ctas_per_chain", "flops_per_sample",
+                                                          "dense_tile_bits", "dense_passes_per_sample",
+                                                          "dense_flops_per_sample")},
+                        "near_boundary_draws_in_warmup": int(r["near"]),
+                        "comparison_samples_per_s": r["arms"],
+                        "mixed_vs_fp32_same_plan": (r["value"] / r["arms"]["fp32_simt_same_plan"]
+                                                    if r["arms"].get("fp32_simt_same_plan") else None)},
+            "roofline": roofline_of(args, r, peak),
             "cpu_baseline": cpu,
             "e2e": {"value": r["e2e"], "unit": "samples/s", "h2d_bytes_per_step": r["h2d"],
                     "d2h_bytes_per_step": r["d2h"]},

@@ -126,6 +126,13 @@ typedef struct {
     uint64_t near_boundary;   /* draws with |u*P - cum| < 1e-6 P */
     uint64_t zero_mass;       /* updates whose block had zero probability */
     uint64_t launches;        /* kernel launches issued */
+    /* HBM engine (measured only when the call gets a stats pointer): */
+    uint64_t dense_passes;    /* dense GEMM passes launched */
+    double dense_ms;          /* their GEMM kernels' total device time (CUDA events around each) */
+    double dense_bytes;       /* their algorithmic HBM bytes: every tensor entry read and
+                                 written once, 16 bytes per complex FP32 entry */
+    double dense_flops;       /* their dense flops: 2^W x 2^k complex multiply-adds (8 flops)
+                                 per chain, times the products of the split (1, 3 or 6) */
 } pw_run_stats_t;
 
 /* ---------------------------------------------------------------- circuit */

@@ -582,7 +582,8 @@ std::mutex& dense_mutex() {
     return mu;
 }
 
-template <int KT, int NP> int launch_tc(const DenseArgs& a, unsigned char* bimg, int nsm, cudaStream_t st) {
+template <int KT, int NP>
+int launch_tc(const DenseArgs& a, unsigned char* bimg, int nsm, cudaStream_t st, cudaEvent_t t0, cudaEvent_t t1) {
     using Cfg = TcCfg<KT, NP>;
     const uint64_t chunks = a.ntens * (uint64_t)Cfg::KR * (Cfg::KR / 8);
     const unsigned gb = (unsigned)std::min<uint64_t>((chunks + 255) / 256, (uint64_t)nsm * 16);
@@ -597,12 +598,14 @@ template <int KT, int NP> int launch_tc(const DenseArgs& a, unsigned char* bimg,
     if (e != cudaSuccess) return dense_fail(e, "cudaFuncSetAttribute(dense tc)");
     const uint64_t tiles = a.ntens << (a.W - KT - 7);
     const unsigned grid = (unsigned)std::min<uint64_t>(tiles, (uint64_t)nsm);
+    if (t0) cudaEventRecord(t0, st);
     kern<<<grid, Cfg::THREADS, Cfg::SMEM, st>>>(a, bimg);
     e = cudaGetLastError();
+    if (t1) cudaEventRecord(t1, st);
     return e == cudaSuccess ? PW_OK : dense_fail(e, "dense tc launch");
 }
 
-template <int KT> int launch_simt(const DenseArgs& a, int nsm, cudaStream_t st) {
+template <int KT> int launch_simt(const DenseArgs& a, int nsm, cudaStream_t st, cudaEvent_t t0, cudaEvent_t t1) {
     constexpr int TE = 1 << KT;
     const size_t smem = (size_t)(TE * 128 + TE * TE) * sizeof(float2);
     auto kern = dense_simt_kernel<KT>;
@@ -614,8 +617,10 @@ template <int KT> int launch_simt(const DenseArgs& a, int nsm, cudaStream_t st) 
     if (e != cudaSuccess) return dense_fail(e, "cudaFuncSetAttribute(dense simt)");
     const uint64_t tiles = a.ntens << (a.W - KT - 7);
     const unsigned grid = (unsigned)std::min<uint64_t>(tiles, (uint64_t)nsm * 2);
+    if (t0) cudaEventRecord(t0, st);
     kern<<<grid, 256, smem, st>>>(a);
     e = cudaGetLastError();
+    if (t1) cudaEventRecord(t1, st);
     return e == cudaSuccess ? PW_OK : dense_fail(e, "dense simt launch");
 }
 
@@ -627,16 +632,18 @@ size_t dense_bimage_bytes(int gemm, int k) {
     return np * kr * kr * 2;
 }
 
-int dense_run(int gemm, const DenseArgs& a, unsigned char* bimg, cudaStream_t st) {
+int dense_run(int gemm, const DenseArgs& a, unsigned char* bimg, cudaStream_t st, cudaEvent_t t0, cudaEvent_t t1) {
     int dev = 0, nsm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     nsm = std::max(nsm, 1);
     if (a.ntens == 0) return PW_OK;
-    if (gemm == PW_GEMM_FP32) return a.k == 5 ? launch_simt<5>(a, nsm, st) : launch_simt<6>(a, nsm, st);
-    if (gemm == PW_GEMM_BF16) return a.k == 5 ? launch_tc<5, 1>(a, bimg, nsm, st) : launch_tc<6, 1>(a, bimg, nsm, st);
-    if (gemm == PW_GEMM_SPLIT2) return a.k == 5 ? launch_tc<5, 2>(a, bimg, nsm, st) : launch_tc<6, 2>(a, bimg, nsm, st);
-    return a.k == 5 ? launch_tc<5, 3>(a, bimg, nsm, st) : launch_tc<6, 3>(a, bimg, nsm, st);
+    if (gemm == PW_GEMM_FP32) return a.k == 5 ? launch_simt<5>(a, nsm, st, t0, t1) : launch_simt<6>(a, nsm, st, t0, t1);
+    if (gemm == PW_GEMM_BF16)
+        return a.k == 5 ? launch_tc<5, 1>(a, bimg, nsm, st, t0, t1) : launch_tc<6, 1>(a, bimg, nsm, st, t0, t1);
+    if (gemm == PW_GEMM_SPLIT2)
+        return a.k == 5 ? launch_tc<5, 2>(a, bimg, nsm, st, t0, t1) : launch_tc<6, 2>(a, bimg, nsm, st, t0, t1);
+    return a.k == 5 ? launch_tc<5, 3>(a, bimg, nsm, st, t0, t1) : launch_tc<6, 3>(a, bimg, nsm, st, t0, t1);
 }
 
 }  // namespace pw

@@ -32,7 +32,9 @@ struct DenseArgs {
 // the SIMT arm).
 size_t dense_bimage_bytes(int gemm, int k);
 
-// Enqueue one pass on stream st (bimg: ntens * dense_bimage_bytes scratch).
-int dense_run(int gemm, const DenseArgs& a, unsigned char* bimg, cudaStream_t st);
+// Enqueue one pass on stream st (bimg: ntens * dense_bimage_bytes scratch);
+// t0 / t1 (nullable) are recorded right before and after the GEMM kernel.
+int dense_run(int gemm, const DenseArgs& a, unsigned char* bimg, cudaStream_t st, cudaEvent_t t0 = nullptr,
+              cudaEvent_t t1 = nullptr);
 
 }  // namespace pw

@@ -197,7 +197,8 @@ int pw_plan_exec_order(const pw_plan* plan, int* order) {
 
 void pw_plan_destroy(pw_plan* plan) {
     if (!plan) return;
-    if (plan->d_blob || plan->d_counters || plan->d_stage || plan->d_out_wire || plan->d_in_wire || plan->d_dense) {
+    if (plan->d_blob || plan->d_counters || plan->d_stage || plan->d_out_wire || plan->d_in_wire || plan->d_dense ||
+        !plan->dense_events.empty()) {
         int cur = -1;
         cudaGetDevice(&cur);
         if (plan->device >= 0 && plan->device != cur) cudaSetDevice(plan->device);
@@ -207,6 +208,7 @@ void pw_plan_destroy(pw_plan* plan) {
         if (plan->d_out_wire) cudaFree(plan->d_out_wire);
         if (plan->d_in_wire) cudaFree(plan->d_in_wire);
         if (plan->d_dense) cudaFree(plan->d_dense);
+        for (void* ev : plan->dense_events) cudaEventDestroy(static_cast<cudaEvent_t>(ev));
         if (plan->device >= 0 && plan->device != cur && cur >= 0) cudaSetDevice(cur);
     }
     delete plan;

@@ -293,6 +293,7 @@ struct pw_plan {
     void* d_dense = nullptr;
     size_t dense_bytes = 0;
     uint64_t dense_chains = 0;
+    std::vector<void*> dense_events;   // cudaEvent_t pairs timing the dense passes of a call
 };
 
 namespace pw {

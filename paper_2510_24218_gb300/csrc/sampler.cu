@@ -1675,7 +1675,15 @@ HbmBuffers hbm_sizes(const HostPlan& hp, const SmemLayout& sm, uint64_t nch) {
 // The HBM engine: launches of the chain kernel that run every chain of a
 // batch from one yield point to the next, with the dense passes of the
 // prepared block (GEMMs on the frontiers in HBM) in between.
-int launch_hbm(pw_plan* plan, KParams& kp, cudaStream_t st, uint64_t* launches) {
+// Timing of the dense passes of one call (pw_sample with stats): an event
+// pair around every pass, from the plan's pool.
+struct DenseTiming {
+    int used = 0;
+    uint64_t passes = 0;
+    double bytes = 0.0, flops = 0.0;
+};
+
+int launch_hbm(pw_plan* plan, KParams& kp, cudaStream_t st, uint64_t* launches, DenseTiming* tm) {
     const HostPlan& hp = plan->hp;
     const int S = hp.hdr.S, P = hp.hdr.P, K = hp.hdr.K;
     kp.sm = make_layout(hp, sizeof(float2));
@@ -1788,8 +1796,27 @@ int launch_hbm(pw_plan* plan, KParams& kp, cudaStream_t st, uint64_t* launches) 
                     a.diag = static_cast<const float2*>(kp.gDiag) + (uint64_t)pi * nch * 4 * 32;
                     a.diag_stride = 4 * 32;
                     a.err = reinterpret_cast<int*>(kp.counters + CNT_DENSE);
-                    const int rc = dense_run(hp.gemm, a, bimg, st);
+                    cudaEvent_t e0 = nullptr, e1 = nullptr;
+                    if (tm) {
+                        while ((int)plan->dense_events.size() < 2 * (tm->used + 1)) {
+                            cudaEvent_t ev;
+                            if ((e = cudaEventCreate(&ev)) != cudaSuccess) return cuda_fail(e, "cudaEventCreate");
+                            plan->dense_events.push_back(ev);
+                        }
+                        e0 = static_cast<cudaEvent_t>(plan->dense_events[2 * tm->used]);
+                        e1 = static_cast<cudaEvent_t>(plan->dense_events[2 * tm->used + 1]);
+                        ++tm->used;
+                    }
+                    // (the events bracket the GEMM kernel alone)
+                    const int rc = dense_run(hp.gemm, a, bimg, st, e0, e1);
                     if (rc) return rc;
+                    if (tm) {
+                        const double entries = (double)cnt * std::ldexp(1.0, a.W);
+                        const int nprod = hp.gemm == PW_GEMM_SPLIT3 ? 6 : hp.gemm == PW_GEMM_SPLIT2 ? 3 : 1;
+                        ++tm->passes;
+                        tm->bytes += 16.0 * entries;
+                        tm->flops += 8.0 * entries * std::ldexp(1.0, a.k) * nprod;
+                    }
                     if (launches) *launches += hp.gemm == PW_GEMM_FP32 ? 1 : 2;
                 }
             }
@@ -1807,10 +1834,11 @@ int launch_hbm(pw_plan* plan, KParams& kp, cudaStream_t st, uint64_t* launches) 
     return PW_OK;
 }
 
-template <typename R> int launch(pw_plan* plan, KParams& kp, cudaStream_t st, uint64_t* launches) {
+template <typename R> int launch(pw_plan* plan, KParams& kp, cudaStream_t st, uint64_t* launches,
+                                 DenseTiming* tm = nullptr) {
     std::lock_guard<std::mutex> attr_lock(launch_mutex());
     if constexpr (sizeof(R) == 4) {
-        if (plan->hp.engine == 1) return launch_hbm(plan, kp, st, launches);
+        if (plan->hp.engine == 1) return launch_hbm(plan, kp, st, launches, tm);
     }
     const HostPlan& hp = plan->hp;
     const size_t csz = 2 * sizeof(R);
@@ -1948,9 +1976,9 @@ template <typename R> int launch(pw_plan* plan, KParams& kp, cudaStream_t st, ui
     return PW_OK;
 }
 
-int run(pw_plan* plan, KParams& kp, cudaStream_t st, uint64_t* launches) {
+int run(pw_plan* plan, KParams& kp, cudaStream_t st, uint64_t* launches, DenseTiming* tm = nullptr) {
     return plan->hp.precision == PW_PREC_FP64 ? launch<double>(plan, kp, st, launches)
-                                              : launch<float>(plan, kp, st, launches);
+                                              : launch<float>(plan, kp, st, launches, tm);
 }
 
 void fill_common(pw_plan* plan, KParams& kp) {
@@ -1992,7 +2020,8 @@ int pw_sample(pw_plan* plan, uint64_t seed, uint64_t first_sample, uint64_t n_sa
     kp.trace = d_trace;
     kp.mode = MODE_SAMPLE;
     uint64_t launches = 0;
-    rc = run(plan, kp, st, &launches);
+    DenseTiming tm;
+    rc = run(plan, kp, st, &launches, stats ? &tm : nullptr);
     if (rc) return rc;
     if (!plan->out_wire.empty()) {   // wires back to qubits (SWAP-class gates)
         if ((rc = permute_output(plan, d_out_bits, n_samples, st))) return rc;
@@ -2006,6 +2035,17 @@ int pw_sample(pw_plan* plan, uint64_t seed, uint64_t first_sample, uint64_t n_sa
         stats->near_boundary = h[CNT_NEAR];
         stats->zero_mass = h[CNT_ZERO];
         stats->launches = launches;
+        stats->dense_passes = tm.passes;
+        stats->dense_bytes = tm.bytes;
+        stats->dense_flops = tm.flops;
+        double ms = 0.0;
+        for (int i = 0; i < tm.used; ++i) {
+            float t = 0.0f;
+            if (cudaEventElapsedTime(&t, static_cast<cudaEvent_t>(plan->dense_events[2 * i]),
+                                     static_cast<cudaEvent_t>(plan->dense_events[2 * i + 1])) == cudaSuccess)
+                ms += t;
+        }
+        stats->dense_ms = ms;
         if (h[CNT_DENSE]) return set_error(PW_ERR_TIMEOUT, "a bounded wait of a tensor-core pass ran out");
     }
     return PW_OK;

@@ -63,7 +63,9 @@ class DenseDesc(C.Structure):
 
 
 class RunStats(C.Structure):
-    _fields_ = [("near_boundary", C.c_uint64), ("zero_mass", C.c_uint64), ("launches", C.c_uint64)]
+    _fields_ = [("near_boundary", C.c_uint64), ("zero_mass", C.c_uint64), ("launches", C.c_uint64),
+                ("dense_passes", C.c_uint64), ("dense_ms", C.c_double), ("dense_bytes", C.c_double),
+                ("dense_flops", C.c_double)]
 
 
 def load_library():
@@ -227,7 +229,9 @@ def pw_sample(plan, seed, first_sample, n_samples, out_bits, trace=None, stream=
                                     C.c_void_p(out_bits.data_ptr()),
                                     C.c_void_p(trace.data_ptr()) if trace is not None else None,
                                     _stream_ptr(stream), C.byref(st) if want_stats else None))
-    return {"near_boundary": st.near_boundary, "zero_mass": st.zero_mass, "launches": st.launches}
+    return {"near_boundary": st.near_boundary, "zero_mass": st.zero_mass, "launches": st.launches,
+            "dense_passes": st.dense_passes, "dense_ms": st.dense_ms, "dense_bytes": st.dense_bytes,
+            "dense_flops": st.dense_flops}
 
 
 def pw_plan_autotune(plan, trial_samples=0, stream=None) -> int:
