@@ -194,7 +194,9 @@ template <int KT, int NP> struct TcCfg {
     static constexpr int SA = (NP * PLANE_B + 2 * NP * PLANE_A) <= 200 * 1024 ? 2 : 1;   // A stages
     static constexpr int TMEM_COLS = 2 * KR;    // two accumulators
     static constexpr size_t SMEM = (size_t)NP * PLANE_B + (size_t)SA * NP * PLANE_A + 6144;
-    static constexpr int THREADS = 416;         // 4 epilogue warps, 8 producer warps, 1 MMA warp
+    // 8 epilogue warps (two per quarter of the accumulator lanes, each reading
+    // half of the columns), 8 producer warps, 1 MMA warp
+    static constexpr int THREADS = 544;
 };
 
 // Per-CTA index tables of a pass. The storage position of logical index i
@@ -281,7 +283,7 @@ __device__ __forceinline__ float2 diag_product(const float2* tab, int ndiag, int
 }
 
 template <int KT, int NP>
-__global__ void __launch_bounds__(416, 1) dense_tc_kernel(const DenseArgs a, const unsigned char* __restrict__ bimg) {
+__global__ void __launch_bounds__(544, 1) dense_tc_kernel(const DenseArgs a, const unsigned char* __restrict__ bimg) {
     using Cfg = TcCfg<KT, NP>;
     constexpr int TE = Cfg::TE, KR = Cfg::KR, SA = Cfg::SA;
     constexpr int PCOLS = TE / 2;   // columns of one producer thread
@@ -293,7 +295,7 @@ __global__ void __launch_bounds__(416, 1) dense_tc_kernel(const DenseArgs a, con
     uint64_t* a_full = bars;            // [SA] producers -> MMA (256 arrivals)
     uint64_t* a_empty = bars + SA;      // [SA] MMA commit -> producers
     uint64_t* acc_full = bars + 2 * SA; // [2] MMA commit -> epilogue
-    uint64_t* acc_empty = bars + 2 * SA + 2;   // [2] epilogue (128 arrivals) -> MMA
+    uint64_t* acc_empty = bars + 2 * SA + 2;   // [2] epilogue (256 arrivals) -> MMA
     uint64_t* b_full = bars + 2 * SA + 4;      // B image landed (TMA bytes)
     int* misc = reinterpret_cast<int*>(bars + 2 * SA + 5);
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(misc);     // written by tcgen05.alloc
@@ -317,13 +319,13 @@ __global__ void __launch_bounds__(416, 1) dense_tc_kernel(const DenseArgs a, con
         }
         for (int s = 0; s < 2; ++s) {
             mbar_init(&acc_full[s], 1);
-            mbar_init(&acc_empty[s], 128);
+            mbar_init(&acc_empty[s], 256);
         }
         mbar_init(b_full, 1);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == 12) {
+    if (warp == 16) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
                      "r"((uint32_t)Cfg::TMEM_COLS)
                      : "memory");
@@ -334,13 +336,13 @@ __global__ void __launch_bounds__(416, 1) dense_tc_kernel(const DenseArgs a, con
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
 
-    if (warp >= 4 && warp < 12) {
+    if (warp >= 8 && warp < 16) {
         // ---------------------------------------------------------- producers
         // thread pt loads the tile's entries e = pt + 256 j in index order: the
         // lanes of a warp cover the tile's lowest index bits (its lowest 5,
         // which are the tensor's lowest 5 since the row bits are the lowest
         // free ones), so every warp load reads whole 128-byte lines
-        const int pt = tid - 128;
+        const int pt = tid - 256;
         uint64_t cur = ~0ull;                  // tensor whose B image is loaded
         uint32_t b_phase = 0;
         for (uint64_t t = t_begin; t < t_end; ++t) {
@@ -383,7 +385,7 @@ __global__ void __launch_bounds__(416, 1) dense_tc_kernel(const DenseArgs a, con
             fence_async_smem();
             mbar_arrive(&a_full[s]);
         }
-    } else if (warp == 12) {
+    } else if (warp == 16) {
         // -------------------------------------------------------------- MMA
         const uint32_t idesc = idesc_bf16(KR);
         for (uint64_t t = t_begin; t < t_end; ++t) {
@@ -422,17 +424,22 @@ __global__ void __launch_bounds__(416, 1) dense_tc_kernel(const DenseArgs a, con
         if (n > 0) mbar_wait(&a_empty[(n - 1) % SA], (uint32_t)(((n - 1) / SA) & 1), abort_flag);
     } else {
         // --------------------------------------------------------- epilogue
-        const int r = tid;   // row of the tile = accumulator lane (warp w reads lanes 32w..32w+31)
+        // warp w reads accumulator lanes 32 (w % 4) .. + 31 (tile rows) and
+        // columns of half w / 4
+        constexpr int EC = TE / 2;   // complex columns per thread
+        const int q = warp & 3, hh = warp >> 2;
+        const int r = 32 * q + lane;
+        const int* pc = T->pcol + hh * EC;
         uint64_t cur = ~0ull;
         for (uint64_t t = t_begin; t < t_end; ++t) {
             const uint64_t it = t - t_begin;
             const int ab = (int)(it & 1);
             const uint64_t tens = t / tiles_per, o = t % tiles_per;
             if (a.ndiag && tens != cur) {
-                // this tensor's diagonal tables (the four epilogue warps: named barrier 1)
-                asm volatile("bar.sync 1, 128;" ::: "memory");
-                for (int e = r; e < a.ndiag * 32; e += 128) stab[e] = a.diag[tens * (uint64_t)a.diag_stride + e];
-                asm volatile("bar.sync 1, 128;" ::: "memory");
+                // this tensor's diagonal tables (the eight epilogue warps: named barrier 1)
+                asm volatile("bar.sync 1, 256;" ::: "memory");
+                for (int e = tid; e < a.ndiag * 32; e += 256) stab[e] = a.diag[tens * (uint64_t)a.diag_stride + e];
+                asm volatile("bar.sync 1, 256;" ::: "memory");
                 cur = tens;
             }
             if (!mbar_wait(&acc_full[ab], (uint32_t)((it >> 1) & 1), abort_flag)) break;
@@ -441,27 +448,32 @@ __global__ void __launch_bounds__(416, 1) dense_tc_kernel(const DenseArgs a, con
             float2* dst = a.L + tens * (uint64_t)N;
             const int64_t pr = swz64(ob, a.swz) ^ T->prow[r];
             const int dr = diag_index_bits(a, ob) ^ T->drow[r];
-#pragma unroll 1
-            for (int c = 0; c < KR / 32; ++c) {
+#pragma unroll
+            for (int c = 0; c < EC / 16; ++c) {
                 float v[32];
-                tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(ab * KR + c * 32), v);
-                if (c == KR / 32 - 1) {
+                tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(ab * KR + hh * (KR / 2) + c * 32), v);
+                if (c == EC / 16 - 1) {
                     tc_fence_before();
                     mbar_arrive(&acc_empty[ab]);
                 }
+                if (a.ndiag) {
 #pragma unroll
-                for (int j = 0; j < 16; ++j) {
-                    const int col = c * 16 + j;
-                    float2 y = make_float2(v[2 * j], v[2 * j + 1]);
-                    if (a.ndiag) y = cmulf(y, diag_product(stab, a.ndiag, dr ^ T->dcol[col]));
-                    dst[pr ^ T->pcol[col]] = y;
+                    for (int j = 0; j < 16; ++j) {
+                        const int col = hh * EC + c * 16 + j;
+                        const float2 y = cmulf(make_float2(v[2 * j], v[2 * j + 1]),
+                                               diag_product(stab, a.ndiag, dr ^ T->dcol[col]));
+                        dst[pr ^ pc[c * 16 + j]] = y;
+                    }
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) dst[pr ^ pc[c * 16 + j]] = make_float2(v[2 * j], v[2 * j + 1]);
                 }
             }
         }
     }
     tc_fence_before();
     __syncthreads();
-    if (warp == 12) {
+    if (warp == 16) {
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)Cfg::TMEM_COLS)
                      : "memory");
