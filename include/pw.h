@@ -348,7 +348,7 @@ typedef struct {
  * t'(i) being i's tile bits. gemm picks the arithmetic (PW_GEMM_*): the
  * tensor-core kinds run tcgen05 MMAs with FP32 accumulation in tensor memory,
  * the operator and the tensor entries split into BF16 terms. Allocates and
- * frees an operator image and an error flag, synchronises the stream.
+ * frees an error flag, synchronises the stream.
  * PW_ERR_ARG for invalid bit sets, PW_ERR_TIMEOUT if a bounded wait of the
  * tensor-core kernel ran out. */
 int pw_dense_apply(int gemm, const pw_dense_desc* desc, uint64_t n_tensors, float* d_tensors,

@@ -24,8 +24,9 @@
 //     scattered index bits) and write the BF16 terms into shared memory in the
 //     128-byte-swizzled K-major layout, four epilogue warps read the
 //     accumulators back (tcgen05.ld) and scatter the rows to HBM. The B
-//     operand (one per chain) is brought into shared memory by TMA
-//     (cp.async.bulk) from a pre-split image built once per call.
+//     operand (one per tensor) is split into its BF16 term planes by the
+//     producers, from the operator's FP32 copy in HBM, whenever the tile
+//     sequence of a CTA reaches the next tensor.
 //   * dense_simt_kernel: the same GEMM on FP32 CUDA cores (the plain-FP32
 //     comparison arm).
 #include <cuda_runtime.h>
@@ -51,10 +52,6 @@ __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
 }
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
     asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.release.cta.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-                 : "memory");
 }
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
     uint32_t ok;
@@ -133,15 +130,6 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
     for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
-}
-
-// Bulk copy global -> shared (TMA engine, no tensor map: a contiguous image),
-// completion counted in bytes on an mbarrier.
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                     smem_u32(dst)),
-                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
-                 : "memory");
 }
 
 // The BF16 terms of x (round to nearest at every step): x = t0 + t1 (+ t2)
@@ -283,7 +271,7 @@ __device__ __forceinline__ float2 diag_product(const float2* tab, int ndiag, int
 }
 
 template <int KT, int NP>
-__global__ void __launch_bounds__(544, 1) dense_tc_kernel(const DenseArgs a, const unsigned char* __restrict__ bimg) {
+__global__ void __launch_bounds__(544, 1) dense_tc_kernel(const DenseArgs a) {
     using Cfg = TcCfg<KT, NP>;
     constexpr int TE = Cfg::TE, KR = Cfg::KR, SA = Cfg::SA;
     constexpr int PCOLS = TE / 2;   // columns of one producer thread
@@ -296,7 +284,6 @@ __global__ void __launch_bounds__(544, 1) dense_tc_kernel(const DenseArgs a, con
     uint64_t* a_empty = bars + SA;      // [SA] MMA commit -> producers
     uint64_t* acc_full = bars + 2 * SA; // [2] MMA commit -> epilogue
     uint64_t* acc_empty = bars + 2 * SA + 2;   // [2] epilogue (256 arrivals) -> MMA
-    uint64_t* b_full = bars + 2 * SA + 4;      // B image landed (TMA bytes)
     int* misc = reinterpret_cast<int*>(bars + 2 * SA + 5);
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(misc);     // written by tcgen05.alloc
     volatile int* abort_flag = misc + 1;                         // a bounded wait ran out
@@ -321,7 +308,6 @@ __global__ void __launch_bounds__(544, 1) dense_tc_kernel(const DenseArgs a, con
             mbar_init(&acc_full[s], 1);
             mbar_init(&acc_empty[s], 256);
         }
-        mbar_init(b_full, 1);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -343,21 +329,35 @@ __global__ void __launch_bounds__(544, 1) dense_tc_kernel(const DenseArgs a, con
         // which are the tensor's lowest 5 since the row bits are the lowest
         // free ones), so every warp load reads whole 128-byte lines
         const int pt = tid - 256;
-        uint64_t cur = ~0ull;                  // tensor whose B image is loaded
-        uint32_t b_phase = 0;
+        uint64_t cur = ~0ull;                  // tensor whose operator is in the B planes
         for (uint64_t t = t_begin; t < t_end; ++t) {
             const uint64_t it = t - t_begin;
             const int s = (int)(it % SA);
             const uint64_t tens = t / tiles_per, o = t % tiles_per;
             if (tens != cur) {
-                // every MMA of the previous tile is complete before B changes
+                // every MMA of the previous tile is complete before B changes;
+                // then the producers write this tensor's operator into the B
+                // term planes (real block form, K-major, 128-byte swizzle),
+                // from its FP32 copy in HBM: one 16-byte chunk (4 complex
+                // entries of one output real) per item
                 if (it > 0 && !mbar_wait(&a_empty[(it - 1) % SA], (uint32_t)(((it - 1) / SA) & 1), abort_flag)) break;
-                if (pt == 0) {
-                    mbar_expect_tx(b_full, (uint32_t)(NP * Cfg::PLANE_B));
-                    bulk_g2s(sB, bimg + tens * (size_t)(NP * Cfg::PLANE_B), (uint32_t)(NP * Cfg::PLANE_B), b_full);
+                const float2* op = a.ops + tens * (uint64_t)TE * TE;
+                for (int u = pt; u < KR * (KR / 8); u += 256) {
+                    const int n = u / (KR / 8), g = u % (KR / 8);   // output real n, chunk g (reals 8g..8g+7)
+                    const int cp = n & 1;
+                    const float4* w4 = reinterpret_cast<const float4*>(op + (n >> 1) * TE + 4 * g);
+                    const float4 w01 = w4[0], w23 = w4[1];
+                    const float2 w[4] = {make_float2(w01.x, w01.y), make_float2(w01.z, w01.w),
+                                         make_float2(w23.x, w23.y), make_float2(w23.z, w23.w)};
+                    uint32_t h[NP][4];
+#pragma unroll
+                    for (int j = 0; j < 4; ++j)   // row (t', cp) of [[Re, -Im], [Im, Re]] against (t, re), (t, im)
+                        pack_terms<NP>(cp == 0 ? w[j].x : w[j].y, cp == 0 ? -w[j].y : w[j].x, h, j);
+                    const uint32_t off = sw128_chunk(KR, n, g >> 3, g & 7);
+#pragma unroll
+                    for (int qq = 0; qq < NP; ++qq)
+                        *reinterpret_cast<uint4*>(sB + qq * Cfg::PLANE_B + off) = make_uint4(h[qq][0], h[qq][1], h[qq][2], h[qq][3]);
                 }
-                if (!mbar_wait(b_full, b_phase, abort_flag)) break;
-                b_phase ^= 1;
                 cur = tens;
             }
             // (positions combine by XOR: the swizzle mixes the bits of the parts)
@@ -481,35 +481,6 @@ __global__ void __launch_bounds__(544, 1) dense_tc_kernel(const DenseArgs a, con
     if (tid == 0 && *abort_flag) atomicExch(a.err, 1);
 }
 
-// The B operand image of every tensor: NP BF16 planes of the real block form
-// of its operator, K-major and 128-byte swizzled exactly as the MMA reads them
-// from shared memory (one thread per 16-byte chunk).
-template <int KT, int NP>
-__global__ void dense_bimage_kernel(const float2* __restrict__ ops, uint64_t ntens, unsigned char* __restrict__ img) {
-    using Cfg = TcCfg<KT, NP>;
-    constexpr int TE = Cfg::TE, KR = Cfg::KR;
-    const uint64_t chunks = ntens * (uint64_t)KR * (KR / 8);
-    for (uint64_t u = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; u < chunks; u += (uint64_t)gridDim.x * blockDim.x) {
-        const uint64_t tens = u / ((uint64_t)KR * (KR / 8));
-        const int rem = (int)(u % ((uint64_t)KR * (KR / 8)));
-        const int n = rem / (KR / 8), g = rem % (KR / 8);   // output real n, chunk g (reals 8g..8g+7)
-        const int tp = n >> 1, cp = n & 1;
-        const float2* op = ops + tens * (uint64_t)TE * TE + (uint64_t)tp * TE;
-        uint32_t h[NP][4];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const float2 w = op[4 * g + j];   // Op[t'][t], t = 4g + j
-            // row (t', cp) of [[Re, -Im], [Im, Re]] against input (t, re) and (t, im)
-            pack_terms<NP>(cp == 0 ? w.x : w.y, cp == 0 ? -w.y : w.x, h, j);
-        }
-        unsigned char* base = img + tens * (size_t)(NP * Cfg::PLANE_B);
-        const uint32_t off = sw128_chunk(KR, n, g >> 3, g & 7);
-#pragma unroll
-        for (int q = 0; q < NP; ++q)
-            *reinterpret_cast<uint4*>(base + q * Cfg::PLANE_B + off) = make_uint4(h[q][0], h[q][1], h[q][2], h[q][3]);
-    }
-}
-
 // --------------------------------------------------------------------- SIMT
 // One CTA per tile of 128 rows: the rows and the operator in shared memory,
 // every thread an 8 x 4 block of complex outputs, FP32 fused multiply-adds.
@@ -594,15 +565,10 @@ std::mutex& dense_mutex() {
     return mu;
 }
 
-template <int KT, int NP>
-int launch_tc(const DenseArgs& a, unsigned char* bimg, int nsm, cudaStream_t st, cudaEvent_t t0, cudaEvent_t t1) {
+template <int KT, int NP> int launch_tc(const DenseArgs& a, int nsm, cudaStream_t st, cudaEvent_t t0, cudaEvent_t t1) {
     using Cfg = TcCfg<KT, NP>;
-    const uint64_t chunks = a.ntens * (uint64_t)Cfg::KR * (Cfg::KR / 8);
-    const unsigned gb = (unsigned)std::min<uint64_t>((chunks + 255) / 256, (uint64_t)nsm * 16);
-    dense_bimage_kernel<KT, NP><<<gb, 256, 0, st>>>(a.ops, a.ntens, bimg);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return dense_fail(e, "dense B-image launch");
     auto kern = dense_tc_kernel<KT, NP>;
+    cudaError_t e;
     {
         std::lock_guard<std::mutex> lk(dense_mutex());
         e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::SMEM);
@@ -611,7 +577,7 @@ int launch_tc(const DenseArgs& a, unsigned char* bimg, int nsm, cudaStream_t st,
     const uint64_t tiles = a.ntens << (a.W - KT - 7);
     const unsigned grid = (unsigned)std::min<uint64_t>(tiles, (uint64_t)nsm);
     if (t0) cudaEventRecord(t0, st);
-    kern<<<grid, Cfg::THREADS, Cfg::SMEM, st>>>(a, bimg);
+    kern<<<grid, Cfg::THREADS, Cfg::SMEM, st>>>(a);
     e = cudaGetLastError();
     if (t1) cudaEventRecord(t1, st);
     return e == cudaSuccess ? PW_OK : dense_fail(e, "dense tc launch");
@@ -638,13 +604,7 @@ template <int KT> int launch_simt(const DenseArgs& a, int nsm, cudaStream_t st, 
 
 }  // namespace
 
-size_t dense_bimage_bytes(int gemm, int k) {
-    const int np = gemm == PW_GEMM_BF16 ? 1 : gemm == PW_GEMM_SPLIT2 ? 2 : gemm == PW_GEMM_SPLIT3 ? 3 : 0;
-    const size_t kr = (size_t)2 << k;
-    return np * kr * kr * 2;
-}
-
-int dense_run(int gemm, const DenseArgs& a, unsigned char* bimg, cudaStream_t st, cudaEvent_t t0, cudaEvent_t t1) {
+int dense_run(int gemm, const DenseArgs& a, cudaStream_t st, cudaEvent_t t0, cudaEvent_t t1) {
     int dev = 0, nsm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
@@ -652,10 +612,10 @@ int dense_run(int gemm, const DenseArgs& a, unsigned char* bimg, cudaStream_t st
     if (a.ntens == 0) return PW_OK;
     if (gemm == PW_GEMM_FP32) return a.k == 5 ? launch_simt<5>(a, nsm, st, t0, t1) : launch_simt<6>(a, nsm, st, t0, t1);
     if (gemm == PW_GEMM_BF16)
-        return a.k == 5 ? launch_tc<5, 1>(a, bimg, nsm, st, t0, t1) : launch_tc<6, 1>(a, bimg, nsm, st, t0, t1);
+        return a.k == 5 ? launch_tc<5, 1>(a, nsm, st, t0, t1) : launch_tc<6, 1>(a, nsm, st, t0, t1);
     if (gemm == PW_GEMM_SPLIT2)
-        return a.k == 5 ? launch_tc<5, 2>(a, bimg, nsm, st, t0, t1) : launch_tc<6, 2>(a, bimg, nsm, st, t0, t1);
-    return a.k == 5 ? launch_tc<5, 3>(a, bimg, nsm, st, t0, t1) : launch_tc<6, 3>(a, bimg, nsm, st, t0, t1);
+        return a.k == 5 ? launch_tc<5, 2>(a, nsm, st, t0, t1) : launch_tc<6, 2>(a, nsm, st, t0, t1);
+    return a.k == 5 ? launch_tc<5, 3>(a, nsm, st, t0, t1) : launch_tc<6, 3>(a, nsm, st, t0, t1);
 }
 
 }  // namespace pw
@@ -713,22 +673,15 @@ extern "C" int pw_dense_apply(int gemm, const pw_dense_desc* desc, uint64_t n_te
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     cudaError_t e;
     int* d_err = nullptr;
-    unsigned char* bimg = nullptr;
-    const size_t img = dense_bimage_bytes(gemm, a.k) * n_tensors;
     if ((e = cudaMalloc(&d_err, sizeof(int))) != cudaSuccess) return dense_fail(e, "cudaMalloc(flag)");
-    if (img && (e = cudaMalloc(&bimg, img)) != cudaSuccess) {
-        cudaFree(d_err);
-        return dense_fail(e, "cudaMalloc(operator image)");
-    }
     a.err = d_err;
     int rc = PW_OK;
     if ((e = cudaMemsetAsync(d_err, 0, sizeof(int), st)) != cudaSuccess) rc = dense_fail(e, "cudaMemsetAsync");
-    if (!rc) rc = dense_run(gemm, a, bimg, st);
+    if (!rc) rc = dense_run(gemm, a, st);
     int h_err = 0;
     if (!rc && (e = cudaMemcpyAsync(&h_err, d_err, sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
         rc = dense_fail(e, "reading the error flag");
     if ((e = cudaStreamSynchronize(st)) != cudaSuccess && !rc) rc = dense_fail(e, "cudaStreamSynchronize");
-    cudaFree(bimg);
     cudaFree(d_err);
     if (!rc && h_err) rc = set_error(PW_ERR_TIMEOUT, "a bounded wait of the tensor-core pass ran out");
     return rc;

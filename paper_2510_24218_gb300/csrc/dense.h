@@ -28,13 +28,8 @@ struct DenseArgs {
     int* err;              // device flag: a bounded wait ran out
 };
 
-// Bytes of the operator image of one tensor for the tensor-core arm (0 for
-// the SIMT arm).
-size_t dense_bimage_bytes(int gemm, int k);
-
-// Enqueue one pass on stream st (bimg: ntens * dense_bimage_bytes scratch);
-// t0 / t1 (nullable) are recorded right before and after the GEMM kernel.
-int dense_run(int gemm, const DenseArgs& a, unsigned char* bimg, cudaStream_t st, cudaEvent_t t0 = nullptr,
-              cudaEvent_t t1 = nullptr);
+// Enqueue one pass on stream st; t0 / t1 (nullable) are recorded right
+// before and after the GEMM kernel.
+int dense_run(int gemm, const DenseArgs& a, cudaStream_t st, cudaEvent_t t0 = nullptr, cudaEvent_t t1 = nullptr);
 
 }  // namespace pw

@@ -1657,7 +1657,7 @@ std::mutex& launch_mutex() {
 // Device buffers of the HBM engine for nch chains (kept by the plan and
 // reused; enlarged when a call needs more chains).
 struct HbmBuffers {
-    size_t L, R, state, ops, diag, bimg, total;
+    size_t L, R, state, ops, diag, total;
 };
 HbmBuffers hbm_sizes(const HostPlan& hp, const SmemLayout& sm, uint64_t nch) {
     const int S = hp.hdr.S, P = std::max(hp.hdr.P, 1), K = std::max(hp.hdr.K, 1), k = std::max(hp.dense_k, 1);
@@ -1667,8 +1667,7 @@ HbmBuffers hbm_sizes(const HostPlan& hp, const SmemLayout& sm, uint64_t nch) {
     b.state = align16(nch * (size_t)(sm.group_bytes - sm.R));
     b.ops = align16((size_t)std::max(hp.hdr.dense_npass, 1) * nch * (sizeof(float2) << (2 * k)));
     b.diag = align16((size_t)std::max(hp.hdr.dense_npass, 1) * nch * 4 * 32 * sizeof(float2));
-    b.bimg = align16(nch * dense_bimage_bytes(hp.gemm, k));
-    b.total = b.L + b.R + b.state + b.ops + b.diag + b.bimg;
+    b.total = b.L + b.R + b.state + b.ops + b.diag;
     return b;
 }
 
@@ -1728,7 +1727,6 @@ int launch_hbm(pw_plan* plan, KParams& kp, cudaStream_t st, uint64_t* launches, 
     kp.gState = base + ha.L + ha.R;
     kp.gOps = base + ha.L + ha.R + ha.state;
     kp.gDiag = base + ha.L + ha.R + ha.state + ha.ops;
-    unsigned char* bimg = base + ha.L + ha.R + ha.state + ha.ops + ha.diag;
     kp.strideR = (uint64_t)K << (S * std::max(P - 1, 0));
     kp.state_off = kp.sm.R;
     kp.state_bytes = kp.sm.group_bytes - kp.sm.R;
@@ -1808,7 +1806,7 @@ int launch_hbm(pw_plan* plan, KParams& kp, cudaStream_t st, uint64_t* launches, 
                         ++tm->used;
                     }
                     // (the events bracket the GEMM kernel alone)
-                    const int rc = dense_run(hp.gemm, a, bimg, st, e0, e1);
+                    const int rc = dense_run(hp.gemm, a, st, e0, e1);
                     if (rc) return rc;
                     if (tm) {
                         const double entries = (double)cnt * std::ldexp(1.0, a.W);
@@ -1817,7 +1815,7 @@ int launch_hbm(pw_plan* plan, KParams& kp, cudaStream_t st, uint64_t* launches, 
                         tm->bytes += 16.0 * entries;
                         tm->flops += 8.0 * entries * std::ldexp(1.0, a.k) * nprod;
                     }
-                    if (launches) *launches += hp.gemm == PW_GEMM_FP32 ? 1 : 2;
+                    if (launches) ++*launches;
                 }
             }
             kp.y_from = y;
