@@ -291,7 +291,7 @@ __global__ void __launch_bounds__(544, 1) dense_tc_kernel(const DenseArgs a) {
     float2* stab = reinterpret_cast<float2*>(T + 1);             // [4][32] diagonal tables of the current tensor
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const uint64_t tiles_per = (uint64_t)1 << (a.W - KT - 7);
+    const uint64_t tiles_per = (uint64_t)1 << a.nouter;   // (dead outer legs excluded)
     const uint64_t total = a.ntens * tiles_per;
     const uint64_t per = (total + gridDim.x - 1) / gridDim.x;
     const uint64_t t_begin = (uint64_t)blockIdx.x * per;
@@ -494,7 +494,7 @@ __global__ void __launch_bounds__(256) dense_simt_kernel(const DenseArgs a) {
     __shared__ PassTables T;
     __shared__ float2 stab[4 * 32];
     const int tid = threadIdx.x;
-    const uint64_t tiles_per = (uint64_t)1 << (a.W - KT - 7);
+    const uint64_t tiles_per = (uint64_t)1 << a.nouter;   // (dead outer legs excluded)
     const uint64_t total = a.ntens * tiles_per;
     const int64_t N = (int64_t)1 << a.W;
     fill_pass_tables(a, &T, tid, 256);
@@ -574,7 +574,7 @@ template <int KT, int NP> int launch_tc(const DenseArgs& a, int nsm, cudaStream_
         e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::SMEM);
     }
     if (e != cudaSuccess) return dense_fail(e, "cudaFuncSetAttribute(dense tc)");
-    const uint64_t tiles = a.ntens << (a.W - KT - 7);
+    const uint64_t tiles = a.ntens << a.nouter;
     const unsigned grid = (unsigned)std::min<uint64_t>(tiles, (uint64_t)nsm);
     if (t0) cudaEventRecord(t0, st);
     kern<<<grid, Cfg::THREADS, Cfg::SMEM, st>>>(a);
@@ -593,7 +593,7 @@ template <int KT> int launch_simt(const DenseArgs& a, int nsm, cudaStream_t st, 
         e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     }
     if (e != cudaSuccess) return dense_fail(e, "cudaFuncSetAttribute(dense simt)");
-    const uint64_t tiles = a.ntens << (a.W - KT - 7);
+    const uint64_t tiles = a.ntens << a.nouter;
     const unsigned grid = (unsigned)std::min<uint64_t>(tiles, (uint64_t)nsm * 2);
     if (t0) cudaEventRecord(t0, st);
     kern<<<grid, 256, smem, st>>>(a);

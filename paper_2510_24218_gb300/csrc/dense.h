@@ -20,7 +20,8 @@ struct DenseArgs {
     int swz;               // 1: entry i stored at i ^ ((i >> 4) & 15)
     int tile_pos[8];       // operator index bit j <-> tensor index bit tile_pos[j]
     int row_pos[7];        // the index bits numbering the 128 rows of a GEMM tile
-    int outer_pos[32];     // the other index bits, numbering the tiles of a tensor
+    int outer_pos[32];     // the index bits numbering the tiles of a tensor (the other bits are
+                           // fixed to 0 in the tiles processed)
     int nouter;
     int ndiag;
     int diag_nb[4];

@@ -106,8 +106,9 @@ int pw_plan_build(const pw_circuit* c, const pw_plan_opts* opts, pw_plan** out) 
         delete plan;
         return rc;
     }
-    // (the HBM engine streams frontiers from HBM in its readouts: 256 threads per chain)
-    int tpc = plan->hp.engine == 1 && o.threads_per_chain <= 0 ? 256 : choose_threads(plan->hp, o.threads_per_chain);
+    // (the HBM engine: 128 threads per chain, four chains per SM, whose
+    // readouts stream their frontiers from HBM concurrently)
+    int tpc = plan->hp.engine == 1 && o.threads_per_chain <= 0 ? 128 : choose_threads(plan->hp, o.threads_per_chain);
     if (tpc < 0) {
         delete plan;
         return set_error(PW_ERR_ARG, "threads_per_chain must be a power of two in 32..256");

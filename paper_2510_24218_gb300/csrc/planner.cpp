@@ -1277,17 +1277,37 @@ int build_plan(const pw_circuit* c, const pw_plan_opts& opts, HostPlan& hp) {
     // dense passes: each a GEMM of 2^(S m) entries x 2^kd complex multiply-adds
     hp.hdr.dense_mask = 0;
     hp.hdr.dense_npass = 0;
+    hp.pass_live_in.assign(hp.fused.size(), 0);
+    hp.pass_live_out.assign(hp.fused.size(), 0);
     for (int m = 1; m <= P; ++m) {
         const int kd = dense_k(m);
         if (!kd) continue;
         hp.hdr.dense_mask |= 1 << m;
         hp.dense_k = kd;
+        // live legs: a 2x2 stage that copies a leg (a new site's leg) makes it
+        // live, one whose second row is zero (a leg summed out) makes it dead,
+        // any other keeps it live; diagonal factors keep every leg
+        uint32_t live = 0;
         for (int k = 0; k < K; ++k) {
             const DevBlockRange& br = hp.block_ranges[(size_t)m * K + k];
             const int np = br.fwd_end - br.fwd_begin;
             hp.hdr.dense_npass = std::max(hp.hdr.dense_npass, np);
             hp.dense_passes_per_sample += np;
-            hp.dense_flops_per_sample += np * std::ldexp(8.0, S * m + kd);
+            for (int fi = br.fwd_begin; fi < br.fwd_end; ++fi) {
+                const DevFused& f = hp.fused[fi];
+                hp.pass_live_in[fi] = live;
+                for (int s2 = 0; s2 < f.nst; ++s2) {
+                    const DevStage& st = hp.stages[f.st_begin + s2];
+                    if (st.type != ST_MAT) continue;
+                    const uint32_t bit = 1u << f.tbits[st.arg];
+                    live = st.form == MF_ROW0 ? live & ~bit : live | bit;
+                }
+                hp.pass_live_out[fi] = live;
+                // the GEMM covers 2^(kd + 7) entries per tile, its tiles the live outer bits
+                int rows[7], outer[32];
+                const int no = dense_pass_bits(hp, fi, S * m, rows, outer);
+                hp.dense_flops_per_sample += std::ldexp(8.0, 2 * kd + 7 + no);
+            }
         }
     }
     // the amplitude of the whole circuit contracts only the last layer's

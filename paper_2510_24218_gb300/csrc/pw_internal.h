@@ -261,12 +261,39 @@ struct HostPlan {
     int dense_k = 0;                      // tile bits of the widest dense layer's passes
     double dense_flops_per_sample = 0.0;  // real flops of the dense passes (dense operators) per sample
     double dense_passes_per_sample = 0.0;
+    // dense passes (by fused index): the frontier bits that may be nonzero
+    // before and after the pass (a summed-out leg is zero until a new site
+    // expands it; the frontier starts as a delta at index 0)
+    std::vector<uint32_t> pass_live_in, pass_live_out;
     int wloc = 0;                         // log2 of the frontier entries per CTA then
     size_t smem_per_chain = 0;
     bool noisy = false;
     // amplitude API helpers: position of every executed mixer op (layer, block, index)
     std::vector<int> exec_layer, exec_block, exec_pos;
 };
+
+// Index bits of dense pass fi on a 2^W frontier: its tile bits, the 7 row
+// bits of a GEMM tile (the lowest live bits outside the tile, then dead ones
+// if too few are live) and the outer bits the tiles enumerate (the other live
+// bits: a tile with a dead leg set holds zeros before and after the pass and
+// is skipped). Returns the number of outer bits.
+inline int dense_pass_bits(const HostPlan& hp, int fi, int W, int* rows, int* outer) {
+    const DevFused& f = hp.fused[fi];
+    uint32_t tb = 0;
+    for (int j = 0; j < f.ntb; ++j) tb |= 1u << f.tbits[j];
+    const uint32_t live = hp.pass_live_in.empty() ? ~0u : hp.pass_live_in[fi];
+    int nr = 0, no = 0;
+    for (int pass = 0; pass < 2; ++pass)   // live bits first, then dead ones for the rows
+        for (int b = 0; b < W && nr < 7; ++b) {
+            const bool l = (live >> b) & 1;
+            if (((tb >> b) & 1) || l != (pass == 0)) continue;
+            rows[nr++] = b;
+            tb |= 1u << b;
+        }
+    for (int b = 0; b < W; ++b)
+        if (!((tb >> b) & 1) && ((live >> b) & 1)) outer[no++] = b;
+    return no;
+}
 
 int build_plan(const pw_circuit* c, const pw_plan_opts& opts, HostPlan& out);
 size_t plan_device_bytes(const HostPlan& hp);

@@ -1771,18 +1771,10 @@ int launch_hbm(pw_plan* plan, KParams& kp, cudaStream_t st, uint64_t* launches, 
                     a.W = S * m;
                     a.k = f.ntb;
                     a.swz = 1;
-                    uint64_t used = 0;
-                    for (int j = 0; j < a.k; ++j) {
-                        a.tile_pos[j] = f.tbits[j];
-                        used |= 1ull << f.tbits[j];
-                    }
-                    for (int b = 0, r = 0; b < a.W && r < 7; ++b)
-                        if (!((used >> b) & 1)) {
-                            a.row_pos[r++] = b;
-                            used |= 1ull << b;
-                        }
-                    for (int b = 0; b < a.W; ++b)
-                        if (!((used >> b) & 1)) a.outer_pos[a.nouter++] = b;
+                    for (int j = 0; j < a.k; ++j) a.tile_pos[j] = f.tbits[j];
+                    // rows: the lowest live legs; tiles: the other live legs (a tile
+                    // with a dead leg set holds zeros and is skipped)
+                    a.nouter = dense_pass_bits(hp, fi, a.W, a.row_pos, a.outer_pos);
                     for (int s2 = 0; s2 < f.nst; ++s2) {
                         const DevStage& sg = hp.stages[f.st_begin + s2];
                         if (sg.type != ST_DIAG || !sg.epi) continue;
@@ -1809,7 +1801,7 @@ int launch_hbm(pw_plan* plan, KParams& kp, cudaStream_t st, uint64_t* launches, 
                     const int rc = dense_run(hp.gemm, a, st, e0, e1);
                     if (rc) return rc;
                     if (tm) {
-                        const double entries = (double)cnt * std::ldexp(1.0, a.W);
+                        const double entries = (double)cnt * std::ldexp(1.0, a.k + 7 + a.nouter);
                         const int nprod = hp.gemm == PW_GEMM_SPLIT3 ? 6 : hp.gemm == PW_GEMM_SPLIT2 ? 3 : 1;
                         ++tm->passes;
                         tm->bytes += 16.0 * entries;
