@@ -363,6 +363,22 @@ int pw_dense_apply(int gemm, const pw_dense_desc* desc, uint64_t n_tensors, floa
  * the stream; allocates nothing. */
 int pw_device_fma_rate(int precision, void* stream, double* tflops);
 
+/* Device memory of the library's internal buffers (plan tables and
+ * counters, staging of pw_sample_host, the HBM engine's frontiers and
+ * operators, gradient and autotune scratch): cudaMalloc / cudaFree unless
+ * the caller registers an allocator (not in the paper: the boundary's
+ * convention that the caller's memory manager, e.g. a framework's caching
+ * allocator, owns all device memory). alloc(bytes, device, stream, ctx)
+ * returns device memory on `device` (the current device) or NULL (the call
+ * then fails with PW_ERR_OOM); free(ptr, device, stream, ctx) releases it;
+ * stream is NULL (the legacy stream). Process-wide; both NULL restores
+ * cudaMalloc / cudaFree. A buffer is always released by the pair that
+ * allocated it, after the device has gone idle. pw_sample_static allocates
+ * nothing either way. */
+typedef void* (*pw_alloc_fn)(uint64_t bytes, int device, void* stream, void* ctx);
+typedef void (*pw_free_fn)(void* ptr, int device, void* stream, void* ctx);
+int pw_set_allocator(pw_alloc_fn alloc, pw_free_fn free, void* ctx);
+
 /* Thread-local message describing the last failure of this thread. */
 const char* pw_last_error(void);
 

@@ -296,7 +296,7 @@ __global__ void __launch_bounds__(544, 1) dense_tc_kernel(const DenseArgs a) {
     const uint64_t per = (total + gridDim.x - 1) / gridDim.x;
     const uint64_t t_begin = (uint64_t)blockIdx.x * per;
     const uint64_t t_end = t_begin + per < total ? t_begin + per : total;
-    const int64_t N = (int64_t)1 << a.W;
+    const uint64_t N = a.stride;   // entries between consecutive tensors (>= 2^W)
 
     fill_pass_tables(a, T, tid, Cfg::THREADS);
     if (tid == 0) {
@@ -361,7 +361,7 @@ __global__ void __launch_bounds__(544, 1) dense_tc_kernel(const DenseArgs a) {
                 cur = tens;
             }
             // (positions combine by XOR: the swizzle mixes the bits of the parts)
-            const float2* src = a.L + tens * (uint64_t)N;
+            const float2* src = a.L + tens * N;
             const int64_t pr = swz64(outer_offset(a, o), a.swz) ^ T->plo[pt & 63];
             const int rtl = T->rtlo[pt & 63];
             unsigned char* stage = sA + (size_t)s * NP * Cfg::PLANE_A;
@@ -445,7 +445,7 @@ __global__ void __launch_bounds__(544, 1) dense_tc_kernel(const DenseArgs a) {
             if (!mbar_wait(&acc_full[ab], (uint32_t)((it >> 1) & 1), abort_flag)) break;
             tc_fence_after();
             const int64_t ob = outer_offset(a, o);
-            float2* dst = a.L + tens * (uint64_t)N;
+            float2* dst = a.L + tens * N;
             const int64_t pr = swz64(ob, a.swz) ^ T->prow[r];
             const int dr = diag_index_bits(a, ob) ^ T->drow[r];
 #pragma unroll
@@ -496,7 +496,7 @@ __global__ void __launch_bounds__(256) dense_simt_kernel(const DenseArgs a) {
     const int tid = threadIdx.x;
     const uint64_t tiles_per = (uint64_t)1 << a.nouter;   // (dead outer legs excluded)
     const uint64_t total = a.ntens * tiles_per;
-    const int64_t N = (int64_t)1 << a.W;
+    const uint64_t N = a.stride;   // entries between consecutive tensors (>= 2^W)
     fill_pass_tables(a, &T, tid, 256);
     uint64_t cur = ~0ull;
     const int tx = tid & 15, ty = tid >> 4;
@@ -513,7 +513,7 @@ __global__ void __launch_bounds__(256) dense_simt_kernel(const DenseArgs a) {
             cur = tens;
         }
         const int64_t ob = outer_offset(a, o);
-        float2* L = a.L + tens * (uint64_t)N;
+        float2* L = a.L + tens * N;
         const int64_t pob = swz64(ob, a.swz);
         const int dob = diag_index_bits(a, ob);
         for (int e = tid; e < TE * 128; e += 256) {
@@ -636,6 +636,7 @@ extern "C" int pw_dense_apply(int gemm, const pw_dense_desc* desc, uint64_t n_te
     DenseArgs a;
     std::memset(&a, 0, sizeof(a));
     a.W = d.width_bits;
+    a.stride = (uint64_t)1 << a.W;
     a.k = d.tile_bits;
     a.swz = d.swizzled ? 1 : 0;
     // the tile and row bits: distinct, in range; the others are the outer bits
@@ -673,7 +674,7 @@ extern "C" int pw_dense_apply(int gemm, const pw_dense_desc* desc, uint64_t n_te
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     cudaError_t e;
     int* d_err = nullptr;
-    if ((e = cudaMalloc(&d_err, sizeof(int))) != cudaSuccess) return dense_fail(e, "cudaMalloc(flag)");
+    if (int rc0 = dev_alloc(reinterpret_cast<void**>(&d_err), sizeof(int), "error flag")) return rc0;
     a.err = d_err;
     int rc = PW_OK;
     if ((e = cudaMemsetAsync(d_err, 0, sizeof(int), st)) != cudaSuccess) rc = dense_fail(e, "cudaMemsetAsync");
@@ -682,7 +683,7 @@ extern "C" int pw_dense_apply(int gemm, const pw_dense_desc* desc, uint64_t n_te
     if (!rc && (e = cudaMemcpyAsync(&h_err, d_err, sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
         rc = dense_fail(e, "reading the error flag");
     if ((e = cudaStreamSynchronize(st)) != cudaSuccess && !rc) rc = dense_fail(e, "cudaStreamSynchronize");
-    cudaFree(d_err);
+    dev_free(d_err);
     if (!rc && h_err) rc = set_error(PW_ERR_TIMEOUT, "a bounded wait of the tensor-core pass ran out");
     return rc;
 }

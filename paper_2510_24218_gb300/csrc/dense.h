@@ -16,6 +16,7 @@ struct DenseArgs {
     const float2* diag;    // per tensor diag_stride entries: ndiag tables of 32
     int diag_stride;
     uint64_t ntens;
+    uint64_t stride;       // entries from one tensor to the next (>= 2^W)
     int W, k;
     int swz;               // 1: entry i stored at i ^ ((i >> 4) & 15)
     int tile_pos[8];       // operator index bit j <-> tensor index bit tile_pos[j]

@@ -83,8 +83,8 @@ struct Lane {
         if (s) cudaStreamSynchronize(s);
         if (done) cudaEventDestroy(done);
         if (s) cudaStreamDestroy(s);
-        cudaFree(amp);
-        cudaFree(acc);
+        pw::dev_free(amp);
+        pw::dev_free(acc);
     }
 };
 
@@ -176,10 +176,12 @@ int run_terms(const pw_circuit* base, const std::vector<Term>& terms, int ncol, 
     std::vector<Lane> lanes(n_lanes);
     for (Lane& ln : lanes) {
         if ((e = cudaStreamCreateWithFlags(&ln.s, cudaStreamNonBlocking)) != cudaSuccess ||
-            (e = cudaEventCreateWithFlags(&ln.done, cudaEventDisableTiming)) != cudaSuccess ||
-            (e = cudaMalloc(&ln.amp, n_strings * sizeof(double2))) != cudaSuccess ||
-            (e = cudaMalloc(&ln.acc, n_strings * ncol * sizeof(double2))) != cudaSuccess)
+            (e = cudaEventCreateWithFlags(&ln.done, cudaEventDisableTiming)) != cudaSuccess)
             return grad_cuda_fail(e, "gradient lane set-up");
+        if (int rc0 = pw::dev_alloc(reinterpret_cast<void**>(&ln.amp), n_strings * sizeof(double2), "gradient lane"))
+            return rc0;
+        if (int rc0 = pw::dev_alloc(reinterpret_cast<void**>(&ln.acc), n_strings * ncol * sizeof(double2), "gradient lane"))
+            return rc0;
         if ((e = cudaStreamWaitEvent(ln.s, ready, 0)) != cudaSuccess ||
             (e = cudaMemsetAsync(ln.acc, 0, n_strings * ncol * sizeof(double2), ln.s)) != cudaSuccess)
             return grad_cuda_fail(e, "gradient lane set-up");
@@ -254,10 +256,10 @@ int run_terms(const pw_circuit* base, const std::vector<Term>& terms, int ncol, 
     std::vector<const double2*> acc_ptrs(n_lanes);
     for (int l = 0; l < n_lanes; ++l) acc_ptrs[l] = lanes[l].acc;
     const double2** d_ptrs = nullptr;
-    if ((e = cudaMalloc(&d_ptrs, n_lanes * sizeof(double2*))) != cudaSuccess) return grad_cuda_fail(e, "cudaMalloc");
+    if (int rc0 = pw::dev_alloc(reinterpret_cast<void**>(&d_ptrs), n_lanes * sizeof(double2*), "lane table")) return rc0;
     struct PtrFree {
         const double2** q;
-        ~PtrFree() { cudaFree(q); }
+        ~PtrFree() { pw::dev_free(const_cast<double2**>(q)); }
     } ptr_free{d_ptrs};
     if ((e = cudaMemcpy(d_ptrs, acc_ptrs.data(), n_lanes * sizeof(double2*), cudaMemcpyHostToDevice)) != cudaSuccess ||
         (e = cudaStreamSynchronize(cudaStreamLegacy)) != cudaSuccess)
@@ -405,7 +407,7 @@ __global__ void cost_score_finish(const double* __restrict__ partial, unsigned b
 
 struct DevBuf {
     void* p = nullptr;
-    ~DevBuf() { cudaFree(p); }
+    ~DevBuf() { pw::dev_free(p); }
 };
 
 }  // namespace
@@ -428,8 +430,10 @@ extern "C" int pw_qaoa_cost_grad(int n, int n_edges, const int* edges, const dou
     const size_t h_b = h ? (size_t)n * sizeof(double) : 0;
     auto up = [](size_t b) { return (b + 255) & ~size_t(255); };
     DevBuf buf;
-    cudaError_t e = cudaMalloc(&buf.p, up(amp_b) + up(grad_b) + up(part_b) + up(edge_b) + up(w_b) + up(h_b));
-    if (e != cudaSuccess) return grad_cuda_fail(e, "cudaMalloc(cost gradient scratch)");
+    if (int rc0 = pw::dev_alloc(&buf.p, up(amp_b) + up(grad_b) + up(part_b) + up(edge_b) + up(w_b) + up(h_b),
+                                "cost gradient scratch"))
+        return rc0;
+    cudaError_t e = cudaSuccess;
     struct SyncOnExit {   // destroyed before the scratch: nothing is freed under running copies or kernels
         cudaStream_t s;
         ~SyncOnExit() { cudaStreamSynchronize(s); }

@@ -41,10 +41,10 @@ int perm_fail(cudaError_t e, const char* what) {
 int upload_map(const std::vector<int>& map, int** out) {
     int* d = nullptr;
     cudaError_t e;
-    if ((e = cudaMalloc(&d, sizeof(int) * map.size())) != cudaSuccess) return perm_fail(e, "cudaMalloc(wire map)");
+    if (int rc = pw::dev_alloc(reinterpret_cast<void**>(&d), sizeof(int) * map.size(), "wire map")) return rc;
     if ((e = cudaMemcpy(d, map.data(), sizeof(int) * map.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
         (e = cudaStreamSynchronize(cudaStreamLegacy)) != cudaSuccess) {
-        cudaFree(d);
+        pw::dev_free(d);
         return perm_fail(e, "cudaMemcpy(wire map)");
     }
     *out = d;

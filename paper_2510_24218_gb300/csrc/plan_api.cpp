@@ -203,12 +203,12 @@ void pw_plan_destroy(pw_plan* plan) {
         int cur = -1;
         cudaGetDevice(&cur);
         if (plan->device >= 0 && plan->device != cur) cudaSetDevice(plan->device);
-        if (plan->d_blob) cudaFree(plan->d_blob);
-        if (plan->d_counters) cudaFree(plan->d_counters);
-        if (plan->d_stage) cudaFree(plan->d_stage);
-        if (plan->d_out_wire) cudaFree(plan->d_out_wire);
-        if (plan->d_in_wire) cudaFree(plan->d_in_wire);
-        if (plan->d_dense) cudaFree(plan->d_dense);
+        if (plan->d_blob) dev_free(plan->d_blob);
+        if (plan->d_counters) dev_free(plan->d_counters);
+        if (plan->d_stage) dev_free(plan->d_stage);
+        if (plan->d_out_wire) dev_free(plan->d_out_wire);
+        if (plan->d_in_wire) dev_free(plan->d_in_wire);
+        if (plan->d_dense) dev_free(plan->d_dense);
         for (void* ev : plan->dense_events) cudaEventDestroy(static_cast<cudaEvent_t>(ev));
         if (plan->device >= 0 && plan->device != cur && cur >= 0) cudaSetDevice(cur);
     }

@@ -17,6 +17,12 @@ using cd = std::complex<double>;
 // ----------------------------------------------------------------- errors
 int set_error(int code, const std::string& msg);
 
+// ------------------------------------------------------- device memory
+// Internal device buffers: the registered allocator (pw_set_allocator) or
+// cudaMalloc; dev_free releases through the pair that allocated.
+int dev_alloc(void** out, size_t bytes, const char* what);
+void dev_free(void* p);
+
 // ---------------------------------------------------------------- circuit
 enum OpKind { OP_GATE = 0, OP_KRAUS = 1 };
 

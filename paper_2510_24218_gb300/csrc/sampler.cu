@@ -117,7 +117,7 @@ struct KParams {
     int hbm;
     int y_from;
     int ybase[8];                 // first yield point of layer m
-    void* gL;                     // frontiers: chain c at layer m at gL + c * 2^(S m) entries
+    void* gL;                     // frontiers: chain c at gL + c * 2^(S P) entries (every layer)
     void* gR;                     // right environments: chain c at gR + c * strideR entries
     uint64_t strideR;
     unsigned char* gState;        // saved chain states, state_bytes each
@@ -1418,7 +1418,9 @@ __device__ __forceinline__ void run_chain_hbm(const KParams& p, const Chain<floa
         const bool resume_here = ny > 0 && y0 >= yb;
         const int Wl = S * (m - 1), W = S * m;
         const int NL = 1 << Wl, N = 1 << W;
-        ch.L = static_cast<C*>(p.gL) + chain * ((uint64_t)1 << W);
+        // a chain's frontier sits at the same place at every layer (stride of
+        // the widest one): chains at different layers run concurrently
+        ch.L = static_cast<C*>(p.gL) + chain * ((uint64_t)1 << (S * P));
         const int kstop = p.mode == MODE_AMP ? p.amp_block : 0;
         const int w32 = p.tpc < 32 ? p.tpc : 32;
         auto phase_nt = [&](int e) { return e > 1024 ? p.tpc : (e >= 256 && p.tpc >= 256) ? 128 : w32; };
@@ -1611,19 +1613,19 @@ int ensure_device_plan(pw_plan* plan) {
     }
     std::vector<unsigned char> blob = make_blob(plan->hp, plan->off);
     void* d = nullptr;
-    if ((e = cudaMalloc(&d, blob.size())) != cudaSuccess) return cuda_fail(e, "cudaMalloc(plan)");
+    if (int rc0 = dev_alloc(&d, blob.size(), "plan tables")) return rc0;
     // cudaMemcpy from pageable memory returns once the source is staged; the
     // copy itself is ordered on the legacy stream only. Wait for it, so that a
     // launch on any stream (also a non-blocking one) reads complete tables.
     if ((e = cudaMemcpy(d, blob.data(), blob.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
         (e = cudaStreamSynchronize(cudaStreamLegacy)) != cudaSuccess) {
-        cudaFree(d);
+        dev_free(d);
         return cuda_fail(e, "cudaMemcpy(plan)");
     }
     unsigned long long* cnt = nullptr;
-    if ((e = cudaMalloc(&cnt, 4 * sizeof(unsigned long long))) != cudaSuccess) {
-        cudaFree(d);
-        return cuda_fail(e, "cudaMalloc(counters)");
+    if (int rc0 = dev_alloc(reinterpret_cast<void**>(&cnt), 4 * sizeof(unsigned long long), "counters")) {
+        dev_free(d);
+        return rc0;
     }
     plan->d_blob = d;
     plan->blob_bytes = blob.size();
@@ -1710,12 +1712,10 @@ int launch_hbm(pw_plan* plan, KParams& kp, cudaStream_t st, uint64_t* launches, 
                                                          : std::min<uint64_t>({kp.count, 8192, by_mem});
     const HbmBuffers hb = hbm_sizes(hp, kp.sm, per_launch);
     if (!plan->d_dense || plan->dense_chains < per_launch) {
-        if (plan->d_dense) cudaFree(plan->d_dense);
+        if (plan->d_dense) dev_free(plan->d_dense);
         plan->d_dense = nullptr;
         plan->dense_chains = 0;
-        if ((e = cudaMalloc(&plan->d_dense, hb.total)) != cudaSuccess)
-            return set_error(PW_ERR_OOM, std::string("HBM engine buffers (") + std::to_string(hb.total >> 20) +
-                                             " MiB): " + cudaGetErrorString(e));
+        if (int rc0 = dev_alloc(&plan->d_dense, hb.total, "HBM engine buffers")) return rc0;
         plan->dense_bytes = hb.total;
         plan->dense_chains = per_launch;
     }
@@ -1769,6 +1769,7 @@ int launch_hbm(pw_plan* plan, KParams& kp, cudaStream_t st, uint64_t* launches, 
                     a.L = static_cast<float2*>(kp.gL);
                     a.ntens = cnt;
                     a.W = S * m;
+                    a.stride = (uint64_t)1 << (S * P);   // a chain's frontier keeps its place at every layer
                     a.k = f.ntb;
                     a.swz = 1;
                     for (int j = 0; j < a.k; ++j) a.tile_pos[j] = f.tbits[j];
@@ -2054,11 +2055,11 @@ int pw_plan_autotune(pw_plan* plan, uint64_t trial_samples, void* stream, int* c
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     uint64_t* d_out = nullptr;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
-    cudaError_t e = cudaMalloc(&d_out, n * hp.hdr.words * sizeof(uint64_t));
-    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (int rc0 = dev_alloc(reinterpret_cast<void**>(&d_out), n * hp.hdr.words * sizeof(uint64_t), "autotune output")) return rc0;
+    cudaError_t e = cudaEventCreate(&e0);
     if (e == cudaSuccess) e = cudaEventCreate(&e1);
     if (e != cudaSuccess) {
-        if (d_out) cudaFree(d_out);
+        if (d_out) dev_free(d_out);
         if (e0) cudaEventDestroy(e0);
         return cuda_fail(e, "autotune set-up");
     }
@@ -2088,7 +2089,7 @@ int pw_plan_autotune(pw_plan* plan, uint64_t trial_samples, void* stream, int* c
     hp.threads_per_chain = best;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    cudaFree(d_out);
+    dev_free(d_out);
     if (best_ms == 0.0f) {
         hp.threads_per_chain = keep;
         return set_error(PW_ERR_CUDA, "autotune: no configuration ran");
@@ -2111,10 +2112,10 @@ int pw_sample_host(pw_plan* plan, uint64_t seed, uint64_t first_sample, uint64_t
     const size_t need = align16(bits_bytes) + tr_bytes;
     cudaError_t e;
     if (plan->stage_bytes < need) {
-        if (plan->d_stage) cudaFree(plan->d_stage);
+        if (plan->d_stage) dev_free(plan->d_stage);
         plan->d_stage = nullptr;
         plan->stage_bytes = 0;
-        if ((e = cudaMalloc(&plan->d_stage, need)) != cudaSuccess) return cuda_fail(e, "cudaMalloc(staging)");
+        if (int rc0 = dev_alloc(&plan->d_stage, need, "staging")) return rc0;
         plan->stage_bytes = need;
     }
     uint64_t* d_bits = static_cast<uint64_t*>(plan->d_stage);
@@ -2162,15 +2163,16 @@ int pw_amplitudes(pw_plan* plan, int prefix_ops, uint64_t n_strings, const uint6
     if (!relabelled) return run(plan, kp, st, nullptr);
     // the kernel reads the bits per wire: reorder a copy of the strings
     uint64_t* d_wire_bits = nullptr;
-    if ((e = cudaMalloc(&d_wire_bits, n_strings * hp.hdr.words * sizeof(uint64_t))) != cudaSuccess)
-        return cuda_fail(e, "cudaMalloc(wire-ordered strings)");
+    if ((rc = dev_alloc(reinterpret_cast<void**>(&d_wire_bits), n_strings * hp.hdr.words * sizeof(uint64_t),
+                        "wire-ordered strings")))
+        return rc;
     rc = permute_input(plan, d_bits, d_wire_bits, n_strings, st);
     if (!rc) {
         kp.in_bits = d_wire_bits;
         rc = run(plan, kp, st, nullptr);
     }
     e = cudaStreamSynchronize(st);   // before the copy is freed
-    cudaFree(d_wire_bits);
+    dev_free(d_wire_bits);
     if (!rc && e != cudaSuccess) rc = cuda_fail(e, "cudaStreamSynchronize");
     return rc;
 }

@@ -62,6 +62,11 @@ class DenseDesc(C.Structure):
                 ("diag_pos", (C.c_int * 5) * 4), ("reserved", C.c_int * 8)]
 
 
+_ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_uint64, C.c_int, C.c_void_p, C.c_void_p)
+_FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p)
+_ALLOCATOR_REFS = []   # the registered callbacks stay alive while registered
+
+
 class RunStats(C.Structure):
     _fields_ = [("near_boundary", C.c_uint64), ("zero_mass", C.c_uint64), ("launches", C.c_uint64),
                 ("dense_passes", C.c_uint64), ("dense_ms", C.c_double), ("dense_bytes", C.c_double),
@@ -101,6 +106,7 @@ def load_library():
                                         C.c_uint64, vp, vp, vp]),
         "pw_sample_static": (C.c_int, [vp, C.c_uint64, C.c_uint64, C.c_uint64, vp, vp, C.POINTER(RunStats)]),
         "pw_device_fma_rate": (C.c_int, [C.c_int, vp, dp]),
+        "pw_set_allocator": (C.c_int, [_ALLOC_FN, _FREE_FN, vp]),
         "pw_dense_apply": (C.c_int, [C.c_int, C.POINTER(DenseDesc), C.c_uint64, vp, vp, vp, vp]),
         "pw_last_error": (C.c_char_p, []),
     }
@@ -284,6 +290,47 @@ def pw_dense_apply(gemm, desc, n_tensors, tensors, ops, diag=None, stream=None):
                                          C.c_void_p(ops.data_ptr()) if ops is not None else None,
                                          C.c_void_p(diag.data_ptr()) if diag is not None else None,
                                          _stream_ptr(stream)))
+
+
+def pw_set_allocator(alloc=None, free=None):
+    """Register Python callables alloc(bytes, device) -> int pointer (0 for
+    failure) and free(ptr, device) for the library's internal device buffers;
+    no arguments restores cudaMalloc / cudaFree."""
+    lib = load_library()
+    if alloc is None and free is None:
+        _check(lib.pw_set_allocator(_ALLOC_FN(), _FREE_FN(), None))
+        _ALLOCATOR_REFS.clear()
+        return
+
+    def _a(nbytes, device, stream, ctx):
+        try:
+            return int(alloc(int(nbytes), int(device))) or None
+        except Exception:   # (an exception cannot cross the C ABI: report no memory)
+            return None
+
+    def _f(ptr, device, stream, ctx):
+        try:
+            free(int(ptr), int(device))
+        except Exception:
+            pass
+
+    fa, ff = _ALLOC_FN(_a), _FREE_FN(_f)
+    _check(lib.pw_set_allocator(fa, ff, None))
+    _ALLOCATOR_REFS[:] = [fa, ff]
+
+
+def use_torch_allocator():
+    """Route the library's internal device buffers through torch's caching
+    allocator (torch.cuda.memory_allocated() then accounts for them)."""
+    import torch
+
+    def alloc(nbytes, device):
+        return torch.cuda.caching_allocator_alloc(nbytes, device=device)
+
+    def free(ptr, device):
+        torch.cuda.caching_allocator_delete(ptr)
+
+    pw_set_allocator(alloc, free)
 
 
 def pw_sample_host(plan, seed, first_sample, n_samples, out_bits: np.ndarray, trace: np.ndarray | None = None):

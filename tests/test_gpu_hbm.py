@@ -160,3 +160,18 @@ def test_hbm_wide_chain_against_alg1(pw):
     assert len(rows) == g["plan_stats"]["sampled_gates"]
     worst = max(pair_err(rows[r][1], g["trace"][1, r]) for r in range(len(rows)))
     assert worst < 1e-5
+
+
+def test_hbm_without_trace_matches_on_chip(pw):
+    """Without an amplitude trace (the sampling configuration of the bench),
+    512 chains of the 64-qubit noisy workload on the HBM engine and on the
+    on-chip engine: the same samples, and no block of zero mass. (Chains at
+    different layers run at the same time: each keeps its frontier at one
+    place for all layers, so a chain's layer-1 frontier can never sit inside
+    another chain's layer-2 frontier.)"""
+    spec = W.grid_8x8_p2_noisy()
+    a = run_gpu(pw, spec, 512, seed=7, trace=False, chains_per_launch=512)
+    b = run_gpu(pw, spec, 512, seed=7, trace=False, engine=HBM, gemm=SPLIT3, chains_per_launch=512)
+    assert b["stats"]["zero_mass"] == 0 and a["stats"]["zero_mass"] == 0
+    differ = int((~(a["bits"] == b["bits"]).all(axis=1)).sum())
+    assert differ <= max(a["stats"]["near_boundary"], b["stats"]["near_boundary"])

@@ -59,6 +59,60 @@ def grid_edges(rows: int, cols: int) -> np.ndarray:
     return np.array(sorted(e), dtype=np.int64).reshape(-1, 2)
 
 
+def kings_edges(rows: int, cols: int) -> np.ndarray:
+    """King's-graph edges (the square lattice plus both diagonals of every
+    plaquette), qubits numbered row-major, pairs sorted."""
+    e = []
+    for r in range(rows):
+        for c in range(cols):
+            q = r * cols + c
+            for dr, dc in ((0, 1), (1, -1), (1, 0), (1, 1)):
+                rr, cc = r + dr, c + dc
+                if 0 <= rr < rows and 0 <= cc < cols:
+                    e.append(tuple(sorted((q, rr * cols + cc))))
+    return np.array(sorted(e), dtype=np.int64).reshape(-1, 2)
+
+
+def chimera_edges(m: int, n: int, t: int = 4) -> np.ndarray:
+    """Chimera C(m, n, t) edges: an m x n array of unit cells, each the
+    complete bipartite graph K_{t,t} between its 'vertical' and 'horizontal'
+    qubits; vertical qubits couple to the cell below, horizontal ones to the
+    cell to the right. Qubit (i, j, side, k) is numbered ((i n + j) 2 + side) t + k."""
+    def q(i, j, side, k):
+        return ((i * n + j) * 2 + side) * t + k
+    e = []
+    for i in range(m):
+        for j in range(n):
+            for a in range(t):
+                for b in range(t):
+                    e.append((q(i, j, 0, a), q(i, j, 1, b)))
+                if i + 1 < m:
+                    e.append((q(i, j, 0, a), q(i + 1, j, 0, a)))
+                if j + 1 < n:
+                    e.append((q(i, j, 1, a), q(i, j + 1, 1, a)))
+    return np.array(sorted(tuple(sorted(x)) for x in e), dtype=np.int64).reshape(-1, 2)
+
+
+def gaussian_ising(name: str, n: int, e: np.ndarray, p: int, seed: int, with_h: bool = False) -> QaoaSpec:
+    """QAOA on an Ising instance with Gaussian couplings (and fields), angles
+    U[0, pi) from the same seed (the topologies of Sec. 4.3's timing study)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    w = rng.normal(size=len(e))
+    h = rng.normal(size=n) if with_h else None
+    g, b = uniform_angles(p, seed=seed)
+    return QaoaSpec(n=n, edges=e, weights=w, gammas=g, betas=b, h=h, name=name)
+
+
+def kings_10x10_p1() -> QaoaSpec:
+    """p=1 QAOA on the 10x10 King's graph (100 qubits), Gaussian couplings."""
+    return gaussian_ising("qaoa_p1_kings10x10", 100, kings_edges(10, 10), 1, seed=6)
+
+
+def chimera_c444_p1() -> QaoaSpec:
+    """p=1 QAOA on Chimera C(4, 4, 4) (128 qubits), Gaussian couplings."""
+    return gaussian_ising("qaoa_p1_chimera444", 128, chimera_edges(4, 4, 4), 1, seed=7)
+
+
 def random_regular_edges(n: int, d: int, seed: int, max_tries: int = 10000) -> np.ndarray:
     """Random d-regular simple graph: configuration model with rejection."""
     if (n * d) % 2:
