@@ -259,11 +259,19 @@ def run_ours(args, rank, world):
     circ = pw.pw_circuit_qaoa(spec.n, spec.edges, spec.weights, spec.h, spec.p, spec.gammas, spec.betas,
                               spec.depol2, spec.ad_gamma)
     eng, gemm = ENGINES[args.engine], GEMMS[args.gemm]
-    plan = pw.pw_plan_build(circ, precision=prec, chains_per_launch=B, engine=eng, gemm=gemm)
-    tuned = pw.pw_plan_autotune(plan, 0, torch.cuda.current_stream(dev)) if args.autotune else 0
+    opts = dict(precision=prec, chains_per_launch=B, engine=eng, gemm=gemm)
+    shape = {"tuned": False}
+    if args.autotune:
+        # the plan shape (readout block size, sweep order, threads per chain)
+        # searched on this device before the warm-up; the engine, the
+        # arithmetic and the batch stay the workload's
+        cache = os.environ.get("PW_AUTOTUNE_CACHE") or os.path.join(tempfile.gettempdir(), "pw_autotune.jsonl")
+        opts, trial_rate, hit = pw.pw_autotune(circ, min(n_samples, 16384), cache, torch.cuda.current_stream(dev),
+                                               **opts)
+        shape = {"tuned": True, "from_cache": hit, "trial_samples_per_s": trial_rate,
+                 **{k: opts[k] for k in ("max_block", "order", "threads_per_chain")}}
+    plan = pw.pw_plan_build(circ, **opts)
     pst = pw.pw_plan_stats(plan)
-    # the end-to-end leg builds its plans with the tuned shape (single-CTA plans)
-    e2e_tpc = tuned if 0 < tuned <= 256 and pst["ctas_per_chain"] == 1 else 0
     words = (spec.n + 63) // 64
     out = torch.empty((n_samples, words), dtype=torch.int64, device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # > L2 (129 MB)
@@ -316,10 +324,12 @@ def run_ours(args, rank, world):
     total = n_samples * args.steps * world
     value = total / (ms / 1e3)
 
-    def rate_of(engine, gemm_kind, steps=2):
+    def rate_of(engine, gemm_kind, steps=2, shape=True):
         """samples/s of the same workload on another engine or arithmetic
-        (warm-up call, then `steps` timed steps): the comparison arms."""
-        p2 = pw.pw_plan_build(circ, precision=prec, chains_per_launch=B, engine=engine, gemm=gemm_kind)
+        (warm-up call, then `steps` timed steps): the comparison arms (with
+        the tuned plan shape, or the plan's default one)."""
+        base = opts if shape else dict(precision=prec, chains_per_launch=B)
+        p2 = pw.pw_plan_build(circ, **{**base, "engine": engine, "gemm": gemm_kind})
         try:
             step(0, pl=p2)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -335,7 +345,7 @@ def run_ours(args, rank, world):
     arms = {}
     if hbm and rank == 0 and not args.no_arms:
         arms["fp32_simt_same_plan"] = rate_of(ENGINES["hbm"], GEMMS["fp32"])
-        arms["onchip_engine"] = rate_of(ENGINES["onchip"], 0)
+        arms["onchip_engine"] = rate_of(ENGINES["onchip"], 0, shape=False)
     per_launch_ms = ms / max(1, launches)
     # roofline of the sampler kernel: algorithmic flops of one launch / launch time
     flops_per_launch = pst["flops_per_sample"] * (n_samples / max(1, launches / args.steps))
@@ -351,8 +361,7 @@ def run_ours(args, rank, world):
         t0 = time.perf_counter()
         c2 = pw.pw_circuit_qaoa(spec.n, spec.edges, spec.weights, spec.h, spec.p, spec.gammas, spec.betas,
                                 spec.depol2, spec.ad_gamma)
-        p2 = pw.pw_plan_build(c2, precision=prec, chains_per_launch=B, threads_per_chain=e2e_tpc, engine=eng,
-                              gemm=gemm)
+        p2 = pw.pw_plan_build(c2, **opts)
         pw.pw_sample_host(p2, args.seed, first + i * n_samples, n_samples, host_out)
         pw.pw_plan_destroy(p2)
         pw.pw_circuit_destroy(c2)
@@ -363,7 +372,7 @@ def run_ours(args, rank, world):
     pw.pw_plan_destroy(plan)
     pw.pw_circuit_destroy(circ)
     return dict(value=value, ms=ms, launches=launches, near=near, pst=pst, desc=desc, n_samples=n_samples, B=B,
-                achieved=achieved, peak=peak, hbm=hbm, dense=dense, arms=arms, per_launch_ms=per_launch_ms, flops_per_launch=flops_per_launch, clocks=clocks,
+                achieved=achieved, peak=peak, hbm=hbm, dense=dense, arms=arms, shape=shape, per_launch_ms=per_launch_ms, flops_per_launch=flops_per_launch, clocks=clocks,
                 e2e=e2e_value, h2d=h2d, d2h=n_samples * words * 8, wall=t_wall)
 
 
@@ -500,17 +509,22 @@ def run_grad(args, rank, world):
 
 KERNEL_SOURCES = ("paper_2510_24218_gb300/csrc/sampler.cu", "paper_2510_24218_gb300/csrc/pw_internal.h",
                   "paper_2510_24218_gb300/csrc/smem_layout.h", "paper_2510_24218_gb300/csrc/planner.cpp")
+# the dense GEMM passes of the HBM engine: their kernels, and the planner that
+# chooses their tile, row and outer bits
+DENSE_SOURCES = ("paper_2510_24218_gb300/csrc/dense.cu", "paper_2510_24218_gb300/csrc/dense.h",
+                 "paper_2510_24218_gb300/csrc/pw_internal.h", "paper_2510_24218_gb300/csrc/planner.cpp")
 PROFILE_OF = {"grid6x6": "pw_chain_kernel_grid6x6_p2.md", "grid8x8noisy": "pw_chain_kernel_grid8x8_p2_noisy.md",
-              "heavyhex400": "pw_chain_kernel_heavyhex400_p1.md"}
+              "heavyhex400": "pw_chain_kernel_heavyhex400_p1.md",
+              "grid8x8noisy_hbm": "dense_tc_kernel_grid8x8_p2_noisy_hbm.md"}
 
 
-def kernel_sources_sha256():
+def kernel_sources_sha256(files=KERNEL_SOURCES):
     """sha256 of the kernel's sources with comments and blank space removed:
     it changes with the code, not with its comments."""
     import hashlib
     import re
     h = hashlib.sha256()
-    for f in KERNEL_SOURCES:
+    for f in files:
         with open(os.path.join(ROOT, f)) as fh:
             src = fh.read()
         src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
@@ -519,10 +533,14 @@ def kernel_sources_sha256():
     return h.hexdigest()
 
 
-def profiled_traffic(workload_name, chains_per_launch):
-    """DRAM bytes (read + write) of one FP32 launch, from the ncu capture
-    summarised under profiles/, or None when there is none for this workload
-    and launch size or the kernel sources have changed since it was taken."""
+def profiled_traffic(workload_name, chains_per_launch, algorithmic_bytes=None):
+    """DRAM bytes (read + write) of one launch of the profiled kernel, from the
+    ncu capture summarised under profiles/, or None when there is none for
+    this workload, or the kernel sources have changed since it was taken.
+    A summary of the sampler kernel gives the bytes of one launch of the
+    captured size (None for another size); a summary of the dense passes
+    gives their DRAM bytes per algorithmic byte over all passes of a run,
+    scaled here to the algorithmic bytes of the timed launches."""
     name = PROFILE_OF.get(workload_name)
     if name is None:
         return None
@@ -532,12 +550,18 @@ def profiled_traffic(workload_name, chains_per_launch):
     fields = {}
     for ln in open(path):
         if ":" in ln and ln.startswith("    ") and ln.strip().split(":")[0] in (
-                "kernel-sources-sha256", "dram-bytes-per-launch", "chains-per-launch"):
+                "kernel-sources-sha256", "dram-bytes-per-launch", "chains-per-launch",
+                "dram-bytes-per-algorithmic-byte"):
             k, v = ln.strip().split(":", 1)
             fields[k] = v.strip()
-    if fields.get("kernel-sources-sha256") != kernel_sources_sha256():
+    files = DENSE_SOURCES if workload_name.endswith("_hbm") else KERNEL_SOURCES
+    if fields.get("kernel-sources-sha256") != kernel_sources_sha256(files):
         return None
     try:
+        if "dram-bytes-per-algorithmic-byte" in fields:
+            if not algorithmic_bytes:
+                return None
+            return float(fields["dram-bytes-per-algorithmic-byte"]) * algorithmic_bytes
         if int(fields.get("chains-per-launch", -1)) != chains_per_launch:
             return None
         return float(fields["dram-bytes-per-launch"])
@@ -566,7 +590,7 @@ def roofline_of(args, r, fma_peak):
         tc = args.gemm != "fp32"
         return {"bound": "hbm", "achieved": gbs, "peak": hbm_gbs, "unit": "GB/s",
                 "frac": gbs / hbm_gbs if gbs else None,
-                "traffic": profiled_traffic(args.workload + "_hbm", r["B"]),
+                "traffic": profiled_traffic(args.workload + "_hbm", r["B"], d["bytes"] / max(1, d["passes"])),
                 "kernel": "dense_tc_kernel<6,3>" if args.gemm == "split3" else
                           ("dense_simt_kernel<6>" if not tc else f"dense_tc_kernel ({args.gemm})"),
                 "launches_timed": d["passes"], "algorithmic_bytes_per_launch": d["bytes"] / max(1, d["passes"]),
@@ -599,7 +623,9 @@ def main():
     ap.add_argument("--grad-instances", type=int, default=0,
                     help="grad3reg: time only the first N fitting instances (profiling)")
     ap.add_argument("--no-autotune", dest="autotune", action="store_false",
-                    help="keep the plan's own threads per chain (default: tune it before the warm-up)")
+                    help="keep the plan's default shape (default: search readout block size, sweep order and "
+                         "threads per chain with pw_autotune before the warm-up; results cached in "
+                         "$PW_AUTOTUNE_CACHE or the temp directory)")
     ap.add_argument("--engine", default=None, choices=list(ENGINES),
                     help="default: the workload's own (hbm for grid8x8noisy, onchip otherwise)")
     ap.add_argument("--gemm", default="split3", choices=list(GEMMS),
@@ -661,6 +687,7 @@ def main():
                                                           "chains_per_cta", "ctas_per_chain", "flops_per_sample",
                                                           "dense_tile_bits", "dense_passes_per_sample",
                                                           "dense_flops_per_sample")},
+                        "plan_shape": r["shape"],
                         "near_boundary_draws_in_warmup": int(r["near"]),
                         "comparison_samples_per_s": r["arms"],
                         "mixed_vs_fp32_same_plan": (r["value"] / r["arms"]["fp32_simt_same_plan"]

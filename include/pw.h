@@ -223,6 +223,28 @@ int pw_sample(pw_plan* plan, uint64_t seed, uint64_t first_sample, uint64_t n_sa
  * configuration runs. */
 int pw_plan_autotune(pw_plan* plan, uint64_t trial_samples, void* stream, int* chosen);
 
+/* Plan-shape search for a circuit (the schedule, not the arithmetic): builds
+ * and times plans of c over the options that change only how the sampler
+ * runs - engine (FP32 plans), max_block, order, threads_per_chain,
+ * chains_per_launch - one dimension at a time from *base (nullable: defaults),
+ * each shape timed as the fastest of two pw_sample calls of trial_samples
+ * chains (0: 16384) after a warm-up on `stream`, and writes the fastest
+ * options to *best (its rate, samples/s, to *samples_per_s, nullable).
+ * Fields of *base that are nonzero stay as given; precision and gemm are
+ * never changed. Sweep order changes which chain a seed draws (the order of
+ * commuting mixer gates), not the distribution; the other options change
+ * only the rounding of amplitudes.
+ * cache_path (nullable): a JSON-lines file, one object per tuned circuit
+ * {"key", "device", "engine", "max_block", "order", "threads_per_chain",
+ * "chains_per_launch", "samples_per_s"}; the key hashes the circuit (qubits,
+ * matrices) and the fixed options, the device names the GPU model and SM
+ * count. A matching line is returned without timing (*from_cache = 1); a new
+ * result is appended (PW_ERR_ARG if the file cannot be written). Allocates a
+ * scratch output of trial_samples words per chain and synchronises the
+ * stream. */
+int pw_autotune(const pw_circuit* c, const pw_plan_opts* base, uint64_t trial_samples, const char* cache_path,
+                void* stream, pw_plan_opts* best, double* samples_per_s, int* from_cache);
+
 /* The same with HOST buffers: h_out_bits (n_samples * ceil(n/64) uint64) and
  * the optional h_trace are written before return; device staging memory is
  * held by the plan and reused between calls. */

@@ -15,7 +15,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libpw.so")
 BUILD = os.path.join(HERE, "_build")
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
-SOURCES = ["circuit.cpp", "planner.cpp", "plan_api.cpp", "sampler.cu", "grad.cu", "perm.cu", "probe.cu", "dense.cu", "alloc.cpp"]
+SOURCES = ["circuit.cpp", "planner.cpp", "plan_api.cpp", "sampler.cu", "grad.cu", "perm.cu", "probe.cu", "dense.cu", "alloc.cpp", "autotune.cpp"]
 
 
 def _nvcc() -> str:

@@ -97,6 +97,8 @@ def load_library():
         "pw_plan_destroy": (None, [vp]),
         "pw_sample": (C.c_int, [vp, C.c_uint64, C.c_uint64, C.c_uint64, vp, vp, vp, C.POINTER(RunStats)]),
         "pw_plan_autotune": (C.c_int, [vp, C.c_uint64, vp, C.POINTER(C.c_int)]),
+        "pw_autotune": (C.c_int, [vp, C.POINTER(PlanOpts), C.c_uint64, C.c_char_p, vp, C.POINTER(PlanOpts),
+                                  dp, ip]),
         "pw_sample_host": (C.c_int, [vp, C.c_uint64, C.c_uint64, C.c_uint64, vp, vp, C.POINTER(RunStats)]),
         "pw_amplitudes": (C.c_int, [vp, C.c_int, C.c_uint64, vp, vp, vp]),
         "pw_qaoa_amp_grad": (C.c_int, [C.c_int, C.c_int, ip, dp, dp, C.c_int, dp, dp, C.POINTER(PlanOpts),
@@ -246,6 +248,24 @@ def pw_plan_autotune(plan, trial_samples=0, stream=None) -> int:
     chosen = C.c_int(0)
     _check(load_library().pw_plan_autotune(plan, int(trial_samples), _stream_ptr(stream), C.byref(chosen)))
     return chosen.value
+
+
+def pw_autotune(circ, trial_samples=0, cache_path=None, stream=None, **base):
+    """Search the plan options that change only the schedule (engine,
+    max_block, order, threads_per_chain, chains_per_launch) for circuit
+    `circ`; keyword arguments are pw_plan_build's options (nonzero ones stay
+    fixed). Returns (options dict for pw_plan_build, samples/s, from_cache)."""
+    b = PlanOpts()
+    for name, v in base.items():
+        setattr(b, name, v)
+    o = PlanOpts()
+    rate = C.c_double(0.0)
+    hit = C.c_int(0)
+    _check(load_library().pw_autotune(circ, C.byref(b), int(trial_samples),
+                                      cache_path.encode() if cache_path else None, _stream_ptr(stream),
+                                      C.byref(o), C.byref(rate), C.byref(hit)))
+    opts = {name: getattr(o, name) for name, _ in PlanOpts._fields_ if name != "reserved"}
+    return opts, rate.value, bool(hit.value)
 
 
 def pw_sample_static(plan, seed, first_sample, n_samples, out_bits, stream=None, want_stats=True):

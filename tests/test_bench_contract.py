@@ -51,9 +51,29 @@ def test_profiled_traffic_follows_the_kernel_sources(monkeypatch):
     import bench
     text = open(os.path.join(ROOT, "profiles", bench.PROFILE_OF["grid6x6"])).read()
     captured = text.split("kernel-sources-sha256:")[1].split()[0]
-    monkeypatch.setattr(bench, "kernel_sources_sha256", lambda: captured)
+    monkeypatch.setattr(bench, "kernel_sources_sha256", lambda *a: captured)
     assert bench.profiled_traffic("grid6x6", 4096) > 0
     assert bench.profiled_traffic("grid6x6", 4095) is None
     assert bench.profiled_traffic("n12", 256) is None            # no FP32 summary mapped
-    monkeypatch.setattr(bench, "kernel_sources_sha256", lambda: "0" * 64)
+    monkeypatch.setattr(bench, "kernel_sources_sha256", lambda *a: "0" * 64)
     assert bench.profiled_traffic("grid6x6", 4096) is None
+
+
+def test_dense_pass_traffic_scales_with_the_timed_launches(monkeypatch, tmp_path):
+    """The dense passes' summary gives DRAM bytes per algorithmic byte; the
+    bench scales it to the algorithmic bytes of its own launches, and drops
+    it when the dense sources no longer hash to the captured value."""
+    sys.path.insert(0, ROOT)
+    import bench
+    (tmp_path / "profiles").mkdir()
+    (tmp_path / "profiles" / "d.md").write_text(
+        "    kernel-sources-sha256: abc\n    dram-bytes-per-algorithmic-byte: 1.25\n")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    monkeypatch.setattr(bench, "PROFILE_OF", {"w_hbm": "d.md"})
+    seen = []
+    monkeypatch.setattr(bench, "kernel_sources_sha256", lambda files=bench.KERNEL_SOURCES: seen.append(files) or "abc")
+    assert bench.profiled_traffic("w_hbm", 8192, 1000.0) == 1250.0
+    assert seen[-1] == bench.DENSE_SOURCES
+    assert bench.profiled_traffic("w_hbm", 8192, None) is None
+    monkeypatch.setattr(bench, "kernel_sources_sha256", lambda files=None: "def")
+    assert bench.profiled_traffic("w_hbm", 8192, 1000.0) is None

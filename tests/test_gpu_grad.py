@@ -375,7 +375,8 @@ def test_gradient_wide_instances_against_elimination_differences(pw):
             continue
         c = pw.pw_circuit_qaoa(s.n, s.edges, s.weights, None, s.p, s.gammas, s.betas)
         try:
-            pl = pw.pw_plan_build(c)
+            # (the gradient workload's instances: frontiers that fit on chip)
+            pl = pw.pw_plan_build(c, engine=pw.PW_ENGINE_ONCHIP)
         except pw.PwError:
             pw.pw_circuit_destroy(c)
             continue
@@ -400,3 +401,35 @@ def test_gradient_wide_instances_against_elimination_differences(pw):
             for k, x in enumerate(xs):
                 fd[k, j] = (TN.amplitudes(spec.n, ops_p, x) - TN.amplitudes(spec.n, ops_m, x)) / (2 * h)
         assert np.abs(grad - fd).max() <= 2e-4 * np.abs(fd).max(), spec.name
+
+
+def test_gradient_on_the_hbm_engine(pw):
+    """A p = 3 instance whose frontier (2^18 entries) exceeds the on-chip
+    engine: every shifted-circuit amplitude runs on the HBM engine with
+    tensor-core passes; the derivatives of one string against central
+    differences (h = 1e-4) of the FP64 elimination oracle, 2e-4 of the
+    largest."""
+    import copy
+    import torch
+    from oracle import circuit as OC
+    from oracle import tn as TN
+    spec = [s for s in W.gradient_instances() if s.name == "qaoa_p3_3reg_n24_i7"][0]
+    c = pw.pw_circuit_qaoa(spec.n, spec.edges, spec.weights, None, spec.p, spec.gammas, spec.betas)
+    pl = pw.pw_plan_build(c)
+    assert pw.pw_plan_stats(pl)["engine"] == pw.PW_ENGINE_HBM
+    bits = torch.empty((1, 1), dtype=torch.int64, device="cuda")
+    pw.pw_sample(pl, 17, 0, 1, bits, None)
+    pw.pw_plan_destroy(pl)
+    pw.pw_circuit_destroy(c)
+    xs = pw.unpack_bits(bits.cpu().numpy(), spec.n)
+    _, grad = _grad(pw, spec, xs, 0)
+    h = 1e-4
+    fd = np.zeros_like(grad)
+    for j in range(2 * spec.p):
+        sp, sm = copy.deepcopy(spec), copy.deepcopy(spec)
+        arr = "gammas" if j < spec.p else "betas"
+        getattr(sp, arr)[j % spec.p] += h
+        getattr(sm, arr)[j % spec.p] -= h
+        fd[0, j] = (TN.amplitudes(spec.n, OC.qaoa_circuit(sp), xs[0]) -
+                    TN.amplitudes(spec.n, OC.qaoa_circuit(sm), xs[0])) / (2 * h)
+    assert np.abs(grad - fd).max() <= 2e-4 * np.abs(fd).max()
