@@ -237,8 +237,7 @@ int pw_plan_autotune(pw_plan* plan, uint64_t trial_samples, void* stream, int* c
  * cache_path (nullable): a JSON-lines file, one object per tuned circuit
  * {"key", "device", "engine", "max_block", "order", "threads_per_chain",
  * "chains_per_launch", "samples_per_s"}; the key hashes the circuit (qubits,
- * matrices) and the fixed options, the device names the GPU model and SM
- * count. A matching line is returned without timing (*from_cache = 1); a new
+ * matrices) and *base, the device names the GPU model and SM count. A matching line is returned without timing (*from_cache = 1); a new
  * result is appended (PW_ERR_ARG if the file cannot be written). Allocates a
  * scratch output of trial_samples words per chain and synchronises the
  * stream. */

@@ -18,8 +18,8 @@ using namespace pw;
 
 namespace {
 
-// FNV-1a over the bytes of the circuit and the options that fix the result's
-// precision (precision, gemm) or that the caller pinned (nonzero fields).
+// FNV-1a over the bytes of the circuit and the options as given (the
+// precision, the arithmetic and the fields the caller pinned).
 struct Fnv {
     uint64_t h = 1469598103934665603ull;
     void bytes(const void* p, size_t n) {
@@ -41,10 +41,9 @@ uint64_t circuit_key(const pw_circuit* c, const pw_plan_opts& o) {
         for (int q : op.qubits) f.val(q);
         f.bytes(op.mats.data(), op.mats.size() * sizeof(cd));
     }
-    f.val(o.precision);
-    f.val(o.gemm);
-    f.val(o.engine);
-    f.val(o.ctas_per_chain);
+    for (int v : {o.precision, o.order, o.max_block, o.threads_per_chain, o.chains_per_launch, o.ctas_per_chain,
+                  o.engine, o.gemm})
+        f.val(v);
     return f.h;
 }
 
