@@ -20,10 +20,11 @@
 //     each) and the products of total order below NP are accumulated: one
 //     product for NP = 1 (plain BF16), three for NP = 2, six for NP = 3
 //     (inputs represented to 24 bits, the FP32 significand). One warp issues
-//     the MMAs, four producer warps gather the A tiles (rows of 2^k entries at
-//     scattered index bits) and write the BF16 terms into shared memory in the
-//     128-byte-swizzled K-major layout, four epilogue warps read the
-//     accumulators back (tcgen05.ld) and scatter the rows to HBM. The B
+//     the MMAs, eight producer warps gather the A tiles (rows of 2^k entries
+//     at scattered index bits) and write the BF16 terms into shared memory in
+//     the 128-byte-swizzled K-major layout, eight epilogue warps (two per
+//     quarter of the accumulator lanes) read the accumulators back
+//     (tcgen05.ld) and scatter the rows to HBM. The B
 //     operand (one per tensor) is split into its BF16 term planes by the
 //     producers, from the operator's FP32 copy in HBM, whenever the tile
 //     sequence of a CTA reaches the next tensor.
@@ -113,46 +114,63 @@ __device__ __forceinline__ void umma_commit(uint64_t* bar) {
                  : "memory");
 }
 
-// 32 lanes x 32 columns of 32-bit accumulators (lane = this warp's quarter of
-// the 128 rows, register j = column col + j).
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
-    uint32_t r[32];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-        : "r"(taddr)
-        : "memory");
+// 16 lanes x 256 bits of 32-bit accumulators, repeated along the columns
+// (NREP = 4 or 8: 32 or 64 columns): thread t holds lane t / 4 in registers
+// 4 i and 4 i + 1, lane t / 4 + 8 in 4 i + 2 and 4 i + 3, at columns
+// col + 8 i + 2 (t % 4) and + 1 (the accumulator fragment of a 16-row MMA).
+template <int NREP> __device__ __forceinline__ void tmem_ld16x256(uint32_t taddr, float (&v)[4 * NREP]) {
+    uint32_t r[4 * NREP];
+    if constexpr (NREP == 8) {
+        asm volatile(
+            "tcgen05.ld.sync.aligned.16x256b.x8.b32 "
+            "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+            "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+              "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+              "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+              "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+            : "r"(taddr)
+            : "memory");
+    } else {
+        static_assert(NREP == 4, "16x256b loads of 4 or 8 repetitions");
+        asm volatile(
+            "tcgen05.ld.sync.aligned.16x256b.x4.b32 "
+            "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+              "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+            : "r"(taddr)
+            : "memory");
+    }
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-    for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
+    for (int j = 0; j < 4 * NREP; ++j) v[j] = __uint_as_float(r[j]);
 }
 
-// The BF16 terms of x (round to nearest at every step): x = t0 + t1 (+ t2)
-// exactly for NP = 3 (the 24 significant bits of an FP32 value), to about
-// 2^-17 |x| for NP = 2.
-template <int NP> __device__ __forceinline__ void split_bf16(float x, __nv_bfloat16 (&t)[NP]) {
-    t[0] = __float2bfloat16_rn(x);
-    if constexpr (NP >= 2) {
-        const float r1 = x - __bfloat162float(t[0]);
-        t[1] = __float2bfloat16_rn(r1);
-        if constexpr (NP >= 3) t[2] = __float2bfloat16_rn(r1 - __bfloat162float(t[1]));
+// The BF16 terms of a pair (x, y), converted together (round to nearest at
+// every step): x = t0 + t1 (+ t2) exactly for NP = 3 (the 24 significant bits
+// of an FP32 value), to about 2^-17 |x| for NP = 2. Word q holds term q of x
+// in its low half and of y in its high half.
+template <int NP> __device__ __forceinline__ void split_pair(float x, float y, uint32_t (&w)[NP]) {
+    float2 r = make_float2(x, y);
+#pragma unroll
+    for (int q = 0; q < NP; ++q) {
+        const __nv_bfloat162 t = __float22bfloat162_rn(r);
+        w[q] = *reinterpret_cast<const uint32_t*>(&t);
+        if (q + 1 < NP) {
+            const float2 f = __bfloat1622float2(t);
+            r.x -= f.x;
+            r.y -= f.y;
+        }
     }
 }
 
 // Word j of every term plane: the BF16 terms of (re, im) side by side (re in
 // the low half: k index 2j before 2j + 1).
 template <int NP> __device__ __forceinline__ void pack_terms(float re, float im, uint32_t (&h)[NP][4], int j) {
-    __nv_bfloat16 tr[NP], ti[NP];
-    split_bf16<NP>(re, tr);
-    split_bf16<NP>(im, ti);
+    uint32_t w[NP];
+    split_pair<NP>(re, im, w);
 #pragma unroll
-    for (int q = 0; q < NP; ++q)
-        h[q][j] = (uint32_t)__bfloat16_as_ushort(tr[q]) | ((uint32_t)__bfloat16_as_ushort(ti[q]) << 16);
+    for (int q = 0; q < NP; ++q) h[q][j] = w[q];
 }
 
 // Byte offset of the 16-byte chunk c (8 BF16 values, k index 8c..8c+7 of the
@@ -160,6 +178,14 @@ template <int NP> __device__ __forceinline__ void pack_terms(float re, float im,
 // operand of `rows` rows: K blocks of 64 values are rows x 128 bytes apart.
 __device__ __forceinline__ uint32_t sw128_chunk(int rows, int r, int kb, int c) {
     return (uint32_t)(kb * rows * 128 + r * 128 + ((c ^ (r & 7)) << 4));
+}
+
+// Byte offset of complex entry (row r, column c) of the A operand: the
+// 4-byte (re, im) pair of c in its 16-byte chunk (c >> 2) & 7. Every field is
+// an XOR of bits of r and c (bits 2, 3: c; 4..6: c ^ r; 7..13: r; 14: c), so
+// the offsets of disjoint bit sets combine by XOR.
+__device__ __forceinline__ int a_offset(int r, int c) {
+    return (int)sw128_chunk(128, r, c >> 5, (c >> 2) & 7) + ((c & 3) << 2);
 }
 
 __device__ __forceinline__ float2 cmulf(float2 a, float2 b) {
@@ -182,9 +208,14 @@ template <int KT, int NP> struct TcCfg {
     static constexpr int SA = (NP * PLANE_B + 2 * NP * PLANE_A) <= 200 * 1024 ? 2 : 1;   // A stages
     static constexpr int TMEM_COLS = 2 * KR;    // two accumulators
     static constexpr size_t SMEM = (size_t)NP * PLANE_B + (size_t)SA * NP * PLANE_A + 6144;
-    // 8 epilogue warps (two per quarter of the accumulator lanes, each reading
-    // half of the columns), 8 producer warps, 1 MMA warp
-    static constexpr int THREADS = 544;
+    // EW epilogue warps (one or two per quarter of the accumulator lanes,
+    // reading all or half of the columns), 8 producer warps, 1 MMA warp. With
+    // 13 warps (EW = 4) every sub-partition of the SM holds at most four, so
+    // a thread may use 128 registers (the producers' register stages of a
+    // tile and of an operator); 17 warps allow 96
+    static constexpr int EW = 8;
+    static constexpr int THREADS = 32 * (EW + 9);
+    static constexpr int PROD0 = EW, MMAW = EW + 8;   // first producer warp, MMA warp
 };
 
 // Per-CTA index tables of a pass. The storage position of logical index i
@@ -196,11 +227,13 @@ template <int KT, int NP> struct TcCfg {
 struct PassTables {
     int prow[128], drow[128];
     int pcol[64], dcol[64];
-    // the tile's 2^(k+7) entries in index order: entry e has the tile's
-    // (row and column) bits in ascending position, e's low 6 bits giving the
-    // lowest six of them; positions and (row | column << 8) of both halves
-    int plo[64], rtlo[64];
-    int phi[128], rthi[128];
+    int tcol[64];   // operator index of GEMM column g (its bit j is bit col_of[j] of the index)
+    // the tile's 2^(k+7) entries in the producers' order: bit i of entry e
+    // is tensor index bit e_bits[i] (its low 5 bits, a warp's lanes, the
+    // lowest bits or nearly); tensor positions and A-operand byte offsets of
+    // the low 6 and the high k + 1 bits of e (both XOR-linear in the bits)
+    int plo[64], slo[64];
+    int phi[128], shi[128];
 };
 
 __device__ __forceinline__ int64_t swz64(int64_t i, int swz) { return swz ? (i ^ ((i >> 4) & 15)) : i; }
@@ -214,19 +247,16 @@ __device__ __forceinline__ int diag_index_bits(const DenseArgs& a, int64_t i) {
 
 __device__ void fill_pass_tables(const DenseArgs& a, PassTables* T, int tid, int nthreads) {
     {
-        // the tile's bits in ascending order, with their row / column role
-        int pos[13], role[13], nb = 0;   // role: row bit j (j), or column bit j (16 + j)
-        for (int b = 0; b < a.W && nb < a.k + 7; ++b) {
+        // the entry bits with their row / column role
+        int pos[13], role[13];   // role: row bit j (j), or GEMM column bit j (16 + j)
+        const int nb = a.k + 7;
+        for (int i = 0; i < nb; ++i) {
+            pos[i] = a.e_bits[i];
+            role[i] = 0;
             for (int j = 0; j < 7; ++j)
-                if (a.row_pos[j] == b) {
-                    pos[nb] = b;
-                    role[nb++] = j;
-                }
+                if (a.row_pos[j] == pos[i]) role[i] = j;
             for (int j = 0; j < a.k; ++j)
-                if (a.tile_pos[j] == b) {
-                    pos[nb] = b;
-                    role[nb++] = 16 + j;
-                }
+                if (a.tile_pos[a.col_of[j]] == pos[i]) role[i] = 16 + j;
         }
         for (int u = tid; u < 64 + (1 << (a.k + 1)); u += nthreads) {
             const bool lo = u < 64;
@@ -241,10 +271,10 @@ __device__ void fill_pass_tables(const DenseArgs& a, PassTables* T, int tid, int
                 }
             if (lo) {
                 T->plo[e] = (int)swz64(off, a.swz);
-                T->rtlo[e] = rt;
+                T->slo[e] = a_offset(rt & 255, rt >> 8);
             } else {
                 T->phi[e] = (int)swz64(off, a.swz);
-                T->rthi[e] = rt;
+                T->shi[e] = a_offset(rt & 255, rt >> 8);
             }
         }
     }
@@ -256,9 +286,14 @@ __device__ void fill_pass_tables(const DenseArgs& a, PassTables* T, int tid, int
     }
     for (int t = tid; t < (1 << a.k); t += nthreads) {
         int64_t o = 0;
-        for (int b = 0; b < a.k; ++b) o |= (int64_t)((t >> b) & 1) << a.tile_pos[b];
+        int ti = 0;
+        for (int b = 0; b < a.k; ++b) {
+            o |= (int64_t)((t >> b) & 1) << a.tile_pos[a.col_of[b]];
+            ti |= ((t >> b) & 1) << a.col_of[b];
+        }
         T->pcol[t] = (int)swz64(o, a.swz);
         T->dcol[t] = diag_index_bits(a, o);
+        T->tcol[t] = ti;
     }
 }
 
@@ -270,20 +305,54 @@ __device__ __forceinline__ float2 diag_product(const float2* tab, int ndiag, int
     return f;
 }
 
+// The deferred diagonal factors of rows a and b at this thread's NR columns
+// (packed table indices da ^ dc[i], dc[i] = dcl[cs i]): per factor, the
+// lookups of all 2 NR outputs are issued together, then multiplied in, so a
+// shared-memory latency is paid once per factor rather than per output.
+template <int NR>
+__device__ __forceinline__ void row_factors(const float2* tab, int nd, int da, int db, const int* dcl, int cs,
+                                            float2 (&fa)[NR], float2 (&fb)[NR]) {
+    int dc[NR];
+#pragma unroll
+    for (int i = 0; i < NR; ++i) dc[i] = dcl[cs * i];
+#pragma unroll
+    for (int i = 0; i < NR; ++i) {
+        fa[i] = tab[(da ^ dc[i]) & 31];
+        fb[i] = tab[(db ^ dc[i]) & 31];
+    }
+    for (int d = 1; d < nd; ++d) {
+        float2 ga[NR], gb[NR];
+#pragma unroll
+        for (int i = 0; i < NR; ++i) {
+            ga[i] = tab[32 * d + (((da ^ dc[i]) >> (8 * d)) & 31)];
+            gb[i] = tab[32 * d + (((db ^ dc[i]) >> (8 * d)) & 31)];
+        }
+#pragma unroll
+        for (int i = 0; i < NR; ++i) {
+            fa[i] = cmulf(fa[i], ga[i]);
+            fb[i] = cmulf(fb[i], gb[i]);
+        }
+    }
+}
+
 template <int KT, int NP>
-__global__ void __launch_bounds__(544, 1) dense_tc_kernel(const DenseArgs a) {
+__global__ void __launch_bounds__(TcCfg<KT, NP>::THREADS, 1) dense_tc_kernel(const DenseArgs a) {
     using Cfg = TcCfg<KT, NP>;
     constexpr int TE = Cfg::TE, KR = Cfg::KR, SA = Cfg::SA;
     constexpr int PCOLS = TE / 2;   // columns of one producer thread
     extern __shared__ __align__(1024) unsigned char smem_raw[];
-    unsigned char* smem = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    // (rounded up to 1024 bytes by pointer arithmetic on the shared array, so
+    // that every pointer derived from it stays a shared-memory pointer: plain
+    // shared loads and stores, which the compiler keeps apart from the global
+    // ones)
+    unsigned char* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
     unsigned char* sB = smem;                                   // NP planes of B
     unsigned char* sA = smem + NP * Cfg::PLANE_B;               // SA stages x NP planes of A
     uint64_t* bars = reinterpret_cast<uint64_t*>(sA + SA * NP * Cfg::PLANE_A);
     uint64_t* a_full = bars;            // [SA] producers -> MMA (256 arrivals)
     uint64_t* a_empty = bars + SA;      // [SA] MMA commit -> producers
     uint64_t* acc_full = bars + 2 * SA; // [2] MMA commit -> epilogue
-    uint64_t* acc_empty = bars + 2 * SA + 2;   // [2] epilogue (256 arrivals) -> MMA
+    uint64_t* acc_empty = bars + 2 * SA + 2;   // [2] epilogue (32 EW arrivals) -> MMA
     int* misc = reinterpret_cast<int*>(bars + 2 * SA + 5);
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(misc);     // written by tcgen05.alloc
     volatile int* abort_flag = misc + 1;                         // a bounded wait ran out
@@ -306,12 +375,12 @@ __global__ void __launch_bounds__(544, 1) dense_tc_kernel(const DenseArgs a) {
         }
         for (int s = 0; s < 2; ++s) {
             mbar_init(&acc_full[s], 1);
-            mbar_init(&acc_empty[s], 256);
+            mbar_init(&acc_empty[s], 32 * Cfg::EW);
         }
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == 16) {
+    if (warp == Cfg::MMAW) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
                      "r"((uint32_t)Cfg::TMEM_COLS)
                      : "memory");
@@ -322,70 +391,79 @@ __global__ void __launch_bounds__(544, 1) dense_tc_kernel(const DenseArgs a) {
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
 
-    if (warp >= 8 && warp < 16) {
+    if (warp >= Cfg::PROD0 && warp < Cfg::MMAW) {
         // ---------------------------------------------------------- producers
         // thread pt loads the tile's entries e = pt + 256 j in index order: the
         // lanes of a warp cover the tile's lowest index bits (its lowest 5,
         // which are the tensor's lowest 5 since the row bits are the lowest
         // free ones), so every warp load reads whole 128-byte lines
-        const int pt = tid - 256;
+        const int pt = tid - 32 * Cfg::PROD0;
+        constexpr int BITEMS = TE * TE / 4 / 256;   // operator chunks (4 complex entries) per thread
         uint64_t cur = ~0ull;                  // tensor whose operator is in the B planes
         for (uint64_t t = t_begin; t < t_end; ++t) {
             const uint64_t it = t - t_begin;
             const int s = (int)(it % SA);
             const uint64_t tens = t / tiles_per, o = t % tiles_per;
-            if (tens != cur) {
+            const bool newt = tens != cur;
+            // positions combine by XOR (the swizzle mixes the bits of the
+            // parts); the tile's loads are in flight while the previous tile's
+            // MMAs still read the shared stage (a register stage in front of
+            // the shared one), except after a tensor change
+            const float2* src = a.L + tens * N;
+            const int64_t pr = swz64(outer_offset(a, o), a.swz) ^ T->plo[pt & 63];
+            const int sl = T->slo[pt & 63];
+            unsigned char* stage = sA + (size_t)s * NP * Cfg::PLANE_A;
+            if (newt) {
                 // every MMA of the previous tile is complete before B changes;
-                // then the producers write this tensor's operator into the B
-                // term planes (real block form, K-major, 128-byte swizzle),
-                // from its FP32 copy in HBM: one 16-byte chunk (4 complex
-                // entries of one output real) per item
+                // then this tensor's operator goes into the B term planes (real
+                // block form, K-major, 128-byte swizzle): per operator chunk
+                // (row t', complex columns 4g..4g+3) the 16-byte chunks g of
+                // output reals 2t' and 2t' + 1
                 if (it > 0 && !mbar_wait(&a_empty[(it - 1) % SA], (uint32_t)(((it - 1) / SA) & 1), abort_flag)) break;
+                float2 w[BITEMS][4];   // (all loads issued before the first use)
                 const float2* op = a.ops + tens * (uint64_t)TE * TE;
-                for (int u = pt; u < KR * (KR / 8); u += 256) {
-                    const int n = u / (KR / 8), g = u % (KR / 8);   // output real n, chunk g (reals 8g..8g+7)
-                    const int cp = n & 1;
-                    const float4* w4 = reinterpret_cast<const float4*>(op + (n >> 1) * TE + 4 * g);
-                    const float4 w01 = w4[0], w23 = w4[1];
-                    const float2 w[4] = {make_float2(w01.x, w01.y), make_float2(w01.z, w01.w),
-                                         make_float2(w23.x, w23.y), make_float2(w23.z, w23.w)};
-                    uint32_t h[NP][4];
 #pragma unroll
-                    for (int j = 0; j < 4; ++j)   // row (t', cp) of [[Re, -Im], [Im, Re]] against (t, re), (t, im)
-                        pack_terms<NP>(cp == 0 ? w[j].x : w[j].y, cp == 0 ? -w[j].y : w[j].x, h, j);
-                    const uint32_t off = sw128_chunk(KR, n, g >> 3, g & 7);
+                for (int i = 0; i < BITEMS; ++i) {
+                    const int u = pt + 256 * i, tp = u / (TE / 4), g = u % (TE / 4);
+                    const float2* orow = op + T->tcol[tp] * TE;   // (GEMM columns in operator order)
 #pragma unroll
-                    for (int qq = 0; qq < NP; ++qq)
-                        *reinterpret_cast<uint4*>(sB + qq * Cfg::PLANE_B + off) = make_uint4(h[qq][0], h[qq][1], h[qq][2], h[qq][3]);
+                    for (int j = 0; j < 4; ++j) w[i][j] = orow[T->tcol[4 * g + j]];
+                }
+#pragma unroll
+                for (int i = 0; i < BITEMS; ++i) {
+                    const int u = pt + 256 * i, tp = u / (TE / 4), g = u % (TE / 4);
+#pragma unroll
+                    for (int cp = 0; cp < 2; ++cp) {
+                        const int n = 2 * tp + cp;
+                        uint32_t h[NP][4];
+#pragma unroll
+                        for (int j = 0; j < 4; ++j)   // row (t', cp) of [[Re, -Im], [Im, Re]] against (t, re), (t, im)
+                            pack_terms<NP>(cp == 0 ? w[i][j].x : w[i][j].y, cp == 0 ? -w[i][j].y : w[i][j].x, h, j);
+                        const uint32_t off = sw128_chunk(KR, n, g >> 3, g & 7);
+#pragma unroll
+                        for (int qq = 0; qq < NP; ++qq)
+                            *reinterpret_cast<uint4*>(sB + qq * Cfg::PLANE_B + off) =
+                                make_uint4(h[qq][0], h[qq][1], h[qq][2], h[qq][3]);
+                    }
                 }
                 cur = tens;
             }
-            // (positions combine by XOR: the swizzle mixes the bits of the parts)
-            const float2* src = a.L + tens * N;
-            const int64_t pr = swz64(outer_offset(a, o), a.swz) ^ T->plo[pt & 63];
-            const int rtl = T->rtlo[pt & 63];
-            unsigned char* stage = sA + (size_t)s * NP * Cfg::PLANE_A;
-            // the loads are in flight while the stage is still being read by
-            // the previous tile's MMAs (a register stage in front of the shared one)
             float2 v[PCOLS];
 #pragma unroll
             for (int j = 0; j < PCOLS; ++j) v[j] = src[pr ^ T->phi[(pt >> 6) + 4 * j]];
             if (it >= (uint64_t)SA && !mbar_wait(&a_empty[s], (uint32_t)(((it / SA) - 1) & 1), abort_flag)) break;
 #pragma unroll
             for (int j = 0; j < PCOLS; ++j) {
-                const int rt = rtl | T->rthi[(pt >> 6) + 4 * j];
-                const int r = rt & 255, c = rt >> 8;   // row, operator column (complex entry)
-                uint32_t h[NP][4];
-                pack_terms<NP>(v[j].x, v[j].y, h, 0);
-                // the 4-byte (re, im) pair of entry c in its 16-byte chunk (c >> 2) & 7
-                const uint32_t off = sw128_chunk(128, r, c >> 5, (c >> 2) & 7) + (uint32_t)((c & 3) << 2);
+                uint32_t w[NP];
+                split_pair<NP>(v[j].x, v[j].y, w);
+                const int off = sl ^ T->shi[(pt >> 6) + 4 * j];
 #pragma unroll
-                for (int q = 0; q < NP; ++q) *reinterpret_cast<uint32_t*>(stage + q * Cfg::PLANE_A + off) = h[q][0];
+                for (int q = 0; q < NP; ++q) *reinterpret_cast<uint32_t*>(stage + q * Cfg::PLANE_A + off) = w[q];
             }
             fence_async_smem();
             mbar_arrive(&a_full[s]);
         }
-    } else if (warp == 16) {
+    } else if (warp == Cfg::MMAW) {
         // -------------------------------------------------------------- MMA
         const uint32_t idesc = idesc_bf16(KR);
         for (uint64_t t = t_begin; t < t_end; ++t) {
@@ -425,55 +503,75 @@ __global__ void __launch_bounds__(544, 1) dense_tc_kernel(const DenseArgs a) {
     } else {
         // --------------------------------------------------------- epilogue
         // warp w reads accumulator lanes 32 (w % 4) .. + 31 (tile rows) and
-        // columns of half w / 4
-        constexpr int EC = TE / 2;   // complex columns per thread
-        const int q = warp & 3, hh = warp >> 2;
-        const int r = 32 * q + lane;
-        const int* pc = T->pcol + hh * EC;
+        // the columns of its halves (both, or half w / 4), 16 lanes at a time:
+        // lane t holds rows t / 4 and t / 4 + 8 of the 16 at complex columns
+        // t % 4 (+ 4 i), so a warp's store covers row bits 0..2 and column
+        // bits 0, 1, which the host puts on the tensor's lowest index bits
+        // (whole sectors)
+        constexpr int EW = Cfg::EW;
+        constexpr int NH = 8 / EW;          // column halves per warp
+        constexpr int EC = TE / 2;          // complex columns of a half
+        constexpr int NREP = EC / 4;        // 16x256b repetitions (8 real columns each)
+        const int q = warp & 3, h0 = NH == 1 ? warp >> 2 : 0;
+        const int rq = lane >> 2, cq = lane & 3;
+        const int* pcl = T->pcol + h0 * EC + cq;   // column c of half hi: [hi * EC + 4 i]
+        const int* dcl = T->dcol + h0 * EC + cq;
         uint64_t cur = ~0ull;
         for (uint64_t t = t_begin; t < t_end; ++t) {
             const uint64_t it = t - t_begin;
             const int ab = (int)(it & 1);
             const uint64_t tens = t / tiles_per, o = t % tiles_per;
             if (a.ndiag && tens != cur) {
-                // this tensor's diagonal tables (the eight epilogue warps: named barrier 1)
-                asm volatile("bar.sync 1, 256;" ::: "memory");
-                for (int e = tid; e < a.ndiag * 32; e += 256) stab[e] = a.diag[tens * (uint64_t)a.diag_stride + e];
-                asm volatile("bar.sync 1, 256;" ::: "memory");
+                // this tensor's diagonal tables (the epilogue warps: named barrier 1)
+                asm volatile("bar.sync 1, %0;" ::"r"(32 * EW) : "memory");
+                for (int e = tid; e < a.ndiag * 32; e += 32 * EW) stab[e] = a.diag[tens * (uint64_t)a.diag_stride + e];
+                asm volatile("bar.sync 1, %0;" ::"r"(32 * EW) : "memory");
                 cur = tens;
             }
             if (!mbar_wait(&acc_full[ab], (uint32_t)((it >> 1) & 1), abort_flag)) break;
             tc_fence_after();
             const int64_t ob = outer_offset(a, o);
             float2* dst = a.L + tens * N;
-            const int64_t pr = swz64(ob, a.swz) ^ T->prow[r];
-            const int dr = diag_index_bits(a, ob) ^ T->drow[r];
+            const int64_t pob = swz64(ob, a.swz);
+            const int dob = diag_index_bits(a, ob);
 #pragma unroll
-            for (int c = 0; c < EC / 16; ++c) {
-                float v[32];
-                tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(ab * KR + hh * (KR / 2) + c * 32), v);
-                if (c == EC / 16 - 1) {
-                    tc_fence_before();
-                    mbar_arrive(&acc_empty[ab]);
-                }
-                if (a.ndiag) {
+            for (int hi = 0; hi < NH; ++hi)
 #pragma unroll
-                    for (int j = 0; j < 16; ++j) {
-                        const int col = hh * EC + c * 16 + j;
-                        const float2 y = cmulf(make_float2(v[2 * j], v[2 * j + 1]),
-                                               diag_product(stab, a.ndiag, dr ^ T->dcol[col]));
-                        dst[pr ^ pc[c * 16 + j]] = y;
+                for (int hp = 0; hp < 2; ++hp) {
+                    const int r0 = 32 * q + 16 * hp + rq, r1 = r0 + 8;
+                    const int64_t p0 = pob ^ T->prow[r0], p1 = pob ^ T->prow[r1];
+                    float2 f0[NREP], f1[NREP];
+                    if (a.ndiag)
+                        row_factors<NREP>(stab, a.ndiag, dob ^ T->drow[r0], dob ^ T->drow[r1], dcl + hi * EC, 4, f0, f1);
+                    float v[4 * NREP];
+                    tmem_ld16x256<NREP>(tmem + ((uint32_t)(32 * q + 16 * hp) << 16) +
+                                            (uint32_t)(ab * KR + (h0 + hi) * (KR / 2)),
+                                        v);
+                    if (hi == NH - 1 && hp == 1) {
+                        tc_fence_before();
+                        mbar_arrive(&acc_empty[ab]);
                     }
-                } else {
+                    if (a.ndiag) {
 #pragma unroll
-                    for (int j = 0; j < 16; ++j) dst[pr ^ pc[c * 16 + j]] = make_float2(v[2 * j], v[2 * j + 1]);
+                        for (int i = 0; i < NREP; ++i) {
+                            const int pc = pcl[hi * EC + 4 * i];
+                            dst[p0 ^ pc] = cmulf(make_float2(v[4 * i], v[4 * i + 1]), f0[i]);
+                            dst[p1 ^ pc] = cmulf(make_float2(v[4 * i + 2], v[4 * i + 3]), f1[i]);
+                        }
+                    } else {
+#pragma unroll
+                        for (int i = 0; i < NREP; ++i) {
+                            const int pc = pcl[hi * EC + 4 * i];
+                            dst[p0 ^ pc] = make_float2(v[4 * i], v[4 * i + 1]);
+                            dst[p1 ^ pc] = make_float2(v[4 * i + 2], v[4 * i + 3]);
+                        }
+                    }
                 }
-            }
         }
     }
     tc_fence_before();
     __syncthreads();
-    if (warp == 16) {
+    if (warp == Cfg::MMAW) {
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)Cfg::TMEM_COLS)
                      : "memory");
@@ -506,8 +604,8 @@ __global__ void __launch_bounds__(256) dense_simt_kernel(const DenseArgs a) {
         if (tens != cur) {
             const float2* op = a.ops + tens * (uint64_t)TE * TE;
             for (int e = tid; e < TE * TE; e += 256) {
-                const int tp = e / TE, ti = e % TE;
-                sO[ti * TE + tp] = op[e];
+                const int tp = e / TE, ti = e % TE;   // GEMM column indices
+                sO[ti * TE + tp] = op[T.tcol[tp] * TE + T.tcol[ti]];
             }
             for (int e = tid; e < a.ndiag * 32; e += 256) stab[e] = a.diag[tens * (uint64_t)a.diag_stride + e];
             cur = tens;
@@ -604,7 +702,73 @@ template <int KT> int launch_simt(const DenseArgs& a, int nsm, cudaStream_t st, 
 
 }  // namespace
 
-int dense_run(int gemm, const DenseArgs& a, cudaStream_t st, cudaEvent_t t0, cudaEvent_t t1) {
+namespace {
+
+// The order of the GEMM's rows and columns and of the producers' entries,
+// chosen per pass from the bit roles. The producers' lanes (entry bits 0..4)
+// take the tensor's lowest tile or row bits (whole sectors per warp load),
+// with at least two column bits among them: the lanes' columns become the
+// GEMM's lowest column bits and their rows row bits max(0, x - 2).. (x the
+// lanes' columns), so that the A operand's 4-byte words written by a warp
+// fall in 32 distinct banks (the 128-byte swizzle puts word (c & 3) +
+// 4 ((c >> 2) ^ r) mod 8 of row r in bank order). The epilogue's lanes cover
+// column bits 0, 1 and row bits 0..2: the same lowest bits.
+void arrange_roles(DenseArgs& a) {
+    struct Bit {
+        int pos, col;   // tensor index bit; operator index bit, or -1 for a row bit
+    };
+    const int nb = a.k + 7;
+    Bit all[13];
+    for (int j = 0; j < a.k; ++j) all[j] = {a.tile_pos[j], j};
+    for (int j = 0; j < 7; ++j) all[a.k + j] = {a.row_pos[j], -1};
+    std::sort(all, all + nb, [](const Bit& x, const Bit& y) { return x.pos < y.pos; });
+    bool lane[13] = {};
+    int x = 0;
+    for (int i = 0; i < 5; ++i) {
+        lane[i] = true;
+        x += all[i].col >= 0;
+    }
+    // fewer than two columns among the lowest five: the lowest (5 - y) bits
+    // and the y lowest columns above them
+    for (int y = 2 - x; y > 0; --y) {
+        for (int i = 4; i >= 0; --i)
+            if (lane[i] && all[i].col < 0) {
+                lane[i] = false;
+                break;
+            }
+        for (int i = 5; i < nb; ++i)
+            if (!lane[i] && all[i].col >= 0) {
+                lane[i] = true;
+                break;
+            }
+    }
+    int xl = 0;
+    for (int i = 0; i < nb; ++i) xl += lane[i] && all[i].col >= 0;
+    int nc = 0, ne = 0, rows[7];
+    for (int j = 0; j < 7; ++j) rows[j] = -1;
+    int nr = std::max(0, xl - 2);
+    for (int pass = 0; pass < 2; ++pass)
+        for (int i = 0; i < nb; ++i) {
+            if (lane[i] != (pass == 0)) continue;
+            a.e_bits[ne++] = all[i].pos;
+            if (all[i].col >= 0) {
+                a.col_of[nc++] = all[i].col;
+            } else if (pass == 0) {
+                rows[nr++] = all[i].pos;
+            } else {
+                int j = 0;
+                while (rows[j] >= 0) ++j;
+                rows[j] = all[i].pos;
+            }
+        }
+    for (int j = 0; j < 7; ++j) a.row_pos[j] = rows[j];
+}
+
+}  // namespace
+
+int dense_run(int gemm, const DenseArgs& args, cudaStream_t st, cudaEvent_t t0, cudaEvent_t t1) {
+    DenseArgs a = args;
+    arrange_roles(a);
     int dev = 0, nsm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);

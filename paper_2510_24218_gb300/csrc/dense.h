@@ -28,6 +28,11 @@ struct DenseArgs {
     int diag_nb[4];
     int diag_pos[4][5];
     int* err;              // device flag: a bounded wait ran out
+    // set by dense_run (any order of the row bits above is accepted and
+    // replaced): the GEMM's column bit j is operator index bit col_of[j], and
+    // the producers' entry order takes tensor index bit e_bits[i] as bit i
+    int col_of[8];
+    int e_bits[13];
 };
 
 // Enqueue one pass on stream st; t0 / t1 (nullable) are recorded right

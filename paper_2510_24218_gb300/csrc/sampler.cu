@@ -776,14 +776,32 @@ __device__ void readout_and_sample(const KParams& p, const Chain<R>& ch, const G
         }
         ch.part[g.lt] = mk<R>(acc[0].x + acc[1].x + acc[2].x + acc[3].x, acc[0].y + acc[1].y + acc[2].y + acc[3].y);
     } else {
+        // eight rows in flight per thread (the frontier of the HBM engine is
+        // read from HBM here), summed in a fixed order
         for (int hh = g.lt; hh < H; hh += g.nt) {
-            C acc = zero;
-            for (int l = 0; l < NLl; ++l) {
+            C acc[8] = {zero, zero, zero, zero, zero, zero, zero, zero};
+            int l = 0;
+            for (; l + 8 <= NLl; l += 8) {
+                C v[8];
+#pragma unroll
+                for (int a = 0; a < 8; ++a) v[a] = L[swz((l + a) * H + hh)];
+#pragma unroll
+                for (int a = 0; a < 8; ++a) {
+                    acc[a] = cfma(v[a], Rk[swz(l0 + l + a)], acc[a]);
+                    mx = rmax(mx, rmax(rabs(v[a].x), rabs(v[a].y)));
+                }
+            }
+            for (; l < NLl; ++l) {
                 const C v = L[swz(l * H + hh)];
-                acc = cfma(v, Rk[swz(l0 + l)], acc);
+                acc[0] = cfma(v, Rk[swz(l0 + l)], acc[0]);
                 mx = rmax(mx, rmax(rabs(v.x), rabs(v.y)));
             }
-            ch.rowdot[hh] = acc;
+#pragma unroll
+            for (int a = 1; a < 8; ++a) {
+                acc[0].x += acc[a].x;
+                acc[0].y += acc[a].y;
+            }
+            ch.rowdot[hh] = acc[0];
         }
     }
     // The readout weight of a top configuration hv is the product over the S
