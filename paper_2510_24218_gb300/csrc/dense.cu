@@ -205,9 +205,16 @@ template <int KT, int NP> struct TcCfg {
     static constexpr int PLANE_A = 128 * KR * 2;
     static constexpr int PLANE_B = KR * KR * 2;
     static constexpr int NPROD = NP == 1 ? 1 : NP == 2 ? 3 : 6;
-    static constexpr int SA = (NP * PLANE_B + 2 * NP * PLANE_A) <= 200 * 1024 ? 2 : 1;   // A stages
-    static constexpr int TMEM_COLS = 2 * KR;    // two accumulators
-    static constexpr size_t SMEM = (size_t)NP * PLANE_B + (size_t)SA * NP * PLANE_A + 6144;
+    // A stages: two whole tiles when they fit next to B; else (k = 6, three
+    // terms) two halves of one tile, split along K (the GEMM's column bit
+    // k - 1), each accumulated in its own TMEM accumulator, so that one half
+    // is converted while the other's MMAs run
+    static constexpr bool WHOLE2 = (NP * PLANE_B + 2 * NP * PLANE_A) <= 200 * 1024;
+    static constexpr int KH = WHOLE2 ? 1 : 2;             // K parts per tile
+    static constexpr int NS = 2;                          // A stages (of a tile or of a half)
+    static constexpr int SPLANE = PLANE_A / KH;           // one term plane of a stage
+    static constexpr int TMEM_COLS = 2 * KH * KR;         // two accumulator sets of KH parts
+    static constexpr size_t SMEM = (size_t)NP * PLANE_B + (size_t)NS * NP * SPLANE + 6144;
     // EW epilogue warps (one or two per quarter of the accumulator lanes,
     // reading all or half of the columns), 8 producer warps, 1 MMA warp. With
     // 13 warps (EW = 4) every sub-partition of the SM holds at most four, so
@@ -338,7 +345,7 @@ __device__ __forceinline__ void row_factors(const float2* tab, int nd, int da, i
 template <int KT, int NP>
 __global__ void __launch_bounds__(TcCfg<KT, NP>::THREADS, 1) dense_tc_kernel(const DenseArgs a) {
     using Cfg = TcCfg<KT, NP>;
-    constexpr int TE = Cfg::TE, KR = Cfg::KR, SA = Cfg::SA;
+    constexpr int TE = Cfg::TE, KR = Cfg::KR, KH = Cfg::KH, NS = Cfg::NS;
     constexpr int PCOLS = TE / 2;   // columns of one producer thread
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     // (rounded up to 1024 bytes by pointer arithmetic on the shared array, so
@@ -347,13 +354,13 @@ __global__ void __launch_bounds__(TcCfg<KT, NP>::THREADS, 1) dense_tc_kernel(con
     // ones)
     unsigned char* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
     unsigned char* sB = smem;                                   // NP planes of B
-    unsigned char* sA = smem + NP * Cfg::PLANE_B;               // SA stages x NP planes of A
-    uint64_t* bars = reinterpret_cast<uint64_t*>(sA + SA * NP * Cfg::PLANE_A);
-    uint64_t* a_full = bars;            // [SA] producers -> MMA (256 arrivals)
-    uint64_t* a_empty = bars + SA;      // [SA] MMA commit -> producers
-    uint64_t* acc_full = bars + 2 * SA; // [2] MMA commit -> epilogue
-    uint64_t* acc_empty = bars + 2 * SA + 2;   // [2] epilogue (32 EW arrivals) -> MMA
-    int* misc = reinterpret_cast<int*>(bars + 2 * SA + 5);
+    unsigned char* sA = smem + NP * Cfg::PLANE_B;               // NS stages x NP planes of A
+    uint64_t* bars = reinterpret_cast<uint64_t*>(sA + NS * NP * Cfg::SPLANE);
+    uint64_t* a_full = bars;            // [NS] producers -> MMA (256 arrivals)
+    uint64_t* a_empty = bars + NS;      // [NS] MMA commit -> producers
+    uint64_t* acc_full = bars + 2 * NS; // [2] MMA commit -> epilogue
+    uint64_t* acc_empty = bars + 2 * NS + 2;   // [2] epilogue (32 EW arrivals) -> MMA
+    int* misc = reinterpret_cast<int*>(bars + 2 * NS + 5);
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(misc);     // written by tcgen05.alloc
     volatile int* abort_flag = misc + 1;                         // a bounded wait ran out
     PassTables* T = reinterpret_cast<PassTables*>(misc + 4);
@@ -369,7 +376,7 @@ __global__ void __launch_bounds__(TcCfg<KT, NP>::THREADS, 1) dense_tc_kernel(con
 
     fill_pass_tables(a, T, tid, Cfg::THREADS);
     if (tid == 0) {
-        for (int s = 0; s < SA; ++s) {
+        for (int s = 0; s < NS; ++s) {
             mbar_init(&a_full[s], 256);
             mbar_init(&a_empty[s], 1);
         }
@@ -402,7 +409,6 @@ __global__ void __launch_bounds__(TcCfg<KT, NP>::THREADS, 1) dense_tc_kernel(con
         uint64_t cur = ~0ull;                  // tensor whose operator is in the B planes
         for (uint64_t t = t_begin; t < t_end; ++t) {
             const uint64_t it = t - t_begin;
-            const int s = (int)(it % SA);
             const uint64_t tens = t / tiles_per, o = t % tiles_per;
             const bool newt = tens != cur;
             // positions combine by XOR (the swizzle mixes the bits of the
@@ -412,14 +418,16 @@ __global__ void __launch_bounds__(TcCfg<KT, NP>::THREADS, 1) dense_tc_kernel(con
             const float2* src = a.L + tens * N;
             const int64_t pr = swz64(outer_offset(a, o), a.swz) ^ T->plo[pt & 63];
             const int sl = T->slo[pt & 63];
-            unsigned char* stage = sA + (size_t)s * NP * Cfg::PLANE_A;
             if (newt) {
                 // every MMA of the previous tile is complete before B changes;
                 // then this tensor's operator goes into the B term planes (real
                 // block form, K-major, 128-byte swizzle): per operator chunk
                 // (row t', complex columns 4g..4g+3) the 16-byte chunks g of
                 // output reals 2t' and 2t' + 1
-                if (it > 0 && !mbar_wait(&a_empty[(it - 1) % SA], (uint32_t)(((it - 1) / SA) & 1), abort_flag)) break;
+                if (it > 0) {
+                    const uint64_t ul = it * KH - 1;   // the previous tile's last A unit
+                    if (!mbar_wait(&a_empty[ul % NS], (uint32_t)((ul / NS) & 1), abort_flag)) break;
+                }
                 float2 w[BITEMS][4];   // (all loads issued before the first use)
                 const float2* op = a.ops + tens * (uint64_t)TE * TE;
 #pragma unroll
@@ -448,58 +456,86 @@ __global__ void __launch_bounds__(TcCfg<KT, NP>::THREADS, 1) dense_tc_kernel(con
                 }
                 cur = tens;
             }
-            float2 v[PCOLS];
+            // the tile in KH parts (K halves: the GEMM's top column bit is the
+            // top bit of j, so part h is j in [h PCOLS / KH, (h + 1) PCOLS / KH))
+            bool stop = false;
+#pragma unroll 1
+            for (int h = 0; h < KH && !stop; ++h) {
+                const uint64_t u = it * KH + h;   // A unit
+                const int s = (int)(u % NS);
+                unsigned char* stage = sA + (size_t)s * NP * Cfg::SPLANE;
+                constexpr int PJ = PCOLS / KH;
+                float2 v[PJ];
 #pragma unroll
-            for (int j = 0; j < PCOLS; ++j) v[j] = src[pr ^ T->phi[(pt >> 6) + 4 * j]];
-            if (it >= (uint64_t)SA && !mbar_wait(&a_empty[s], (uint32_t)(((it / SA) - 1) & 1), abort_flag)) break;
+                for (int j = 0; j < PJ; ++j) v[j] = src[pr ^ T->phi[(pt >> 6) + 4 * (h * PJ + j)]];
+                if (u >= (uint64_t)NS && !mbar_wait(&a_empty[s], (uint32_t)(((u / NS) - 1) & 1), abort_flag)) {
+                    stop = true;
+                    break;
+                }
 #pragma unroll
-            for (int j = 0; j < PCOLS; ++j) {
-                uint32_t w[NP];
-                split_pair<NP>(v[j].x, v[j].y, w);
-                const int off = sl ^ T->shi[(pt >> 6) + 4 * j];
+                for (int j = 0; j < PJ; ++j) {
+                    uint32_t w[NP];
+                    split_pair<NP>(v[j].x, v[j].y, w);
+                    // (a half-tile stage holds one 64-real K block: the block bit dropped)
+                    const int off = (sl ^ T->shi[(pt >> 6) + 4 * (h * PJ + j)]) & (Cfg::SPLANE - 1);
 #pragma unroll
-                for (int q = 0; q < NP; ++q) *reinterpret_cast<uint32_t*>(stage + q * Cfg::PLANE_A + off) = w[q];
+                    for (int q = 0; q < NP; ++q) *reinterpret_cast<uint32_t*>(stage + q * Cfg::SPLANE + off) = w[q];
+                }
+                fence_async_smem();
+                mbar_arrive(&a_full[s]);
             }
-            fence_async_smem();
-            mbar_arrive(&a_full[s]);
+            if (stop) break;
         }
     } else if (warp == Cfg::MMAW) {
         // -------------------------------------------------------------- MMA
         const uint32_t idesc = idesc_bf16(KR);
-        for (uint64_t t = t_begin; t < t_end; ++t) {
+        bool stop = false;
+        for (uint64_t t = t_begin; t < t_end && !stop; ++t) {
             const uint64_t it = t - t_begin;
-            const int s = (int)(it % SA), ab = (int)(it & 1);
-            if (!mbar_wait(&a_full[s], (uint32_t)((it / SA) & 1), abort_flag)) break;
-            if (it >= 2 && !mbar_wait(&acc_empty[ab], (uint32_t)(((it >> 1) - 1) & 1), abort_flag)) break;
-            tc_fence_after();
-            if (lane == 0) {
-                const uint32_t a0 = smem_u32(sA + (size_t)s * NP * Cfg::PLANE_A), b0 = smem_u32(sB);
-                const uint32_t d = tmem + (uint32_t)(ab * KR);
-                int first = 1;
-#pragma unroll
-                for (int pr = 0; pr < Cfg::NPROD; ++pr) {
-                    // products of total order < NP, smallest first: the last three
-                    // are those of NP = 2, the last one that of NP = 1
-                    constexpr int PA[6] = {2, 1, 0, 1, 0, 0}, PB[6] = {0, 1, 2, 0, 1, 0};
-                    constexpr int off = NP == 1 ? 5 : NP == 2 ? 3 : 0;
-                    const int pa = PA[off + pr], pb = PB[off + pr];
-#pragma unroll
-                    for (int ks = 0; ks < KR / 16; ++ks) {
-                        const uint32_t koff = (uint32_t)((ks >> 2) * 128 * 128 + (ks & 3) * 32);
-                        const uint32_t kofb = (uint32_t)((ks >> 2) * KR * 128 + (ks & 3) * 32);
-                        umma_bf16(d, smem_desc(a0 + pa * Cfg::PLANE_A + koff), smem_desc(b0 + pb * Cfg::PLANE_B + kofb),
-                                  idesc, first ? 0u : 1u);
-                        first = 0;
-                    }
+            const int ab = (int)(it & 1);
+#pragma unroll 1
+            for (int h = 0; h < KH; ++h) {
+                const uint64_t u = it * KH + h;
+                const int s = (int)(u % NS);
+                if (!mbar_wait(&a_full[s], (uint32_t)((u / NS) & 1), abort_flag)) {
+                    stop = true;
+                    break;
                 }
-                umma_commit(&a_empty[s]);
-                umma_commit(&acc_full[ab]);
+                if (h == 0 && it >= 2 && !mbar_wait(&acc_empty[ab], (uint32_t)(((it >> 1) - 1) & 1), abort_flag)) {
+                    stop = true;
+                    break;
+                }
+                tc_fence_after();
+                if (lane == 0) {
+                    const uint32_t a0 = smem_u32(sA + (size_t)s * NP * Cfg::SPLANE), b0 = smem_u32(sB);
+                    const uint32_t d = tmem + (uint32_t)((ab * KH + h) * KR);   // accumulator of part h
+                    int first = 1;
+#pragma unroll
+                    for (int pr = 0; pr < Cfg::NPROD; ++pr) {
+                        // products of total order < NP, smallest first: the last three
+                        // are those of NP = 2, the last one that of NP = 1
+                        constexpr int PA[6] = {2, 1, 0, 1, 0, 0}, PB[6] = {0, 1, 2, 0, 1, 0};
+                        constexpr int off = NP == 1 ? 5 : NP == 2 ? 3 : 0;
+                        const int pa = PA[off + pr], pb = PB[off + pr];
+#pragma unroll
+                        for (int ks = 0; ks < KR / 16 / KH; ++ks) {
+                            const int kg = h * (KR / 16 / KH) + ks;   // K step of the whole tile
+                            const uint32_t koff = (uint32_t)(((ks >> 2) * 128 * 128) + (ks & 3) * 32);
+                            const uint32_t kofb = (uint32_t)((kg >> 2) * KR * 128 + (kg & 3) * 32);
+                            umma_bf16(d, smem_desc(a0 + pa * Cfg::SPLANE + koff),
+                                      smem_desc(b0 + pb * Cfg::PLANE_B + kofb), idesc, first ? 0u : 1u);
+                            first = 0;
+                        }
+                    }
+                    umma_commit(&a_empty[s]);
+                    if (h == KH - 1) umma_commit(&acc_full[ab]);
+                }
+                __syncwarp();
             }
-            __syncwarp();
         }
         // the last commits complete before tensor memory is released
-        const uint64_t n = t_end > t_begin ? t_end - t_begin : 0;
-        if (n > 0) mbar_wait(&a_empty[(n - 1) % SA], (uint32_t)(((n - 1) / SA) & 1), abort_flag);
+        const uint64_t n = t_end > t_begin ? (t_end - t_begin) * KH : 0;
+        if (n > 0) mbar_wait(&a_empty[(n - 1) % NS], (uint32_t)(((n - 1) / NS) & 1), abort_flag);
     } else {
         // --------------------------------------------------------- epilogue
         // warp w reads accumulator lanes 32 (w % 4) .. + 31 (tile rows) and
@@ -534,6 +570,7 @@ __global__ void __launch_bounds__(TcCfg<KT, NP>::THREADS, 1) dense_tc_kernel(con
             float2* dst = a.L + tens * N;
             const int64_t pob = swz64(ob, a.swz);
             const int dob = diag_index_bits(a, ob);
+            constexpr int NCH = NREP / 4;   // 16x256b.x4 loads (32 columns) per half
 #pragma unroll
             for (int hi = 0; hi < NH; ++hi)
 #pragma unroll
@@ -543,27 +580,35 @@ __global__ void __launch_bounds__(TcCfg<KT, NP>::THREADS, 1) dense_tc_kernel(con
                     float2 f0[NREP], f1[NREP];
                     if (a.ndiag)
                         row_factors<NREP>(stab, a.ndiag, dob ^ T->drow[r0], dob ^ T->drow[r1], dcl + hi * EC, 4, f0, f1);
-                    float v[4 * NREP];
-                    tmem_ld16x256<NREP>(tmem + ((uint32_t)(32 * q + 16 * hp) << 16) +
-                                            (uint32_t)(ab * KR + (h0 + hi) * (KR / 2)),
-                                        v);
-                    if (hi == NH - 1 && hp == 1) {
-                        tc_fence_before();
-                        mbar_arrive(&acc_empty[ab]);
-                    }
-                    if (a.ndiag) {
 #pragma unroll
-                        for (int i = 0; i < NREP; ++i) {
-                            const int pc = pcl[hi * EC + 4 * i];
-                            dst[p0 ^ pc] = cmulf(make_float2(v[4 * i], v[4 * i + 1]), f0[i]);
-                            dst[p1 ^ pc] = cmulf(make_float2(v[4 * i + 2], v[4 * i + 3]), f1[i]);
+                    for (int cc = 0; cc < NCH; ++cc) {
+                        // the tile's sum: the accumulators of its KH parts
+                        const uint32_t col = (uint32_t)((h0 + hi) * (KR / 2) + cc * 32);
+                        const uint32_t lanes = (uint32_t)(32 * q + 16 * hp) << 16;
+                        float v[16];
+                        tmem_ld16x256<4>(tmem + lanes + (uint32_t)(ab * KH * KR) + col, v);
+                        if constexpr (KH == 2) {
+                            float w[16];
+                            tmem_ld16x256<4>(tmem + lanes + (uint32_t)((ab * KH + 1) * KR) + col, w);
+#pragma unroll
+                            for (int j = 0; j < 16; ++j) v[j] += w[j];
                         }
-                    } else {
+                        if (hi == NH - 1 && hp == 1 && cc == NCH - 1) {
+                            tc_fence_before();
+                            mbar_arrive(&acc_empty[ab]);
+                        }
 #pragma unroll
-                        for (int i = 0; i < NREP; ++i) {
+                        for (int ii = 0; ii < 4; ++ii) {
+                            const int i = 4 * cc + ii;
                             const int pc = pcl[hi * EC + 4 * i];
-                            dst[p0 ^ pc] = make_float2(v[4 * i], v[4 * i + 1]);
-                            dst[p1 ^ pc] = make_float2(v[4 * i + 2], v[4 * i + 3]);
+                            float2 y0 = make_float2(v[4 * ii], v[4 * ii + 1]);
+                            float2 y1 = make_float2(v[4 * ii + 2], v[4 * ii + 3]);
+                            if (a.ndiag) {
+                                y0 = cmulf(y0, f0[i]);
+                                y1 = cmulf(y1, f1[i]);
+                            }
+                            dst[p0 ^ pc] = y0;
+                            dst[p1 ^ pc] = y1;
                         }
                     }
                 }
@@ -747,12 +792,16 @@ void arrange_roles(DenseArgs& a) {
     int nc = 0, ne = 0, rows[7];
     for (int j = 0; j < 7; ++j) rows[j] = -1;
     int nr = std::max(0, xl - 2);
+    int top = -1;   // the last column bit (the GEMM's top one)
     for (int pass = 0; pass < 2; ++pass)
         for (int i = 0; i < nb; ++i) {
             if (lane[i] != (pass == 0)) continue;
-            a.e_bits[ne++] = all[i].pos;
             if (all[i].col >= 0) {
                 a.col_of[nc++] = all[i].col;
+                if (nc == a.k && pass == 1) {
+                    top = all[i].pos;
+                    continue;   // (placed last below)
+                }
             } else if (pass == 0) {
                 rows[nr++] = all[i].pos;
             } else {
@@ -760,7 +809,11 @@ void arrange_roles(DenseArgs& a) {
                 while (rows[j] >= 0) ++j;
                 rows[j] = all[i].pos;
             }
+            a.e_bits[ne++] = all[i].pos;
         }
+    // the GEMM's top column bit is the producers' top entry bit, so a K half
+    // of the tile (that bit fixed) is half of every thread's entries
+    if (top >= 0) a.e_bits[ne++] = top;
     for (int j = 0; j < 7; ++j) a.row_pos[j] = rows[j];
 }
 

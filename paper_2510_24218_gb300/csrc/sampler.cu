@@ -1309,15 +1309,30 @@ __device__ void compose_dense(const KParams& p, const Chain<float>& ch, const Gr
         for (int s2 = 0; s2 < f.nst; ++s2) {
             const DevStage& st = ch.stg[f.st_begin - br.fwd_st + s2];
             const float2* tab = ch.tab + st.tab_off;
+            // (a stage's items are disjoint: each thread loads four of them
+            // before it computes and stores any, so their latencies overlap)
             if (st.type == ST_MAT) {
                 const int a = st.arg;
                 const float2 m00 = tab[0], m01 = tab[1], m10 = tab[2], m11 = tab[3];
-                for (int w = G.lt; w < (E >> 1) * E; w += G.nt) {
-                    const int c = w & (E - 1), hr = w >> k;   // column, row pair
-                    const int r0 = ((hr >> a) << (a + 1)) | (hr & ((1 << a) - 1)), r1 = r0 | (1 << a);
-                    const float2 x0 = ob[r0 * E + c], x1 = ob[r1 * E + c];
-                    ob[r0 * E + c] = cfma(m00, x0, cmul(m01, x1));
-                    ob[r1 * E + c] = cfma(m10, x0, cmul(m11, x1));
+                for (int w0 = G.lt; w0 < (E >> 1) * E; w0 += 4 * G.nt) {
+                    int i0[4], i1[4];
+                    float2 x0[4], x1[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int w = w0 + u * G.nt;
+                        const int c = w & (E - 1), hr = (w >> k) & ((E >> 1) - 1);   // column, row pair
+                        const int r0 = ((hr >> a) << (a + 1)) | (hr & ((1 << a) - 1));
+                        i0[u] = r0 * E + c;
+                        i1[u] = (r0 | (1 << a)) * E + c;
+                        x0[u] = ob[i0[u]];
+                        x1[u] = ob[i1[u]];
+                    }
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        if (w0 + u * G.nt >= (E >> 1) * E) break;
+                        ob[i0[u]] = cfma(m00, x0[u], cmul(m01, x1[u]));
+                        ob[i1[u]] = cfma(m10, x0[u], cmul(m11, x1[u]));
+                    }
                 }
             } else if (!st.epi) {
                 int tpos[5];   // tile index of each table bit
@@ -1326,11 +1341,21 @@ __device__ void compose_dense(const KParams& p, const Chain<float>& ch, const Gr
                     for (int t = 0; t < k; ++t)
                         if (f.tbits[t] == st.dbits[j]) tpos[j] = t;
                 }
-                for (int i = G.lt; i < E * E; i += G.nt) {
-                    const int r = i >> k;
-                    int e = 0;
-                    for (int j = 0; j < st.arg; ++j) e |= ((r >> tpos[j]) & 1) << j;
-                    ob[i] = cmul(ob[i], tab[e]);
+                for (int i0 = G.lt; i0 < E * E; i0 += 4 * G.nt) {
+                    float2 x[4], d[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int i = (i0 + u * G.nt) & (E * E - 1), r = i >> k;
+                        int e = 0;
+                        for (int j = 0; j < st.arg; ++j) e |= ((r >> tpos[j]) & 1) << j;
+                        x[u] = ob[i];
+                        d[u] = tab[e];
+                    }
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        if (i0 + u * G.nt >= E * E) break;
+                        ob[i0 + u * G.nt] = cmul(x[u], d[u]);
+                    }
                 }
             } else {
                 continue;   // deferred to the epilogue: no barrier needed
