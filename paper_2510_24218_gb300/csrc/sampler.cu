@@ -1466,7 +1466,9 @@ __device__ __forceinline__ void run_chain_hbm(const KParams& p, const Chain<floa
         ch.L = static_cast<C*>(p.gL) + chain * ((uint64_t)1 << (S * P));
         const int kstop = p.mode == MODE_AMP ? p.amp_block : 0;
         const int w32 = p.tpc < 32 ? p.tpc : 32;
-        auto phase_nt = [&](int e) { return e > 1024 ? p.tpc : (e >= 256 && p.tpc >= 256) ? 128 : w32; };
+        // (phases of 256 entries and more take the whole group: at four chains
+        // per SM the group's other warps would otherwise idle)
+        auto phase_nt = [&](int e) { return e >= 256 ? (p.tpc > 128 && e <= 1024 ? 128 : p.tpc) : w32; };
         const int ntb = phase_nt(NL), ntf = dense ? p.tpc : phase_nt(N);
         const Grp GB{lt, ntb, gid, p.tpc, ntb == 32 && p.tpc > 32, false};
         const Grp GF{lt, ntf, gid, p.tpc, ntf == 32 && p.tpc > 32, false};
