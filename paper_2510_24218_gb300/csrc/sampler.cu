@@ -161,7 +161,6 @@ struct Grp {
 template <typename R> struct Chain {
     using C = typename CT<R>::T;
     C* L;         // frontier tensor, 2^W (top legs in the low S bits)
-    C* ob;        // HBM engine: the dense operator being composed (shared memory)
     C* Rt;        // right environments, K x 2^Wl
     int* Rexp;    // their power-of-two exponents
     C* rowdot;    // 2^S
@@ -1280,35 +1279,34 @@ template <typename R> __device__ __forceinline__ Chain<R> make_chain(const KPara
     ch.pd = reinterpret_cast<double2*>(g + p.sm.pd);
     ch.rL = reinterpret_cast<C**>(g + p.sm.rlp);
     ch.cmax = reinterpret_cast<float*>(g + p.sm.cmax);
-    ch.ob = ch.L;
     ch.rank = 0;
     return ch;
 }
 
 // ------------------------------------------------------------ HBM engine
-// Dense operators of the passes of block program br (HBM engine): every pass
-// is the product of its stages restricted to its tile bits, Op[t'][t] over
-// the 2^k tile settings, composed in shared memory stage by stage over all
-// the group's threads (a 2x2 stage updates 2^(k-1) row pairs of every
-// column, a diagonal one scales every entry), then written to HBM for the
-// GEMM kernels; the stages deferred to the epilogue (diagonal factors that
-// read bits outside the tile) write their tables instead.
-__device__ void compose_dense(const KParams& p, const Chain<float>& ch, const Grp& G, const DevBlockRange& br,
-                              uint64_t chain) {
+// The dense operator of pass fi of block program br (HBM engine): the
+// product of the pass's stages restricted to its tile bits, Op[t'][t] over
+// the 2^k tile settings, composed in shared memory stage by stage over the
+// group's threads (a 2x2 stage updates 2^(k-1) row pairs of every column, a
+// diagonal one scales every entry), then written to HBM for the GEMM
+// kernels; the stages deferred to the epilogue (diagonal factors that read
+// bits outside the tile) write their tables instead.
+__device__ void compose_pass(const KParams& p, float2* ob, const float2* tabs, const DevStage* stg, const Grp& G,
+                             const DevBlockRange& br, int fi, uint64_t chain) {
     const DevFused* F = P_<DevFused>(p, p.off.fused);
     const float2 one = make_float2(1.f, 0.f), zero = make_float2(0.f, 0.f);
     float2* gops = static_cast<float2*>(p.gOps);
     float2* gdiag = static_cast<float2*>(p.gDiag);
-    float2* ob = ch.ob;   // Op[r][c] at ob[r * E + c]
-    for (int fi = br.fwd_begin; fi < br.fwd_end; ++fi) {
+    // ob: Op[r][c] at ob[r * E + c]; tabs: the block's tables; stg: its stages
+    {
         const DevFused f = F[fi];
         const int k = f.ntb, E = 1 << k;
         const uint64_t slot = (uint64_t)(fi - br.fwd_begin) * p.nch + chain;
         for (int i = G.lt; i < E * E; i += G.nt) ob[i] = (i >> k) == (i & (E - 1)) ? one : zero;
         G.sync();
         for (int s2 = 0; s2 < f.nst; ++s2) {
-            const DevStage& st = ch.stg[f.st_begin - br.fwd_st + s2];
-            const float2* tab = ch.tab + st.tab_off;
+            const DevStage& st = stg[f.st_begin - br.fwd_st + s2];
+            const float2* tab = tabs + st.tab_off;
             // (a stage's items are disjoint: each thread loads four of them
             // before it computes and stores any, so their latencies overlap)
             if (st.type == ST_MAT) {
@@ -1367,9 +1365,9 @@ __device__ void compose_dense(const KParams& p, const Chain<float>& ch, const Gr
         // the epilogue's tables, in stage order, 32 entries each
         int d = 0;
         for (int s2 = 0; s2 < f.nst; ++s2) {
-            const DevStage& st = ch.stg[f.st_begin - br.fwd_st + s2];
+            const DevStage& st = stg[f.st_begin - br.fwd_st + s2];
             if (st.type != ST_DIAG || !st.epi) continue;
-            const float2* tab = ch.tab + st.tab_off;
+            const float2* tab = tabs + st.tab_off;
             for (int e = G.lt; e < 32; e += G.nt) gdiag[(slot * 4 + d) * 32 + e] = e < (1 << st.arg) ? tab[e] : zero;
             ++d;
         }
@@ -1534,8 +1532,8 @@ __device__ __forceinline__ void run_chain_hbm(const KParams& p, const Chain<floa
                     build_fslot<R>(p, ch, GF, m, br);
                     GF.sync();
                     if (dense) {
-                        // yield: the GEMM kernels run this block's passes
-                        compose_dense(p, ch, GF, br, chain);
+                        // yield: hbm_compose_kernel composes this block's operators
+                        // from the saved tables, then the GEMM kernels run its passes
                         for (int i = lt; i < p.state_bytes / 16; i += p.tpc) saved[i] = live[i];
                         G.sync();
                         return;
@@ -1602,6 +1600,26 @@ __global__ void __launch_bounds__(512, 1) pw_chain_hbm_kernel(const KParams p) {
     const Chain<float> ch = make_chain<float>(p, g);
     for (uint64_t chain = (uint64_t)blockIdx.x * p.gpc + gid; chain < p.count; chain += (uint64_t)gridDim.x * p.gpc)
         run_chain_hbm(p, ch, g, gid, lt, chain);
+}
+
+// The dense operators of one block of a dense layer for all chains of a
+// batch (HBM engine): CTA work item (chain, pass) composes the pass from the
+// plan's stages and the tables the chain kernel left in the chain's saved
+// state, in shared memory over 256 threads.
+__global__ void __launch_bounds__(256) hbm_compose_kernel(const KParams p, int m, int k, uint64_t cnt) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const DevBlockRange br = P_<DevBlockRange>(p, p.off.block_ranges)[(size_t)m * p.hdr.K + k];
+    const int npass = br.fwd_end - br.fwd_begin;
+    const DevStage* stg = P_<DevStage>(p, p.off.stages) + br.fwd_st;
+    const Grp G{(int)threadIdx.x, 256, 0, 256, false, false};
+    float2* ob = reinterpret_cast<float2*>(smem);
+    for (uint64_t w = blockIdx.x; w < cnt * (uint64_t)npass; w += gridDim.x) {
+        const uint64_t chain = w / npass;
+        const int fi = br.fwd_begin + (int)(w % npass);
+        const float2* tabs = reinterpret_cast<const float2*>(p.gState + chain * (uint64_t)p.state_bytes +
+                                                             (p.sm.tab - p.state_off));
+        compose_pass(p, ob, tabs, stg, G, br, fi, chain);
+    }
 }
 
 // ================================================================= host
@@ -1806,6 +1824,15 @@ int launch_hbm(pw_plan* plan, KParams& kp, cudaStream_t st, uint64_t* launches, 
             if (y >= 0) {
                 const int m = yields[y].first, k = yields[y].second;
                 const DevBlockRange& br = BRs[(size_t)m * K + k];
+                {
+                    // the block's operators, from the tables the chain kernel saved
+                    const uint64_t items = cnt * (uint64_t)(br.fwd_end - br.fwd_begin);
+                    const unsigned cgrid = (unsigned)std::min<uint64_t>(items, (uint64_t)nsm * 6);
+                    const size_t csm = sizeof(float2) << (2 * std::max(hp.dense_k, 1));
+                    hbm_compose_kernel<<<cgrid, 256, csm, st>>>(kp, m, k, cnt);
+                    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "compose launch");
+                    if (launches) ++*launches;
+                }
                 for (int fi = br.fwd_begin; fi < br.fwd_end; ++fi) {
                     const DevFused& f = hp.fused[fi];
                     const int pi = fi - br.fwd_begin;

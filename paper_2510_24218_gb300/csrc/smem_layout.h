@@ -25,12 +25,11 @@ inline SmemLayout make_layout(const HostPlan& hp, size_t csz) {
         return (int)at;
     };
     const int S = h.S, P = std::max(h.P, 1), K = std::max(h.K, 1);
-    // the HBM engine keeps the frontier and the environments in HBM; its L
-    // region holds the dense operator of one pass while it is composed, and
-    // everything after it is the chain state saved between launches
+    // the HBM engine keeps the frontier and the environments in HBM (the
+    // dense operators are composed by their own kernel); everything after
+    // its L region is the chain state saved between launches
     const bool hbm = hp.engine == 1;
-    L.L = take(hbm ? csz << (2 * std::max(hp.dense_k, 1))
-                   : hp.ctas_per_chain > 1 ? csz << hp.wloc : csz << (S * P));   // frontier tensor (this CTA's part)
+    L.L = take(hbm ? 16 : hp.ctas_per_chain > 1 ? csz << hp.wloc : csz << (S * P));   // frontier tensor (this CTA's part)
     L.R = take(hbm ? 16 : (size_t)K * (csz << (S * (P - 1))));    // right environments
     L.Rexp = take(sizeof(int) * K);
     // (one layer in one CTA: every readout collapses straight from L)
