@@ -1286,92 +1286,90 @@ template <typename R> __device__ __forceinline__ Chain<R> make_chain(const KPara
 // ------------------------------------------------------------ HBM engine
 // The dense operator of pass fi of block program br (HBM engine): the
 // product of the pass's stages restricted to its tile bits, Op[t'][t] over
-// the 2^k tile settings, composed in shared memory stage by stage over the
-// group's threads (a 2x2 stage updates 2^(k-1) row pairs of every column, a
-// diagonal one scales every entry), then written to HBM for the GEMM
-// kernels; the stages deferred to the epilogue (diagonal factors that read
-// bits outside the tile) write their tables instead.
-__device__ void compose_pass(const KParams& p, float2* ob, const float2* tabs, const DevStage* stg, const Grp& G,
-                             const DevBlockRange& br, int fi, uint64_t chain) {
-    const DevFused* F = P_<DevFused>(p, p.off.fused);
+// the E = 2^KT tile settings, applied to the identity one column at a time.
+// Column c is held by 256 / E threads of one warp, R = E^2 / 256 entries each
+// (rows j R + i for thread part j): a 2x2 stage on a row bit below log2 R
+// combines a thread's own entries, one on a higher bit exchanges entries with
+// the partner thread (shuffles); a diagonal stage scales every entry. No
+// shared memory and no barriers. Then the operator goes to HBM for the GEMM
+// kernels, and the stages deferred to the epilogue (diagonal factors that
+// read bits outside the tile) write their tables instead.
+template <int LB, int R2>
+__device__ __forceinline__ void mat_local(float2 (&x)[R2], float2 m00, float2 m01, float2 m10, float2 m11) {
+#pragma unroll
+    for (int i = 0; i < R2; ++i)
+        if (!((i >> LB) & 1)) {
+            const float2 x0 = x[i], x1 = x[i | (1 << LB)];
+            x[i] = cfma(m00, x0, cmul(m01, x1));
+            x[i | (1 << LB)] = cfma(m10, x0, cmul(m11, x1));
+        }
+}
+
+template <int KT>
+__device__ __forceinline__ void compose_pass(const KParams& p, const float2* tabs, const DevStage* stg,
+                                             const DevBlockRange& br, int fi, uint64_t chain, int tid) {
+    constexpr int E = 1 << KT, TPC = 256 / E, RR = E * E / 256;   // threads per column, entries per thread
+    constexpr int LR = KT == 6 ? 4 : 2;                           // log2 RR: the thread's own row bits
+    static_assert((1 << LR) == RR, "entries per thread");
+    const DevFused f = P_<DevFused>(p, p.off.fused)[fi];
     const float2 one = make_float2(1.f, 0.f), zero = make_float2(0.f, 0.f);
-    float2* gops = static_cast<float2*>(p.gOps);
-    float2* gdiag = static_cast<float2*>(p.gDiag);
-    // ob: Op[r][c] at ob[r * E + c]; tabs: the block's tables; stg: its stages
-    {
-        const DevFused f = F[fi];
-        const int k = f.ntb, E = 1 << k;
-        const uint64_t slot = (uint64_t)(fi - br.fwd_begin) * p.nch + chain;
-        for (int i = G.lt; i < E * E; i += G.nt) ob[i] = (i >> k) == (i & (E - 1)) ? one : zero;
-        G.sync();
-        for (int s2 = 0; s2 < f.nst; ++s2) {
-            const DevStage& st = stg[f.st_begin - br.fwd_st + s2];
-            const float2* tab = tabs + st.tab_off;
-            // (a stage's items are disjoint: each thread loads four of them
-            // before it computes and stores any, so their latencies overlap)
-            if (st.type == ST_MAT) {
-                const int a = st.arg;
-                const float2 m00 = tab[0], m01 = tab[1], m10 = tab[2], m11 = tab[3];
-                for (int w0 = G.lt; w0 < (E >> 1) * E; w0 += 4 * G.nt) {
-                    int i0[4], i1[4];
-                    float2 x0[4], x1[4];
+    const int c = tid / TPC, j = tid % TPC;   // column, part (row bits LR..KT-1)
+    float2 x[RR];
 #pragma unroll
-                    for (int u = 0; u < 4; ++u) {
-                        const int w = w0 + u * G.nt;
-                        const int c = w & (E - 1), hr = (w >> k) & ((E >> 1) - 1);   // column, row pair
-                        const int r0 = ((hr >> a) << (a + 1)) | (hr & ((1 << a) - 1));
-                        i0[u] = r0 * E + c;
-                        i1[u] = (r0 | (1 << a)) * E + c;
-                        x0[u] = ob[i0[u]];
-                        x1[u] = ob[i1[u]];
-                    }
-#pragma unroll
-                    for (int u = 0; u < 4; ++u) {
-                        if (w0 + u * G.nt >= (E >> 1) * E) break;
-                        ob[i0[u]] = cfma(m00, x0[u], cmul(m01, x1[u]));
-                        ob[i1[u]] = cfma(m10, x0[u], cmul(m11, x1[u]));
-                    }
-                }
-            } else if (!st.epi) {
-                int tpos[5];   // tile index of each table bit
-                for (int j = 0; j < st.arg; ++j) {
-                    tpos[j] = 0;
-                    for (int t = 0; t < k; ++t)
-                        if (f.tbits[t] == st.dbits[j]) tpos[j] = t;
-                }
-                for (int i0 = G.lt; i0 < E * E; i0 += 4 * G.nt) {
-                    float2 x[4], d[4];
-#pragma unroll
-                    for (int u = 0; u < 4; ++u) {
-                        const int i = (i0 + u * G.nt) & (E * E - 1), r = i >> k;
-                        int e = 0;
-                        for (int j = 0; j < st.arg; ++j) e |= ((r >> tpos[j]) & 1) << j;
-                        x[u] = ob[i];
-                        d[u] = tab[e];
-                    }
-#pragma unroll
-                    for (int u = 0; u < 4; ++u) {
-                        if (i0 + u * G.nt >= E * E) break;
-                        ob[i0 + u * G.nt] = cmul(x[u], d[u]);
-                    }
+    for (int i = 0; i < RR; ++i) x[i] = (j * RR + i) == c ? one : zero;
+    for (int s2 = 0; s2 < f.nst; ++s2) {
+        const DevStage st = stg[f.st_begin - br.fwd_st + s2];
+        const float2* tab = tabs + st.tab_off;
+        if (st.type == ST_MAT) {
+            const int a = st.arg;
+            const float2 m00 = tab[0], m01 = tab[1], m10 = tab[2], m11 = tab[3];
+            if (a < LR) {
+                switch (a) {   // (a compile-time bit: the entries stay in registers)
+                    case 0: mat_local<0, RR>(x, m00, m01, m10, m11); break;
+                    case 1: mat_local<1, RR>(x, m00, m01, m10, m11); break;
+                    case 2: if constexpr (LR > 2) mat_local<2, RR>(x, m00, m01, m10, m11); break;
+                    case 3: if constexpr (LR > 3) mat_local<3, RR>(x, m00, m01, m10, m11); break;
+                    default: break;
                 }
             } else {
-                continue;   // deferred to the epilogue: no barrier needed
+                const int bit = a - LR, hi = (j >> bit) & 1;
+#pragma unroll
+                for (int i = 0; i < RR; ++i) {
+                    float2 y;
+                    y.x = __shfl_xor_sync(0xffffffffu, x[i].x, 1 << bit);
+                    y.y = __shfl_xor_sync(0xffffffffu, x[i].y, 1 << bit);
+                    x[i] = hi ? cfma(m10, y, cmul(m11, x[i])) : cfma(m00, x[i], cmul(m01, y));
+                }
             }
-            G.sync();
+        } else if (!st.epi) {
+            int tpos[5];   // tile index of each table bit
+            for (int q = 0; q < st.arg; ++q) {
+                tpos[q] = 0;
+                for (int t = 0; t < KT; ++t)
+                    if (f.tbits[t] == st.dbits[q]) tpos[q] = t;
+            }
+#pragma unroll
+            for (int i = 0; i < RR; ++i) {
+                const int r = j * RR + i;
+                int e = 0;
+                for (int q = 0; q < st.arg; ++q) e |= ((r >> tpos[q]) & 1) << q;
+                x[i] = cmul(x[i], tab[e]);
+            }
         }
-        float2* dst = gops + (slot << (2 * k));
-        for (int i = G.lt; i < E * E; i += G.nt) dst[i] = ob[i];
-        // the epilogue's tables, in stage order, 32 entries each
-        int d = 0;
-        for (int s2 = 0; s2 < f.nst; ++s2) {
-            const DevStage& st = stg[f.st_begin - br.fwd_st + s2];
-            if (st.type != ST_DIAG || !st.epi) continue;
-            const float2* tab = tabs + st.tab_off;
-            for (int e = G.lt; e < 32; e += G.nt) gdiag[(slot * 4 + d) * 32 + e] = e < (1 << st.arg) ? tab[e] : zero;
-            ++d;
-        }
-        G.sync();   // (the next pass reuses the operator buffer)
+    }
+    const uint64_t slot = (uint64_t)(fi - br.fwd_begin) * p.nch + chain;
+    float2* dst = static_cast<float2*>(p.gOps) + (slot << (2 * KT));
+#pragma unroll
+    for (int i = 0; i < RR; ++i) dst[(j * RR + i) * E + c] = x[i];
+    // the epilogue's tables, in stage order, 32 entries each
+    float2* gdiag = static_cast<float2*>(p.gDiag);
+    int d = 0;
+    for (int s2 = 0; s2 < f.nst; ++s2) {
+        const DevStage st = stg[f.st_begin - br.fwd_st + s2];
+        if (st.type != ST_DIAG || !st.epi) continue;
+        const float2* tab = tabs + st.tab_off;
+        if (tid < 32) gdiag[(slot * 4 + d) * 32 + tid] = tid < (1 << st.arg) ? tab[tid] : zero;
+        ++d;
     }
 }
 
@@ -1603,22 +1601,31 @@ __global__ void __launch_bounds__(512, 1) pw_chain_hbm_kernel(const KParams p) {
 }
 
 // The dense operators of one block of a dense layer for all chains of a
-// batch (HBM engine): CTA work item (chain, pass) composes the pass from the
-// plan's stages and the tables the chain kernel left in the chain's saved
-// state, in shared memory over 256 threads.
-__global__ void __launch_bounds__(256) hbm_compose_kernel(const KParams p, int m, int k, uint64_t cnt) {
-    extern __shared__ __align__(16) unsigned char smem[];
+// batch (HBM engine). The block's stages (the same for every chain) are
+// staged in shared memory once per CTA, a chain's tables (left by the chain
+// kernel in its saved state) once per chain, all loads issued together; then
+// each of the block's passes is composed in the registers of the CTA's 256
+// threads.
+__global__ void __launch_bounds__(256) hbm_compose_kernel(const KParams p, int m, int k, uint64_t cnt, int tab_at) {
+    extern __shared__ __align__(16) unsigned char csm[];
     const DevBlockRange br = P_<DevBlockRange>(p, p.off.block_ranges)[(size_t)m * p.hdr.K + k];
-    const int npass = br.fwd_end - br.fwd_begin;
-    const DevStage* stg = P_<DevStage>(p, p.off.stages) + br.fwd_st;
-    const Grp G{(int)threadIdx.x, 256, 0, 256, false, false};
-    float2* ob = reinterpret_cast<float2*>(smem);
-    for (uint64_t w = blockIdx.x; w < cnt * (uint64_t)npass; w += gridDim.x) {
-        const uint64_t chain = w / npass;
-        const int fi = br.fwd_begin + (int)(w % npass);
+    const DevFused* F = P_<DevFused>(p, p.off.fused);
+    DevStage* sst = reinterpret_cast<DevStage*>(csm);
+    float2* stab = reinterpret_cast<float2*>(csm + tab_at);
+    const DevStage* gst = P_<DevStage>(p, p.off.stages) + br.fwd_st;
+    for (int i = threadIdx.x; i < br.fwd_nst; i += 256) sst[i] = gst[i];
+    for (uint64_t chain = blockIdx.x; chain < cnt; chain += gridDim.x) {
         const float2* tabs = reinterpret_cast<const float2*>(p.gState + chain * (uint64_t)p.state_bytes +
                                                              (p.sm.tab - p.state_off));
-        compose_pass(p, ob, tabs, stg, G, br, fi, chain);
+        __syncthreads();   // (the previous chain's tables are no longer read)
+        for (int i = threadIdx.x; i < br.fwd_tab; i += 256) stab[i] = tabs[i];
+        __syncthreads();
+        for (int fi = br.fwd_begin; fi < br.fwd_end; ++fi) {
+            if (F[fi].ntb == 6)
+                compose_pass<6>(p, stab, sst, br, fi, chain, threadIdx.x);
+            else
+                compose_pass<5>(p, stab, sst, br, fi, chain, threadIdx.x);
+        }
     }
 }
 
@@ -1826,10 +1833,15 @@ int launch_hbm(pw_plan* plan, KParams& kp, cudaStream_t st, uint64_t* launches, 
                 const DevBlockRange& br = BRs[(size_t)m * K + k];
                 {
                     // the block's operators, from the tables the chain kernel saved
-                    const uint64_t items = cnt * (uint64_t)(br.fwd_end - br.fwd_begin);
-                    const unsigned cgrid = (unsigned)std::min<uint64_t>(items, (uint64_t)nsm * 6);
-                    const size_t csm = sizeof(float2) << (2 * std::max(hp.dense_k, 1));
-                    hbm_compose_kernel<<<cgrid, 256, csm, st>>>(kp, m, k, cnt);
+                    const unsigned cgrid = (unsigned)std::min<uint64_t>(cnt, (uint64_t)nsm * 8);
+                    const int tab_at = (int)align16(sizeof(DevStage) * (size_t)std::max(1, br.fwd_nst));
+                    const size_t csm = (size_t)tab_at + sizeof(float2) * (size_t)std::max(1, br.fwd_tab);
+                    if (csm > 227 * 1024) return set_error(PW_ERR_TOO_LARGE, "a block's tables exceed shared memory");
+                    if (csm > 48 * 1024 &&
+                        (e = cudaFuncSetAttribute(hbm_compose_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                  (int)csm)) != cudaSuccess)
+                        return cuda_fail(e, "cudaFuncSetAttribute(compose)");
+                    hbm_compose_kernel<<<cgrid, 256, csm, st>>>(kp, m, k, cnt, tab_at);
                     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "compose launch");
                     if (launches) ++*launches;
                 }
