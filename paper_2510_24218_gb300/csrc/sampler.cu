@@ -1342,17 +1342,26 @@ __device__ __forceinline__ void compose_pass(const KParams& p, const float2* tab
                 }
             }
         } else if (!st.epi) {
-            int tpos[5];   // tile index of each table bit
-            for (int q = 0; q < st.arg; ++q) {
-                tpos[q] = 0;
-                for (int t = 0; t < KT; ++t)
-                    if (f.tbits[t] == st.dbits[q]) tpos[q] = t;
+            // the table index is linear over XOR in the row's bits: weight w[t]
+            // of tile bit t (1 << q when it is the table's bit q), the
+            // thread's part j contributing its bits' weights once (all indices
+            // compile-time: no local-memory arrays)
+            int w[KT];
+#pragma unroll
+            for (int t = 0; t < KT; ++t) {
+                w[t] = 0;
+#pragma unroll
+                for (int q = 0; q < 5; ++q)
+                    if (q < st.arg && f.tbits[t] == st.dbits[q]) w[t] = 1 << q;
             }
+            int ej = 0;
+#pragma unroll
+            for (int t = LR; t < KT; ++t) ej ^= ((j >> (t - LR)) & 1) ? w[t] : 0;
 #pragma unroll
             for (int i = 0; i < RR; ++i) {
-                const int r = j * RR + i;
-                int e = 0;
-                for (int q = 0; q < st.arg; ++q) e |= ((r >> tpos[q]) & 1) << q;
+                int e = ej;
+#pragma unroll
+                for (int t = 0; t < LR; ++t) e ^= ((i >> t) & 1) ? w[t] : 0;
                 x[i] = cmul(x[i], tab[e]);
             }
         }
