@@ -321,7 +321,9 @@ __device__ void build_tables(const KParams& p, const Chain<R>& ch, const Grp& g,
         C v;
         if (st.ndep != 0xFF && clean) {   // precomputed variant
             int var = 0;
-            for (int j = 0; j < st.ndep; ++j) var |= ch.s[st.dep[j]] << j;
+#pragma unroll
+            for (int j = 0; j < 4; ++j)   // (compile-time indices: the copy stays in registers)
+                if (j < st.ndep) var |= ch.s[st.dep[j]] << j;
             const int size = st.type == ST_MAT ? 4 : (1 << st.arg);
             const size_t at = (size_t)st.var_off + (size_t)var * size + e;
             if constexpr (sizeof(R) == 4) {
@@ -337,7 +339,9 @@ __device__ void build_tables(const KParams& p, const Chain<R>& ch, const Grp& g,
                 const DevMicroOp o = ops[k];
                 if (!exact && o.recipe == RC_CONST_EDGES) continue;
                 int loc = 0;
-                for (int j = 0; j < o.nbits; ++j) loc |= ((e >> o.fpos[j]) & 1) << j;
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    if (j < o.nbits) loc |= ((e >> o.fpos[j]) & 1) << j;
                 v = cmul(v, build_entry<R>(p, ch, o, loc));
             }
         }
