@@ -206,8 +206,10 @@ void pw_plan_destroy(pw_plan* plan);
  * stream: a cudaStream_t (NULL = legacy default stream). The call is
  * asynchronous with respect to the host unless stats != NULL, in which case it
  * synchronises the stream to read the counters. The first call of a plan on a
- * device uploads its tables (synchronously); later calls with stats == NULL
- * only enqueue work on the stream and can be captured into a CUDA graph. */
+ * device uploads its tables (synchronously), and on the HBM engine allocates
+ * its buffers; later calls with stats == NULL only enqueue work on the
+ * stream. For on-chip engine plans such a call can be captured into a CUDA
+ * graph (a test replays one). */
 int pw_sample(pw_plan* plan, uint64_t seed, uint64_t first_sample, uint64_t n_samples,
               uint64_t* d_out_bits, double* d_trace, void* stream, pw_run_stats_t* stats);
 
@@ -333,7 +335,7 @@ int pw_qaoa_cost_grad(int n, int n_edges, const int* edges, const double* w, con
  * not fit (pw_plan_stats().device_bytes > 2 MiB - 256 B) are rejected with
  * PW_ERR_TOO_LARGE. No cudaMalloc, cudaFree or allocating library routine is
  * called. The first call on a device looks up the array's device address with
- * that device current; make that first call before any stream capture. Every
+ * that device current. Every
  * call reloads the plan tables and zeroes the counters in the shared array, so
  * calls that overlap on the GPU (on different streams, or from different
  * threads) race and must be serialised by the caller. The results are those of
