@@ -10,8 +10,8 @@ s = sin 2beta. Averaging each term over the phase state gives
             + 1/2 sin^2(2 beta) [prod_k cos(2 gamma (w_uk - w_vk)) - prod_k cos(2 gamma (w_uk + w_vk))]
 
 where the last products run over k not in {u, v} with w = 0 on non-edges.
-The derivation is written out in the design notes; a test checks it against
-the dense state vector before it is used as a pin at large n.
+A test checks it against the dense state vector before it is used as a pin
+at large n.
 """
 from __future__ import annotations
 

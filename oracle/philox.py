@@ -9,8 +9,8 @@ is advanced by two Weyl constants between rounds.
 
 Both samplers draw their randomness from this generator so that a given
 (seed, sample, operation) triple gives the same number on the CPU and the GPU.
-The paper does not fix a generator or a draw rule; the choice is documented as
-a reading in the design notes.
+The paper does not fix a generator or a draw rule; this one is a reading of
+the paper, the same on both sides.
 """
 from __future__ import annotations
 

@@ -14,7 +14,7 @@ single-qubit factors, turns each anti-diagonal factor M into the diagonal
 M sigma_X while flipping x[q], and appends the (frame-conjugated) diagonal
 factor. The sample is s XOR x.
 
-Readings of points the paper leaves open (all stated in the design notes):
+Readings of points the paper leaves open:
 * randomness: u = Philox4x32-10(key=seed, ctr=(sample, op_id, purpose)) mapped
   to a 53-bit double; UpdateState takes the smallest candidate y (ascending
   local index) with u * P < sum_{y' <= y} p_{y'}; the Kraus draw uses the same
