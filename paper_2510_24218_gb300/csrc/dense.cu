@@ -423,12 +423,9 @@ __global__ void __launch_bounds__(TcCfg<KT, NP>::THREADS, 1) dense_tc_kernel(con
                 // then this tensor's operator goes into the B term planes (real
                 // block form, K-major, 128-byte swizzle): per operator chunk
                 // (row t', complex columns 4g..4g+3) the 16-byte chunks g of
-                // output reals 2t' and 2t' + 1
-                if (it > 0) {
-                    const uint64_t ul = it * KH - 1;   // the previous tile's last A unit
-                    if (!mbar_wait(&a_empty[ul % NS], (uint32_t)((ul / NS) & 1), abort_flag)) break;
-                }
-                float2 w[BITEMS][4];   // (all loads issued before the first use)
+                // output reals 2t' and 2t' + 1. The operator's loads are issued
+                // first, in flight while those MMAs finish.
+                float2 w[BITEMS][4];
                 const float2* op = a.ops + tens * (uint64_t)TE * TE;
 #pragma unroll
                 for (int i = 0; i < BITEMS; ++i) {
@@ -436,6 +433,10 @@ __global__ void __launch_bounds__(TcCfg<KT, NP>::THREADS, 1) dense_tc_kernel(con
                     const float2* orow = op + T->tcol[tp] * TE;   // (GEMM columns in operator order)
 #pragma unroll
                     for (int j = 0; j < 4; ++j) w[i][j] = orow[T->tcol[4 * g + j]];
+                }
+                if (it > 0) {
+                    const uint64_t ul = it * KH - 1;   // the previous tile's last A unit
+                    if (!mbar_wait(&a_empty[ul % NS], (uint32_t)((ul / NS) & 1), abort_flag)) break;
                 }
 #pragma unroll
                 for (int i = 0; i < BITEMS; ++i) {
