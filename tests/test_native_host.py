@@ -66,6 +66,24 @@ def test_circuit_validation_errors(pw):
     pw.pw_circuit_destroy(c)
 
 
+def test_dense_pass_descriptor_validation(pw):
+    """pw_dense_apply checks its descriptor before any device work (zero
+    tensors: nothing runs): distinct tile and row bits, widths, gemm kinds."""
+    SPLIT3 = 0
+    desc = pw.make_dense_desc(14, [7, 8, 9, 10, 11, 12], [0, 1, 2, 3, 4, 5, 6])
+    pw.pw_dense_apply(SPLIT3, desc, 0, None, None)
+    with pytest.raises(pw.PwError) as e:
+        pw.pw_dense_apply(9, desc, 0, None, None)     # not a PW_GEMM_* kind
+    assert e.value.code == -1
+    with pytest.raises(pw.PwError) as e:             # width below tile_bits + 7
+        pw.pw_dense_apply(SPLIT3, pw.make_dense_desc(12, [7, 8, 9, 10, 11, 5], [0, 1, 2, 3, 4, 6, 12]), 0, None, None)
+    assert e.value.code == -1
+    bad = pw.make_dense_desc(14, [7, 8, 9, 10, 11, 12], [0, 1, 2, 3, 4, 5, 7])   # row bit 7 is a tile bit
+    with pytest.raises(pw.PwError) as e:
+        pw.pw_dense_apply(SPLIT3, bad, 0, None, None)
+    assert e.value.code == -1
+
+
 def test_unsupported_structures_are_rejected(pw):
     H = np.array([[1, 1], [1, -1]]) / np.sqrt(2)
     cnot = np.eye(4)[[0, 3, 2, 1]]
