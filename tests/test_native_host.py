@@ -116,6 +116,29 @@ def test_grid_plans_sweep_rows(pw, spec, S, K):
     pw.pw_circuit_destroy(c)
 
 
+def test_hbm_plan_of_the_64_qubit_grid(pw):
+    """The HBM engine's plan of the 8x8 noisy grid (p = 2): 2^16-entry
+    frontiers, 6-bit GEMM tiles, split-3 passes by default. Readout blocks of
+    6 sites give 11 blocks and 28 dense passes per chain, blocks of 8 give 8
+    and 35. Tiles over dead legs are skipped, so the passes' flops stay well
+    below those of full-width passes (2^16 x 2^6 complex multiply-adds each)."""
+    spec = W.grid_8x8_p2_noisy()
+    c = _circ(pw, spec)
+    auto = pw.pw_plan_build(c)
+    assert pw.pw_plan_stats(auto)["engine"] == pw.PW_ENGINE_ONCHIP   # 2^16 entries fit a cluster
+    pw.pw_plan_destroy(auto)
+    for max_block, blocks, passes in ((6, 11, 28), (8, 8, 35)):
+        plan = pw.pw_plan_build(c, max_block=max_block, engine=pw.PW_ENGINE_HBM)
+        st = pw.pw_plan_stats(plan)
+        assert st["engine"] == pw.PW_ENGINE_HBM and st["gemm"] == pw.PW_GEMM_SPLIT3
+        assert st["width_bits"] == 16 and st["dense_tile_bits"] == 6 and st["noisy"] == 1
+        assert st["n_blocks"] == blocks and st["dense_passes_per_sample"] == passes
+        full = passes * (1 << 16) * (1 << 6) * 8
+        assert 0.2 * full < st["dense_flops_per_sample"] < 0.8 * full
+        pw.pw_plan_destroy(plan)
+    pw.pw_circuit_destroy(c)
+
+
 def test_exec_order_is_a_valid_reordering(pw):
     spec = W.random_qaoa(14, 2, seed=8, with_h=True, depol2=0.01, ad_gamma=0.01)
     c = _circ(pw, spec)
